@@ -1,0 +1,30 @@
+"""FP64 CPU oracle for the Flood complex filtration (test infrastructure).
+
+This package is the independent checker of the CUDA path. It is plain, slow,
+obviously correct numpy/scipy code that follows the paper's definitions:
+
+  fps.py          farthest point sampling (§3.2, greedy k-centre), FP32 keys
+  samples.py      barycentric grid P_sigma of Lemma 1 (§4.1)
+  flood.py        f_P(sigma) = max_{p in P_sigma} min_{x in X} |p - x| (§4.1)
+  grad.py         analytic subgradient of sum_sigma gamma_sigma f(sigma), central FD
+  persistence.py  Z/2 boundary-matrix reduction, diagrams, bottleneck distance (§2)
+
+Only tests, the smoke check and the CPU-baseline leg of the benchmark may
+import it. It shares no code with the CUDA path and imports nothing from the
+product package; inputs (point clouds, simplex lists) are passed in as arrays.
+
+Parity status: every function here is pinned by `-m "not gpu"` tests against
+closed forms, invariants or brute force (see tests/test_oracle_pins.py); none
+is "parity unpinned".
+"""
+from .fps import fps, fps_key
+from .samples import compositions, interior_compositions, full_grid_count, interior_count, sample_points
+from .flood import flood_values, nearest_distance, FloodResult
+from .grad import analytic_gradient, finite_difference
+from .persistence import diagrams, bottleneck
+
+__all__ = [
+    "fps", "fps_key", "compositions", "interior_compositions", "full_grid_count",
+    "interior_count", "sample_points", "flood_values", "nearest_distance", "FloodResult",
+    "analytic_gradient", "finite_difference", "diagrams", "bottleneck",
+]
