@@ -1,0 +1,308 @@
+"""Benchmark of the Flood complex filtration hot path on one B300 (or N replicas).
+
+One step = FPS landmarks -> cell grid over X -> flood values of every simplex
+of Del(L) (interior samples, face-max), i.e. every GPU stage of the method.
+The host Delaunay of L is input and is not timed: it is computed once from
+the first FPS result and reused (FPS is bit-exact, so every step picks the
+same landmarks; the bench checks that).
+
+Prints one JSON line (rank 0). Default workload: 1,000,000-point noisy torus
+(R=1, r=0.3, uniform in angles, sigma=0.005), 2,000 FPS landmarks, m=10.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "torus-1M": dict(gen="torus_cloud", n=1_000_000, n_l=2000, m=10, seed=2),
+    "shapes-5M": dict(gen="shape_mix_cloud", n=5_000_000, n_l=10_000, m=12, seed=3),
+    "sphere-10k": dict(gen="sphere_cloud", n=10_000, n_l=128, m=6, seed=1),
+}
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
+FLOPS_PER_PAIR = 6               # one pair = 3 FMAs: |x'|^2 - 2 p'.x'
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(wl: dict, seed_offset: int = 0):
+    from paper_2509_22432_b300 import data
+    gen = getattr(data, wl["gen"])
+    return gen(wl["n"], seed=wl["seed"] + seed_offset)
+
+
+def cpu_baseline(X, wl, budget_s: float = 20.0):
+    """The oracle as it stands, on a bounded sample of the same workload.
+
+    Sample: FPS for a fixed number of iterations on all of X, the FP64 k-d
+    tree over X, and flood values (full barycentric grid, FP64) of a random
+    sample of simplices; extrapolated to one full step in simplices/s.
+    """
+    import oracle
+    from paper_2509_22432_b300 import delaunay_complex
+
+    t0 = time.perf_counter()
+    j = 24
+    idx, _ = oracle.fps(X, j, 0)
+    t_fps_iter = (time.perf_counter() - t0) / (j - 1)
+    t_fps = t_fps_iter * (wl["n_l"] - 1)
+    idx, _ = oracle.fps(X, min(wl["n_l"], 400), 0)     # landmarks for a representative complex
+    L = X[idx]
+    cx = delaunay_complex(L)
+    t1 = time.perf_counter()
+    index = oracle.flood.KDIndex(X, "kdtree")
+    t_build = time.perf_counter() - t1
+    rng = np.random.default_rng(0)
+    per_dim, sampled = [], 0
+    remaining = max(1.0, budget_s - (time.perf_counter() - t0))
+    sub = [None] * 4
+    for k in (1, 2, 3):
+        n = cx.simplices[k].shape[0]
+        sub[k] = rng.choice(n, min(n, 300), replace=False)
+    t2 = time.perf_counter()
+    res = oracle.flood_values(X, L, cx.simplices, wl["m"], index=index,
+                              subset=[np.zeros(0, np.int64)] + sub[1:])
+    t_sample = time.perf_counter() - t2
+    sampled = sum(len(s) for s in sub[1:])
+    per_simplex = t_sample / sampled
+    return {"per_simplex_s": per_simplex, "t_fps_s": t_fps, "t_build_s": t_build, "sampled": sampled,
+            "note": f"FPS {j} iterations on all {X.shape[0]} points; k-d tree build; "
+                    f"flood values of {sampled} random simplices (dims 1-3) of a {L.shape[0]}-landmark Delaunay"}
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 oracle timed on the host cores."""
+    X = make_inputs(wl)
+    res = cpu_baseline(X, wl)
+    # simplex count of the full workload's complex, estimated from the landmark count
+    n_simplices = 28.1 * wl["n_l"]
+    step_s = res["t_fps_s"] + res["t_build_s"] + res["per_simplex_s"] * n_simplices
+    v = n_simplices / step_s
+    line = {"impl": "reference", "metric": "flood simplices/s", "value": v, "unit": "simplices/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_points": wl["n"], "n_landmarks": wl["n_l"], "m": wl["m"]},
+            "cpu_baseline": {"value": v, "unit": "simplices/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": res["note"]},
+            "e2e": {"value": v, "unit": "simplices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="torus-1M", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_22432_b300 import delaunay_complex, ops
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    X = make_inputs(wl, seed_offset=rank)
+    n_l, m = wl["n_l"], wl["m"]
+    Xd = torch.from_numpy(X).to(dev)
+    idx0, key0 = ops.fps(Xd, n_l, 0)
+    L_host = X[idx0.cpu().numpy()]
+    cx = delaunay_complex(L_host)
+    dcx = ops.to_device(cx, dev)
+    grid0 = ops.build_grid(Xd, 0.0)
+    cell = 0.5 * float(np.sqrt(key0[-1].item()))           # half the FPS covering radius
+    grid0.close()
+    n_simp = sum(cx.counts[1:])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
+
+    def step():
+        idx, key = ops.fps(Xd, n_l, 0)
+        grid = ops.build_grid(Xd, cell)
+        L = Xd[idx]
+        vals, _ = ops.filtration(grid, L, dcx, m, want_src=False)
+        grid.close()
+        return idx, vals
+
+    for _ in range(args.warmup):
+        idx, vals = step()
+    assert torch.equal(idx, idx0), "FPS must be deterministic"
+    stats = ops.last_filtration_stats()
+
+    # ---- device-timed steps (inputs resident in HBM; L2 flushed between steps)
+    times, flood_ms = [], []
+    launches0 = ops.kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            flood_ms.append(sum(ops.last_filtration_stats()["flood_kernel_ms"]))
+        torch.cuda.synchronize()
+    launches = ops.kernel_launches() - launches0
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers
+    Xh = torch.from_numpy(X).pin_memory()
+    simp_h = [t.cpu().pin_memory() for t in dcx.simplices]
+    fac_h = [t.cpu().pin_memory() for t in dcx.facets]
+    h2d = Xh.numel() * 4 + sum(t.numel() * 4 for t in simp_h + fac_h)
+    d2h = n_l * 8 + sum(cx.counts) * 4
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xg = Xh.to(dev, non_blocking=True)
+        idx, key = ops.fps(Xg, n_l, 0)
+        idx_h = idx.cpu()
+        dc = ops.DeviceComplex(cx.n_vertices, [t.to(dev, non_blocking=True) for t in simp_h],
+                               [t.to(dev, non_blocking=True) for t in fac_h])
+        grid = ops.build_grid(Xg, cell)
+        vals, _ = ops.filtration(grid, Xg[idx_h.to(dev)], dc, m, want_src=False)
+        out = [v.cpu() for v in vals]
+        grid.close()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_times))
+
+    peaks, peak_kind = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    pairs = sum(stats["pairs"])
+    fk = float(np.mean(flood_ms))
+    achieved = pairs * FLOPS_PER_PAIR / (fk * 1e-3) / 1e12
+    queries = sum(stats["samples"][1:])
+    line = {
+        "metric": "flood simplices/s", "value": world * n_simp / (ms * 1e-3), "unit": "simplices/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_points": wl["n"], "n_landmarks": n_l, "m": m,
+                   "simplices_per_step": n_simp, "simplex_counts": cx.counts, "cell_size": cell,
+                   "l2": "flushed between steps (256 MB write)", "delaunay": "host, untimed, computed once",
+                   "parallelism": f"replicas x{world}"},
+        "nn_queries_per_s": world * queries / (ms * 1e-3),
+        "pairs_per_step": pairs,
+        "phase_ms": {"flood_kernels": fk},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "k_flood (all dims)", "flops_per_pair": FLOPS_PER_PAIR,
+                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+        "e2e": {"value": world * n_simp / e2e_s, "unit": "simplices/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res = cpu_baseline(X, wl)
+        step_s = res["t_fps_s"] + res["t_build_s"] + res["per_simplex_s"] * n_simp
+        line["cpu_baseline"] = {"value": n_simp / step_s, "unit": "simplices/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": res["note"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

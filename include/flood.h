@@ -1,0 +1,208 @@
+/*
+ * flood.h — C ABI of libflood, a B300 (sm_103a) implementation of the Flood
+ * complex filtration (Graf, Pellizzoni, Uray, Huber, Kwitt: "The Flood
+ * Complex — Large-Scale Persistent Homology on Millions of Points").
+ *
+ * Pipeline: farthest point sampling picks landmarks L ⊂ X (§3.2); the caller
+ * triangulates L on the host (Del(L), §4); every simplex sigma of Del(L) gets
+ *
+ *     f(sigma) = max_{p in P_sigma} min_{x in X} |p - x|            (§4.1)
+ *
+ * over the barycentric grid P_sigma of resolution m (Lemma 1), faces included
+ * (the discretised complex Flood_r(X,L,P) of §4.1 admits a simplex only once
+ * all of its faces are flooded).
+ *
+ * General conventions
+ *   - Every entry point returns a flood_status (0 = FLOOD_OK). No exception,
+ *     abort or device trap crosses the ABI; device-side validation failures
+ *     and bounded-wait timeouts come back as statuses. flood_last_error()
+ *     returns a message for the calling thread's last non-OK status.
+ *   - Pointers documented as "device" must point to memory of the current
+ *     CUDA device; "host" pointers to ordinary host memory. Buffers are owned
+ *     by the caller except the opaque flood_grid, which the library owns and
+ *     frees in flood_grid_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *     enqueued on it; entry points that must report device-side errors
+ *     synchronise that stream before returning (stated per function).
+ *   - Coordinates are float32, row-major (n, 3). Vertex ids are int32 rows of
+ *     L. Values are Euclidean distances (not squared), float32.
+ *   - Scratch device memory is taken from the stream-ordered allocator
+ *     (cudaMallocAsync) and returned before the call ends; failure gives
+ *     FLOOD_ENOMEM.
+ */
+#ifndef FLOOD_H
+#define FLOOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum flood_status {
+    FLOOD_OK = 0,
+    FLOOD_EINVAL = -1,       /* bad argument or input (non-finite point, id out of range, L ⊄ X) */
+    FLOOD_ENOMEM = -2,       /* device or host allocation failed */
+    FLOOD_ECUDA = -3,        /* a CUDA runtime call failed */
+    FLOOD_ETIMEOUT = -4,     /* a bounded device-side wait gave up */
+    FLOOD_EDEGENERATE = -5,  /* FPS ran out of distinct points */
+    FLOOD_ECAPACITY = -6,    /* request exceeds a configured capacity (serving admission) */
+    FLOOD_EINTERNAL = -7     /* an internal consistency check failed */
+} flood_status;
+
+#define FLOOD_MAX_DIM 3      /* simplices of dimension 0..3 (ambient dimension 3) */
+#define FLOOD_MAX_M 64       /* largest supported grid resolution m */
+
+/* ------------------------------------------------------------------------
+ * flood_fps — farthest point sampling (§3.2: greedy k-centre, a factor-2
+ * approximation of the optimal covering radius; used for L in §5).
+ *
+ * l_0 = X[start]; for j >= 1, every point keeps d_i = min over picked l of
+ * kappa(x_i, l), and l_j = argmax_i d_i, ties to the LOWEST index. kappa is
+ * the squared distance in IEEE binary32 with each operation rounded
+ * separately (no fused multiply-add):
+ *     dx = x.x - l.x, ...;  kappa = ((dx*dx + dy*dy) + dz*dz).
+ * This makes the picked indices bit-exact and reproducible.
+ *
+ *   X          device, (n_points, 3) float32, finite
+ *   out_idx    device, int64[n_landmarks]: picked rows of X in pick order
+ *   out_key    device, float32[n_landmarks] or NULL: d of each pick when it
+ *              was picked (out_key[0] = +inf; out_key[j] is the squared
+ *              covering radius of the first j picks)
+ * Errors: FLOOD_EINVAL (sizes, start out of range, non-finite X),
+ *         FLOOD_EDEGENERATE (fewer than n_landmarks distinct points; out_idx
+ *         holds the picks made so far), FLOOD_ETIMEOUT (grid barrier wait).
+ * Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------ */
+int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,
+              int64_t* out_idx, float* out_key, void* stream);
+
+/* ------------------------------------------------------------------------
+ * flood_build_grid — uniform cell grid over X.
+ *
+ * Replaces the paper's axis-presort and masking matrix (§4.2, App. A.1) as
+ * the spatial index from which each simplex gathers the candidate points
+ * that Lemma 2 allows it to restrict to. Points are counting-sorted by the
+ * linear id of their cell (x fastest), so every row of cells along x is one
+ * contiguous range of the sorted array.
+ *
+ *   X          device, (n_points, 3) float32, finite; not retained
+ *   cell_size  edge length h of the cubic cells; <= 0 picks a default from
+ *              the bounding box and n_points. h is enlarged if the dense
+ *              cell table would exceed 2^27 cells.
+ *   out        receives a library-owned grid (free with flood_grid_destroy)
+ * Errors: FLOOD_EINVAL, FLOOD_ENOMEM, FLOOD_ECUDA. Synchronises `stream`.
+ * ------------------------------------------------------------------------ */
+typedef struct flood_grid flood_grid;
+
+typedef struct flood_grid_info {
+    int64_t n_points;
+    int64_t n_cells;
+    int32_t dims[3];         /* cells along x, y, z */
+    float cell_size;
+    float origin[3];         /* lower corner of cell (0,0,0) */
+    float bbox_lo[3];
+    float bbox_hi[3];
+    int64_t device_bytes;    /* device memory held by the grid */
+} flood_grid_info;
+
+int flood_build_grid(const float* X, int64_t n_points, float cell_size,
+                     flood_grid** out, void* stream);
+int flood_grid_get_info(const flood_grid* grid, flood_grid_info* out);
+void flood_grid_destroy(flood_grid* grid);
+
+/* ------------------------------------------------------------------------
+ * flood_filtration — flood values of every simplex of Del(L) (§4.1).
+ *
+ * For each k-simplex (k = 1..3) the interior samples of its grid (all
+ * barycentric parts c_i >= 1, lambda_i = c_i/m; Lemma 1) are evaluated
+ * against the points of X in the simplex's cull box: the box around its
+ * samples enlarged by max_p min_i |p - v_i|, a bound on every sample's
+ * nearest distance since v_i ∈ X (the step at the heart of Lemma 2's
+ * proof). A face-max pass then sets
+ *     f(sigma) = max( sqrt(max over interior samples of the min squared
+ *                     distance), f(tau) for every facet tau of sigma ),
+ * which equals the maximum over the full grid because P_tau ⊂ P_sigma
+ * (App. A.1). Vertices get d(v, X), which is 0 because L ⊂ X is required.
+ *
+ *   grid         from flood_build_grid on X
+ *   L            device, (n_landmarks, 3) float32; every row must equal a
+ *                row of X bit for bit (L ⊂ X), else FLOOD_EINVAL
+ *   simplices[k] device int32 (n_simplices[k], k+1): ascending vertex ids
+ *                (rows of L). simplices[0] may be NULL (vertices = rows of L;
+ *                n_simplices[0] must equal n_landmarks or 0).
+ *   facets[k]    device int32 (n_simplices[k], k+1), k >= 2: column j is the
+ *                row in simplices[k-1] of the facet without vertex j.
+ *                facets[0] and facets[1] are ignored (the facets of an edge
+ *                are its vertices).
+ *   m            grid resolution, 1 <= m <= FLOOD_MAX_M (m+1 points per edge)
+ *   values[k]    device float32 (n_simplices[k]) output; NULL skips output
+ *                of that dimension (it is still computed if a higher
+ *                dimension needs it)
+ *   src[k]       device int32 (n_simplices[k], 2) output or NULL: the
+ *                attaining sample, (dim << 28 | simplex row, interior sample
+ *                rank in lexicographic order). Ties go to the lowest
+ *                (dim, row, sample). Used by flood_filtration_backward.
+ * Empty dimensions (n_simplices[k] == 0) are allowed. Results depend only on
+ * (simplex, sample, point) arithmetic, so they are bitwise reproducible.
+ * Errors: FLOOD_EINVAL (ids out of range, L ⊄ X, m), FLOOD_ENOMEM,
+ *         FLOOD_ETIMEOUT (bounded shared-memory copy waits), FLOOD_ECUDA.
+ * Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------ */
+int flood_filtration(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                     const int32_t* const simplices[4], const int32_t* const facets[4],
+                     const int64_t n_simplices[4], int32_t m,
+                     float* const values[4], int32_t* const src[4], void* stream);
+
+/* Work counters of the calling thread's last successful flood_filtration. */
+typedef struct flood_filtration_stats {
+    int64_t simplices[4];        /* simplices per dimension */
+    int64_t samples[4];          /* interior samples resolved (NN queries) per dimension */
+    int64_t pairs[4];            /* (sample, candidate point) distance evaluations per dimension */
+    int64_t work_items[4];       /* (simplex, candidate chunk) items per dimension */
+    int64_t split_simplices[4];  /* simplices whose candidates were split over several items */
+    float flood_kernel_ms[4];    /* device time of the flood kernel per dimension (CUDA events on `stream`) */
+} flood_filtration_stats;
+
+int flood_last_filtration_stats(flood_filtration_stats* out);
+
+/* ------------------------------------------------------------------------
+ * flood_filtration_backward — gradient of F = sum_sigma g_sigma f(sigma).
+ *
+ * Our derivation from the value definition of §4.1: with p* = sum_j
+ * lambda_j v_j the attaining sample (from src) and x* its nearest point of X
+ * (recomputed over the attaining simplex's cull box, ties to the lowest row
+ * of X), f = |p* - x*| and, if f > 0,
+ *     grad_X[x*]  += g (x* - p*) / f,
+ *     grad_L[v_j] += g lambda_j (p* - x*) / f;
+ * f = 0 (vertices, degenerate cases) contributes nothing.
+ *
+ *   grid, L, simplices, n_simplices, m   as passed to flood_filtration
+ *   src[k]          device int32 (n_k, 2) from flood_filtration
+ *   grad_values[k]  device float32 (n_k) upstream gradients, or NULL (zero)
+ *   grad_X          device float32 (n_points, 3), accumulated into
+ *   grad_L          device float32 (n_landmarks, 3), accumulated into
+ * Accumulation uses atomics, so the summation order (last bits) may vary.
+ * Errors: FLOOD_EINVAL, FLOOD_ENOMEM, FLOOD_ECUDA. Synchronises `stream`.
+ * ------------------------------------------------------------------------ */
+int flood_filtration_backward(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                              const int32_t* const simplices[4], const int64_t n_simplices[4],
+                              int32_t m, const int32_t* const src[4],
+                              const float* const grad_values[4],
+                              float* grad_X, float* grad_L, void* stream);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* flood_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* flood_version(void);
+
+/* Number of CUDA kernels libflood has launched in this process so far. */
+int64_t flood_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLOOD_H */

@@ -1,0 +1,94 @@
+"""ctypes loader for libflood.so: declares every C entry point of include/flood.h.
+
+The library is loaded from this package directory only (never a system
+copy). A missing library raises at first use: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libflood.so")
+
+STATUS = {
+    0: "FLOOD_OK", -1: "FLOOD_EINVAL", -2: "FLOOD_ENOMEM", -3: "FLOOD_ECUDA", -4: "FLOOD_ETIMEOUT",
+    -5: "FLOOD_EDEGENERATE", -6: "FLOOD_ECAPACITY", -7: "FLOOD_EINTERNAL",
+}
+
+
+class FloodError(RuntimeError):
+    def __init__(self, status: int, message: str, where: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.name}: {message}" if where else f"{self.name}: {message}")
+
+
+class GridInfo(C.Structure):
+    _fields_ = [
+        ("n_points", C.c_int64), ("n_cells", C.c_int64), ("dims", C.c_int32 * 3), ("cell_size", C.c_float),
+        ("origin", C.c_float * 3), ("bbox_lo", C.c_float * 3), ("bbox_hi", C.c_float * 3),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+class FiltrationStats(C.Structure):
+    _fields_ = [
+        ("simplices", C.c_int64 * 4), ("samples", C.c_int64 * 4), ("pairs", C.c_int64 * 4),
+        ("work_items", C.c_int64 * 4), ("split_simplices", C.c_int64 * 4),
+        ("flood_kernel_ms", C.c_float * 4),
+    ]
+
+
+P4 = C.c_void_p * 4
+I64x4 = C.c_int64 * 4
+
+_SIGNATURES = {
+    "flood_fps": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flood_build_grid": (C.c_int, [C.c_void_p, C.c_int64, C.c_float, C.POINTER(C.c_void_p), C.c_void_p]),
+    "flood_grid_get_info": (C.c_int, [C.c_void_p, C.POINTER(GridInfo)]),
+    "flood_grid_destroy": (None, [C.c_void_p]),
+    "flood_filtration": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, P4, I64x4, C.c_int32, P4, P4,
+                                   C.c_void_p]),
+    "flood_last_filtration_stats": (C.c_int, [C.POINTER(FiltrationStats)]),
+    "flood_filtration_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, C.c_int32, P4, P4,
+                                            C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flood_last_error": (C.c_char_p, []),
+    "flood_version": (C.c_char_p, []),
+    "flood_kernel_launches": (C.c_int64, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def exported_symbols() -> list:
+    return list(_SIGNATURES)
+
+
+def get() -> C.CDLL:
+    """Load libflood.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            if _build.needs_build():
+                _build.build()
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libflood.so not found at {LIB_PATH}; run paper_2509_22432_b300/build.py")
+            lib = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != 0:
+        msg = get().flood_last_error().decode(errors="replace")
+        raise FloodError(status, msg, where)

@@ -1,0 +1,182 @@
+// flood_filtration_backward: gradient of F = sum_sigma g_sigma f(sigma).
+//
+// Our derivation from the value definition of §4.1: f(sigma) = |p* - x*| with
+// p* = sum_j lambda_j v_j the attaining grid sample of the attaining simplex
+// tau (recorded by flood_filtration as src) and x* its nearest point of X.
+// One warp per simplex recomputes p* with the forward arithmetic, finds x*
+// among the points of the cells within u_{p*} = min_j |p* - v_j| of p* (a
+// bound on d(p*, X) because v_j ∈ X), ties to the lowest row of X, and
+// scatters
+//     grad_X[x*]  += g (x* - p*) / f,    grad_L[v_j] += g lambda_j (p* - x*) / f.
+#include <vector>
+
+#include "geometry.cuh"
+
+namespace flood {
+
+namespace {
+
+struct BwdArgs {
+    int k;
+    int64_t n;
+    const float* grad;
+    const int32_t* src;      // (n, 2)
+    const int32_t* simp[4];  // simplices of every dimension (vertex rows)
+    int64_t n_simp[4];
+    const uint8_t* comp[4];  // interior composition tables
+    int I[4];
+    float m;
+    const float* L;
+    int32_t n_L;
+    GridView g;
+    float* grad_X;
+    float* grad_L;
+    uint32_t* flags;
+};
+
+__global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
+    const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= a.n) return;
+    const float gam = a.grad[w];
+    if (gam == 0.0f) return;
+    const int32_t s0 = a.src[2 * w], sample = a.src[2 * w + 1];
+    const int dim = s0 >> 28;
+    const int64_t tau = s0 & ((1 << 28) - 1);
+    if (dim == 0) return;  // a vertex attains: f = 0, zero subgradient
+    if (dim > 3 || tau >= a.n_simp[dim] || sample < 0 || sample >= a.I[dim]) {
+        if (lane == 0) atomicOr(a.flags, FLAG_RANGE);
+        return;
+    }
+    const int32_t* ids = a.simp[dim] + tau * (dim + 1);
+    for (int j = 0; j <= dim; ++j)
+        if (ids[j] < 0 || ids[j] >= a.n_L) {
+            if (lane == 0) atomicOr(a.flags, FLAG_RANGE);
+            return;
+        }
+    Simplex S;
+    load_simplex(a.L, ids, dim, S);
+    const uint8_t* comp = a.comp[dim] + sample * (dim + 1);
+    float px, py, pz;
+    sample_offset(S, comp, dim, a.m, px, py, pz);
+    const float u = __fsqrt_ru(vertex_bound_sq(S, dim, px, py, pz));
+    const float off[3] = {px, py, pz};
+    const CellBox b = cull_box(a.g, S.v0, off, off, u);
+    const int rows = b.n[1] * b.n[2];
+    // nearest point: minimum of (d^2 bits << 32 | original row), with the
+    // offset x* - p* kept by the lane that holds it
+    unsigned long long best = ~0ull;
+    float bx = 0.0f, by = 0.0f, bz = 0.0f;
+    for (int r = 0; r < rows; ++r) {
+        int32_t rb, re;
+        box_row(a.g, b, r, rb, re);
+        for (int32_t i = rb + lane; i < re; i += 32) {
+            const float4 x = a.g.pts[i];
+            const float dx = __fsub_rn(__fsub_rn(x.x, S.v0[0]), px);
+            const float dy = __fsub_rn(__fsub_rn(x.y, S.v0[1]), py);
+            const float dz = __fsub_rn(__fsub_rn(x.z, S.v0[2]), pz);
+            const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+            const unsigned long long key = (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
+                                           static_cast<uint32_t>(__float_as_int(x.w));
+            if (key < best) {
+                best = key;
+                bx = dx;
+                by = dy;
+                bz = dz;
+            }
+        }
+    }
+    unsigned long long all = best;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = shfl_xor_u64(all, o);
+        all = y < all ? y : all;
+    }
+    if (all == ~0ull) {
+        if (lane == 0) atomicOr(a.flags, FLAG_INTERNAL);
+        return;
+    }
+    const int owner = __ffs(__ballot_sync(0xffffffffu, best == all)) - 1;
+    bx = __shfl_sync(0xffffffffu, bx, owner);
+    by = __shfl_sync(0xffffffffu, by, owner);
+    bz = __shfl_sync(0xffffffffu, bz, owner);
+    const float f = __fsqrt_rn(__uint_as_float(static_cast<uint32_t>(all >> 32)));
+    if (!(f > 0.0f)) return;
+    const float scale = gam / f;
+    const int32_t xi = static_cast<int32_t>(all & 0xffffffffu);
+    if (lane == 0) {
+        atomicAdd(&a.grad_X[3 * int64_t(xi) + 0], scale * bx);
+        atomicAdd(&a.grad_X[3 * int64_t(xi) + 1], scale * by);
+        atomicAdd(&a.grad_X[3 * int64_t(xi) + 2], scale * bz);
+    }
+    if (lane <= dim) {
+        const float lam = __fdiv_rn(static_cast<float>(comp[lane]), a.m);
+        const int32_t v = ids[lane];
+        atomicAdd(&a.grad_L[3 * v + 0], -scale * lam * bx);
+        atomicAdd(&a.grad_L[3 * v + 1], -scale * lam * by);
+        atomicAdd(&a.grad_L[3 * v + 2], -scale * lam * bz);
+    }
+}
+
+}  // namespace
+
+}  // namespace flood
+
+using namespace flood;
+
+extern "C" int flood_filtration_backward(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                                         const int32_t* const simplices[4], const int64_t n_simplices[4], int32_t m,
+                                         const int32_t* const src[4], const float* const grad_values[4],
+                                         float* grad_X, float* grad_L, void* stream_) {
+    if (!grid || !L || n_landmarks < 1 || !simplices || !n_simplices || !src || !grad_values || !grad_X ||
+        !grad_L || m < 1 || m > FLOOD_MAX_M) {
+        set_error("flood_filtration_backward: NULL argument or m out of range");
+        return FLOOD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    Scratch scr(s);
+    uint32_t* flags;
+    int rc;
+    if ((rc = scr.alloc(&flags, 1))) return rc;
+    FLOOD_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), s));
+    BwdArgs a{};
+    a.m = static_cast<float>(m);
+    a.L = L;
+    a.n_L = n_landmarks;
+    a.g = view_of(grid);
+    a.grad_X = grad_X;
+    a.grad_L = grad_L;
+    a.flags = flags;
+    std::vector<uint8_t> tables[4];
+    for (int k = 1; k <= 3; ++k) {
+        a.n_simp[k] = n_simplices[k];
+        a.simp[k] = simplices[k];
+        if (n_simplices[k] <= 0) continue;
+        if (!simplices[k]) {
+            set_error("flood_filtration_backward: simplices[%d] is NULL", k);
+            return FLOOD_EINVAL;
+        }
+        tables[k] = interior_table(m, k);
+        a.I[k] = static_cast<int>(tables[k].size() / (k + 1));
+        if (a.I[k] > 0) {
+            uint8_t* comp;
+            if ((rc = scr.alloc(&comp, tables[k].size()))) return rc;
+            FLOOD_CUDA(cudaMemcpyAsync(comp, tables[k].data(), tables[k].size(), cudaMemcpyHostToDevice, s));
+            a.comp[k] = comp;
+        }
+    }
+    for (int k = 1; k <= 3; ++k) {
+        if (n_simplices[k] <= 0 || !grad_values[k]) continue;
+        if (!src[k]) {
+            set_error("flood_filtration_backward: src[%d] is NULL", k);
+            return FLOOD_EINVAL;
+        }
+        a.k = k;
+        a.n = n_simplices[k];
+        a.grad = grad_values[k];
+        a.src = src[k];
+        k_backward<<<static_cast<unsigned>(ceil_div(a.n * 32, 256)), 256, 0, s>>>(a); note_launch();
+        FLOOD_CUDA(cudaGetLastError());
+    }
+    return finish(s, flags, "flood_filtration_backward");
+}

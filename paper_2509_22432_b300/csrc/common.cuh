@@ -1,0 +1,153 @@
+// Internal helpers shared by the libflood translation units: status plumbing,
+// device status flags, scratch allocation and inline-PTX wrappers for the
+// mbarrier / bulk-copy (TMA) instructions of sm_90+ used on sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/flood.h"
+
+namespace flood {
+
+// ---------------------------------------------------------------- device status flags
+// Kernels OR these into a device status word instead of trapping; the host
+// maps them to a flood_status after the stream has completed.
+enum : uint32_t {
+    FLAG_NONFINITE = 1u << 0,
+    FLAG_RANGE = 1u << 1,       // vertex / facet id out of range
+    FLAG_NOT_SUBSET = 1u << 2,  // a landmark is not a point of X
+    FLAG_TIMEOUT = 1u << 3,     // a bounded wait gave up
+    FLAG_DEGENERATE = 1u << 4,  // FPS ran out of distinct points
+    FLAG_INTERNAL = 1u << 5,    // internal capacity / consistency check
+};
+
+// Bound on polls of a device-side wait (mbarrier phase, grid barrier). Each
+// poll is at least a round trip to L2 or a try_wait time slice, so the bound
+// is seconds, far above any legitimate wait.
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+// ---------------------------------------------------------------- host-side status
+void set_error(const char* fmt, ...);
+int status_from_flags(uint32_t flags, const char* where);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define FLOOD_CUDA(call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return ::flood::cuda_fail(e_, #call); \
+    } while (0)
+
+// Stream-ordered scratch that is returned on scope exit.
+struct Scratch {
+    cudaStream_t stream;
+    void* ptrs[32];
+    int n = 0;
+    explicit Scratch(cudaStream_t s) : stream(s) {}
+    ~Scratch() {
+        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], stream);
+    }
+    template <class T>
+    int alloc(T** out, size_t count) {
+        *out = nullptr;
+        if (count == 0) count = 1;
+        if (n == 32) {
+            set_error("internal: too many scratch buffers");
+            return FLOOD_EINTERNAL;
+        }
+        void* p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation of %zu bytes failed: %s", count * sizeof(T),
+                      cudaGetErrorString(e));
+            return FLOOD_ENOMEM;
+        }
+        ptrs[n++] = p;
+        *out = static_cast<T*>(p);
+        return FLOOD_OK;
+    }
+};
+
+// Wait for `stream`, then turn the device status word into a flood_status.
+int finish(cudaStream_t stream, const uint32_t* d_flags, const char* where);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int device_sm_count();
+
+// Process-wide count of kernels this library has launched (reported by
+// flood_kernel_launches for launch accounting).
+void note_launch(int n = 1);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Order earlier generic-proxy accesses of shared memory before later
+// async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase. Returns false (and raises FLAG_TIMEOUT)
+// if the phase did not complete within kWaitPolls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* flags) {
+    for (uint32_t i = 0; i < kWaitPolls; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(flags, FLAG_TIMEOUT);
+    return false;
+}
+
+// 1-D bulk copy global -> shared through the TMA unit; completion is counted
+// in bytes on `bar`. dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int mask) {
+    uint32_t lo = static_cast<uint32_t>(v), hi = static_cast<uint32_t>(v >> 32);
+    lo = __shfl_xor_sync(0xffffffffu, lo, mask);
+    hi = __shfl_xor_sync(0xffffffffu, hi, mask);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+}  // namespace flood

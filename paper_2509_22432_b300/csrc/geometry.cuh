@@ -1,0 +1,161 @@
+// Device-side geometry shared by the filtration and backward kernels: the
+// cell grid view, the barycentric sample of a simplex (Lemma 1) and its cull
+// box. Every quantity here depends only on (simplex, sample) so that results
+// are identical however the work is tiled.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+struct flood_grid {
+    int64_t n_points;
+    int64_t n_cells;
+    int32_t dims[3];
+    float cell_size;
+    float inv_cell;
+    float origin[3];
+    float bbox_lo[3];
+    float bbox_hi[3];
+    float4* pts;          // points sorted by cell: (x, y, z, original row as int bits)
+    int32_t* cell_start;  // n_cells + 1 offsets into pts
+    int64_t device_bytes;
+};
+
+namespace flood {
+
+// Interior compositions of m into k+1 parts >= 1 (barycentric c_i with
+// lambda_i = c_i / m, Lemma 1), lexicographic in (c_0, ..., c_k), as bytes.
+std::vector<uint8_t> interior_table(int m, int k);
+
+struct GridView {
+    const float4* pts;
+    const int32_t* cell_start;
+    int dx, dy, dz;
+    float ox, oy, oz;
+    float inv_cell;
+};
+
+inline GridView view_of(const flood_grid* g) {
+    GridView v;
+    v.pts = g->pts;
+    v.cell_start = g->cell_start;
+    v.dx = g->dims[0];
+    v.dy = g->dims[1];
+    v.dz = g->dims[2];
+    v.ox = g->origin[0];
+    v.oy = g->origin[1];
+    v.oz = g->origin[2];
+    v.inv_cell = g->inv_cell;
+    return v;
+}
+
+// Cell coordinate of v along one axis; monotone in v and clamped to the grid,
+// so a point inside [lo, hi] always lands between the cells of lo and hi.
+__device__ __forceinline__ int cell_coord(float v, float o, float inv_cell, int dim) {
+    float t = __fmul_rn(__fsub_rn(v, o), inv_cell);
+    t = fminf(fmaxf(t, 0.0f), static_cast<float>(dim - 1));
+    return static_cast<int>(t);
+}
+
+// Vertex coordinates of a k-simplex: origin v0 and edge vectors e_j = v_j - v0.
+struct Simplex {
+    float v0[3];
+    float e[3][3];  // e[j-1] = v_j - v0, j = 1..k
+};
+
+__device__ __forceinline__ void load_simplex(const float* L, const int32_t* ids, int k, Simplex& s) {
+    const int32_t i0 = ids[0];
+    s.v0[0] = L[3 * i0 + 0];
+    s.v0[1] = L[3 * i0 + 1];
+    s.v0[2] = L[3 * i0 + 2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < k) {
+            const int32_t ij = ids[j + 1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s.e[j][c] = __fsub_rn(L[3 * ij + c], s.v0[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s.e[j][c] = 0.0f;
+        }
+    }
+}
+
+// Offset p' = p - v0 = sum_{j>=1} (c_j/m) e_j of the sample with barycentric
+// parts c (Lemma 1: lambda_j = c_j / m). `comp` holds c_0..c_k as bytes.
+__device__ __forceinline__ void sample_offset(const Simplex& s, const uint8_t* comp, int k, float m,
+                                              float& px, float& py, float& pz) {
+    px = 0.0f;
+    py = 0.0f;
+    pz = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < k) {
+            const float w = __fdiv_rn(static_cast<float>(comp[j + 1]), m);
+            px = __fmaf_rn(w, s.e[j][0], px);
+            py = __fmaf_rn(w, s.e[j][1], py);
+            pz = __fmaf_rn(w, s.e[j][2], pz);
+        }
+    }
+}
+
+// Squared distance from a sample offset to the nearest vertex of the simplex:
+// u_p^2 = min_j |p - v_j|^2, an upper bound of d(p, X)^2 because v_j ∈ X.
+__device__ __forceinline__ float vertex_bound_sq(const Simplex& s, int k, float px, float py, float pz) {
+    float u = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < k) {
+            const float dx = __fsub_rn(px, s.e[j][0]);
+            const float dy = __fsub_rn(py, s.e[j][1]);
+            const float dz = __fsub_rn(pz, s.e[j][2]);
+            u = fminf(u, __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+        }
+    }
+    return u;
+}
+
+// Cull box of a simplex, in cells: the bounding box of its samples enlarged by
+// R = max_p u_p (inflated to cover FP32 rounding). Every sample's nearest
+// point of X lies inside it.
+struct CellBox {
+    int32_t c0[3];
+    int32_t n[3];
+};
+
+__device__ __forceinline__ CellBox cull_box(const GridView& g, const float v0[3], const float lo[3],
+                                            const float hi[3], float R) {
+    const float ax = fmaxf(fabsf(v0[0]), fmaxf(fabsf(v0[1]), fabsf(v0[2])));
+    const float ext = fmaxf(fmaxf(fabsf(lo[0]), fabsf(hi[0])),
+                            fmaxf(fmaxf(fabsf(lo[1]), fabsf(hi[1])), fmaxf(fabsf(lo[2]), fabsf(hi[2]))));
+    const float pad = R * (1.0f + 1.0f / 65536.0f) + (ax + ext + R) * (1.0f / 262144.0f);
+    CellBox b;
+    const float o[3] = {g.ox, g.oy, g.oz};
+    const int d[3] = {g.dx, g.dy, g.dz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float a = __fsub_rn(__fadd_rn(v0[c], lo[c]), pad);
+        const float z = __fadd_rn(__fadd_rn(v0[c], hi[c]), pad);
+        const int i0 = cell_coord(a, o[c], g.inv_cell, d[c]);
+        const int i1 = cell_coord(z, o[c], g.inv_cell, d[c]);
+        b.c0[c] = i0;
+        b.n[c] = i1 - i0 + 1;
+    }
+    return b;
+}
+
+// Point range [begin, end) of row r of a cell box (rows run along x).
+__device__ __forceinline__ void box_row(const GridView& g, const CellBox& b, int r, int32_t& begin,
+                                        int32_t& end) {
+    const int cy = b.c0[1] + r % b.n[1];
+    const int cz = b.c0[2] + r / b.n[1];
+    const int64_t base = (static_cast<int64_t>(cz) * g.dy + cy) * g.dx + b.c0[0];
+    begin = g.cell_start[base];
+    end = g.cell_start[base + b.n[0]];
+}
+
+}  // namespace flood

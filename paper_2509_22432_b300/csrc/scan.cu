@@ -1,0 +1,107 @@
+// Exclusive prefix sum of int32 counts (device), used for the cell table and
+// for work-item offsets. Three-phase: per-block scans, a recursive scan of
+// the block totals, then a uniform add.
+#include "scan.cuh"
+
+namespace flood {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* s_warp, int32_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < (kScanThreads / 32) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[31];
+    const int32_t before = warp > 0 ? s_warp[warp - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int32_t* in, int32_t* out, int64_t n,
+                                                             int32_t* tile_sums) {
+    __shared__ int32_t s_warp[32];
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        sum += v[i];
+    }
+    int32_t total;
+    int32_t run = block_exclusive_scan(sum, s_warp, total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0 && tile_sums) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int32_t* out, int64_t n, const int32_t* tile_offsets) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * kScanTile + threadIdx.x;
+    const int32_t add = tile_offsets[blockIdx.x];
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t t = i + static_cast<int64_t>(j) * kScanThreads;
+        if (t < n) out[t] += add;
+    }
+}
+
+__global__ void k_set_total(const int32_t* in, int32_t* out, int64_t n) {
+    // out[n] = out[n-1] + in[n-1]
+    out[n] = (n > 0) ? out[n - 1] + in[n - 1] : 0;
+}
+
+int scan_rec(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch& scr) {
+    if (n <= 0) return FLOOD_OK;
+    const int64_t tiles = ceil_div(n, kScanTile);
+    if (tiles == 1) {
+        k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr); note_launch();
+        FLOOD_CUDA(cudaGetLastError());
+        return FLOOD_OK;
+    }
+    int32_t *sums = nullptr, *offs = nullptr;
+    int rc = scr.alloc(&sums, tiles);
+    if (rc) return rc;
+    rc = scr.alloc(&offs, tiles);
+    if (rc) return rc;
+    k_scan_tiles<<<static_cast<unsigned>(tiles), kScanThreads, 0, s>>>(in, out, n, sums); note_launch();
+    FLOOD_CUDA(cudaGetLastError());
+    rc = scan_rec(sums, offs, tiles, s, scr);
+    if (rc) return rc;
+    k_scan_add<<<static_cast<unsigned>(tiles), kScanThreads, 0, s>>>(out, n, offs); note_launch();
+    FLOOD_CUDA(cudaGetLastError());
+    return FLOOD_OK;
+}
+
+}  // namespace
+
+int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch& scr) {
+    int rc = scan_rec(in, out, n, s, scr);
+    if (rc) return rc;
+    k_set_total<<<1, 1, 0, s>>>(in, out, n); note_launch();
+    FLOOD_CUDA(cudaGetLastError());
+    return FLOOD_OK;
+}
+
+}  // namespace flood

@@ -1,0 +1,189 @@
+"""Torch-facing wrappers of libflood (argument marshalling only).
+
+Every step runs in the CUDA kernels of libflood.so; these functions only
+check shapes and dtypes, pass device pointers and the current CUDA stream,
+and raise FloodError on a non-OK status. Inputs must already live on a CUDA
+device; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FloodError, P4, I64x4
+
+__all__ = ["fps", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration", "filtration_backward",
+           "last_filtration_stats", "FloodFunction", "flood_values"]
+
+
+def _stream_ptr(device: torch.device) -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> C.c_void_p:
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _points(X: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(X, torch.Tensor) or not X.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if X.dtype != torch.float32 or X.dim() != 2 or X.shape[1] != 3:
+        raise ValueError(f"{name} must be float32 of shape (n, 3)")
+    return X.contiguous()
+
+
+def fps(X: torch.Tensor, n_landmarks: int, start: int = 0):
+    """Farthest point sampling (§3.2). Returns (idx int64[n], key float32[n])."""
+    X = _points(X, "X")
+    idx = torch.empty(n_landmarks, dtype=torch.int64, device=X.device)
+    key = torch.empty(n_landmarks, dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.get().flood_fps(_ptr(X), X.shape[0], int(n_landmarks), int(start), _ptr(idx), _ptr(key),
+                                  _stream_ptr(X.device))
+    _lib.check(st, "flood_fps")
+    return idx, key
+
+
+class Grid:
+    """Library-owned uniform cell grid over X (flood_build_grid)."""
+
+    def __init__(self, handle: C.c_void_p, device: torch.device):
+        self._h = handle
+        self.device = device
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if not self._h:
+            raise ValueError("grid already destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = _lib.GridInfo()
+        _lib.check(_lib.get().flood_grid_get_info(self.handle, C.byref(inf)), "flood_grid_get_info")
+        return {"n_points": inf.n_points, "n_cells": inf.n_cells, "dims": tuple(inf.dims),
+                "cell_size": inf.cell_size, "origin": tuple(inf.origin), "bbox_lo": tuple(inf.bbox_lo),
+                "bbox_hi": tuple(inf.bbox_hi), "device_bytes": inf.device_bytes}
+
+    def close(self) -> None:
+        if self._h:
+            _lib.get().flood_grid_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_grid(X: torch.Tensor, cell_size: float = 0.0) -> Grid:
+    X = _points(X, "X")
+    h = C.c_void_p(0)
+    with torch.cuda.device(X.device):
+        st = _lib.get().flood_build_grid(_ptr(X), X.shape[0], float(cell_size), C.byref(h), _stream_ptr(X.device))
+    _lib.check(st, "flood_build_grid")
+    return Grid(h, X.device)
+
+
+@dataclass
+class DeviceComplex:
+    """Simplex lists of Del(L) on the device (int32, layout of complex.SimplexLists)."""
+    n_vertices: int
+    simplices: list   # k -> (n_k, k+1) int32 CUDA tensor
+    facets: list      # k -> (n_k, k+1) int32 CUDA tensor
+
+    @property
+    def counts(self) -> list:
+        return [int(s.shape[0]) for s in self.simplices]
+
+    def arrays(self):
+        s = P4(*[C.c_void_p(t.data_ptr() if t.numel() else 0) for t in self.simplices[:4]] +
+               [C.c_void_p(0)] * (4 - len(self.simplices)))
+        f = P4(*[C.c_void_p(t.data_ptr() if t.numel() else 0) for t in self.facets[:4]] +
+               [C.c_void_p(0)] * (4 - len(self.facets)))
+        n = I64x4(*(self.counts + [0] * (4 - len(self.simplices))))
+        return s, f, n
+
+
+def to_device(cx, device) -> DeviceComplex:
+    sims = [torch.from_numpy(np.ascontiguousarray(s, dtype=np.int32)).to(device) for s in cx.simplices]
+    facs = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.int32)).to(device) for f in cx.facets]
+    return DeviceComplex(int(cx.n_vertices), sims, facs)
+
+
+def filtration(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, want_src: bool = True):
+    """Flood values of every simplex (§4.1). Returns (values[k] float32, src[k] int32 (n_k,2) or None)."""
+    L = _points(L, "L")
+    s, f, n = cx.arrays()
+    vals = [torch.empty(c, dtype=torch.float32, device=L.device) for c in cx.counts]
+    srcs = [torch.empty((c, 2), dtype=torch.int32, device=L.device) for c in cx.counts] if want_src else None
+    vp = P4(*[_ptr(v) if v.numel() else C.c_void_p(0) for v in vals] + [C.c_void_p(0)] * (4 - len(vals)))
+    sp = P4(*([_ptr(t) if t.numel() else C.c_void_p(0) for t in srcs] + [C.c_void_p(0)] * (4 - len(srcs)))
+            if want_src else [C.c_void_p(0)] * 4)
+    with torch.cuda.device(L.device):
+        st = _lib.get().flood_filtration(grid.handle, _ptr(L), L.shape[0], s, f, n, int(m), vp, sp,
+                                         _stream_ptr(L.device))
+    _lib.check(st, "flood_filtration")
+    return vals, srcs
+
+
+def last_filtration_stats() -> dict:
+    st = _lib.FiltrationStats()
+    _lib.check(_lib.get().flood_last_filtration_stats(C.byref(st)), "flood_last_filtration_stats")
+    return {k: list(getattr(st, k)) for k in ("simplices", "samples", "pairs", "work_items", "split_simplices",
+                                               "flood_kernel_ms")}
+
+
+def kernel_launches() -> int:
+    """Kernels libflood has launched in this process so far."""
+    return int(_lib.get().flood_kernel_launches())
+
+
+def filtration_backward(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, src, grads, n_points: int):
+    """(grad_X (N,3), grad_L (n_L,3)) of sum_sigma grads[k][sigma] * f(sigma)."""
+    L = _points(L, "L")
+    s, _, n = cx.arrays()
+    gX = torch.zeros((n_points, 3), dtype=torch.float32, device=L.device)
+    gL = torch.zeros_like(L)
+    srcp = P4(*[_ptr(t) if t is not None and t.numel() else C.c_void_p(0) for t in src] +
+              [C.c_void_p(0)] * (4 - len(src)))
+    gs = [None if g is None else g.to(torch.float32).contiguous() for g in grads]
+    gp = P4(*[_ptr(g) if g is not None and g.numel() else C.c_void_p(0) for g in gs] +
+            [C.c_void_p(0)] * (4 - len(gs)))
+    with torch.cuda.device(L.device):
+        st = _lib.get().flood_filtration_backward(grid.handle, _ptr(L), L.shape[0], s, n, int(m), srcp, gp,
+                                                  _ptr(gX), _ptr(gL), _stream_ptr(L.device))
+    _lib.check(st, "flood_filtration_backward")
+    return gX, gL
+
+
+class FloodFunction(torch.autograd.Function):
+    """Differentiable flood values: forward(X, L, grid, cx, m) -> values of dims 0..3 (concatenated).
+
+    X and L are independent inputs; the grid must have been built from X.
+    """
+
+    @staticmethod
+    def forward(ctx, X, L, grid, cx, m):
+        vals, srcs = filtration(grid, L, cx, m, want_src=True)
+        ctx.grid, ctx.cx, ctx.m, ctx.srcs, ctx.n_points = grid, cx, m, srcs, X.shape[0]
+        ctx.counts = cx.counts
+        ctx.save_for_backward(L)
+        return torch.cat(vals)
+
+    @staticmethod
+    def backward(ctx, g):
+        (L,) = ctx.saved_tensors
+        parts = list(torch.split(g.contiguous(), ctx.counts))
+        gX, gL = filtration_backward(ctx.grid, L, ctx.cx, ctx.m, ctx.srcs, parts, ctx.n_points)
+        return gX, gL, None, None, None
+
+
+def flood_values(X: torch.Tensor, L: torch.Tensor, grid: Grid, cx: DeviceComplex, m: int):
+    """Differentiable flood values split per dimension."""
+    out = FloodFunction.apply(X, L, grid, cx, m)
+    return list(torch.split(out, cx.counts))

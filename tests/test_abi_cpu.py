@@ -1,0 +1,74 @@
+"""CPU checks: libflood.so loads and exports every entry point of include/flood.h,
+and the host-side input preparation (complex builder, generators) is sound."""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from paper_2509_22432_b300 import complex_from_simplices, data, delaunay_complex
+from paper_2509_22432_b300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "flood.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(flood_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.get()
+    declared = _declared_functions()
+    assert len(declared) >= 9
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert name in _lib.exported_symbols(), name
+    assert lib.flood_version().decode() == "0.1.0"
+
+
+def test_library_is_the_in_tree_build():
+    lib = _lib.get()
+    assert os.path.dirname(os.path.abspath(lib._name)) == os.path.join(ROOT, "paper_2509_22432_b300")
+
+
+def test_status_codes_match_header():
+    text = open(os.path.join(ROOT, "include", "flood.h")).read()
+    for code, name in _lib.STATUS.items():
+        assert re.search(rf"{name}\s*=\s*{code}\b", text), name
+
+
+def test_delaunay_complex_is_closed_with_consistent_facets():
+    X = data.shape_mix_cloud(5000, seed=1)
+    cx = delaunay_complex(X[:200])
+    for k in range(1, 4):
+        S = cx.simplices[k]
+        assert np.all(np.diff(S, axis=1) > 0)                     # ascending ids
+        keys = [tuple(r) for r in S]
+        assert keys == sorted(keys)                               # lexicographic rows
+        for j in range(k + 1):
+            face = np.delete(S, j, axis=1)
+            assert np.array_equal(cx.simplices[k - 1][cx.facets[k][:, j]], face)
+    # Euler characteristic of a triangulated 3-ball: V - E + F - T = 1
+    n = cx.counts
+    assert n[0] - n[1] + n[2] - n[3] == 1
+
+
+def test_complex_from_simplices_handles_lower_dims():
+    cx = complex_from_simplices([np.array([[0, 1, 2]]), np.array([[2, 3]])], 4)
+    assert cx.counts == [4, 4, 1]
+    assert np.array_equal(cx.simplices[1], [[0, 1], [0, 2], [1, 2], [2, 3]])
+
+
+def test_generators_are_seeded_float32_and_shaped():
+    for f, n in ((data.sphere_cloud, 1000), (data.torus_cloud, 1000), (data.shape_mix_cloud, 2000),
+                 (data.swisscheese_cloud, 1000)):
+        a, b = f(n), f(n)
+        assert a.dtype == np.float32 and a.shape == (n, 3)
+        assert np.array_equal(a, b)
+    t = data.torus_cloud(20000, noise=0.0)
+    rho = np.sqrt(t[:, 0].astype(np.float64) ** 2 + t[:, 1] ** 2)
+    assert np.allclose((rho - 1.0) ** 2 + t[:, 2].astype(np.float64) ** 2, 0.09, atol=1e-5)
+    s = data.serving_sizes()
+    assert s.min() >= 2000 and s.max() <= 200000 and len(s) == 512

@@ -1,0 +1,293 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: FPS landmark indices bit-exact; flood values within 1e-5 x the diagonal
+of X's bounding box (the tolerance the benchmark spec fixes); integer outputs exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_22432_b300 import complex_from_simplices, data, delaunay_complex
+from paper_2509_22432_b300._lib import FloodError
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _ops():
+    from paper_2509_22432_b300 import ops
+    return ops
+
+
+def _dev():
+    return torch.device("cuda:0")
+
+
+def _diam(X):
+    X = np.asarray(X, np.float64)
+    return float(np.linalg.norm(X.max(0) - X.min(0)))
+
+
+def gpu_flood(X, L, cx, m, cell_size=0.0, want_src=True):
+    ops = _ops()
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).to(_dev())
+    grid = ops.build_grid(Xd, cell_size)
+    Ld = torch.from_numpy(np.ascontiguousarray(L)).to(_dev())
+    vals, src = ops.filtration(grid, Ld, ops.to_device(cx, _dev()), m, want_src=want_src)
+    stats = ops.last_filtration_stats()
+    out = [v.cpu().numpy() for v in vals], ([s.cpu().numpy() for s in src] if want_src else None), stats
+    grid.close()
+    return out
+
+
+def assert_close(vals, ref, X, what=""):
+    tol = TOL * _diam(X)
+    for k in range(len(vals)):
+        got = np.asarray(vals[k], np.float64)
+        assert got.shape == ref[k].shape, (what, k)
+        if got.size:
+            err = np.max(np.abs(got - ref[k]))
+            assert err <= tol, f"{what} dim {k}: max |gpu - oracle| = {err:.3e} > {tol:.3e}"
+
+
+# ----------------------------------------------------------------------------- FPS
+
+@pytest.mark.parametrize("n,n_l,start,seed", [(1, 1, 0, 0), (7, 7, 3, 1), (1000, 64, 0, 2), (4099, 300, 17, 3),
+                                               (10_000, 128, 0, 1)])
+def test_fps_bit_exact_small(n, n_l, start, seed):
+    X = data.sphere_cloud(n, seed=seed)
+    idx, key = _ops().fps(torch.from_numpy(X).to(_dev()), n_l, start)
+    ri, rk = oracle.fps(X, n_l, start)
+    assert np.array_equal(idx.cpu().numpy(), ri)
+    assert np.array_equal(key.cpu().numpy().view(np.uint32), rk.view(np.uint32))
+
+
+def test_fps_ties_and_duplicates():
+    # a lattice has many exactly equal keys; ties must go to the lowest index
+    g = np.stack(np.meshgrid(np.arange(12), np.arange(12), np.arange(12), indexing="ij"), -1).reshape(-1, 3)
+    X = np.concatenate([g, g[:100]]).astype(np.float32)          # duplicated points too
+    idx, _ = _ops().fps(torch.from_numpy(X).to(_dev()), 200, 5)
+    ri, _ = oracle.fps(X, 200, 5)
+    assert np.array_equal(idx.cpu().numpy(), ri)
+
+
+def test_fps_degenerate_and_invalid():
+    ops = _ops()
+    X = np.zeros((10, 3), np.float32)
+    X[1] = 1.0
+    with pytest.raises(FloodError) as e:
+        ops.fps(torch.from_numpy(X).to(_dev()), 3, 0)
+    assert e.value.name == "FLOOD_EDEGENERATE"
+    Y = data.sphere_cloud(100)
+    Y[5, 1] = np.nan
+    with pytest.raises(FloodError) as e:
+        ops.fps(torch.from_numpy(Y).to(_dev()), 5, 0)
+    assert e.value.name == "FLOOD_EINVAL"
+    with pytest.raises(FloodError):
+        ops.fps(torch.from_numpy(data.sphere_cloud(100)).to(_dev()), 101, 0)
+
+
+@pytest.mark.slow
+def test_fps_bit_exact_torus_1m():
+    """1M-point torus, 2000 landmarks (register-resident variant at full size)."""
+    X = data.torus_cloud()
+    idx, key = _ops().fps(torch.from_numpy(X).to(_dev()), 2000, 0)
+    ri, rk = oracle.fps(X, 2000, 0)
+    assert np.array_equal(idx.cpu().numpy(), ri)
+    assert np.array_equal(key.cpu().numpy(), rk)
+
+
+# ----------------------------------------------------------------------------- flood values
+
+def _case(X, n_l, m, method="brute"):
+    idx, _ = oracle.fps(X, n_l, 0)
+    L = X[idx]
+    cx = delaunay_complex(L)
+    ref = oracle.flood_values(X, L, cx.simplices, m, method=method)
+    return L, cx, ref
+
+
+def test_flood_sphere_10k_m6_all_simplices():
+    """Unit sphere + noise, 10,000 points, 128 FPS landmarks, m=6: every simplex vs brute force."""
+    X = data.sphere_cloud()
+    L, cx, ref = _case(X, 128, 6, method="brute")
+    vals, src, stats = gpu_flood(X, L, cx, 6)
+    assert_close(vals, ref.values, X, "sphere")
+    assert np.all(vals[0] == 0)
+    assert stats["pairs"][3] > 0
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 12, 19])
+def test_flood_resolutions(m):
+    X = data.torus_cloud(6000, seed=7)
+    L, cx, ref = _case(X, 40, m, method="kdtree")
+    vals, _, _ = gpu_flood(X, L, cx, m)
+    assert_close(vals, ref.values, X, f"m={m}")
+
+
+@pytest.mark.parametrize("m", [24, 30])
+def test_flood_many_samples_per_simplex(m):
+    """Sample counts beyond one pass of the CTA's registers (multiple sample rounds) and split items."""
+    X = data.sphere_cloud(20_000, seed=9)
+    L, cx, ref = _case(X, 24, m, method="kdtree")
+    vals, _, stats = gpu_flood(X, L, cx, m)
+    assert_close(vals, ref.values, X, f"m={m}")
+    assert stats["split_simplices"][3] > 0
+
+
+@pytest.mark.parametrize("n", [4, 5, 9, 17, 63])
+def test_flood_tiny_ragged_clouds(n):
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((n, 3)).astype(np.float32)
+    n_l = min(n, 6)
+    L, cx, ref = _case(X, n_l, 4)
+    vals, _, _ = gpu_flood(X, L, cx, 4)
+    assert_close(vals, ref.values, X, f"n={n}")
+
+
+def test_flood_closed_forms_on_gpu():
+    # regular tetrahedron with X = its vertices: f = a sqrt(6)/4 exactly at 4 | m
+    V = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=np.float32)
+    cx = complex_from_simplices([np.array([[0, 1, 2, 3]])], 4)
+    vals, src, _ = gpu_flood(V, V, cx, 8)
+    a = 2 * np.sqrt(2)
+    assert abs(vals[3][0] - a * np.sqrt(6) / 4) <= 1e-6
+    assert np.allclose(vals[1], a / 2, atol=1e-6)         # edges between their two points
+    assert (src[3][0, 0] >> 28) == 3                       # attained by the tetrahedron's own interior
+
+
+def test_flood_flat_and_duplicate_points():
+    rng = np.random.default_rng(3)
+    X = np.concatenate([rng.uniform(-1, 1, (3000, 2)), np.zeros((3000, 1))], 1)
+    X[:, 2] += rng.normal(0, 1e-3, 3000)
+    X = np.concatenate([X, X[:500]]).astype(np.float32)
+    L, cx, ref = _case(X, 30, 6, method="kdtree")
+    vals, _, _ = gpu_flood(X, L, cx, 6)
+    assert_close(vals, ref.values, X, "flat")
+
+
+def test_values_bitwise_invariant_to_cell_size():
+    """Each value depends only on (simplex, sample, point) arithmetic: tiling must not change a bit."""
+    X = data.shape_mix_cloud(40_000, seed=31)
+    idx, _ = oracle.fps(X, 80, 0)
+    L = X[idx]
+    cx = delaunay_complex(L)
+    runs = [gpu_flood(X, L, cx, 8, cell_size=h, want_src=True) for h in (0.0, 0.05, 0.2, 1.0)]
+    for v, s, _ in runs[1:]:
+        for k in range(4):
+            assert np.array_equal(v[k].view(np.uint32), runs[0][0][k].view(np.uint32))
+            assert np.array_equal(s[k], runs[0][1][k])
+
+
+def test_src_points_at_attaining_sample():
+    X = data.torus_cloud(8000, seed=5)
+    m = 6
+    L, cx, ref = _case(X, 40, m, method="kdtree")
+    vals, src, _ = gpu_flood(X, L, cx, m)
+    ind = oracle.flood.KDIndex(X)
+    for k in (1, 2, 3):
+        d = src[k][:, 0] >> 28
+        rows = src[k][:, 0] & ((1 << 28) - 1)
+        ok = d >= 1
+        assert np.all(d <= k)
+        for dim in range(1, k + 1):
+            sel = np.nonzero(ok & (d == dim))[0]
+            if sel.size == 0:
+                continue
+            comps = oracle.interior_compositions(m, dim)[src[k][sel, 1]]
+            V = L[cx.simplices[dim][rows[sel]]].astype(np.float64)
+            P = np.einsum("nj,njd->nd", comps / m, V)
+            dist, _ = ind.query(P)
+            assert np.max(np.abs(dist - vals[k][sel])) <= TOL * _diam(X)
+
+
+def test_invalid_inputs_raise():
+    ops = _ops()
+    X = data.sphere_cloud(2000, seed=2)
+    idx, _ = oracle.fps(X, 20, 0)
+    L = X[idx].copy()
+    cx = delaunay_complex(L)
+    Xd = torch.from_numpy(X).to(_dev())
+    grid = ops.build_grid(Xd)
+    dcx = ops.to_device(cx, _dev())
+    Lbad = torch.from_numpy(L + np.float32(1e-3)).to(_dev())
+    with pytest.raises(FloodError) as e:
+        ops.filtration(grid, Lbad, dcx, 6)
+    assert e.value.name == "FLOOD_EINVAL"
+    bad = ops.to_device(cx, _dev())
+    bad.simplices[2][0, 1] = 10_000
+    with pytest.raises(FloodError) as e:
+        ops.filtration(grid, torch.from_numpy(L).to(_dev()), bad, 6)
+    assert e.value.name == "FLOOD_EINVAL"
+    with pytest.raises(FloodError):
+        ops.filtration(grid, torch.from_numpy(L).to(_dev()), dcx, 0)
+    Y = X.copy()
+    Y[3, 0] = np.inf
+    with pytest.raises(FloodError):
+        ops.build_grid(torch.from_numpy(Y).to(_dev()))
+    grid.close()
+
+
+def test_empty_dimensions():
+    X = data.sphere_cloud(3000, seed=4)
+    idx, _ = oracle.fps(X, 10, 0)
+    L = X[idx]
+    full = delaunay_complex(L)
+    edges_only = complex_from_simplices([full.simplices[1]], 10)
+    ref = oracle.flood_values(X, L, edges_only.simplices, 6)
+    vals, _, _ = gpu_flood(X, L, edges_only, 6)
+    assert_close(vals, ref.values, X, "edges only")
+
+
+# ----------------------------------------------------------------------------- backward
+
+def test_backward_matches_oracle_gradient():
+    ops = _ops()
+    X = data.jitter(data.torus_cloud(3000, seed=81), amp=1e-6, seed=82)
+    m = 6
+    idx, _ = oracle.fps(X, 30, 0)
+    L = X[idx].copy()
+    cx = delaunay_complex(L)
+    gamma = data.upstream_gradients(cx.counts, seed=83)
+    res = oracle.flood_values(X, L, cx.simplices, m, method="brute")
+    dX_ref, dL_ref = oracle.analytic_gradient(X, L, cx.simplices, m, gamma, result=res)
+    dev = _dev()
+    Xd = torch.from_numpy(X).to(dev).requires_grad_(True)
+    Ld = torch.from_numpy(L).to(dev).requires_grad_(True)
+    grid = ops.build_grid(Xd.detach())
+    vals = ops.flood_values(Xd, Ld, grid, ops.to_device(cx, dev), m)
+    loss = sum((v * torch.from_numpy(g).to(dev)).sum() for v, g in zip(vals, gamma))
+    loss.backward()
+    gX, gL = Xd.grad.cpu().numpy(), Ld.grad.cpu().numpy()
+    scale = max(1.0, np.abs(dX_ref).max(), np.abs(dL_ref).max())
+    assert np.max(np.abs(gX - dX_ref)) <= 1e-3 * scale
+    assert np.max(np.abs(gL - dL_ref)) <= 1e-3 * scale
+    assert np.array_equal(np.abs(gX).sum(1) > 0, np.abs(dX_ref).sum(1) > 0)
+
+
+def test_backward_matches_central_differences():
+    ops = _ops()
+    X = data.jitter(data.torus_cloud(2000, seed=91), amp=1e-6, seed=92)
+    m = 5
+    idx, _ = oracle.fps(X, 20, 0)
+    L = X[idx].copy()
+    cx = delaunay_complex(L)
+    gamma = data.upstream_gradients(cx.counts, seed=93)
+    dev = _dev()
+    Xd = torch.from_numpy(X).to(dev).requires_grad_(True)
+    Ld = torch.from_numpy(L).to(dev).requires_grad_(True)
+    grid = ops.build_grid(Xd.detach())
+    vals = ops.flood_values(Xd, Ld, grid, ops.to_device(cx, dev), m)
+    sum((v * torch.from_numpy(g).to(dev)).sum() for v, g in zip(vals, gamma)).backward()
+    gX, gL = Xd.grad.cpu().numpy(), Ld.grad.cpu().numpy()
+    rng = np.random.default_rng(0)
+    nz = np.argwhere(np.abs(gX) > 0)
+    probes = [("X", int(a), int(b)) for a, b in nz[rng.choice(len(nz), 30, replace=False)]]
+    probes += [("L", int(a), int(rng.integers(3))) for a in rng.choice(L.shape[0], 15, replace=False)]
+    fd, kink, _ = oracle.finite_difference(X, L, cx.simplices, m, gamma, probes, h=1e-4, method="brute")
+    an = np.array([gX[r, c] if w == "X" else gL[r, c] for (w, r, c) in probes])
+    ok = ~kink
+    assert ok.sum() >= 25
+    assert np.allclose(an[ok], fd[ok], rtol=1e-2, atol=1e-3)
