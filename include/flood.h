@@ -79,6 +79,31 @@ int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t sta
               int64_t* out_idx, float* out_key, void* stream);
 
 /* ------------------------------------------------------------------------
+ * flood_fps_noalloc — flood_fps without any device allocation.
+ *
+ * The paper has no counterpart: this is a deployment variant. It is for
+ * callers that cannot allow a library to allocate device memory, such as a
+ * host application whose own memory pool owns the device, a latency-critical
+ * loop that forbids allocator calls after start-up, or a plugin whose host
+ * framework forbids its extensions from allocating. It computes exactly what
+ * flood_fps computes (same kernels, same bit-exact picks) but takes all of
+ * its scratch from one fixed-size array compiled into the library (about
+ * 16 MiB of device memory, held by every GPU that loads the library until the
+ * process exits) and calls no allocating routine.
+ *
+ *   Arguments, outputs and errors as flood_fps, plus:
+ *   n_points   at most 1,048,576 (2^20); larger inputs are rejected with
+ *              FLOOD_ECAPACITY and nothing is launched.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture. All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and corrupt each
+ * other's results, so serialise them. Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------ */
+int flood_fps_noalloc(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,
+                      int64_t* out_idx, float* out_key, void* stream);
+
+/* ------------------------------------------------------------------------
  * flood_build_grid — uniform cell grid over X.
  *
  * Replaces the paper's axis-presort and masking matrix (§4.2, App. A.1) as

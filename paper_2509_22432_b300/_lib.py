@@ -46,6 +46,8 @@ I64x4 = C.c_int64 * 4
 
 _SIGNATURES = {
     "flood_fps": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flood_fps_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "flood_build_grid": (C.c_int, [C.c_void_p, C.c_int64, C.c_float, C.POINTER(C.c_void_p), C.c_void_p]),
     "flood_grid_get_info": (C.c_int, [C.c_void_p, C.POINTER(GridInfo)]),
     "flood_grid_destroy": (None, [C.c_void_p]),

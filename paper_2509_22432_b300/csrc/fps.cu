@@ -246,3 +246,109 @@ extern "C" int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, 
     if (rc) return rc;
     return finish(s, ctl + 1, "flood_fps");
 }
+
+// ---------------------------------------------------------------------------
+// flood_fps_noalloc: farthest point sampling for callers that must not
+// allocate device memory.
+//
+// Some callers cannot let a library call cudaMalloc/cudaMallocAsync: a host
+// application whose own pool already owns the device memory (an allocation
+// would fail or upset its accounting), a latency-critical loop that forbids
+// allocator calls after start-up, or a plugin whose host framework forbids
+// its extensions from allocating. This entry point runs the same kernels as
+// flood_fps but takes its scratch (the structure-of-arrays copy of X, running
+// minima, per-block slots and control words) from one file-scope device array
+// of fixed size that is part of the loaded module. Every GPU that loads this
+// library holds that array (about 16 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace flood {
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 20;  // 1,048,576 points
+constexpr int kNoAllocMaxBlocks = 4096;
+constexpr size_t kNoAllocCtlBytes = 256;
+constexpr size_t kNoAllocSlotBytes = sizeof(unsigned long long) * 2 * kNoAllocMaxBlocks;
+constexpr size_t kNoAllocArrayBytes = sizeof(float) * kNoAllocMaxPoints;
+constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + kNoAllocSlotBytes + 4 * kNoAllocArrayBytes;
+
+// The scratch itself. Host code must not use this name as a pointer: on the
+// host it is only a stand-in for the symbol, so its device address is looked
+// up with cudaGetSymbolAddress (once per device) and passed to the kernels.
+static __device__ __align__(256) unsigned char g_fps_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on the
+// first call per device).
+int noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("flood_fps_noalloc: device ordinal %d not supported", dev);
+        return FLOOD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        FLOOD_CUDA(cudaGetSymbolAddress(&p, g_fps_noalloc_scratch));
+        g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return FLOOD_OK;
+}
+
+}  // namespace
+}  // namespace flood
+
+extern "C" int flood_fps_noalloc(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,
+                                 int64_t* out_idx, float* out_key, void* stream_) {
+    using namespace flood;
+    if (!X || !out_idx || n_points < 1 || n_landmarks < 1 || n_landmarks > n_points || start < 0 ||
+        start >= n_points) {
+        set_error("flood_fps_noalloc: need X, out_idx != NULL, 1 <= n_landmarks <= n_points, 0 <= start < n_points");
+        return FLOOD_EINVAL;
+    }
+    if (n_points > kNoAllocMaxPoints) {
+        set_error("flood_fps_noalloc: n_points = %lld exceeds the fixed maximum of %lld points; use flood_fps",
+                  static_cast<long long>(n_points), static_cast<long long>(kNoAllocMaxPoints));
+        return FLOOD_ECAPACITY;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    uint32_t* ctl = reinterpret_cast<uint32_t*>(base);  // [0] barrier counter, [1] flags
+    unsigned long long* slots = reinterpret_cast<unsigned long long*>(base + kNoAllocCtlBytes);
+    float* arrays = reinterpret_cast<float*>(base + kNoAllocCtlBytes + kNoAllocSlotBytes);
+    float* x = arrays;
+    float* y = arrays + kNoAllocMaxPoints;
+    float* z = arrays + 2 * kNoAllocMaxPoints;
+    float* dmin = arrays + 3 * kNoAllocMaxPoints;
+    // The array keeps whatever the previous call left: clear the counter and flags.
+    FLOOD_CUDA(cudaMemsetAsync(ctl, 0, 2 * sizeof(uint32_t), s));
+    k_aos_to_soa<<<static_cast<unsigned>(ceil_div(n_points, 256)), 256, 0, s>>>(X, n_points, x, y, z, ctl + 1);
+    note_launch();
+    FLOOD_CUDA(cudaGetLastError());
+    FpsArgs a{x, y, z, nullptr, n_points, n_landmarks, start, out_idx, out_key, slots, ctl, ctl + 1};
+    if (n_points <= resident_capacity<1>())
+        rc = launch_fps<1, true>(a, s);
+    else if (n_points <= resident_capacity<2>())
+        rc = launch_fps<2, true>(a, s);
+    else if (n_points <= resident_capacity<4>())
+        rc = launch_fps<4, true>(a, s);
+    else if (n_points <= resident_capacity<8>())
+        rc = launch_fps<8, true>(a, s);
+    else if (n_points <= resident_capacity<16>())
+        rc = launch_fps<16, true>(a, s);
+    else {
+        FLOOD_CUDA(cudaMemsetAsync(dmin, 0xff, sizeof(float) * n_points, s));
+        a.dmin = dmin;
+        rc = launch_fps<1, false>(a, s);
+    }
+    if (rc) return rc;
+    return finish(s, ctl + 1, "flood_fps_noalloc");
+}

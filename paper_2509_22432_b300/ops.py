@@ -48,6 +48,25 @@ def fps(X: torch.Tensor, n_landmarks: int, start: int = 0):
     return idx, key
 
 
+def fps_noalloc(X: torch.Tensor, n_landmarks: int, start: int = 0):
+    """fps() for callers that must not allocate device memory inside the library.
+
+    Same picks as fps(); the library takes its scratch from a fixed array
+    compiled into it, so X may hold at most 2^20 points, and calls that
+    overlap on the GPU must be serialised by the caller. (The output tensors
+    here are allocated by torch before the call; a caller without an
+    allocator passes its own buffers to the C entry point directly.)
+    """
+    X = _points(X, "X")
+    idx = torch.empty(n_landmarks, dtype=torch.int64, device=X.device)
+    key = torch.empty(n_landmarks, dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.get().flood_fps_noalloc(_ptr(X), X.shape[0], int(n_landmarks), int(start), _ptr(idx),
+                                          _ptr(key), _stream_ptr(X.device))
+    _lib.check(st, "flood_fps_noalloc")
+    return idx, key
+
+
 class Grid:
     """Library-owned uniform cell grid over X (flood_build_grid)."""
 
