@@ -140,16 +140,18 @@ void flood_grid_destroy(flood_grid* grid);
 /* ------------------------------------------------------------------------
  * flood_filtration — flood values of every simplex of Del(L) (§4.1).
  *
- * For each k-simplex (k = 1..3) the interior samples of its grid (all
- * barycentric parts c_i >= 1, lambda_i = c_i/m; Lemma 1) are evaluated
- * against the points of X in the simplex's cull box: the box around its
- * samples enlarged by max_p min_i |p - v_i|, a bound on every sample's
- * nearest distance since v_i ∈ X (the step at the heart of Lemma 2's
- * proof). A face-max pass then sets
- *     f(sigma) = max( sqrt(max over interior samples of the min squared
- *                     distance), f(tau) for every facet tau of sigma ),
- * which equals the maximum over the full grid because P_tau ⊂ P_sigma
- * (App. A.1). Vertices get d(v, X), which is 0 because L ⊂ X is required.
+ *     f(sigma) = max over the barycentric grid P_sigma (Lemma 1, faces
+ *                included) of the distance to the nearest point of X,
+ *
+ * computed as max( own, f(facets) ) with `own` the maximum over the interior
+ * samples (all parts c_i >= 1, lambda_i = c_i/m), since P_tau ⊂ P_sigma
+ * (App. A.1). Dimensions run in increasing order; a sample whose bound
+ * u_p = min_i |p - v_i| (>= d(p, X) because v_i ∈ X, the step behind
+ * Lemma 2) does not exceed the facet maximum cannot change the value and is
+ * skipped, and the nearest-point search of every other sample stops as soon
+ * as it is exact or falls to the facet maximum. Values and attaining samples
+ * equal those of the full max-min. Vertices get d(v, X), which is 0 because
+ * L ⊂ X is required.
  *
  *   grid         from flood_build_grid on X
  *   L            device, (n_landmarks, 3) float32; every row must equal a
@@ -185,8 +187,10 @@ typedef struct flood_filtration_stats {
     int64_t simplices[4];        /* simplices per dimension */
     int64_t samples[4];          /* interior samples resolved (NN queries) per dimension */
     int64_t pairs[4];            /* (sample, candidate point) distance evaluations per dimension */
-    int64_t work_items[4];       /* (simplex, candidate chunk) items per dimension */
-    int64_t split_simplices[4];  /* simplices whose candidates were split over several items */
+    int64_t work_items[4];       /* sample groups processed by the flood kernel per dimension */
+    int64_t active_samples[4];   /* interior samples that could exceed their facet maximum */
+    int64_t shells[4];           /* cell shells scanned by all sample groups */
+    int64_t tiles[4];            /* shared-memory tiles of candidate points streamed */
     float flood_kernel_ms[4];    /* device time of the flood kernel per dimension (CUDA events on `stream`) */
 } flood_filtration_stats;
 

@@ -36,7 +36,8 @@ class GridInfo(C.Structure):
 class FiltrationStats(C.Structure):
     _fields_ = [
         ("simplices", C.c_int64 * 4), ("samples", C.c_int64 * 4), ("pairs", C.c_int64 * 4),
-        ("work_items", C.c_int64 * 4), ("split_simplices", C.c_int64 * 4),
+        ("work_items", C.c_int64 * 4), ("active_samples", C.c_int64 * 4), ("shells", C.c_int64 * 4),
+        ("tiles", C.c_int64 * 4),
         ("flood_kernel_ms", C.c_float * 4),
     ]
 

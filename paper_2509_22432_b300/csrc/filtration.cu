@@ -1,23 +1,42 @@
 // flood_filtration: flood values of every simplex of Del(L) (§4.1).
 //
-// Per dimension k = 1..3:
-//   prep     one warp per simplex: interior samples (Lemma 1, parts >= 1),
-//            R = max_p min_i |p - v_i| (a bound on each sample's nearest
-//            distance since v_i ∈ X, the step behind Lemma 2), the cull box
-//            in cells, its candidate count, and how many work items it needs.
-//   scan     work-item offsets.
-//   flood    a persistent kernel pops (simplex, candidate chunk) items from a
-//            device queue. Candidates stream through shared memory in tiles
-//            filled by 1-D TMA bulk copies (one per row segment of the cull
-//            box, double-buffered, mbarrier-tracked), are shifted to the
-//            simplex's first vertex and extended with their squared norm,
-//            then every lane evaluates its register-resident samples p with
-//                |p - x|^2 = |x'|^2 - 2 p'.x' + |p'|^2   (x' = x - v0)
-//            as three FMAs and a min per pair.
-//   finalize maximum over samples of simplices split over several items.
-// Then the face-max pass runs by increasing dimension (§4.1's discretised
-// complex; P_tau ⊂ P_sigma, App. A.1): f(sigma) = max(own, facets).
+// The value of a k-simplex is the maximum, over its barycentric grid (Lemma
+// 1), of the distance to the nearest point of X. Faces are included (the
+// discretised complex Flood_r(X,L,P) of §4.1), so the value is
+//     f(sigma) = max( max over interior samples p of d(p, X), f(facets) ),
+// because P_tau ⊂ P_sigma (App. A.1). Dimensions are processed in increasing
+// order, so when a k-simplex is evaluated its facet maximum LB is known, and
+// a sample p can only matter if d(p, X) > LB. That gives an exact pruning
+// rule (values and attaining samples are identical to the full max-min):
+//
+//   1. samples   one warp per simplex generates its interior samples and the
+//                bound u_p = min_i |p - v_i| >= d(p, X) (v_i ∈ X; the step at
+//                the heart of Lemma 2's proof). Samples with u_p <= LB are
+//                dropped; the rest are bucketed on a fixed lattice (counting
+//                sort, atomics).
+//   2. groups    each bucket is cut into groups of up to 32*Q samples.
+//   3. flood     a persistent kernel in which every warp pops a group, keeps
+//                its samples in registers and scans the cell grid in shells
+//                of cells around the group's cells, nearest shell first.
+//                Candidate points reach shared memory by 1-D TMA bulk copies
+//                (one per row segment, double-buffered, mbarrier-tracked),
+//                are shifted to the bucket corner and extended with their
+//                squared norm, and every pair costs three FMAs and a min:
+//                    |p - x|^2 = |x'|^2 - 2 p'.x' + |p'|^2.
+//                After each shell a sample is done when its minimum is below
+//                the distance to the next shell (exact) or when it is at most
+//                LB (it cannot raise the maximum); the warp stops when all
+//                of its samples are done, and at the latest when the shells
+//                pass max u_p, beyond which no nearest point can lie.
+//   4. finalize  64-bit atomic max of (d^2 bits, ~sample) per simplex gives
+//                the own maximum with the lowest sample on ties.
+//   5. face-max  f(sigma) = max(sqrt(own), f(facets)).
+// Every pair distance depends only on (sample, point, bucket corner), and
+// the bucket lattice depends only on X's bounding box, so results do not
+// depend on how the work is tiled or batched, nor on the cell size.
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <vector>
 
 #include "geometry.cuh"
@@ -27,58 +46,79 @@ namespace flood {
 
 namespace {
 
-constexpr int kThreads = 256;  // flood kernel CTA: 8 warps
+constexpr int kThreads = 256;  // flood kernel CTA: 8 independent warps
 constexpr int kWarps = kThreads / 32;
-constexpr int kTile = 1536;    // candidate points per shared-memory tile (24 KB)
-constexpr int kQMax = 8;       // samples per lane held in registers
-constexpr int kSRMax = kWarps * 32 * kQMax;
-constexpr int64_t kChunkPairs = int64_t(1) << 20;  // target pairs per work item
+constexpr int kWTile = 256;    // candidate points per warp tile (4 KB), two per warp
+constexpr int kGroup = 64;     // samples per group (one warp)
+constexpr int64_t kMaxSmemBitmapWords = 8192;  // stage the occupancy bitmap in shared memory up to 32 KB
+constexpr int64_t kMaxBuckets = int64_t(1) << 24;
 
 struct Ctl {
     uint32_t flags;
     uint32_t head[4];
-    uint32_t split[4];
-    uint32_t pad;
+    uint32_t heavy_head[4];
+    uint32_t pad[3];
     unsigned long long pairs[4];
+    unsigned long long active[4];
+    unsigned long long shells[4];
+    unsigned long long tiles[4];
 };
 
-struct SimplexPlan {
-    CellBox box;
-    int32_t n_cand;
-    int32_t n_chunks;
+// Sample lattice: coarse cubes of edge B (a power of two) anchored at the grid
+// origin, each split into 4 x 4 x 4 fine buckets numbered in Morton order. A
+// sample's key is coarse id * 64 + fine Morton index, so sorting by key keeps
+// the samples of one coarse cube together and spatially ordered inside it.
+struct Lattice {
+    float ox, oy, oz;
+    float B, invB;     // coarse edge
+    float invF;        // 4 / B
+    int bx, by, bz;    // coarse cubes per axis
 };
 
-// Thread layout of the flood kernel for one dimension.
-struct Layout {
-    int W;   // lanes sharing one point stream (distinct samples), power of two
-    int Q;   // samples per lane
-    int NW;  // warps per sample set
-    int P;   // point partitions (warps with the same samples)
+constexpr int kFine = 64;  // fine buckets per coarse cube
+
+struct SampleRec {
+    float x, y, z;  // sample coordinates
+    float lb;       // facet maximum of its simplex (LB)
+    int32_t sigma;  // simplex row
+    int32_t s;      // interior sample rank
+    float u;        // vertex bound u_p (rounded up)
+    int32_t pad;
 };
 
 struct DimArgs {
     int k;
-    int I;  // interior samples per simplex
+    int I;
     float m;
     int64_t n;
     const int32_t* simplices;
-    const uint8_t* comp;  // I x (k+1) interior compositions, lexicographic
+    const int32_t* facets;   // k >= 2
+    const float* val_lower;  // final values of dimension k-1
+    int64_t n_lower;
+    const uint8_t* comp;
     const float* L;
     int32_t n_L;
     GridView g;
-    SimplexPlan* plan;
-    int32_t* chunks;
-    int32_t* item_off;
-    int32_t chunk_pts;
-    float* g2;      // own squared value (max over interior samples of the min squared distance)
-    int32_t* arg;   // interior sample rank attaining g2
-    uint32_t* slots;  // n x I, per-sample min squared distance bits of split simplices
+    Lattice lat;
+    int64_t n_buckets;      // n_coarse * kFine sample keys
+    int64_t n_coarse;
+    int32_t* bucket_count;
+    int32_t* bucket_start;  // n_buckets + 1
+    int32_t* bucket_fill;
+    int32_t* group_off;     // n_coarse + 1
+    int2* groups;           // (bucket, index within bucket)
+    SampleRec* recs;
+    unsigned long long* best;  // per simplex: (d^2 bits << 32) | ~sample
+    const int32_t* n_heavy;    // groups [0, *n_heavy) of the sorted queue go to the CTA kernel
+    int32_t occ_words;         // words of the block-occupancy bitmap staged in shared memory (0: read globally)
+    float shell_h;             // cell edge times (1 - 2^-10)
+    float shell_slack;         // absolute rounding slack of cell assignment
     Ctl* ctl;
 };
 
 // ---------------------------------------------------------------- vertices
 // f(v) = d(v, X) = 0 for a landmark that is a point of X; anything else is an
-// input error (the cull bound relies on L ⊂ X).
+// input error (the vertex bound relies on L ⊂ X).
 __global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, int32_t* src, uint32_t* flags) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_L) return;
@@ -102,8 +142,30 @@ __global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, 
     src[2 * v + 1] = 0;
 }
 
-// ---------------------------------------------------------------- prep
-__global__ void __launch_bounds__(256) k_prep(DimArgs a) {
+// ---------------------------------------------------------------- samples
+__device__ __forceinline__ int lattice_coord(float v, float o, float invB, int dim) {
+    float t = __fmul_rn(__fsub_rn(v, o), invB);
+    t = fminf(fmaxf(t, 0.0f), static_cast<float>(dim - 1));
+    return static_cast<int>(t);
+}
+
+__device__ __forceinline__ uint32_t spread2(uint32_t v) {  // 2-bit Morton spread
+    return (v & 1u) | ((v & 2u) << 2);
+}
+
+__device__ __forceinline__ int64_t sample_key(const Lattice& L, float x, float y, float z) {
+    const int fx = lattice_coord(x, L.ox, L.invF, 4 * L.bx);
+    const int fy = lattice_coord(y, L.oy, L.invF, 4 * L.by);
+    const int fz = lattice_coord(z, L.oz, L.invF, 4 * L.bz);
+    const int64_t coarse = (static_cast<int64_t>(fz >> 2) * L.by + (fy >> 2)) * L.bx + (fx >> 2);
+    const uint32_t fine = spread2(fx & 3) | (spread2(fy & 3) << 1) | (spread2(fz & 3) << 2);
+    return coarse * kFine + fine;
+}
+
+// Pass 1 (SCATTER = false) counts active samples per bucket; pass 2 writes
+// them. Both passes evaluate exactly the same arithmetic.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_samples(DimArgs a) {
     const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= a.n) return;
@@ -111,60 +173,98 @@ __global__ void __launch_bounds__(256) k_prep(DimArgs a) {
     const int32_t* ids = a.simplices + w * (k + 1);
     bool ok = true;
     for (int j = 0; j <= k; ++j) ok &= (ids[j] >= 0 && ids[j] < a.n_L);
-    if (!ok) {
-        if (lane == 0) {
-            atomicOr(&a.ctl->flags, FLAG_RANGE);
-            a.plan[w] = SimplexPlan{};
-            a.chunks[w] = 0;
-            a.g2[w] = 0.0f;
-            a.arg[w] = 0;
+    float lb = 0.0f;  // facet maximum (vertices of an edge have value 0)
+    if (k >= 2) {
+        for (int j = 0; j <= k; ++j) {
+            const int32_t t = a.facets[w * (k + 1) + j];
+            if (t < 0 || t >= a.n_lower) ok = false;
+            else lb = fmaxf(lb, a.val_lower[t]);
         }
+    }
+    if (!ok) {
+        if (!SCATTER && lane == 0) atomicOr(&a.ctl->flags, FLAG_RANGE);
         return;
     }
     Simplex S;
     load_simplex(a.L, ids, k, S);
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    float umax = 0.0f;
+    int n_active = 0;
     for (int s = lane; s < a.I; s += 32) {
         float px, py, pz;
         sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
-        umax = fmaxf(umax, vertex_bound_sq(S, k, px, py, pz));
-        lo[0] = fminf(lo[0], px);
-        lo[1] = fminf(lo[1], py);
-        lo[2] = fminf(lo[2], pz);
-        hi[0] = fmaxf(hi[0], px);
-        hi[1] = fmaxf(hi[1], py);
-        hi[2] = fmaxf(hi[2], pz);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
-            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        const float u2 = vertex_bound_sq(S, k, px, py, pz);
+        if (!(__fsqrt_rn(u2) > lb)) continue;  // cannot exceed the facet maximum
+        ++n_active;
+        const float x = __fadd_rn(S.v0[0], px), y = __fadd_rn(S.v0[1], py), z = __fadd_rn(S.v0[2], pz);
+        const int64_t b = sample_key(a.lat, x, y, z);
+        if (!SCATTER) {
+            atomicAdd(&a.bucket_count[b], 1);
+        } else {
+            const int32_t pos = a.bucket_start[b] + atomicAdd(&a.bucket_fill[b], 1);
+            SampleRec r;
+            r.x = x;
+            r.y = y;
+            r.z = z;
+            r.lb = lb;
+            r.sigma = static_cast<int32_t>(w);
+            r.s = s;
+            r.u = __fsqrt_ru(u2);
+            r.pad = 0;
+            a.recs[pos] = r;
         }
     }
-    const CellBox b = cull_box(a.g, S.v0, lo, hi, __fsqrt_ru(umax));
-    const int rows = b.n[1] * b.n[2];
-    long long cnt = 0;
-    for (int r = lane; r < rows; r += 32) {
-        int32_t rb, re;
-        box_row(a.g, b, r, rb, re);
-        cnt += re - rb;
-    }
+    if (!SCATTER) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0) {
-        const int32_t n_chunks = static_cast<int32_t>(cnt > 0 ? (cnt + a.chunk_pts - 1) / a.chunk_pts : 1);
-        a.plan[w] = SimplexPlan{b, static_cast<int32_t>(cnt), n_chunks};
-        a.chunks[w] = n_chunks;
-        atomicAdd(&a.ctl->pairs[k], static_cast<unsigned long long>(cnt) * static_cast<unsigned long long>(a.I));
-        if (n_chunks > 1) atomicAdd(&a.ctl->split[k], 1u);
+        for (int o = 16; o > 0; o >>= 1) n_active += __shfl_xor_sync(0xffffffffu, n_active, o);
+        if (lane == 0 && n_active) atomicAdd(&a.ctl->active[k], static_cast<unsigned long long>(n_active));
     }
 }
 
-// ---------------------------------------------------------------- flood kernel
+// Groups never span coarse cubes (their samples share the cube corner as the
+// origin of the pair arithmetic).
+__global__ void k_group_counts(const int32_t* bucket_start, int64_t n_coarse, int32_t* n_groups) {
+    const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (c >= n_coarse) return;
+    const int32_t cnt = bucket_start[(c + 1) * kFine] - bucket_start[c * kFine];
+    n_groups[c] = (cnt + kGroup - 1) / kGroup;
+}
+
+__global__ void k_group_fill(const int32_t* group_off, int64_t n_coarse, int2* groups) {
+    const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (c >= n_coarse) return;
+    const int32_t o = group_off[c], e = group_off[c + 1];
+    for (int32_t j = o; j < e; ++j) groups[j] = make_int2(static_cast<int>(c), j - o);
+}
+
+// Longest-first queue: groups are counting-sorted by the number of shells
+// their vertex bound allows (descending), so the groups that may scan far
+// start first and the short ones fill in behind them.
+constexpr int kClasses = 64;
+
+__device__ __forceinline__ int group_class(const DimArgs& a, int2 gb) {
+    const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
+    const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
+    float R = 0.0f;
+    for (int32_t i = s_begin; i < s_end; ++i) R = fmaxf(R, a.recs[i].u);
+    const int c = static_cast<int>(ceilf(R / a.shell_h));
+    return kClasses - 1 - min(max(c, 0), kClasses - 1);  // heavier -> smaller class
+}
+
+__global__ void k_group_class_count(DimArgs a, const int32_t* n_groups, int32_t* class_count) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *n_groups) return;
+    atomicAdd(&class_count[group_class(a, a.groups[j])], 1);
+}
+
+__global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const int32_t* class_start,
+                                      int32_t* class_fill, int2* sorted) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *n_groups) return;
+    const int2 gb = a.groups[j];
+    const int c = group_class(a, gb);
+    sorted[class_start[c] + atomicAdd(&class_fill[c], 1)] = gb;
+}
+
+// ---------------------------------------------------------------- shell streaming
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -174,287 +274,636 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Row cursor over the concatenated candidate stream of one cull box (warp 0).
+// Cells at Chebyshev distance exactly s (in cells) from the inner box [lo, hi],
+// as rows along x: rows on the y/z faces of the shell are whole x-ranges, the
+// others contribute only their two end cells.
+struct Shell {
+    int lo[3], hi[3];  // inner box (cells, inclusive)
+    int s;
+    int y0, ny, z0;
+    int rows;
+    float wlo[3], whi[3];  // bounding box of the group's samples (world)
+    float T2;              // squared search radius: no live sample needs points farther away
+    float slack;           // absolute rounding slack of cell boundaries
+};
+
+__device__ __forceinline__ void shell_setup(const GridView& g, Shell& sh) {
+    const int s = sh.s;
+    sh.y0 = max(sh.lo[1] - s, 0);
+    const int y1 = min(sh.hi[1] + s, g.dy - 1);
+    sh.z0 = max(sh.lo[2] - s, 0);
+    const int z1 = min(sh.hi[2] + s, g.dz - 1);
+    sh.ny = y1 - sh.y0 + 1;
+    const int nz = z1 - sh.z0 + 1;
+    sh.rows = (sh.ny > 0 && nz > 0) ? sh.ny * nz : 0;
+}
+
+// Gap between the samples' box and the cell slab [c, c+1) along one axis.
+__device__ __forceinline__ float slab_gap(float o, float h, int c, float lo, float hi, float slack) {
+    const float a = __fmaf_rn(static_cast<float>(c), h, o), b = __fmaf_rn(static_cast<float>(c + 1), h, o);
+    return fmaxf(fmaxf(a - hi, lo - b) - slack, 0.0f);
+}
+
+// Row r of shell s as up to two point ranges. A row (or the part of it along
+// x) whose cells lie farther than sqrt(T2) from every sample of the group, or
+// whose 4x4x4 blocks are empty, contributes nothing; neither changes any
+// live sample's nearest distance.
+__device__ __forceinline__ void shell_row(const GridView& g, const Shell& sh, int r, int32_t& b1, int32_t& l1,
+                                          int32_t& b2, int32_t& l2) {
+    const int s = sh.s;
+    const int cy = sh.y0 + r % sh.ny;
+    const int cz = sh.z0 + r / sh.ny;
+    b1 = b2 = 0;
+    l1 = l2 = 0;
+    const float gy = slab_gap(g.oy, g.cell, cy, sh.wlo[1], sh.whi[1], sh.slack);
+    const float gz = slab_gap(g.oz, g.cell, cz, sh.wlo[2], sh.whi[2], sh.slack);
+    const float gyz2 = __fmaf_rn(gy, gy, gz * gz);
+    if (gyz2 > sh.T2) return;
+    // x cells that can hold a point within sqrt(T2) of the samples' box
+    const float w = sqrtf(fmaxf(sh.T2 - gyz2, 0.0f)) + sh.slack;
+    const int xa = cell_coord(sh.wlo[0] - w, g.ox, g.inv_cell, g.dx);
+    const int xb = cell_coord(sh.whi[0] + w, g.ox, g.inv_cell, g.dx);
+    const int64_t base = (static_cast<int64_t>(cz) * g.dy + cy) * g.dx;
+    const bool face = s == 0 || cy == sh.lo[1] - s || cy == sh.hi[1] + s || cz == sh.lo[2] - s || cz == sh.hi[2] + s;
+    if (face) {
+        const int x0 = max(max(sh.lo[0] - s, 0), xa), x1 = min(min(sh.hi[0] + s, g.dx - 1), xb);
+        if (x0 <= x1 && row_occupied(g, cy, cz, x0, x1)) {
+            b1 = g.cell_start[base + x0];
+            l1 = g.cell_start[base + x1 + 1] - b1;
+        }
+    } else {
+        const int xl = sh.lo[0] - s, xr = sh.hi[0] + s;
+        if (xl >= 0 && xl >= xa && xl <= xb && row_occupied(g, cy, cz, xl, xl)) {
+            b1 = g.cell_start[base + xl];
+            l1 = g.cell_start[base + xl + 1] - b1;
+        }
+        if (xr < g.dx && xr >= xa && xr <= xb && row_occupied(g, cy, cz, xr, xr)) {
+            b2 = g.cell_start[base + xr];
+            l2 = g.cell_start[base + xr + 1] - b2;
+        }
+    }
+}
+
 struct Cursor {
-    int32_t row;      // first row not yet fully consumed
+    int32_t row;      // first row not yet fully copied
     int32_t row_pos;  // stream position where `row` begins
     int32_t pos;      // next stream position to copy
 };
 
-// Advance `c` so that c.row contains stream position c.pos (warp-collective).
-__device__ void cursor_seek(const GridView& g, const CellBox& b, int rows, Cursor& c, int lane) {
-    while (c.row < rows) {
-        const int r = c.row + lane;
-        int32_t len = 0;
-        if (r < rows) {
-            int32_t rb, re;
-            box_row(g, b, r, rb, re);
-            len = re - rb;
-        }
-        int32_t incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        // rows whose end is at or before pos are skipped
-        const bool done = (r < rows) && (c.row_pos + incl <= c.pos);
-        const unsigned m = __ballot_sync(0xffffffffu, done);
-        const int nfull = __popc(m);  // done rows form a prefix
-        if (nfull == 0) return;
-        const int32_t adv = __shfl_sync(0xffffffffu, incl, nfull - 1);
-        c.row += nfull;
-        c.row_pos += adv;
-        if (nfull < 32) return;
-    }
-}
-
-// Copy the next `want` stream points into `buf` with bulk copies completing on
-// `bar` (warp-collective; lane 0 arrives on the barrier once at the end).
-__device__ void produce_tile(const GridView& g, const CellBox& b, int rows, Cursor& c, int want, float4* buf,
-                             uint64_t* bar, int lane) {
+// Copy up to `want` further points of the shell stream into `buf` with bulk
+// copies that complete on `bar` (warp-collective; lane 0 arrives once).
+// Returns the number of points copied (warp-uniform).
+__device__ __noinline__ int produce_shell_tile(const GridView& g, const Shell& sh, Cursor& c, int want, float4* buf,
+                                  uint64_t* bar, int lane, int* n_out = nullptr) {
     int filled = 0;
-    while (filled < want && c.row < rows) {
+    while (filled < want && c.row < sh.rows) {
         const int r = c.row + lane;
-        int32_t rb = 0, len = 0;
-        if (r < rows) {
-            int32_t re;
-            box_row(g, b, r, rb, re);
-            len = re - rb;
-        }
+        int32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
+        if (r < sh.rows) shell_row(g, sh, r, b1, l1, b2, l2);
+        const int32_t len = l1 + l2;
         int32_t incl = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        const int32_t seg_lo = c.row_pos + incl - len, seg_hi = c.row_pos + incl;
+        const int32_t seg = c.row_pos + incl - len;
         const int32_t win_lo = c.pos, win_hi = c.pos + (want - filled);
-        const int32_t ov_lo = max(seg_lo, win_lo), ov_hi = min(seg_hi, win_hi);
-        const int32_t n = (r < rows && ov_hi > ov_lo) ? ov_hi - ov_lo : 0;
-        int32_t total = n;
+        const int32_t o1lo = max(seg, win_lo), o1hi = min(seg + l1, win_hi);
+        const int32_t o2lo = max(seg + l1, win_lo), o2hi = min(seg + len, win_hi);
+        const int32_t n1 = (r < sh.rows && o1hi > o1lo) ? o1hi - o1lo : 0;
+        const int32_t n2 = (r < sh.rows && o2hi > o2lo) ? o2hi - o2lo : 0;
+        int32_t total = n1 + n2;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
         if (total > 0) {
             if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(total) * 16u);
             __syncwarp();
-            if (n > 0)
-                bulk_copy_g2s(buf + filled + (ov_lo - win_lo), g.pts + rb + (ov_lo - seg_lo),
-                              static_cast<uint32_t>(n) * 16u, bar);
+            if (n1 > 0)
+                bulk_copy_g2s(buf + filled + (o1lo - win_lo), g.pts + b1 + (o1lo - seg),
+                              static_cast<uint32_t>(n1) * 16u, bar);
+            if (n2 > 0)
+                bulk_copy_g2s(buf + filled + (o2lo - win_lo), g.pts + b2 + (o2lo - seg - l1),
+                              static_cast<uint32_t>(n2) * 16u, bar);
         }
         filled += total;
         c.pos += total;
-        // retire rows that are now fully copied
-        const bool done = (r < rows) && (seg_hi <= c.pos);
-        const unsigned m = __ballot_sync(0xffffffffu, done);
-        const int nfull = __popc(m);
+        const bool done = (r < sh.rows) && (seg + len <= c.pos);
+        const int nfull = __popc(__ballot_sync(0xffffffffu, done));
         if (nfull > 0) {
             c.row_pos += __shfl_sync(0xffffffffu, incl, nfull - 1);
             c.row += nfull;
         }
-        if (total == 0 && nfull == 0) break;  // nothing left in range (defensive)
+        if (total == 0 && nfull == 0) break;  // nothing left (defensive)
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(bar);
+    if (lane == 0) {
+        if (n_out) *n_out = filled;  // visible to waiters: the arrive releases it
+        mbar_arrive(bar);
+    }
+    return filled;
 }
 
-template <int Q>
-__global__ void __launch_bounds__(kThreads) k_flood(DimArgs a, Layout lay) {
-    extern __shared__ __align__(128) float4 s_tiles[];  // 2 x kTile
+// ---------------------------------------------------------------- flood kernel
+// Copy the block-occupancy bitmap into shared memory (when it fits) and point
+// the kernel's grid view at it: the shell walk tests it for every row.
+__device__ __forceinline__ void stage_bitmap(const DimArgs& a, GridView& g, uint32_t* s_occ) {
+    if (a.occ_words > 0) {
+        for (int i = threadIdx.x; i < a.occ_words; i += blockDim.x) s_occ[i] = a.g.occupied[i];
+        g.occupied = s_occ;
+    }
+}
+
+struct WarpCounters {
+    unsigned long long pairs = 0ull, shells = 0ull, tiles = 0ull;
+};
+
+// One group of samples on one warp. The warp is W sample lanes x 32/W point
+// streams: lane (g, l) = (lane / W, lane % W) holds samples q*W + l for
+// q < NS and evaluates them on staged points g, g + 32/W, ...; the partial
+// minima of the 32/W streams are combined (shuffles over the stream bits)
+// whenever a decision needs them. W is the smallest power of two with
+// W * NS >= group size, so small groups keep every lane busy.
+template <int NS>
+__device__ __forceinline__ void process_group(const DimArgs& a, const GridView& g, int W, int32_t s_begin,
+                                              int32_t s_end, float ox, float oy, float oz, float4* tiles,
+                                              uint64_t* bar, float* s_u, float* s_lb, uint32_t& phases, bool& abort,
+                                              WarpCounters& cnt, int lane) {
+    float ax[NS], ay[NS], az[NS], pp[NS], mn[NS];
+    bool live[NS];
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
+    float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float R = 0.0f;
+    const int G = 32 / W;  // point streams
+    const int gs = lane / W, lw = lane % W;
+    __syncwarp();  // the previous group's reads of s_u / s_lb are complete
+    for (int i = lane; i < s_end - s_begin; i += 32) {
+        s_u[i] = a.recs[s_begin + i].u;
+        s_lb[i] = a.recs[s_begin + i].lb;
+    }
+    __syncwarp();
+    auto slot = [&](int q) { return s_begin + q * W + lw; };
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        const int32_t i = slot(q);
+        live[q] = i < s_end;
+        ax[q] = ay[q] = az[q] = pp[q] = 0.0f;
+        mn[q] = INFINITY;
+        if (live[q]) {
+            const SampleRec r = a.recs[i];
+            const float px = __fsub_rn(r.x, ox), py = __fsub_rn(r.y, oy), pz = __fsub_rn(r.z, oz);
+            ax[q] = -2.0f * px;
+            ay[q] = -2.0f * py;
+            az[q] = -2.0f * pz;
+            pp[q] = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
+            R = fmaxf(R, r.u);
+            wlo[0] = fminf(wlo[0], r.x);
+            wlo[1] = fminf(wlo[1], r.y);
+            wlo[2] = fminf(wlo[2], r.z);
+            whi[0] = fmaxf(whi[0], r.x);
+            whi[1] = fmaxf(whi[1], r.y);
+            whi[2] = fmaxf(whi[2], r.z);
+            const int cx = cell_coord(r.x, g.ox, g.inv_cell, g.dx);
+            const int cy = cell_coord(r.y, g.oy, g.inv_cell, g.dy);
+            const int cz = cell_coord(r.z, g.oz, g.inv_cell, g.dz);
+            lo[0] = min(lo[0], cx);
+            lo[1] = min(lo[1], cy);
+            lo[2] = min(lo[2], cz);
+            hi[0] = max(hi[0], cx);
+            hi[1] = max(hi[1], cy);
+            hi[2] = max(hi[2], cz);
+        }
+    }
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = min(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+                hi[c] = max(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+                wlo[c] = fminf(wlo[c], __shfl_xor_sync(0xffffffffu, wlo[c], o));
+                whi[c] = fmaxf(whi[c], __shfl_xor_sync(0xffffffffu, whi[c], o));
+            }
+        }
+    }
+    const int n_valid = s_end - s_begin;
+    // Beyond shell s every point is at least s*h (less rounding slack) from
+    // every sample; at max u_p no nearest point can lie farther out.
+    const int dmax = max(g.dx, max(g.dy, g.dz));
+    const int s_max = min(static_cast<int>(ceilf((R + a.shell_slack) / a.shell_h)) + 1, dmax);
+    Shell sh;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        sh.lo[c] = lo[c];
+        sh.hi[c] = hi[c];
+        sh.wlo[c] = wlo[c];
+        sh.whi[c] = whi[c];
+    }
+    sh.slack = a.shell_slack + g.cell * (1.0f / 1024.0f);
+    // combine the partial minima of the point streams
+    auto combine = [&]() {
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+#pragma unroll
+            for (int o = W; o < 32; o <<= 1) mn[q] = fminf(mn[q], __shfl_xor_sync(0xffffffffu, mn[q], o));
+    };
+    // Search radius: the largest current bound of a live sample (its nearest
+    // distance so far, or its vertex bound), slightly inflated.
+    auto search_radius2 = [&]() {
+        combine();
+        float t = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+            if (live[q]) t = fmaxf(t, fminf(sqrtf(fmaxf(__fadd_rn(mn[q], pp[q]), 0.0f)), s_u[slot(q) - s_begin]));
+#pragma unroll
+        for (int o = 1; o < W; o <<= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+        const float T = t * (1.0f + 1.0f / 1024.0f) + sh.slack;
+        return T * T;
+    };
+    for (int s = 0; s <= s_max; ++s) {
+        sh.s = s;
+        shell_setup(g, sh);
+        sh.T2 = search_radius2();
+        ++cnt.shells;
+        if (sh.rows > 0) {
+            Cursor cur{0, 0, 0};
+            int nbuf[2];
+            nbuf[0] = produce_shell_tile(g, sh, cur, kWTile, tiles, &bar[0], lane);
+            int b = 0;
+            for (;;) {
+                const int n = nbuf[b];
+                if (!mbar_wait(&bar[b], (phases >> b) & 1u, &a.ctl->flags)) abort = true;
+                phases ^= 1u << b;
+                if (n == 0 || abort) break;
+                const bool more = cur.row < sh.rows;
+                if (more)
+                    nbuf[b ^ 1] = produce_shell_tile(g, sh, cur, kWTile, tiles + (b ^ 1) * kWTile, &bar[b ^ 1], lane);
+                float4* buf = tiles + b * kWTile;
+                for (int e = lane; e < n; e += 32) {
+                    float4 p = buf[e];
+                    p.x = __fsub_rn(p.x, ox);
+                    p.y = __fsub_rn(p.y, oy);
+                    p.z = __fsub_rn(p.z, oz);
+                    p.w = __fmaf_rn(p.x, p.x, __fmaf_rn(p.y, p.y, __fmul_rn(p.z, p.z)));
+                    buf[e] = p;
+                }
+                __syncwarp();
+#pragma unroll 2
+                for (int j = gs; j < n; j += G) {
+                    const float4 x = buf[j];
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) {
+                        const float t = __fmaf_rn(ax[q], x.x, __fmaf_rn(ay[q], x.y, __fmaf_rn(az[q], x.z, x.w)));
+                        mn[q] = fminf(mn[q], t);
+                    }
+                }
+                cnt.pairs += static_cast<unsigned long long>(n) * static_cast<unsigned long long>(n_valid);
+                ++cnt.tiles;
+                // A row's length depends on the radius, so the radius may only
+                // tighten between rows, never inside a partly copied one.
+                if (cur.pos == cur.row_pos) sh.T2 = search_radius2();
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (!more) break;
+                b ^= 1;
+            }
+        }
+        if (abort) break;
+        combine();
+        const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * a.shell_h, a.shell_slack), 0.0f);
+        const float sl2 = __fmul_rn(sl, sl);
+        bool done = true;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            if (live[q]) {
+                const float d2 = fmaxf(__fadd_rn(mn[q], pp[q]), 0.0f);
+                live[q] = !((d2 <= sl2) || (__fsqrt_rn(d2) <= s_lb[slot(q) - s_begin]));
+                done &= !live[q];
+            }
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+    }
+    combine();
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        const int32_t i = slot(q);
+        if (i < s_end && gs == 0) {
+            const SampleRec r = a.recs[i];
+            const float d2 = fmaxf(__fadd_rn(mn[q], pp[q]), 0.0f);
+            if (__fsqrt_rn(d2) > r.lb)
+                atomicMax(&a.best[r.sigma], (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
+                                                (0xffffffffu - static_cast<uint32_t>(r.s)));
+        }
+    }
+}
+
+constexpr int kNS = 8;  // samples per lane
+
+__global__ void __launch_bounds__(kThreads, 2) k_flood(DimArgs a) {
+    extern __shared__ __align__(128) float4 s_tiles[];  // kWarps x 2 x kWTile, then the bitmap
+    __shared__ __align__(8) uint64_t s_bar[kWarps][2];
+    __shared__ float s_ub[kWarps][2][kGroup];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4* tiles = s_tiles + warp * 2 * kWTile;
+    uint64_t* bar = s_bar[warp];
+    GridView gv = a.g;
+    stage_bitmap(a, gv, reinterpret_cast<uint32_t*>(s_tiles + kWarps * 2 * kWTile));
+    __syncthreads();
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t phases = 0u;
+    bool abort = false;
+    WarpCounters cnt;
+    const int32_t total = a.group_off[a.n_coarse];
+    const int32_t first = *a.n_heavy;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = first + static_cast<int>(atomicAdd(&a.ctl->head[a.k], 1u));
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total || abort) break;
+        const int2 gb = a.groups[item];
+        const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
+        const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
+        // coarse cube corner: the origin of the pair arithmetic for this group
+        const int bxi = gb.x % a.lat.bx, byi = (gb.x / a.lat.bx) % a.lat.by, bzi = gb.x / (a.lat.bx * a.lat.by);
+        const float ox = __fadd_rn(a.lat.ox, static_cast<float>(bxi) * a.lat.B);
+        const float oy = __fadd_rn(a.lat.oy, static_cast<float>(byi) * a.lat.B);
+        const float oz = __fadd_rn(a.lat.oz, static_cast<float>(bzi) * a.lat.B);
+        const int n = s_end - s_begin;
+        const int W = n <= kNS ? 1 : n <= 2 * kNS ? 2 : n <= 4 * kNS ? 4 : 8;
+        process_group<kNS>(a, gv, W, s_begin, s_end, ox, oy, oz, tiles, bar, s_ub[warp][0], s_ub[warp][1], phases,
+                           abort, cnt, lane);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.ctl->pairs[a.k], cnt.pairs);
+        atomicAdd(&a.ctl->shells[a.k], cnt.shells);
+        atomicAdd(&a.ctl->tiles[a.k], cnt.tiles);
+    }
+}
+
+// ---------------------------------------------------------------- heavy groups
+// Groups whose vertex bound allows many shells (samples in empty regions)
+// scan far and long; one whole CTA takes each of them. Warp 0 fills large
+// shared tiles while all eight warps evaluate them; the thread layout is the
+// warp kernel's (W sample lanes x 256/W point streams) stretched over the CTA,
+// and per-sample minima are combined in shared memory.
+constexpr int kHeavyTile = 2048;
+constexpr int kHeavyShells = 8;  // class threshold: groups with >= this many shells are heavy
+
+// Evaluate the NSL used sample slots of one tile (NSL <= kNS).
+template <int NSL>
+__device__ __forceinline__ void heavy_tile(const float4* buf, int n, int gs, int G, const float* ax, const float* ay,
+                                           const float* az, float* mn) {
+#pragma unroll 2
+    for (int j = gs; j < n; j += G) {
+        const float4 x = buf[j];
+#pragma unroll
+        for (int q = 0; q < NSL; ++q) {
+            const float t = __fmaf_rn(ax[q], x.x, __fmaf_rn(ay[q], x.y, __fmaf_rn(az[q], x.z, x.w)));
+            mn[q] = fminf(mn[q], t);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(DimArgs a) {
+    extern __shared__ __align__(128) float4 s_tiles[];  // 2 x kHeavyTile, then the bitmap
     __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ uint32_t s_min[kSRMax];
-    __shared__ unsigned long long s_red[kWarps];
-    __shared__ unsigned long long s_best;
-    __shared__ int s_item, s_sigma, s_chunk, s_abort;
-    __shared__ float s_geo[12];
-
+    __shared__ uint32_t s_min[kGroup];
+    __shared__ int s_live[kGroup];
+    __shared__ float s_u[kGroup], s_lb[kGroup];
+    __shared__ uint32_t s_ub2[kGroup];
+    __shared__ int s_item, s_n[2], s_done, s_abort;
+    __shared__ float s_T2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int W = lay.W, G = 32 / W, NW = lay.NW, P = lay.P;
-    const int ss = warp % NW, pp = warp / NW;
-    const bool computes = pp < P;
-    const int gsub = lane / W, lig = lane % W;
-    const int SR = NW * W * Q;
-    const int k = a.k, I = a.I;
-
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         fence_mbar_init();
         s_abort = 0;
     }
+    GridView g = a.g;
+    stage_bitmap(a, g, reinterpret_cast<uint32_t*>(s_tiles + 2 * kHeavyTile));
     __syncthreads();
-    uint32_t phases = 0u;  // bit b: parity of the next completion of s_bar[b]
-    const int32_t total_items = a.item_off[a.n];
-
+    uint32_t phases = 0u;
+    unsigned long long pairs = 0ull, n_shells = 0ull, n_tiles = 0ull;
+    const int32_t n_heavy = *a.n_heavy;
     for (;;) {
-        if (tid == 0) {
-            int item = static_cast<int>(atomicAdd(&a.ctl->head[k], 1u));
-            if (s_abort) item = total_items;
-            s_item = item;
-            if (item < total_items) {
-                // simplex owning this item: largest sigma with item_off[sigma] <= item
-                int64_t lo = 0, hi = a.n - 1;
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi + 1) >> 1;
-                    if (a.item_off[mid] <= item) lo = mid;
-                    else hi = mid - 1;
-                }
-                s_sigma = static_cast<int>(lo);
-                s_chunk = item - a.item_off[lo];
-                Simplex S;
-                load_simplex(a.L, a.simplices + lo * (k + 1), k, S);
-                for (int c = 0; c < 3; ++c) {
-                    s_geo[c] = S.v0[c];
-                    s_geo[3 + c] = S.e[0][c];
-                    s_geo[6 + c] = S.e[1][c];
-                    s_geo[9 + c] = S.e[2][c];
-                }
-            }
-        }
+        if (tid == 0) s_item = static_cast<int>(atomicAdd(&a.ctl->heavy_head[a.k], 1u));
         __syncthreads();
         const int item = s_item;
-        if (item >= total_items) break;
-        const int sigma = s_sigma, chunk = s_chunk;
-        const SimplexPlan pl = a.plan[sigma];
-        Simplex S;
-        for (int c = 0; c < 3; ++c) {
-            S.v0[c] = s_geo[c];
-            S.e[0][c] = s_geo[3 + c];
-            S.e[1][c] = s_geo[6 + c];
-            S.e[2][c] = s_geo[9 + c];
+        if (item >= n_heavy || s_abort) break;
+        const int2 gb = a.groups[item];
+        const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
+        const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
+        const int n_valid = s_end - s_begin;
+        const int bxi = gb.x % a.lat.bx, byi = (gb.x / a.lat.bx) % a.lat.by, bzi = gb.x / (a.lat.bx * a.lat.by);
+        const float ox = __fadd_rn(a.lat.ox, static_cast<float>(bxi) * a.lat.B);
+        const float oy = __fadd_rn(a.lat.oy, static_cast<float>(byi) * a.lat.B);
+        const float oz = __fadd_rn(a.lat.oz, static_cast<float>(bzi) * a.lat.B);
+        const int W = n_valid <= kNS ? 1 : n_valid <= 2 * kNS ? 2 : n_valid <= 4 * kNS ? 4 : 8;
+        const int G = kThreads / W;
+        const int gs = tid / W, lw = tid % W;
+        const int nsl = (n_valid + W - 1) / W;  // sample slots in use per thread
+        float ax[kNS], ay[kNS], az[kNS], pp[kNS], mn[kNS];
+        bool val[kNS];
+        // group geometry (every thread reads the same records: cached loads)
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
+        float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        float R = 0.0f;
+        for (int32_t i = s_begin; i < s_end; ++i) {
+            const SampleRec r = a.recs[i];
+            R = fmaxf(R, r.u);
+            wlo[0] = fminf(wlo[0], r.x);
+            wlo[1] = fminf(wlo[1], r.y);
+            wlo[2] = fminf(wlo[2], r.z);
+            whi[0] = fmaxf(whi[0], r.x);
+            whi[1] = fmaxf(whi[1], r.y);
+            whi[2] = fmaxf(whi[2], r.z);
+            const int cx = cell_coord(r.x, g.ox, g.inv_cell, g.dx);
+            const int cy = cell_coord(r.y, g.oy, g.inv_cell, g.dy);
+            const int cz = cell_coord(r.z, g.oz, g.inv_cell, g.dz);
+            lo[0] = min(lo[0], cx);
+            lo[1] = min(lo[1], cy);
+            lo[2] = min(lo[2], cz);
+            hi[0] = max(hi[0], cx);
+            hi[1] = max(hi[1], cy);
+            hi[2] = max(hi[2], cz);
         }
-        const int rows = pl.box.n[1] * pl.box.n[2];
-        const int32_t pos_begin = chunk * a.chunk_pts;
-        const int32_t pos_end = min(pos_begin + a.chunk_pts, pl.n_cand);
-        const int n_tiles = static_cast<int>((max(pos_end - pos_begin, 0) + kTile - 1) / kTile);
-        const bool single = pl.n_chunks == 1;
-        if (tid == 0) s_best = 0ull;
-
-        for (int round = 0; round * SR < I; ++round) {
-            // ---- samples of this lane: a = -2 p', min accumulator
-            float ax[Q], ay[Q], az[Q], mn[Q];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int s = round * SR + ss * (W * Q) + q * W + lig;
-                float px = 0.0f, py = 0.0f, pz = 0.0f;
-                if (s < I) sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
+        for (int q = 0; q < kNS; ++q) {
+            const int32_t i = s_begin + q * W + lw;
+            val[q] = i < s_end;
+            ax[q] = ay[q] = az[q] = pp[q] = 0.0f;
+            mn[q] = INFINITY;
+            if (val[q]) {
+                const SampleRec r = a.recs[i];
+                const float px = __fsub_rn(r.x, ox), py = __fsub_rn(r.y, oy), pz = __fsub_rn(r.z, oz);
                 ax[q] = -2.0f * px;
                 ay[q] = -2.0f * py;
                 az[q] = -2.0f * pz;
-                mn[q] = INFINITY;
+                pp[q] = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
             }
-            for (int i = tid; i < SR; i += kThreads) s_min[i] = 0xffffffffu;
-            __syncthreads();
-
-            // ---- stream candidate tiles
-            Cursor cur{0, 0, pos_begin};
-            if (warp == 0) {
-                cursor_seek(a.g, pl.box, rows, cur, lane);
-                if (n_tiles > 0)
-                    produce_tile(a.g, pl.box, rows, cur, min(kTile, pos_end - pos_begin), s_tiles, &s_bar[0], lane);
-            }
-            for (int t = 0; t < n_tiles; ++t) {
-                const int bsel = t & 1;
-                float4* buf = s_tiles + bsel * kTile;
-                const int32_t t_lo = pos_begin + t * kTile;
-                const int n_tile = min(kTile, pos_end - t_lo);
-                if (warp == 0 && t + 1 < n_tiles)
-                    produce_tile(a.g, pl.box, rows, cur, min(kTile, pos_end - (t_lo + kTile)),
-                                 s_tiles + (bsel ^ 1) * kTile, &s_bar[bsel ^ 1], lane);
-                if (!mbar_wait(&s_bar[bsel], (phases >> bsel) & 1u, &a.ctl->flags)) s_abort = 1;
-                phases ^= 1u << bsel;
-                // shift to the simplex origin and append |x'|^2
-                for (int e = tid; e < n_tile; e += kThreads) {
-                    float4 p = buf[e];
-                    p.x = __fsub_rn(p.x, S.v0[0]);
-                    p.y = __fsub_rn(p.y, S.v0[1]);
-                    p.z = __fsub_rn(p.z, S.v0[2]);
-                    p.w = __fmaf_rn(p.x, p.x, __fmaf_rn(p.y, p.y, __fmul_rn(p.z, p.z)));
-                    buf[e] = p;
-                }
-                __syncthreads();
-                if (computes) {
-                    const int step = G * P;
-#pragma unroll 2
-                    for (int j = pp * G + gsub; j < n_tile; j += step) {
-                        const float4 x = buf[j];
-#pragma unroll
-                        for (int q = 0; q < Q; ++q) {
-                            const float t2 = __fmaf_rn(ax[q], x.x, __fmaf_rn(ay[q], x.y, __fmaf_rn(az[q], x.z, x.w)));
-                            mn[q] = fminf(mn[q], t2);
-                        }
-                    }
-                }
-                fence_proxy_async_smem();
-                __syncthreads();
-            }
-
-            // ---- per-sample minimum over all streams of the CTA
-            if (computes) {
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    for (int o = W; o < 32; o <<= 1) mn[q] = fminf(mn[q], __shfl_xor_sync(0xffffffffu, mn[q], o));
-                    if (gsub == 0) {
-                        const int l = ss * (W * Q) + q * W + lig;
-                        const float pp2 = 0.25f * __fmaf_rn(ax[q], ax[q], __fmaf_rn(ay[q], ay[q], __fmul_rn(az[q], az[q])));
-                        const float d2 = fmaxf(__fadd_rn(mn[q], pp2), 0.0f);
-                        atomicMin(&s_min[l], __float_as_uint(d2));
-                    }
-                }
-            }
-            __syncthreads();
-            if (single) {
-                unsigned long long best = 0ull;
-                for (int l = tid; l < SR; l += kThreads) {
-                    const int s = round * SR + l;
-                    if (s < I) {
-                        const unsigned long long key = (static_cast<unsigned long long>(s_min[l]) << 32) |
-                                                       (0xffffffffu - static_cast<uint32_t>(s));
-                        best = max(best, key);
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) best = max(best, static_cast<unsigned long long>(shfl_xor_u64(best, o)));
-                if (lane == 0) s_red[warp] = best;
-                __syncthreads();
-                if (tid == 0) {
-                    unsigned long long b = s_best;
-                    for (int w2 = 0; w2 < kWarps; ++w2) b = max(b, s_red[w2]);
-                    s_best = b;
-                }
-            } else {
-                uint32_t* slot = a.slots + static_cast<int64_t>(sigma) * I;
-                for (int l = tid; l < SR; l += kThreads) {
-                    const int s = round * SR + l;
-                    if (s < I && s_min[l] != 0xffffffffu) atomicMin(&slot[s], s_min[l]);
-                }
-            }
-            __syncthreads();
         }
-        if (single && tid == 0) {
-            const unsigned long long b = s_best;
-            a.g2[sigma] = __uint_as_float(static_cast<uint32_t>(b >> 32));
-            a.arg[sigma] = static_cast<int32_t>(0xffffffffu - static_cast<uint32_t>(b));
+        if (tid < kGroup) {
+            s_min[tid] = 0xffffffffu;
+            s_live[tid] = tid < n_valid;
+            if (tid < n_valid) {
+                s_u[tid] = a.recs[s_begin + tid].u;
+                s_lb[tid] = a.recs[s_begin + tid].lb;
+            }
+            s_ub2[tid] = 0x7f800000u;  // +inf
+        }
+        __syncthreads();
+        // Every landmark is a point of X, so the distance to the nearest one is
+        // also an upper bound of d(p, X), usually far tighter than the simplex's
+        // own vertices for samples in empty space; it narrows the search radius.
+        for (int l = tid; l < a.n_L; l += kThreads) {
+            const float lx = a.L[3 * l], ly = a.L[3 * l + 1], lz = a.L[3 * l + 2];
+            for (int i = 0; i < n_valid; ++i) {
+                const SampleRec& r = a.recs[s_begin + i];
+                const float dx = __fsub_rn(lx, r.x), dy = __fsub_rn(ly, r.y), dz = __fsub_rn(lz, r.z);
+                const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+                if (d2 < s_u[i] * s_u[i]) atomicMin(reinterpret_cast<unsigned int*>(&s_ub2[i]), __float_as_uint(d2));
+            }
+        }
+        __syncthreads();
+        if (tid < n_valid) s_u[tid] = fminf(s_u[tid], __fsqrt_ru(__uint_as_float(s_ub2[tid])) * (1.0f + 1.0f / 65536.0f));
+        __syncthreads();
+        R = 0.0f;
+        for (int i = 0; i < n_valid; ++i) R = fmaxf(R, s_u[i]);
+        const int dmax = max(g.dx, max(g.dy, g.dz));
+        const int s_max = min(static_cast<int>(ceilf((R + a.shell_slack) / a.shell_h)) + 1, dmax);
+        Shell sh;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sh.lo[c] = lo[c];
+            sh.hi[c] = hi[c];
+            sh.wlo[c] = wlo[c];
+            sh.whi[c] = whi[c];
+        }
+        sh.slack = a.shell_slack + g.cell * (1.0f / 1024.0f);
+        // Fold the threads' partial minima into s_min (squared distances >= 0
+        // order like their bit patterns) and recompute the search radius.
+        auto fold = [&]() {
+#pragma unroll
+            for (int q = 0; q < kNS; ++q) {
+                float m = mn[q];
+                for (int o = W; o < 32; o <<= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (val[q] && gs % (32 / W) == 0 && m < INFINITY)
+                    atomicMin(&s_min[q * W + lw], __float_as_uint(fmaxf(__fadd_rn(m, pp[q]), 0.0f)));
+            }
+            __syncthreads();
+            if (warp == 0) {
+                float t = 0.0f;
+                for (int i = lane; i < n_valid; i += 32)
+                    if (s_live[i]) {
+                        const float d = s_min[i] == 0xffffffffu ? INFINITY : sqrtf(__uint_as_float(s_min[i]));
+                        t = fmaxf(t, fminf(d, s_u[i]));
+                    }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+                if (lane == 0) {
+                    const float T = t * (1.0f + 1.0f / 1024.0f) + sh.slack;
+                    s_T2 = T * T;
+                }
+            }
+            __syncthreads();
+        };
+        for (int s = 0; s <= s_max; ++s) {
+            sh.s = s;
+            shell_setup(g, sh);
+            sh.T2 = s_T2 = 0.0f;
+            fold();
+            sh.T2 = s_T2;
+            ++n_shells;
+            if (sh.rows > 0) {
+                Cursor cur{0, 0, 0};
+                if (warp == 0) produce_shell_tile(g, sh, cur, kHeavyTile, s_tiles, &s_bar[0], lane, &s_n[0]);
+                int b = 0;
+                for (;;) {
+                    if (!mbar_wait(&s_bar[b], (phases >> b) & 1u, &a.ctl->flags)) s_abort = 1;
+                    phases ^= 1u << b;
+                    const int n = s_n[b];
+                    __syncthreads();  // every thread has read s_n[b] and any timeout is visible
+                    if (n == 0 || s_abort) break;
+                    if (warp == 0) {
+                        const int more_all = cur.row < sh.rows;
+                        if (more_all)
+                            produce_shell_tile(g, sh, cur, kHeavyTile, s_tiles + (b ^ 1) * kHeavyTile, &s_bar[b ^ 1],
+                                               lane, &s_n[b ^ 1]);
+                        if (lane == 0) s_done = more_all;
+                    }
+                    float4* buf = s_tiles + b * kHeavyTile;
+                    for (int e = tid; e < n; e += kThreads) {
+                        float4 p = buf[e];
+                        p.x = __fsub_rn(p.x, ox);
+                        p.y = __fsub_rn(p.y, oy);
+                        p.z = __fsub_rn(p.z, oz);
+                        p.w = __fmaf_rn(p.x, p.x, __fmaf_rn(p.y, p.y, __fmul_rn(p.z, p.z)));
+                        buf[e] = p;
+                    }
+                    __syncthreads();
+                    if (nsl == 1)
+                        heavy_tile<1>(buf, n, gs, G, ax, ay, az, mn);
+                    else if (nsl == 2)
+                        heavy_tile<2>(buf, n, gs, G, ax, ay, az, mn);
+                    else if (nsl <= 4)
+                        heavy_tile<4>(buf, n, gs, G, ax, ay, az, mn);
+                    else
+                        heavy_tile<kNS>(buf, n, gs, G, ax, ay, az, mn);
+                    pairs += tid == 0 ? static_cast<unsigned long long>(n) * n_valid : 0ull;
+                    n_tiles += tid == 0;
+                    fence_proxy_async_smem();
+                    __syncthreads();
+                    const int cont = s_done;
+                    if (!cont) break;
+                    b ^= 1;
+                }
+            }
+            if (s_abort) break;
+            fold();
+            // termination: every sample exact (below the next shell) or dominated
+            const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * a.shell_h, a.shell_slack), 0.0f);
+            const float sl2 = __fmul_rn(sl, sl);
+            int live = 0;
+            if (tid < n_valid && s_live[tid]) {
+                const float d2 = s_min[tid] == 0xffffffffu ? INFINITY : __uint_as_float(s_min[tid]);
+                const bool fin = (d2 <= sl2) || (__fsqrt_rn(d2) <= s_lb[tid]);
+                s_live[tid] = !fin;
+                live = !fin;
+            }
+            if (!__syncthreads_or(live)) break;
+        }
+        fold();
+        if (tid < n_valid) {
+            const SampleRec r = a.recs[s_begin + tid];
+            const float d2 = __uint_as_float(s_min[tid]);
+            if (s_min[tid] != 0xffffffffu && __fsqrt_rn(d2) > r.lb)
+                atomicMax(&a.best[r.sigma], (static_cast<unsigned long long>(s_min[tid]) << 32) |
+                                                (0xffffffffu - static_cast<uint32_t>(r.s)));
         }
         __syncthreads();
     }
+    if (tid == 0) {
+        atomicAdd(&a.ctl->pairs[a.k], pairs);
+        atomicAdd(&a.ctl->shells[a.k], n_shells);
+        atomicAdd(&a.ctl->tiles[a.k], n_tiles);
+    }
 }
 
-// Max over the per-sample minima of simplices split over several items.
-__global__ void k_finalize(DimArgs a) {
-    const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= a.n || a.chunks[w] <= 1) return;
-    const uint32_t* slot = a.slots + w * a.I;
-    unsigned long long best = 0ull;
-    for (int s = lane; s < a.I; s += 32)
-        best = max(best, (static_cast<unsigned long long>(slot[s]) << 32) | (0xffffffffu - static_cast<uint32_t>(s)));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = max(best, static_cast<unsigned long long>(shfl_xor_u64(best, o)));
-    if (lane == 0) {
-        a.g2[w] = __uint_as_float(static_cast<uint32_t>(best >> 32));
-        a.arg[w] = static_cast<int32_t>(0xffffffffu - static_cast<uint32_t>(best));
-    }
+// Own maximum per simplex from the packed atomic maxima (0 when no sample can
+// exceed the facet maximum).
+__global__ void k_finalize(const unsigned long long* best, int64_t n, float* g2, int32_t* arg) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long b = best[i];
+    g2[i] = b ? __uint_as_float(static_cast<uint32_t>(b >> 32)) : 0.0f;
+    arg[i] = b ? static_cast<int32_t>(0xffffffffu - static_cast<uint32_t>(b)) : 0;
 }
 
 // ---------------------------------------------------------------- face-max
@@ -487,51 +936,55 @@ __global__ void k_facemax(int k, int64_t n, const int32_t* simplices, const int3
 }
 
 // ---------------------------------------------------------------- host side
-// Pick (W, Q, NW) minimising the modelled per-lane instruction count per
-// candidate point: rounds * (4 Q + 3 + bank-conflict replays) / (G * P).
-Layout choose_layout(int I) {
-    Layout best{32, 1, 8, 1};
-    double best_cost = 1e30;
-    for (int W = 1; W <= 32; W <<= 1)
-        for (int Q = 1; Q <= kQMax; ++Q)
-            for (int NW = 1; NW <= kWarps; NW <<= 1) {
-                const int P = kWarps / NW, G = 32 / W;
-                const int SR = NW * W * Q;
-                const int rounds = (I + SR - 1) / SR;
-                const double replay = G > 8 ? 2.0 * (G / 8 - 1) : 0.0;
-                const double cost = rounds * (4.0 * Q + 3.0 + replay) / (G * P);
-                if (cost < best_cost - 1e-12) {
-                    best_cost = cost;
-                    best = Layout{W, Q, NW, P};
-                }
-            }
-    return best;
-}
-
-template <int Q>
-int launch_flood_q(const DimArgs& a, const Layout& lay, cudaStream_t s) {
-    const size_t smem = size_t(2) * kTile * sizeof(float4);
-    FLOOD_CUDA(cudaFuncSetAttribute(k_flood<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+int launch_flood_heavy(const DimArgs& a, cudaStream_t s) {
+    const size_t smem = size_t(2) * kHeavyTile * sizeof(float4) + sizeof(uint32_t) * a.occ_words;
+    FLOOD_CUDA(cudaFuncSetAttribute(k_flood_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
-    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood<Q>, kThreads, smem));
+    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood_heavy, kThreads, smem));
     per_sm = std::max(per_sm, 1);
-    const int64_t grid = int64_t(device_sm_count()) * per_sm;
-    k_flood<Q><<<static_cast<unsigned>(grid), kThreads, smem, s>>>(a, lay); note_launch();
+    k_flood_heavy<<<static_cast<unsigned>(device_sm_count() * per_sm), kThreads, smem, s>>>(a);
+    note_launch();
     FLOOD_CUDA(cudaGetLastError());
     return FLOOD_OK;
 }
 
-int launch_flood(const DimArgs& a, const Layout& lay, cudaStream_t s) {
-    switch (lay.Q) {
-        case 1: return launch_flood_q<1>(a, lay, s);
-        case 2: return launch_flood_q<2>(a, lay, s);
-        case 3: return launch_flood_q<3>(a, lay, s);
-        case 4: return launch_flood_q<4>(a, lay, s);
-        case 5: return launch_flood_q<5>(a, lay, s);
-        case 6: return launch_flood_q<6>(a, lay, s);
-        case 7: return launch_flood_q<7>(a, lay, s);
-        default: return launch_flood_q<8>(a, lay, s);
+int launch_flood(const DimArgs& a, cudaStream_t s) {
+    const size_t smem = size_t(kWarps) * 2 * kWTile * sizeof(float4) + sizeof(uint32_t) * a.occ_words;
+    FLOOD_CUDA(cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int per_sm = 0;
+    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood, kThreads, smem));
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = int64_t(device_sm_count()) * per_sm;
+    k_flood<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(a);
+    note_launch();
+    FLOOD_CUDA(cudaGetLastError());
+    return FLOOD_OK;
+}
+
+// Sample lattice: coarse edge B = a power of two near extent/40, anchored at
+// the grid origin; it depends only on X's bounding box.
+Lattice make_lattice(const flood_grid* grid) {
+    Lattice L{};
+    L.ox = grid->origin[0];
+    L.oy = grid->origin[1];
+    L.oz = grid->origin[2];
+    float ext[3], emax = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+        ext[c] = grid->bbox_hi[c] - grid->bbox_lo[c];
+        emax = std::max(emax, ext[c]);
     }
+    float B = emax > 0.0f ? std::exp2(std::round(std::log2(emax / 40.0f))) : 1.0f;
+    for (;;) {
+        L.bx = static_cast<int>(std::floor(ext[0] / B)) + 1;
+        L.by = static_cast<int>(std::floor(ext[1] / B)) + 1;
+        L.bz = static_cast<int>(std::floor(ext[2] / B)) + 1;
+        if (int64_t(L.bx) * L.by * L.bz * kFine <= kMaxBuckets) break;
+        B *= 2.0f;
+    }
+    L.B = B;
+    L.invB = 1.0f / B;
+    L.invF = 4.0f / B;
+    return L;
 }
 
 thread_local flood_filtration_stats g_stats;
@@ -576,7 +1029,6 @@ std::vector<uint8_t> interior_table(int m, int k) {
     return out;
 }
 
-
 }  // namespace flood
 
 using namespace flood;
@@ -619,6 +1071,9 @@ extern "C" int flood_filtration(const flood_grid* grid, const float* L, int32_t 
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
     Scratch scr(s);
     GridView gv = view_of(grid);
+    const Lattice lat = make_lattice(grid);
+    const int64_t n_coarse = int64_t(lat.bx) * lat.by * lat.bz;
+    const int64_t n_buckets = n_coarse * kFine;
     Ctl* ctl;
     int rc;
     if ((rc = scr.alloc(&ctl, 1))) return rc;
@@ -634,89 +1089,140 @@ extern "C" int flood_filtration(const flood_grid* grid, const float* L, int32_t 
         if (!sr[k] && (rc = scr.alloc(&sr[k], 2 * nk[k]))) return rc;
     }
     k_vertices<<<static_cast<unsigned>(ceil_div(n_landmarks, 256)), 256, 0, s>>>(L, n_landmarks, gv, val[0], sr[0],
-                                                                                 &ctl->flags); note_launch();
+                                                                                 &ctl->flags);
+    note_launch();
     FLOOD_CUDA(cudaGetLastError());
 
+    // per-dimension scratch, sized for the largest dimension and reused
+    int64_t max_samples = 1, max_n = 1;
     std::vector<uint8_t> tables[4];
-    EventPairs ev;
-    float* g2[4] = {};
-    int32_t* arg[4] = {};
-    int32_t* item_off[4] = {};
+    int I[4] = {0, 0, 0, 0};
     for (int k = 1; k <= 3; ++k) {
-        const int64_t n = nk[k];
-        if (n == 0) continue;
+        if (nk[k] == 0) continue;
         tables[k] = interior_table(m, k);
-        const int I = static_cast<int>(tables[k].size() / (k + 1));
-        if (I == 0) {
-            // m <= k: no interior samples; the value is the face maximum alone.
-            if ((rc = scr.alloc(&g2[k], n)) || (rc = scr.alloc(&arg[k], n))) return rc;
-            FLOOD_CUDA(cudaMemsetAsync(g2[k], 0, sizeof(float) * n, s));
-            FLOOD_CUDA(cudaMemsetAsync(arg[k], 0, sizeof(int32_t) * n, s));
-            continue;
-        }
-        uint8_t* comp;
-        SimplexPlan* plan;
-        int32_t* chunks;
-        uint32_t* slots;
-        if ((rc = scr.alloc(&comp, tables[k].size())) || (rc = scr.alloc(&plan, n)) || (rc = scr.alloc(&chunks, n)) ||
-            (rc = scr.alloc(&item_off[k], n + 1)) || (rc = scr.alloc(&g2[k], n)) || (rc = scr.alloc(&arg[k], n)) ||
-            (rc = scr.alloc(&slots, n * I)))
-            return rc;
-        FLOOD_CUDA(cudaMemcpyAsync(comp, tables[k].data(), tables[k].size(), cudaMemcpyHostToDevice, s));
-        FLOOD_CUDA(cudaMemsetAsync(slots, 0xff, sizeof(uint32_t) * n * I, s));
-        DimArgs a{};
-        a.k = k;
-        a.I = I;
-        a.m = static_cast<float>(m);
-        a.n = n;
-        a.simplices = simplices[k];
-        a.comp = comp;
-        a.L = L;
-        a.n_L = n_landmarks;
-        a.g = gv;
-        a.plan = plan;
-        a.chunks = chunks;
-        a.item_off = item_off[k];
-        a.chunk_pts = static_cast<int32_t>(std::max<int64_t>(kTile, kChunkPairs / I));
-        a.g2 = g2[k];
-        a.arg = arg[k];
-        a.slots = slots;
-        a.ctl = ctl;
-        k_prep<<<static_cast<unsigned>(ceil_div(n * 32, 256)), 256, 0, s>>>(a); note_launch();
-        FLOOD_CUDA(cudaGetLastError());
-        if ((rc = exclusive_scan(chunks, item_off[k], n, s, scr))) return rc;
-        const Layout lay = choose_layout(I);
-        if (cudaEventCreate(&ev[k][0]) == cudaSuccess && cudaEventCreate(&ev[k][1]) == cudaSuccess)
-            cudaEventRecord(ev[k][0], s);
-        if ((rc = launch_flood(a, lay, s))) return rc;
-        if (ev[k][1]) cudaEventRecord(ev[k][1], s);
-        k_finalize<<<static_cast<unsigned>(ceil_div(n * 32, 256)), 256, 0, s>>>(a); note_launch();
-        FLOOD_CUDA(cudaGetLastError());
+        I[k] = static_cast<int>(tables[k].size() / (k + 1));
+        max_samples = std::max(max_samples, nk[k] * I[k]);
+        max_n = std::max(max_n, nk[k]);
     }
+    int32_t *bcount, *bstart, *bfill, *goff, *g_arg;
+    int2 *groups, *groups_sorted;
+    int32_t* cls;
+    SampleRec* recs;
+    unsigned long long* best;
+    float* g_own;
+    const int64_t max_groups = max_samples / kGroup + n_coarse + 1;
+    if ((rc = scr.alloc(&bcount, n_buckets)) || (rc = scr.alloc(&bstart, n_buckets + 1)) ||
+        (rc = scr.alloc(&bfill, n_buckets)) || (rc = scr.alloc(&goff, n_coarse + 1)) ||
+        (rc = scr.alloc(&groups, max_groups)) || (rc = scr.alloc(&groups_sorted, max_groups)) ||
+        (rc = scr.alloc(&cls, 2 * (kClasses + 1))) || (rc = scr.alloc(&recs, max_samples)) ||
+        (rc = scr.alloc(&best, max_n)) || (rc = scr.alloc(&g_own, max_n)) || (rc = scr.alloc(&g_arg, max_n)))
+        return rc;
+
+    const float emax = std::max(grid->bbox_hi[0] - grid->bbox_lo[0],
+                                std::max(grid->bbox_hi[1] - grid->bbox_lo[1], grid->bbox_hi[2] - grid->bbox_lo[2]));
+    const float amax =
+        std::max(std::fabs(grid->origin[0]), std::max(std::fabs(grid->origin[1]), std::fabs(grid->origin[2])));
+    EventPairs ev;
+    int32_t h_items[4] = {0, 0, 0, 0};
     for (int k = 1; k <= 3; ++k) {
         const int64_t n = nk[k];
         if (n == 0) continue;
+        FLOOD_CUDA(cudaMemsetAsync(best, 0, sizeof(unsigned long long) * n, s));
+        if (I[k] > 0) {
+            uint8_t* comp;
+            if ((rc = scr.alloc(&comp, tables[k].size()))) return rc;
+            FLOOD_CUDA(cudaMemcpyAsync(comp, tables[k].data(), tables[k].size(), cudaMemcpyHostToDevice, s));
+            DimArgs a{};
+            a.k = k;
+            a.I = I[k];
+            a.m = static_cast<float>(m);
+            a.n = n;
+            a.simplices = simplices[k];
+            a.facets = k >= 2 ? facets[k] : nullptr;
+            a.val_lower = val[k - 1];
+            a.n_lower = nk[k - 1];
+            a.comp = comp;
+            a.L = L;
+            a.n_L = n_landmarks;
+            a.g = gv;
+            a.lat = lat;
+            a.n_buckets = n_buckets;
+            a.n_coarse = n_coarse;
+            a.bucket_count = bcount;
+            a.bucket_start = bstart;
+            a.bucket_fill = bfill;
+            a.group_off = goff;
+            a.groups = groups;
+            a.recs = recs;
+            a.best = best;
+            {
+                const int64_t blocks = int64_t(grid->bdims[0]) * grid->bdims[1] * grid->bdims[2];
+                const int64_t words = (blocks + 31) / 32;
+                a.occ_words = words <= kMaxSmemBitmapWords ? static_cast<int32_t>(words) : 0;
+            }
+            a.shell_h = grid->cell_size * (1.0f - 1.0f / 1024.0f);
+            a.shell_slack = (amax + emax) * (1.0f / 262144.0f);
+            a.ctl = ctl;
+            FLOOD_CUDA(cudaMemsetAsync(bcount, 0, sizeof(int32_t) * n_buckets, s));
+            FLOOD_CUDA(cudaMemsetAsync(bfill, 0, sizeof(int32_t) * n_buckets, s));
+            const unsigned wb = static_cast<unsigned>(ceil_div(n * 32, 256));
+            k_samples<false><<<wb, 256, 0, s>>>(a);
+            note_launch();
+            if ((rc = exclusive_scan(bcount, bstart, n_buckets, s, scr))) return rc;
+            k_samples<true><<<wb, 256, 0, s>>>(a);
+            note_launch();
+            const unsigned bb = static_cast<unsigned>(ceil_div(n_coarse, 256));
+            k_group_counts<<<bb, 256, 0, s>>>(bstart, n_coarse, bcount);
+            note_launch();
+            if ((rc = exclusive_scan(bcount, goff, n_coarse, s, scr))) return rc;
+            k_group_fill<<<bb, 256, 0, s>>>(goff, n_coarse, groups);
+            note_launch();
+            FLOOD_CUDA(cudaGetLastError());
+            // longest-first order; the group count stays on the device
+            {
+                const int32_t* n_groups = goff + n_coarse;
+                FLOOD_CUDA(cudaMemsetAsync(cls, 0, sizeof(int32_t) * 2 * (kClasses + 1), s));
+                const unsigned gbk = static_cast<unsigned>(ceil_div(max_groups, 256));
+                k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, cls);
+                note_launch();
+                if ((rc = exclusive_scan(cls, cls + kClasses + 1, kClasses, s, scr))) return rc;
+                FLOOD_CUDA(cudaMemsetAsync(cls, 0, sizeof(int32_t) * kClasses, s));
+                k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, cls + kClasses + 1, cls, groups_sorted);
+                note_launch();
+                FLOOD_CUDA(cudaGetLastError());
+                a.groups = groups_sorted;
+            }
+            // heavy groups: shell bound >= kHeavyShells, i.e. classes [0, kClasses - kHeavyShells]
+            a.n_heavy = cls + kClasses + 1 + (kClasses - kHeavyShells);
+            FLOOD_CUDA(cudaMemcpyAsync(&h_items[k], goff + n_coarse, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            if (cudaEventCreate(&ev[k][0]) == cudaSuccess && cudaEventCreate(&ev[k][1]) == cudaSuccess)
+                cudaEventRecord(ev[k][0], s);
+            if ((rc = launch_flood_heavy(a, s))) return rc;
+            if ((rc = launch_flood(a, s))) return rc;
+            if (ev[k][1]) cudaEventRecord(ev[k][1], s);
+        }
+        k_finalize<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(best, n, g_own, g_arg);
+        note_launch();
         k_facemax<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(
-            k, n, simplices[k], facets ? facets[k] : nullptr, nk[k - 1], g2[k], arg[k], val[k - 1], sr[k - 1], val[k],
-            sr[k], &ctl->flags); note_launch();
+            k, n, simplices[k], facets ? facets[k] : nullptr, nk[k - 1], g_own, g_arg, val[k - 1], sr[k - 1], val[k],
+            sr[k], &ctl->flags);
+        note_launch();
         FLOOD_CUDA(cudaGetLastError());
     }
     Ctl h_ctl{};
-    int32_t h_items[4] = {0, 0, 0, 0};
     FLOOD_CUDA(cudaMemcpyAsync(&h_ctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-    for (int k = 1; k <= 3; ++k)
-        if (item_off[k]) FLOOD_CUDA(cudaMemcpyAsync(&h_items[k], item_off[k] + nk[k], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FLOOD_CUDA(cudaStreamSynchronize(s));
     rc = status_from_flags(h_ctl.flags, "flood_filtration");
     if (rc) return rc;
     flood_filtration_stats st{};
     for (int k = 0; k <= 3; ++k) {
         st.simplices[k] = nk[k];
-        const int I = k == 0 ? 1 : static_cast<int>(tables[k].size() / (k + 1));
-        st.samples[k] = nk[k] * (k == 0 ? 0 : I);
+        st.samples[k] = k == 0 ? 0 : nk[k] * I[k];
         st.pairs[k] = static_cast<int64_t>(h_ctl.pairs[k]);
         st.work_items[k] = h_items[k];
-        st.split_simplices[k] = h_ctl.split[k];
+        st.active_samples[k] = static_cast<int64_t>(h_ctl.active[k]);
+        st.shells[k] = static_cast<int64_t>(h_ctl.shells[k]);
+        st.tiles[k] = static_cast<int64_t>(h_ctl.tiles[k]);
         st.flood_kernel_ms[k] = 0.0f;
         if (ev[k][0] && ev[k][1]) cudaEventElapsedTime(&st.flood_kernel_ms[k], ev[k][0], ev[k][1]);
     }

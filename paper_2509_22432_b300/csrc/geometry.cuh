@@ -22,6 +22,8 @@ struct flood_grid {
     float bbox_hi[3];
     float4* pts;          // points sorted by cell: (x, y, z, original row as int bits)
     int32_t* cell_start;  // n_cells + 1 offsets into pts
+    uint32_t* occupied;   // one bit per block of 4 x 4 x 4 cells that holds any point
+    int32_t bdims[3];     // blocks per axis
     int64_t device_bytes;
 };
 
@@ -34,15 +36,23 @@ std::vector<uint8_t> interior_table(int m, int k);
 struct GridView {
     const float4* pts;
     const int32_t* cell_start;
+    const uint32_t* occupied;
     int dx, dy, dz;
+    int bx, by, bz;
     float ox, oy, oz;
     float inv_cell;
+    float cell;
 };
 
 inline GridView view_of(const flood_grid* g) {
     GridView v;
     v.pts = g->pts;
     v.cell_start = g->cell_start;
+    v.occupied = g->occupied;
+    v.bx = g->bdims[0];
+    v.by = g->bdims[1];
+    v.bz = g->bdims[2];
+    v.cell = g->cell_size;
     v.dx = g->dims[0];
     v.dy = g->dims[1];
     v.dz = g->dims[2];
@@ -59,6 +69,17 @@ __device__ __forceinline__ int cell_coord(float v, float o, float inv_cell, int 
     float t = __fmul_rn(__fsub_rn(v, o), inv_cell);
     t = fminf(fmaxf(t, 0.0f), static_cast<float>(dim - 1));
     return static_cast<int>(t);
+}
+
+// Whether any block of 4 x 4 x 4 cells along the row (cy, cz), cells
+// [x0, x1] of x, holds a point.
+__device__ __forceinline__ bool row_occupied(const GridView& g, int cy, int cz, int x0, int x1) {
+    const int64_t base = (static_cast<int64_t>(cz >> 2) * g.by + (cy >> 2)) * g.bx;
+    for (int b = x0 >> 2; b <= (x1 >> 2); ++b) {
+        const int64_t bit = base + b;
+        if (g.occupied[bit >> 5] & (1u << (bit & 31))) return true;
+    }
+    return false;
 }
 
 // Vertex coordinates of a k-simplex: origin v0 and edge vectors e_j = v_j - v0.

@@ -92,6 +92,23 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const float* X, int64_t n,
     pts[pos] = make_float4(X[3 * i + 0], X[3 * i + 1], X[3 * i + 2], __int_as_float(static_cast<int>(i)));
 }
 
+// One bit per block of 4 x 4 x 4 cells: set when any of its cells is non-empty.
+__global__ void k_block_bits(GridView g, uint32_t* bits) {
+    const int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t nb = int64_t(g.bx) * g.by * g.bz;
+    if (b >= nb) return;
+    const int bx = static_cast<int>(b % g.bx), by = static_cast<int>((b / g.bx) % g.by),
+              bz = static_cast<int>(b / (int64_t(g.bx) * g.by));
+    bool any = false;
+    for (int z = 4 * bz; z < min(4 * bz + 4, g.dz) && !any; ++z)
+        for (int y = 4 * by; y < min(4 * by + 4, g.dy) && !any; ++y) {
+            const int64_t row = (static_cast<int64_t>(z) * g.dy + y) * g.dx;
+            const int x0 = 4 * bx, x1 = min(4 * bx + 4, g.dx);
+            any = g.cell_start[row + x1] > g.cell_start[row + x0];
+        }
+    if (any) atomicOr(&bits[b >> 5], 1u << (b & 31));
+}
+
 }  // namespace
 
 // Default edge length: the cube root of the volume per point times 2, with
@@ -183,15 +200,20 @@ extern "C" int flood_build_grid(const float* X, int64_t n_points, float cell_siz
     g->cell_size = h;
     g->inv_cell = 1.0f / h;
 
+    for (int c = 0; c < 3; ++c) g->bdims[c] = (g->dims[c] + 3) / 4;
+    const int64_t n_blocks = int64_t(g->bdims[0]) * g->bdims[1] * g->bdims[2];
+    const int64_t n_words = (n_blocks + 31) / 32;
     cudaError_t e1 = cudaMalloc(&g->pts, sizeof(float4) * n_points);
     cudaError_t e2 = cudaMalloc(&g->cell_start, sizeof(int32_t) * (g->n_cells + 1));
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaError_t e3 = cudaMalloc(&g->occupied, sizeof(uint32_t) * n_words);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         cudaGetLastError();
         flood_grid_destroy(g);
         set_error("flood_build_grid: device allocation failed");
         return FLOOD_ENOMEM;
     }
-    g->device_bytes = int64_t(sizeof(float4)) * n_points + int64_t(sizeof(int32_t)) * (g->n_cells + 1);
+    g->device_bytes = int64_t(sizeof(float4)) * n_points + int64_t(sizeof(int32_t)) * (g->n_cells + 1) +
+                      int64_t(sizeof(uint32_t)) * n_words;
 
     int32_t *d_cell = nullptr, *d_count = nullptr;
     if ((rc = scr.alloc(&d_cell, n_points)) || (rc = scr.alloc(&d_count, g->n_cells))) {
@@ -206,6 +228,9 @@ extern "C" int flood_build_grid(const float* X, int64_t n_points, float cell_siz
     if (rc == FLOOD_OK) {
         cudaMemsetAsync(d_count, 0, sizeof(int32_t) * g->n_cells, s);
         k_scatter<<<nb, kThreads, 0, s>>>(X, n_points, d_cell, g->cell_start, d_count, g->pts); note_launch();
+        cudaMemsetAsync(g->occupied, 0, sizeof(uint32_t) * n_words, s);
+        k_block_bits<<<static_cast<unsigned>(ceil_div(n_blocks, kThreads)), kThreads, 0, s>>>(view_of(g), g->occupied);
+        note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "flood_build_grid kernels");
     }
@@ -243,5 +268,6 @@ extern "C" void flood_grid_destroy(flood_grid* g) {
     if (!g) return;
     if (g->pts) cudaFree(g->pts);
     if (g->cell_start) cudaFree(g->cell_start);
+    if (g->occupied) cudaFree(g->occupied);
     free(g);
 }

@@ -153,8 +153,8 @@ def filtration(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, want_src:
 def last_filtration_stats() -> dict:
     st = _lib.FiltrationStats()
     _lib.check(_lib.get().flood_last_filtration_stats(C.byref(st)), "flood_last_filtration_stats")
-    return {k: list(getattr(st, k)) for k in ("simplices", "samples", "pairs", "work_items", "split_simplices",
-                                               "flood_kernel_ms")}
+    return {k: list(getattr(st, k)) for k in ("simplices", "samples", "pairs", "work_items", "active_samples",
+                                               "shells", "tiles", "flood_kernel_ms")}
 
 
 def kernel_launches() -> int:

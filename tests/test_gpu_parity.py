@@ -129,12 +129,12 @@ def test_flood_resolutions(m):
 
 @pytest.mark.parametrize("m", [24, 30])
 def test_flood_many_samples_per_simplex(m):
-    """Sample counts beyond one pass of the CTA's registers (multiple sample rounds) and split items."""
+    """Many samples per simplex (hundreds to thousands) through the bucketed sample groups."""
     X = data.sphere_cloud(20_000, seed=9)
     L, cx, ref = _case(X, 24, m, method="kdtree")
     vals, _, stats = gpu_flood(X, L, cx, m)
     assert_close(vals, ref.values, X, f"m={m}")
-    assert stats["split_simplices"][3] > 0
+    assert 0 < stats["active_samples"][3] <= stats["samples"][3]
 
 
 @pytest.mark.parametrize("n", [4, 5, 9, 17, 63])
@@ -174,7 +174,9 @@ def test_values_bitwise_invariant_to_cell_size():
     idx, _ = oracle.fps(X, 80, 0)
     L = X[idx]
     cx = delaunay_complex(L)
-    runs = [gpu_flood(X, L, cx, 8, cell_size=h, want_src=True) for h in (0.0, 0.05, 0.2, 1.0)]
+    runs = [gpu_flood(X, L, cx, 8, cell_size=h, want_src=True) for h in (0.0, 0.05, 0.2, 1.0, 3.0)]
+    ref = oracle.flood_values(X, L, cx.simplices, 8, method="kdtree")
+    assert_close(runs[0][0], ref.values, X, "default cell size")
     for v, s, _ in runs[1:]:
         for k in range(4):
             assert np.array_equal(v[k].view(np.uint32), runs[0][0][k].view(np.uint32))
