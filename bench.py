@@ -203,11 +203,23 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
 
-    def step():
+    phase_events = []
+
+    def step(record=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        if record:
+            ev[0].record(stream)
         idx, key = ops.fps(Xd, n_l, 0)
+        if record:
+            ev[1].record(stream)
         grid = ops.build_grid(Xd, cell)
+        if record:
+            ev[2].record(stream)
         L = Xd[idx]
         vals, _ = ops.filtration(grid, L, dcx, m, want_src=False)
+        if record:
+            ev[3].record(stream)
+            phase_events.append(ev)
         grid.close()
         return idx, vals
 
@@ -227,7 +239,7 @@ def main():
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step()
+            step(record=True)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -283,7 +295,10 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "nn_queries_per_s": world * queries / (ms * 1e-3),
         "pairs_per_step": pairs,
-        "phase_ms": {"flood_kernels": fk},
+        "phase_ms": {"fps": float(np.mean([e[0].elapsed_time(e[1]) for e in phase_events])),
+                     "grid": float(np.mean([e[1].elapsed_time(e[2]) for e in phase_events])),
+                     "filtration": float(np.mean([e[2].elapsed_time(e[3]) for e in phase_events])),
+                     "flood_kernels": fk},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
                      "kernel": "k_flood (all dims)", "flops_per_pair": FLOPS_PER_PAIR,

@@ -21,7 +21,6 @@ namespace flood {
 
 namespace {
 
-constexpr int kFpsThreads = 512;
 
 __global__ void __launch_bounds__(256) k_aos_to_soa(const float* X, int64_t n, float* x, float* y, float* z,
                                                    uint32_t* flags) {
@@ -47,6 +46,22 @@ __device__ __forceinline__ uint64_t pack_key(float d, uint32_t i) {
     return (static_cast<uint64_t>(__float_as_uint(d)) << 32) | static_cast<uint64_t>(0xffffffffu - i);
 }
 
+// Per-block candidate of one iteration, in one 64-bit word that is written
+// and read atomically (naturally aligned):
+//   bits 63..62  iteration tag (j mod 4)
+//   bits 61..31  key bits (non-negative binary32, sign bit dropped)
+//   bits 30..0   0x7fffffff - index (ties go to the lowest index)
+// Readers poll the slots of iteration j until every tag matches, which both
+// synchronises the grid and delivers the candidates in one pass. Slots are
+// double-buffered by parity; a block cannot run two iterations ahead of a
+// reader because it needs that reader's next slot first.
+using FpsSlot = unsigned long long;
+
+__device__ __forceinline__ uint64_t pack_slot(float d, uint32_t i, int j) {
+    return (static_cast<uint64_t>(j & 3) << 62) | (static_cast<uint64_t>(__float_as_uint(d) & 0x7fffffffu) << 31) |
+           static_cast<uint64_t>(0x7fffffffu - i);
+}
+
 struct FpsArgs {
     const float* x;
     const float* y;
@@ -57,29 +72,33 @@ struct FpsArgs {
     int64_t start;
     int64_t* out_idx;
     float* out_key;
-    unsigned long long* slots;  // 2 * gridDim.x
+    FpsSlot* slots;  // 2 * gridDim.x
     uint32_t* counter;
     uint32_t* flags;
 };
 
+constexpr uint64_t kSlotValue = (uint64_t(1) << 62) - 1;
+
 // K points per thread live in registers when RESIDENT; otherwise coordinates
 // and running minima stream from global memory every iteration.
-template <int K, bool RESIDENT>
-__global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
-    __shared__ unsigned long long s_red[kFpsThreads / 32];
+template <int K, bool RESIDENT, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_fps(FpsArgs a) {
+    constexpr int kWarpsPerBlock = THREADS / 32;
+    __shared__ unsigned long long s_key[kWarpsPerBlock];
     __shared__ unsigned long long s_win;
     __shared__ int s_stop;
     const int nb = gridDim.x;
-    const int64_t stride = int64_t(nb) * blockDim.x;
-    const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t n = static_cast<uint32_t>(a.n);
+    const uint32_t stride = static_cast<uint32_t>(nb) * THREADS;
+    const uint32_t gt = blockIdx.x * THREADS + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     float px[RESIDENT ? K : 1], py[RESIDENT ? K : 1], pz[RESIDENT ? K : 1], pd[RESIDENT ? K : 1];
     if (RESIDENT) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const int64_t i = gt + k * stride;
-            const bool ok = i < a.n;
+            const uint32_t i = gt + k * stride;
+            const bool ok = i < n;
             px[k] = ok ? a.x[i] : 0.0f;
             py[k] = ok ? a.y[i] : 0.0f;
             pz[k] = ok ? a.z[i] : 0.0f;
@@ -90,9 +109,8 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
         a.out_idx[0] = a.start;
         if (a.out_key) a.out_key[0] = __int_as_float(0x7f800000);
     }
-    int64_t cur = a.start;
+    float lx = a.x[a.start], ly = a.y[a.start], lz = a.z[a.start];
     for (int j = 1; j < a.n_landmarks; ++j) {
-        const float lx = a.x[cur], ly = a.y[cur], lz = a.z[cur];
         float best = -1.0f;
         uint32_t bi = 0;
         if (RESIDENT) {
@@ -101,66 +119,75 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
                 pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], lx, ly, lz));
                 if (pd[k] > best) {
                     best = pd[k];
-                    bi = static_cast<uint32_t>(gt + k * stride);
+                    bi = gt + k * stride;
                 }
             }
         } else {
-            for (int64_t i = gt; i < a.n; i += stride) {
+            for (uint32_t i = gt; i < n; i += stride) {
                 const float d = fminf(a.dmin[i], fps_key(a.x[i], a.y[i], a.z[i], lx, ly, lz));
                 a.dmin[i] = d;
                 if (d > best) {
                     best = d;
-                    bi = static_cast<uint32_t>(i);
+                    bi = i;
                 }
             }
         }
-        uint64_t key = best >= 0.0f ? pack_key(best, bi) : 0ull;
+        uint64_t key = best >= 0.0f ? (pack_slot(best, bi, 0) & kSlotValue) : 0ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) key = umax64(key, shfl_xor_u64(key, o));
-        if (lane == 0) s_red[warp] = key;
+        if (lane == 0) s_key[warp] = key;
         __syncthreads();
         if (warp == 0) {
-            key = lane < (kFpsThreads / 32) ? s_red[lane] : 0ull;
+            uint64_t bk = lane < kWarpsPerBlock ? s_key[lane] : 0ull;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) key = umax64(key, shfl_xor_u64(key, o));
-            if (lane == 0) {
-                unsigned long long* slot = a.slots + (j & 1) * nb;
-                __stcg(slot + blockIdx.x, static_cast<unsigned long long>(key));
-                __threadfence();
-                atomicAdd(a.counter, 1u);
-                // Grid barrier: every block has published iteration j.
-                const uint32_t target = static_cast<uint32_t>(j) * static_cast<uint32_t>(nb);
-                uint32_t polls = 0;
-                int stop = 0;
-                while (ld_acquire_u32(a.counter) < target) {
-                    if (++polls > kWaitPolls) {
-                        atomicOr(a.flags, FLAG_TIMEOUT);
-                        stop = 1;
-                        break;
-                    }
+            for (int o = 16; o > 0; o >>= 1) bk = umax64(bk, shfl_xor_u64(bk, o));
+            const uint64_t tag = static_cast<uint64_t>(j & 3) << 62;
+            FpsSlot* buf = a.slots + (j & 1) * nb;
+            if (lane == 0) __stcg(buf + blockIdx.x, tag | bk);
+            // Poll every block's slot of iteration j (bounded); the maximum of
+            // the values is the winner.
+            uint64_t w = 0ull;
+            uint32_t polls = 0;
+            int stop = 0;
+            for (;;) {
+                bool ready = true;
+                uint64_t m = 0ull;
+                for (int b = lane; b < nb; b += 32) {
+                    const uint64_t v = __ldcg(buf + b);
+                    ready &= (v & ~kSlotValue) == tag;
+                    m = umax64(m, v & kSlotValue);
                 }
-                s_stop = stop;
+                if (__all_sync(0xffffffffu, ready)) {
+                    w = m;
+                    break;
+                }
+                if (++polls > kWaitPolls) {
+                    stop = 1;
+                    if (lane == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+                    break;
+                }
             }
-            __syncwarp();
-            const unsigned long long* slot = a.slots + (j & 1) * nb;
-            uint64_t w = 0;
-            for (int b = lane; b < nb; b += 32) w = umax64(w, __ldcg(slot + b));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) w = umax64(w, shfl_xor_u64(w, o));
-            if (lane == 0) s_win = w;
+            if (lane == 0) {
+                s_win = w;
+                s_stop = stop;
+            }
         }
         __syncthreads();
         const uint64_t w = s_win;
         const int stop = s_stop;
         __syncthreads();
         if (stop) break;
-        const float wkey = __uint_as_float(static_cast<uint32_t>(w >> 32));
-        const int64_t widx = static_cast<int64_t>(0xffffffffu - static_cast<uint32_t>(w));
+        const float wkey = __uint_as_float(static_cast<uint32_t>(w >> 31));
+        const uint32_t widx = 0x7fffffffu - static_cast<uint32_t>(w & 0x7fffffffu);
         if (!(wkey > 0.0f) || w == 0ull) {
             if (gt == 0) atomicOr(a.flags, FLAG_DEGENERATE);
             break;
         }
-        cur = widx;
+        lx = a.x[widx];
+        ly = a.y[widx];
+        lz = a.z[widx];
         if (gt == 0) {
             a.out_idx[j] = widx;
             if (a.out_key) a.out_key[j] = wkey;
@@ -168,10 +195,13 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
     }
 }
 
-template <int K, bool RESIDENT>
+constexpr int kResidentThreads = 1024;
+constexpr int kStreamThreads = 512;
+
+template <int K, bool RESIDENT, int THREADS>
 int launch_fps(const FpsArgs& a, cudaStream_t s) {
     int per_sm = 0;
-    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fps<K, RESIDENT>, kFpsThreads, 0));
+    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fps<K, RESIDENT, THREADS>, THREADS, 0));
     if (per_sm < 1) {
         set_error("flood_fps: kernel does not fit on an SM");
         return FLOOD_EINTERNAL;
@@ -183,8 +213,8 @@ int launch_fps(const FpsArgs& a, cudaStream_t s) {
     }
     FpsArgs b = a;
     void* args[] = {&b};
-    FLOOD_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_fps<K, RESIDENT>), dim3(nb),
-                                           dim3(kFpsThreads), args, 0, s));
+    FLOOD_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_fps<K, RESIDENT, THREADS>), dim3(nb),
+                                           dim3(THREADS), args, 0, s));
     note_launch();
     return FLOOD_OK;
 }
@@ -193,9 +223,25 @@ int launch_fps(const FpsArgs& a, cudaStream_t s) {
 template <int K>
 int64_t resident_capacity() {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fps<K, true>, kFpsThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fps<K, true, kResidentThreads>, kResidentThreads,
+                                                      0) != cudaSuccess)
         return 0;
-    return int64_t(per_sm) * device_sm_count() * kFpsThreads * K;
+    return int64_t(per_sm) * device_sm_count() * kResidentThreads * K;
+}
+
+// Launch the register-resident variant that covers n points, else the streaming one.
+int launch_fps_any(FpsArgs a, float* dmin, cudaStream_t s) {
+    const int64_t n = a.n;
+    // Slot tags must start from zero (stale tags could match iteration 1 or 2).
+    FLOOD_CUDA(cudaMemsetAsync(a.slots, 0, sizeof(FpsSlot) * 2 * 4096, s));
+    if (n <= resident_capacity<1>()) return launch_fps<1, true, kResidentThreads>(a, s);
+    if (n <= resident_capacity<2>()) return launch_fps<2, true, kResidentThreads>(a, s);
+    if (n <= resident_capacity<4>()) return launch_fps<4, true, kResidentThreads>(a, s);
+    if (n <= resident_capacity<8>()) return launch_fps<8, true, kResidentThreads>(a, s);
+    // 0xffffffff is a NaN, and fminf(NaN, key) = key: the first update installs the key.
+    FLOOD_CUDA(cudaMemsetAsync(dmin, 0xff, sizeof(float) * n, s));
+    a.dmin = dmin;
+    return launch_fps<1, false, kStreamThreads>(a, s);
 }
 
 }  // namespace
@@ -214,7 +260,7 @@ extern "C" int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, 
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
     Scratch scr(s);
     float *x, *y, *z, *dmin = nullptr;
-    unsigned long long* slots;
+    FpsSlot* slots;
     uint32_t* ctl;  // [0] counter, [1] flags
     int rc;
     if ((rc = scr.alloc(&x, n_points)) || (rc = scr.alloc(&y, n_points)) || (rc = scr.alloc(&z, n_points)) ||
@@ -224,25 +270,9 @@ extern "C" int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, 
     k_aos_to_soa<<<static_cast<unsigned>(ceil_div(n_points, 256)), 256, 0, s>>>(X, n_points, x, y, z, ctl + 1); note_launch();
     FLOOD_CUDA(cudaGetLastError());
 
+    if (n_points > resident_capacity<8>() && (rc = scr.alloc(&dmin, n_points))) return rc;
     FpsArgs a{x, y, z, nullptr, n_points, n_landmarks, start, out_idx, out_key, slots, ctl, ctl + 1};
-    if (n_points <= resident_capacity<1>())
-        rc = launch_fps<1, true>(a, s);
-    else if (n_points <= resident_capacity<2>())
-        rc = launch_fps<2, true>(a, s);
-    else if (n_points <= resident_capacity<4>())
-        rc = launch_fps<4, true>(a, s);
-    else if (n_points <= resident_capacity<8>())
-        rc = launch_fps<8, true>(a, s);
-    else if (n_points <= resident_capacity<16>())
-        rc = launch_fps<16, true>(a, s);
-    else {
-        if ((rc = scr.alloc(&dmin, n_points))) return rc;
-        // 0x7f = +inf bit pattern per byte would not give +inf; fill with a kernel-free memset of 0xff:
-        // 0xffffffff is a NaN, and fminf(NaN, key) = key, so the first update installs the key.
-        FLOOD_CUDA(cudaMemsetAsync(dmin, 0xff, sizeof(float) * n_points, s));
-        a.dmin = dmin;
-        rc = launch_fps<1, false>(a, s);
-    }
+    rc = launch_fps_any(a, dmin, s);
     if (rc) return rc;
     return finish(s, ctl + 1, "flood_fps");
 }
@@ -269,7 +299,7 @@ namespace {
 constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 20;  // 1,048,576 points
 constexpr int kNoAllocMaxBlocks = 4096;
 constexpr size_t kNoAllocCtlBytes = 256;
-constexpr size_t kNoAllocSlotBytes = sizeof(unsigned long long) * 2 * kNoAllocMaxBlocks;
+constexpr size_t kNoAllocSlotBytes = sizeof(FpsSlot) * 2 * kNoAllocMaxBlocks;
 constexpr size_t kNoAllocArrayBytes = sizeof(float) * kNoAllocMaxPoints;
 constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + kNoAllocSlotBytes + 4 * kNoAllocArrayBytes;
 
@@ -322,7 +352,7 @@ extern "C" int flood_fps_noalloc(const float* X, int64_t n_points, int32_t n_lan
     int rc = noalloc_scratch(&base);
     if (rc) return rc;
     uint32_t* ctl = reinterpret_cast<uint32_t*>(base);  // [0] barrier counter, [1] flags
-    unsigned long long* slots = reinterpret_cast<unsigned long long*>(base + kNoAllocCtlBytes);
+    FpsSlot* slots = reinterpret_cast<FpsSlot*>(base + kNoAllocCtlBytes);
     float* arrays = reinterpret_cast<float*>(base + kNoAllocCtlBytes + kNoAllocSlotBytes);
     float* x = arrays;
     float* y = arrays + kNoAllocMaxPoints;
@@ -334,21 +364,7 @@ extern "C" int flood_fps_noalloc(const float* X, int64_t n_points, int32_t n_lan
     note_launch();
     FLOOD_CUDA(cudaGetLastError());
     FpsArgs a{x, y, z, nullptr, n_points, n_landmarks, start, out_idx, out_key, slots, ctl, ctl + 1};
-    if (n_points <= resident_capacity<1>())
-        rc = launch_fps<1, true>(a, s);
-    else if (n_points <= resident_capacity<2>())
-        rc = launch_fps<2, true>(a, s);
-    else if (n_points <= resident_capacity<4>())
-        rc = launch_fps<4, true>(a, s);
-    else if (n_points <= resident_capacity<8>())
-        rc = launch_fps<8, true>(a, s);
-    else if (n_points <= resident_capacity<16>())
-        rc = launch_fps<16, true>(a, s);
-    else {
-        FLOOD_CUDA(cudaMemsetAsync(dmin, 0xff, sizeof(float) * n_points, s));
-        a.dmin = dmin;
-        rc = launch_fps<1, false>(a, s);
-    }
+    rc = launch_fps_any(a, dmin, s);
     if (rc) return rc;
     return finish(s, ctl + 1, "flood_fps_noalloc");
 }
