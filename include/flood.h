@@ -182,7 +182,33 @@ int flood_filtration(const flood_grid* grid, const float* L, int32_t n_landmarks
                      const int64_t n_simplices[4], int32_t m,
                      float* const values[4], int32_t* const src[4], void* stream);
 
-/* Work counters of the calling thread's last successful flood_filtration. */
+/* ------------------------------------------------------------------------
+ * flood_filtration_batch — flood_filtration for several clouds at once.
+ *
+ * Same definition and results as flood_filtration, per job (bit for bit:
+ * every value depends only on its own cloud). The clouds' sample groups share
+ * one persistent flood kernel launch per dimension, so many small clouds keep
+ * the GPU busy together. Jobs may use different grids, complexes and m.
+ *   jobs    host array of n_jobs job descriptions (device pointers inside,
+ *           with the meaning and layout of flood_filtration's arguments)
+ * Errors as flood_filtration; a bad job fails the whole call before any
+ * launch. Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------ */
+typedef struct flood_filtration_job {
+    const flood_grid* grid;
+    const float* L;
+    int32_t n_landmarks;
+    int32_t m;
+    const int32_t* simplices[4];
+    const int32_t* facets[4];
+    int64_t n_simplices[4];
+    float* values[4];
+    int32_t* src[4];
+} flood_filtration_job;
+
+int flood_filtration_batch(const flood_filtration_job* jobs, int32_t n_jobs, void* stream);
+
+/* Work counters of the calling thread's last successful flood_filtration(_batch). */
 typedef struct flood_filtration_stats {
     int64_t simplices[4];        /* simplices per dimension */
     int64_t samples[4];          /* interior samples resolved (NN queries) per dimension */

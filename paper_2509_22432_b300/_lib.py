@@ -45,6 +45,14 @@ class FiltrationStats(C.Structure):
 P4 = C.c_void_p * 4
 I64x4 = C.c_int64 * 4
 
+
+class FiltrationJob(C.Structure):
+    _fields_ = [
+        ("grid", C.c_void_p), ("L", C.c_void_p), ("n_landmarks", C.c_int32), ("m", C.c_int32),
+        ("simplices", C.c_void_p * 4), ("facets", C.c_void_p * 4), ("n_simplices", C.c_int64 * 4),
+        ("values", C.c_void_p * 4), ("src", C.c_void_p * 4),
+    ]
+
 _SIGNATURES = {
     "flood_fps": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "flood_fps_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
@@ -55,6 +63,7 @@ _SIGNATURES = {
     "flood_filtration": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, P4, I64x4, C.c_int32, P4, P4,
                                    C.c_void_p]),
     "flood_last_filtration_stats": (C.c_int, [C.POINTER(FiltrationStats)]),
+    "flood_filtration_batch": (C.c_int, [C.POINTER(FiltrationJob), C.c_int32, C.c_void_p]),
     "flood_filtration_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, C.c_int32, P4, P4,
                                             C.c_void_p, C.c_void_p, C.c_void_p]),
     "flood_last_error": (C.c_char_p, []),

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/flood.h"
 
@@ -43,20 +44,15 @@ int cuda_fail(cudaError_t e, const char* what);
 // Stream-ordered scratch that is returned on scope exit.
 struct Scratch {
     cudaStream_t stream;
-    void* ptrs[32];
-    int n = 0;
+    std::vector<void*> ptrs;
     explicit Scratch(cudaStream_t s) : stream(s) {}
     ~Scratch() {
-        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], stream);
+        for (void* p : ptrs) cudaFreeAsync(p, stream);
     }
     template <class T>
     int alloc(T** out, size_t count) {
         *out = nullptr;
         if (count == 0) count = 1;
-        if (n == 32) {
-            set_error("internal: too many scratch buffers");
-            return FLOOD_EINTERNAL;
-        }
         void* p = nullptr;
         cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), stream);
         if (e != cudaSuccess) {
@@ -65,7 +61,7 @@ struct Scratch {
                       cudaGetErrorString(e));
             return FLOOD_ENOMEM;
         }
-        ptrs[n++] = p;
+        ptrs.push_back(p);
         *out = static_cast<T*>(p);
         return FLOOD_OK;
     }

@@ -50,7 +50,6 @@ constexpr int kThreads = 256;  // flood kernel CTA: 8 independent warps
 constexpr int kWarps = kThreads / 32;
 constexpr int kWTile = 256;    // candidate points per warp tile (4 KB), two per warp
 constexpr int kGroup = 64;     // samples per group (one warp)
-constexpr int64_t kMaxSmemBitmapWords = 8192;  // stage the occupancy bitmap in shared memory up to 32 KB
 constexpr int64_t kMaxBuckets = int64_t(1) << 24;
 
 struct Ctl {
@@ -110,7 +109,6 @@ struct DimArgs {
     SampleRec* recs;
     unsigned long long* best;  // per simplex: (d^2 bits << 32) | ~sample
     const int32_t* n_heavy;    // groups [0, *n_heavy) of the sorted queue go to the CTA kernel
-    int32_t occ_words;         // words of the block-occupancy bitmap staged in shared memory (0: read globally)
     float shell_h;             // cell edge times (1 - 2^-10)
     float shell_slack;         // absolute rounding slack of cell assignment
     Ctl* ctl;
@@ -405,15 +403,6 @@ __device__ __noinline__ int produce_shell_tile(const GridView& g, const Shell& s
 }
 
 // ---------------------------------------------------------------- flood kernel
-// Copy the block-occupancy bitmap into shared memory (when it fits) and point
-// the kernel's grid view at it: the shell walk tests it for every row.
-__device__ __forceinline__ void stage_bitmap(const DimArgs& a, GridView& g, uint32_t* s_occ) {
-    if (a.occ_words > 0) {
-        for (int i = threadIdx.x; i < a.occ_words; i += blockDim.x) s_occ[i] = a.g.occupied[i];
-        g.occupied = s_occ;
-    }
-}
-
 struct WarpCounters {
     unsigned long long pairs = 0ull, shells = 0ull, tiles = 0ull;
 };
@@ -600,16 +589,27 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
 
 constexpr int kNS = 8;  // samples per lane
 
-__global__ void __launch_bounds__(kThreads, 2) k_flood(DimArgs a) {
-    extern __shared__ __align__(128) float4 s_tiles[];  // kWarps x 2 x kWTile, then the bitmap
+// Largest j with off[j] <= item (off has n + 1 non-decreasing entries).
+__device__ __forceinline__ int job_of(const int32_t* off, int n, int32_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Light groups of every cloud of the batch: the queue is the concatenation of
+// each cloud's sorted groups after its heavy prefix (offsets in light_off).
+__global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int n_jobs, const int32_t* light_off,
+                                                       Ctl* ctl, int k) {
+    extern __shared__ __align__(128) float4 s_tiles[];  // kWarps x 2 x kWTile
     __shared__ __align__(8) uint64_t s_bar[kWarps][2];
     __shared__ float s_ub[kWarps][2][kGroup];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4* tiles = s_tiles + warp * 2 * kWTile;
     uint64_t* bar = s_bar[warp];
-    GridView gv = a.g;
-    stage_bitmap(a, gv, reinterpret_cast<uint32_t*>(s_tiles + kWarps * 2 * kWTile));
-    __syncthreads();
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -619,14 +619,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(DimArgs a) {
     uint32_t phases = 0u;
     bool abort = false;
     WarpCounters cnt;
-    const int32_t total = a.group_off[a.n_coarse];
-    const int32_t first = *a.n_heavy;
+    const int32_t total = light_off[n_jobs];
     for (;;) {
         int item = 0;
-        if (lane == 0) item = first + static_cast<int>(atomicAdd(&a.ctl->head[a.k], 1u));
+        if (lane == 0) item = static_cast<int>(atomicAdd(&ctl->head[k], 1u));
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total || abort) break;
-        const int2 gb = a.groups[item];
+        const int j = job_of(light_off, n_jobs, item);
+        const DimArgs& a = jobs[j];
+        const GridView gv = a.g;
+        const int2 gb = a.groups[*a.n_heavy + (item - light_off[j])];
         const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
         const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
         // coarse cube corner: the origin of the pair arithmetic for this group
@@ -640,9 +642,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(DimArgs a) {
                            abort, cnt, lane);
     }
     if (lane == 0) {
-        atomicAdd(&a.ctl->pairs[a.k], cnt.pairs);
-        atomicAdd(&a.ctl->shells[a.k], cnt.shells);
-        atomicAdd(&a.ctl->tiles[a.k], cnt.tiles);
+        atomicAdd(&ctl->pairs[k], cnt.pairs);
+        atomicAdd(&ctl->shells[k], cnt.shells);
+        atomicAdd(&ctl->tiles[k], cnt.tiles);
     }
 }
 
@@ -670,8 +672,9 @@ __device__ __forceinline__ void heavy_tile(const float4* buf, int n, int gs, int
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(DimArgs a) {
-    extern __shared__ __align__(128) float4 s_tiles[];  // 2 x kHeavyTile, then the bitmap
+__global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs, int n_jobs,
+                                                             const int32_t* heavy_off, Ctl* ctl, int k) {
+    extern __shared__ __align__(128) float4 s_tiles[];  // 2 x kHeavyTile
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_min[kGroup];
     __shared__ int s_live[kGroup];
@@ -686,18 +689,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(DimArgs a) {
         fence_mbar_init();
         s_abort = 0;
     }
-    GridView g = a.g;
-    stage_bitmap(a, g, reinterpret_cast<uint32_t*>(s_tiles + 2 * kHeavyTile));
     __syncthreads();
     uint32_t phases = 0u;
     unsigned long long pairs = 0ull, n_shells = 0ull, n_tiles = 0ull;
-    const int32_t n_heavy = *a.n_heavy;
+    const int32_t n_heavy = heavy_off[n_jobs];
     for (;;) {
-        if (tid == 0) s_item = static_cast<int>(atomicAdd(&a.ctl->heavy_head[a.k], 1u));
+        if (tid == 0) s_item = static_cast<int>(atomicAdd(&ctl->heavy_head[k], 1u));
         __syncthreads();
         const int item = s_item;
         if (item >= n_heavy || s_abort) break;
-        const int2 gb = a.groups[item];
+        const int jb = job_of(heavy_off, n_jobs, item);
+        const DimArgs& a = jobs[jb];
+        const GridView g = a.g;
+        const int2 gb = a.groups[item - heavy_off[jb]];
         const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
         const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
         const int n_valid = s_end - s_begin;
@@ -890,10 +894,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(DimArgs a) {
         __syncthreads();
     }
     if (tid == 0) {
-        atomicAdd(&a.ctl->pairs[a.k], pairs);
-        atomicAdd(&a.ctl->shells[a.k], n_shells);
-        atomicAdd(&a.ctl->tiles[a.k], n_tiles);
+        atomicAdd(&ctl->pairs[k], pairs);
+        atomicAdd(&ctl->shells[k], n_shells);
+        atomicAdd(&ctl->tiles[k], n_tiles);
     }
+}
+
+// Prefix offsets of the heavy and light queues over the clouds of a batch.
+__global__ void k_queue_offsets(const DimArgs* jobs, int n_jobs, int32_t* heavy_off, int32_t* light_off) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int32_t h = 0, l = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        heavy_off[j] = h;
+        light_off[j] = l;
+        const int32_t nh = *jobs[j].n_heavy;
+        const int32_t ng = jobs[j].group_off[jobs[j].n_coarse];
+        h += nh;
+        l += ng - nh;
+    }
+    heavy_off[n_jobs] = h;
+    light_off[n_jobs] = l;
 }
 
 // Own maximum per simplex from the packed atomic maxima (0 when no sample can
@@ -936,34 +956,39 @@ __global__ void k_facemax(int k, int64_t n, const int32_t* simplices, const int3
 }
 
 // ---------------------------------------------------------------- host side
-int launch_flood_heavy(const DimArgs& a, cudaStream_t s) {
-    const size_t smem = size_t(2) * kHeavyTile * sizeof(float4) + sizeof(uint32_t) * a.occ_words;
+int launch_flood_heavy(const DimArgs* jobs, int n_jobs, const int32_t* heavy_off, Ctl* ctl, int k,
+                       cudaStream_t s) {
+    const size_t smem = size_t(2) * kHeavyTile * sizeof(float4);
     FLOOD_CUDA(cudaFuncSetAttribute(k_flood_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
     FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood_heavy, kThreads, smem));
     per_sm = std::max(per_sm, 1);
-    k_flood_heavy<<<static_cast<unsigned>(device_sm_count() * per_sm), kThreads, smem, s>>>(a);
+    k_flood_heavy<<<static_cast<unsigned>(device_sm_count() * per_sm), kThreads, smem, s>>>(jobs, n_jobs, heavy_off,
+                                                                                          ctl, k);
     note_launch();
     FLOOD_CUDA(cudaGetLastError());
     return FLOOD_OK;
 }
 
-int launch_flood(const DimArgs& a, cudaStream_t s) {
-    const size_t smem = size_t(kWarps) * 2 * kWTile * sizeof(float4) + sizeof(uint32_t) * a.occ_words;
+int launch_flood(const DimArgs* jobs, int n_jobs, const int32_t* light_off, Ctl* ctl, int k, cudaStream_t s) {
+    const size_t smem = size_t(kWarps) * 2 * kWTile * sizeof(float4);
     FLOOD_CUDA(cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
     FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood, kThreads, smem));
     per_sm = std::max(per_sm, 1);
     const int64_t grid = int64_t(device_sm_count()) * per_sm;
-    k_flood<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(a);
+    k_flood<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(jobs, n_jobs, light_off, ctl, k);
     note_launch();
     FLOOD_CUDA(cudaGetLastError());
     return FLOOD_OK;
 }
 
-// Sample lattice: coarse edge B = a power of two near extent/40, anchored at
-// the grid origin; it depends only on X's bounding box.
-Lattice make_lattice(const flood_grid* grid) {
+// Sample lattice: coarse edge B = a power of two near extent / c, anchored at
+// the grid origin, with c = cbrt(samples / 64) clamped to [4, 40] so that a
+// coarse cube holds enough samples for full groups. It depends only on X's
+// bounding box and the size of the complex, never on the cell size or on
+// how clouds are batched.
+Lattice make_lattice(const flood_grid* grid, int64_t n_samples) {
     Lattice L{};
     L.ox = grid->origin[0];
     L.oy = grid->origin[1];
@@ -973,7 +998,8 @@ Lattice make_lattice(const flood_grid* grid) {
         ext[c] = grid->bbox_hi[c] - grid->bbox_lo[c];
         emax = std::max(emax, ext[c]);
     }
-    float B = emax > 0.0f ? std::exp2(std::round(std::log2(emax / 40.0f))) : 1.0f;
+    const float div = std::min(40.0f, std::max(4.0f, std::cbrt(static_cast<float>(n_samples) / 64.0f)));
+    float B = emax > 0.0f ? std::exp2(std::round(std::log2(emax / div))) : 1.0f;
     for (;;) {
         L.bx = static_cast<int>(std::floor(ext[0] / B)) + 1;
         L.by = static_cast<int>(std::floor(ext[1] / B)) + 1;
@@ -1042,182 +1068,242 @@ extern "C" int flood_last_filtration_stats(flood_filtration_stats* out) {
     return FLOOD_OK;
 }
 
-extern "C" int flood_filtration(const flood_grid* grid, const float* L, int32_t n_landmarks,
-                                const int32_t* const simplices[4], const int32_t* const facets[4],
-                                const int64_t n_simplices[4], int32_t m, float* const values[4],
-                                int32_t* const src[4], void* stream_) {
-    if (!grid || !L || n_landmarks < 1 || !simplices || !n_simplices || !values || m < 1 || m > FLOOD_MAX_M) {
-        set_error("flood_filtration: need grid, L, simplices, n_simplices, values and 1 <= m <= %d", FLOOD_MAX_M);
+namespace flood {
+namespace {
+
+// Per-cloud state of one batched filtration call.
+struct JobState {
+    flood_filtration_job in;
+    float* val[4];
+    int32_t* src[4];
+    int64_t nk[4];
+    int I[4];
+    Lattice lat;
+    int64_t n_coarse, n_buckets, max_samples, max_n, max_groups;
+    std::vector<uint8_t> tables[4];
+    uint8_t* comp[4];
+    int32_t *bcount, *bstart, *bfill, *goff, *g_arg, *cls;
+    int2 *groups, *groups_sorted;
+    SampleRec* recs;
+    unsigned long long* best;
+    float* g_own;
+    float shell_slack;
+};
+
+int check_job(const flood_filtration_job& j, int idx) {
+    if (!j.grid || !j.L || j.n_landmarks < 1 || j.m < 1 || j.m > FLOOD_MAX_M) {
+        set_error("flood_filtration: job %d needs grid, L, n_landmarks >= 1 and 1 <= m <= %d", idx, FLOOD_MAX_M);
         return FLOOD_EINVAL;
     }
-    if (n_simplices[0] != 0 && n_simplices[0] != n_landmarks) {
-        set_error("flood_filtration: n_simplices[0] must be 0 or n_landmarks");
+    if (j.n_simplices[0] != 0 && j.n_simplices[0] != j.n_landmarks) {
+        set_error("flood_filtration: job %d: n_simplices[0] must be 0 or n_landmarks", idx);
         return FLOOD_EINVAL;
     }
     for (int k = 1; k <= 3; ++k) {
-        if (n_simplices[k] < 0 || n_simplices[k] >= (int64_t(1) << 28)) {
-            set_error("flood_filtration: n_simplices[%d] out of range", k);
+        if (j.n_simplices[k] < 0 || j.n_simplices[k] >= (int64_t(1) << 28)) {
+            set_error("flood_filtration: job %d: n_simplices[%d] out of range", idx, k);
             return FLOOD_EINVAL;
         }
-        if (n_simplices[k] > 0 && (!simplices[k] || (k >= 2 && (!facets || !facets[k])))) {
-            set_error("flood_filtration: simplices[%d] (and facets for k >= 2) must be given", k);
+        if (j.n_simplices[k] > 0 && (!j.simplices[k] || (k >= 2 && !j.facets[k]))) {
+            set_error("flood_filtration: job %d: simplices[%d] (and facets for k >= 2) must be given", idx, k);
             return FLOOD_EINVAL;
         }
-        if (n_simplices[k] > 0 && k >= 2 && n_simplices[k - 1] == 0) {
-            set_error("flood_filtration: dimension %d present without its facets (dimension %d)", k, k - 1);
+        if (j.n_simplices[k] > 0 && k >= 2 && j.n_simplices[k - 1] == 0) {
+            set_error("flood_filtration: job %d: dimension %d present without dimension %d", idx, k, k - 1);
             return FLOOD_EINVAL;
         }
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    return FLOOD_OK;
+}
+
+int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s) {
+    if (n_jobs < 0 || (n_jobs > 0 && !in)) {
+        set_error("flood_filtration_batch: bad job array");
+        return FLOOD_EINVAL;
+    }
+    for (int i = 0; i < n_jobs; ++i)
+        if (int rc = check_job(in[i], i)) return rc;
     Scratch scr(s);
-    GridView gv = view_of(grid);
-    const Lattice lat = make_lattice(grid);
-    const int64_t n_coarse = int64_t(lat.bx) * lat.by * lat.bz;
-    const int64_t n_buckets = n_coarse * kFine;
     Ctl* ctl;
     int rc;
     if ((rc = scr.alloc(&ctl, 1))) return rc;
     FLOOD_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
-
-    float* val[4];
-    int32_t* sr[4];
-    const int64_t nk[4] = {n_landmarks, n_simplices[1], n_simplices[2], n_simplices[3]};
-    for (int k = 0; k <= 3; ++k) {
-        val[k] = values[k];
-        sr[k] = src ? src[k] : nullptr;
-        if (!val[k] && (rc = scr.alloc(&val[k], nk[k]))) return rc;
-        if (!sr[k] && (rc = scr.alloc(&sr[k], 2 * nk[k]))) return rc;
-    }
-    k_vertices<<<static_cast<unsigned>(ceil_div(n_landmarks, 256)), 256, 0, s>>>(L, n_landmarks, gv, val[0], sr[0],
+    std::vector<JobState> js(n_jobs);
+    for (int i = 0; i < n_jobs; ++i) {
+        JobState& J = js[i];
+        J.in = in[i];
+        const flood_grid* grid = J.in.grid;
+        J.nk[0] = J.in.n_landmarks;
+        for (int k = 1; k <= 3; ++k) J.nk[k] = J.in.n_simplices[k];
+        for (int k = 0; k <= 3; ++k) {
+            J.val[k] = J.in.values[k];
+            J.src[k] = J.in.src[k];
+            if (!J.val[k] && (rc = scr.alloc(&J.val[k], J.nk[k]))) return rc;
+            if (!J.src[k] && (rc = scr.alloc(&J.src[k], 2 * J.nk[k]))) return rc;
+        }
+        k_vertices<<<static_cast<unsigned>(ceil_div(J.nk[0], 256)), 256, 0, s>>>(J.in.L, J.in.n_landmarks,
+                                                                                 view_of(grid), J.val[0], J.src[0],
                                                                                  &ctl->flags);
-    note_launch();
-    FLOOD_CUDA(cudaGetLastError());
-
-    // per-dimension scratch, sized for the largest dimension and reused
-    int64_t max_samples = 1, max_n = 1;
-    std::vector<uint8_t> tables[4];
-    int I[4] = {0, 0, 0, 0};
-    for (int k = 1; k <= 3; ++k) {
-        if (nk[k] == 0) continue;
-        tables[k] = interior_table(m, k);
-        I[k] = static_cast<int>(tables[k].size() / (k + 1));
-        max_samples = std::max(max_samples, nk[k] * I[k]);
-        max_n = std::max(max_n, nk[k]);
+        note_launch();
+        FLOOD_CUDA(cudaGetLastError());
+        J.max_samples = 1;
+        J.max_n = 1;
+        int64_t total_samples = 0;
+        for (int k = 1; k <= 3; ++k) {
+            J.I[k] = 0;
+            J.comp[k] = nullptr;
+            if (J.nk[k] == 0) continue;
+            J.tables[k] = interior_table(J.in.m, k);
+            J.I[k] = static_cast<int>(J.tables[k].size() / (k + 1));
+            J.max_samples = std::max(J.max_samples, J.nk[k] * J.I[k]);
+            J.max_n = std::max(J.max_n, J.nk[k]);
+            total_samples += J.nk[k] * J.I[k];
+            if (J.I[k] > 0) {
+                if ((rc = scr.alloc(&J.comp[k], J.tables[k].size()))) return rc;
+                FLOOD_CUDA(cudaMemcpyAsync(J.comp[k], J.tables[k].data(), J.tables[k].size(), cudaMemcpyHostToDevice,
+                                           s));
+            }
+        }
+        J.lat = make_lattice(grid, total_samples);
+        J.n_coarse = int64_t(J.lat.bx) * J.lat.by * J.lat.bz;
+        J.n_buckets = J.n_coarse * kFine;
+        J.max_groups = J.max_samples / kGroup + J.n_coarse + 1;
+        if ((rc = scr.alloc(&J.bcount, J.n_buckets)) || (rc = scr.alloc(&J.bstart, J.n_buckets + 1)) ||
+            (rc = scr.alloc(&J.bfill, J.n_buckets)) || (rc = scr.alloc(&J.goff, J.n_coarse + 1)) ||
+            (rc = scr.alloc(&J.groups, J.max_groups)) || (rc = scr.alloc(&J.groups_sorted, J.max_groups)) ||
+            (rc = scr.alloc(&J.cls, 2 * (kClasses + 1))) || (rc = scr.alloc(&J.recs, J.max_samples)) ||
+            (rc = scr.alloc(&J.best, J.max_n)) || (rc = scr.alloc(&J.g_own, J.max_n)) ||
+            (rc = scr.alloc(&J.g_arg, J.max_n)))
+            return rc;
+        const float emax = std::max(grid->bbox_hi[0] - grid->bbox_lo[0],
+                                    std::max(grid->bbox_hi[1] - grid->bbox_lo[1], grid->bbox_hi[2] - grid->bbox_lo[2]));
+        const float amax =
+            std::max(std::fabs(grid->origin[0]), std::max(std::fabs(grid->origin[1]), std::fabs(grid->origin[2])));
+        J.shell_slack = (amax + emax) * (1.0f / 262144.0f);
     }
-    int32_t *bcount, *bstart, *bfill, *goff, *g_arg;
-    int2 *groups, *groups_sorted;
-    int32_t* cls;
-    SampleRec* recs;
-    unsigned long long* best;
-    float* g_own;
-    const int64_t max_groups = max_samples / kGroup + n_coarse + 1;
-    if ((rc = scr.alloc(&bcount, n_buckets)) || (rc = scr.alloc(&bstart, n_buckets + 1)) ||
-        (rc = scr.alloc(&bfill, n_buckets)) || (rc = scr.alloc(&goff, n_coarse + 1)) ||
-        (rc = scr.alloc(&groups, max_groups)) || (rc = scr.alloc(&groups_sorted, max_groups)) ||
-        (rc = scr.alloc(&cls, 2 * (kClasses + 1))) || (rc = scr.alloc(&recs, max_samples)) ||
-        (rc = scr.alloc(&best, max_n)) || (rc = scr.alloc(&g_own, max_n)) || (rc = scr.alloc(&g_arg, max_n)))
+    DimArgs* d_jobs;
+    int32_t *d_off, *d_counts;
+    if ((rc = scr.alloc(&d_jobs, std::max(n_jobs, 1))) || (rc = scr.alloc(&d_off, 2 * (n_jobs + 1))) ||
+        (rc = scr.alloc(&d_counts, 4 * std::max(n_jobs, 1))))
         return rc;
-
-    const float emax = std::max(grid->bbox_hi[0] - grid->bbox_lo[0],
-                                std::max(grid->bbox_hi[1] - grid->bbox_lo[1], grid->bbox_hi[2] - grid->bbox_lo[2]));
-    const float amax =
-        std::max(std::fabs(grid->origin[0]), std::max(std::fabs(grid->origin[1]), std::fabs(grid->origin[2])));
+    FLOOD_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * 4 * std::max(n_jobs, 1), s));
+    std::vector<DimArgs> h_jobs;
+    h_jobs.reserve(n_jobs);
     EventPairs ev;
-    int32_t h_items[4] = {0, 0, 0, 0};
+    int64_t h_items[4] = {0, 0, 0, 0};
+    std::vector<int32_t> items_per_job(static_cast<size_t>(n_jobs) * 4, 0);
     for (int k = 1; k <= 3; ++k) {
-        const int64_t n = nk[k];
-        if (n == 0) continue;
-        FLOOD_CUDA(cudaMemsetAsync(best, 0, sizeof(unsigned long long) * n, s));
-        if (I[k] > 0) {
-            uint8_t* comp;
-            if ((rc = scr.alloc(&comp, tables[k].size()))) return rc;
-            FLOOD_CUDA(cudaMemcpyAsync(comp, tables[k].data(), tables[k].size(), cudaMemcpyHostToDevice, s));
+        h_jobs.clear();
+        for (int i = 0; i < n_jobs; ++i) {
+            JobState& J = js[i];
+            const int64_t n = J.nk[k];
+            if (n == 0) continue;
+            FLOOD_CUDA(cudaMemsetAsync(J.best, 0, sizeof(unsigned long long) * n, s));
+            if (J.I[k] == 0) continue;
+            const flood_grid* grid = J.in.grid;
             DimArgs a{};
             a.k = k;
-            a.I = I[k];
-            a.m = static_cast<float>(m);
+            a.I = J.I[k];
+            a.m = static_cast<float>(J.in.m);
             a.n = n;
-            a.simplices = simplices[k];
-            a.facets = k >= 2 ? facets[k] : nullptr;
-            a.val_lower = val[k - 1];
-            a.n_lower = nk[k - 1];
-            a.comp = comp;
-            a.L = L;
-            a.n_L = n_landmarks;
-            a.g = gv;
-            a.lat = lat;
-            a.n_buckets = n_buckets;
-            a.n_coarse = n_coarse;
-            a.bucket_count = bcount;
-            a.bucket_start = bstart;
-            a.bucket_fill = bfill;
-            a.group_off = goff;
-            a.groups = groups;
-            a.recs = recs;
-            a.best = best;
-            {
-                const int64_t blocks = int64_t(grid->bdims[0]) * grid->bdims[1] * grid->bdims[2];
-                const int64_t words = (blocks + 31) / 32;
-                a.occ_words = words <= kMaxSmemBitmapWords ? static_cast<int32_t>(words) : 0;
-            }
+            a.simplices = J.in.simplices[k];
+            a.facets = k >= 2 ? J.in.facets[k] : nullptr;
+            a.val_lower = J.val[k - 1];
+            a.n_lower = J.nk[k - 1];
+            a.comp = J.comp[k];
+            a.L = J.in.L;
+            a.n_L = J.in.n_landmarks;
+            a.g = view_of(grid);
+            a.lat = J.lat;
+            a.n_buckets = J.n_buckets;
+            a.n_coarse = J.n_coarse;
+            a.bucket_count = J.bcount;
+            a.bucket_start = J.bstart;
+            a.bucket_fill = J.bfill;
+            a.group_off = J.goff;
+            a.groups = J.groups;
+            a.recs = J.recs;
+            a.best = J.best;
             a.shell_h = grid->cell_size * (1.0f - 1.0f / 1024.0f);
-            a.shell_slack = (amax + emax) * (1.0f / 262144.0f);
+            a.shell_slack = J.shell_slack;
             a.ctl = ctl;
-            FLOOD_CUDA(cudaMemsetAsync(bcount, 0, sizeof(int32_t) * n_buckets, s));
-            FLOOD_CUDA(cudaMemsetAsync(bfill, 0, sizeof(int32_t) * n_buckets, s));
+            FLOOD_CUDA(cudaMemsetAsync(J.bcount, 0, sizeof(int32_t) * J.n_buckets, s));
+            FLOOD_CUDA(cudaMemsetAsync(J.bfill, 0, sizeof(int32_t) * J.n_buckets, s));
             const unsigned wb = static_cast<unsigned>(ceil_div(n * 32, 256));
             k_samples<false><<<wb, 256, 0, s>>>(a);
             note_launch();
-            if ((rc = exclusive_scan(bcount, bstart, n_buckets, s, scr))) return rc;
+            if ((rc = exclusive_scan(J.bcount, J.bstart, J.n_buckets, s, scr))) return rc;
             k_samples<true><<<wb, 256, 0, s>>>(a);
             note_launch();
-            const unsigned bb = static_cast<unsigned>(ceil_div(n_coarse, 256));
-            k_group_counts<<<bb, 256, 0, s>>>(bstart, n_coarse, bcount);
+            const unsigned bb = static_cast<unsigned>(ceil_div(J.n_coarse, 256));
+            k_group_counts<<<bb, 256, 0, s>>>(J.bstart, J.n_coarse, J.bcount);
             note_launch();
-            if ((rc = exclusive_scan(bcount, goff, n_coarse, s, scr))) return rc;
-            k_group_fill<<<bb, 256, 0, s>>>(goff, n_coarse, groups);
+            if ((rc = exclusive_scan(J.bcount, J.goff, J.n_coarse, s, scr))) return rc;
+            k_group_fill<<<bb, 256, 0, s>>>(J.goff, J.n_coarse, J.groups);
+            note_launch();
+            // longest-first order of this cloud's groups; the count stays on the device
+            const int32_t* n_groups = J.goff + J.n_coarse;
+            FLOOD_CUDA(cudaMemsetAsync(J.cls, 0, sizeof(int32_t) * 2 * (kClasses + 1), s));
+            const unsigned gbk = static_cast<unsigned>(ceil_div(J.max_groups, 256));
+            k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, J.cls);
+            note_launch();
+            if ((rc = exclusive_scan(J.cls, J.cls + kClasses + 1, kClasses, s, scr))) return rc;
+            FLOOD_CUDA(cudaMemsetAsync(J.cls, 0, sizeof(int32_t) * kClasses, s));
+            k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, J.cls + kClasses + 1, J.cls, J.groups_sorted);
             note_launch();
             FLOOD_CUDA(cudaGetLastError());
-            // longest-first order; the group count stays on the device
-            {
-                const int32_t* n_groups = goff + n_coarse;
-                FLOOD_CUDA(cudaMemsetAsync(cls, 0, sizeof(int32_t) * 2 * (kClasses + 1), s));
-                const unsigned gbk = static_cast<unsigned>(ceil_div(max_groups, 256));
-                k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, cls);
-                note_launch();
-                if ((rc = exclusive_scan(cls, cls + kClasses + 1, kClasses, s, scr))) return rc;
-                FLOOD_CUDA(cudaMemsetAsync(cls, 0, sizeof(int32_t) * kClasses, s));
-                k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, cls + kClasses + 1, cls, groups_sorted);
-                note_launch();
-                FLOOD_CUDA(cudaGetLastError());
-                a.groups = groups_sorted;
-            }
-            // heavy groups: shell bound >= kHeavyShells, i.e. classes [0, kClasses - kHeavyShells]
-            a.n_heavy = cls + kClasses + 1 + (kClasses - kHeavyShells);
-            FLOOD_CUDA(cudaMemcpyAsync(&h_items[k], goff + n_coarse, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            a.groups = J.groups_sorted;
+            // heavy groups: shell bound >= kHeavyShells, i.e. classes [0, kClasses - kHeavyShells)
+            a.n_heavy = J.cls + kClasses + 1 + (kClasses - kHeavyShells);
+            FLOOD_CUDA(cudaMemcpyAsync(d_counts + i * 4 + k, n_groups, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            h_jobs.push_back(a);
+        }
+        const int nj = static_cast<int>(h_jobs.size());
+        if (nj > 0) {
+            DimArgs* dj = d_jobs;
+            // the per-dimension job table lives in its own buffer (earlier launches may still read the old one)
+            if (k > 1 && (rc = scr.alloc(&dj, nj))) return rc;
+            FLOOD_CUDA(cudaMemcpyAsync(dj, h_jobs.data(), sizeof(DimArgs) * nj, cudaMemcpyHostToDevice, s));
+            int32_t* heavy_off = d_off;
+            int32_t* light_off = d_off + (n_jobs + 1);
+            if (k > 1 && (rc = scr.alloc(&heavy_off, 2 * (nj + 1)))) return rc;
+            if (k > 1) light_off = heavy_off + (nj + 1);
+            k_queue_offsets<<<1, 32, 0, s>>>(dj, nj, heavy_off, light_off);
+            note_launch();
             if (cudaEventCreate(&ev[k][0]) == cudaSuccess && cudaEventCreate(&ev[k][1]) == cudaSuccess)
                 cudaEventRecord(ev[k][0], s);
-            if ((rc = launch_flood_heavy(a, s))) return rc;
-            if ((rc = launch_flood(a, s))) return rc;
+            if ((rc = launch_flood_heavy(dj, nj, heavy_off, ctl, k, s))) return rc;
+            if ((rc = launch_flood(dj, nj, light_off, ctl, k, s))) return rc;
             if (ev[k][1]) cudaEventRecord(ev[k][1], s);
         }
-        k_finalize<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(best, n, g_own, g_arg);
-        note_launch();
-        k_facemax<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(
-            k, n, simplices[k], facets ? facets[k] : nullptr, nk[k - 1], g_own, g_arg, val[k - 1], sr[k - 1], val[k],
-            sr[k], &ctl->flags);
-        note_launch();
-        FLOOD_CUDA(cudaGetLastError());
+        for (int i = 0; i < n_jobs; ++i) {
+            JobState& J = js[i];
+            const int64_t n = J.nk[k];
+            if (n == 0) continue;
+            k_finalize<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(J.best, n, J.g_own, J.g_arg);
+            note_launch();
+            k_facemax<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(
+                k, n, J.in.simplices[k], J.in.facets[k], J.nk[k - 1], J.g_own, J.g_arg, J.val[k - 1], J.src[k - 1],
+                J.val[k], J.src[k], &ctl->flags);
+            note_launch();
+            FLOOD_CUDA(cudaGetLastError());
+        }
     }
     Ctl h_ctl{};
     FLOOD_CUDA(cudaMemcpyAsync(&h_ctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    if (n_jobs > 0)
+        FLOOD_CUDA(cudaMemcpyAsync(items_per_job.data(), d_counts, sizeof(int32_t) * 4 * n_jobs,
+                                   cudaMemcpyDeviceToHost, s));
     FLOOD_CUDA(cudaStreamSynchronize(s));
     rc = status_from_flags(h_ctl.flags, "flood_filtration");
     if (rc) return rc;
     flood_filtration_stats st{};
     for (int k = 0; k <= 3; ++k) {
-        st.simplices[k] = nk[k];
-        st.samples[k] = k == 0 ? 0 : nk[k] * I[k];
+        for (int i = 0; i < n_jobs; ++i) {
+            st.simplices[k] += js[i].nk[k];
+            st.samples[k] += k == 0 ? 0 : js[i].nk[k] * js[i].I[k];
+            h_items[k] += items_per_job[i * 4 + k];
+        }
         st.pairs[k] = static_cast<int64_t>(h_ctl.pairs[k]);
         st.work_items[k] = h_items[k];
         st.active_samples[k] = static_cast<int64_t>(h_ctl.active[k]);
@@ -1228,4 +1314,34 @@ extern "C" int flood_filtration(const flood_grid* grid, const float* L, int32_t 
     }
     g_stats = st;
     return FLOOD_OK;
+}
+
+}  // namespace
+}  // namespace flood
+
+extern "C" int flood_filtration_batch(const flood_filtration_job* jobs, int32_t n_jobs, void* stream) {
+    return filtration_batch(jobs, n_jobs, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int flood_filtration(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                                const int32_t* const simplices[4], const int32_t* const facets[4],
+                                const int64_t n_simplices[4], int32_t m, float* const values[4],
+                                int32_t* const src[4], void* stream) {
+    if (!simplices || !n_simplices || !values) {
+        set_error("flood_filtration: simplices, n_simplices and values must be given");
+        return FLOOD_EINVAL;
+    }
+    flood_filtration_job j{};
+    j.grid = grid;
+    j.L = L;
+    j.n_landmarks = n_landmarks;
+    j.m = m;
+    for (int k = 0; k < 4; ++k) {
+        j.simplices[k] = simplices[k];
+        j.facets[k] = facets ? facets[k] : nullptr;
+        j.n_simplices[k] = n_simplices[k];
+        j.values[k] = values[k];
+        j.src[k] = src ? src[k] : nullptr;
+    }
+    return filtration_batch(&j, 1, static_cast<cudaStream_t>(stream));
 }

@@ -16,7 +16,8 @@ import torch
 from . import _lib
 from ._lib import FloodError, P4, I64x4
 
-__all__ = ["fps", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration", "filtration_backward",
+__all__ = ["fps", "fps_noalloc", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
+           "filtration_batch", "filtration_backward",
            "last_filtration_stats", "FloodFunction", "flood_values"]
 
 
@@ -148,6 +149,41 @@ def filtration(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, want_src:
                                          _stream_ptr(L.device))
     _lib.check(st, "flood_filtration")
     return vals, srcs
+
+
+def filtration_batch(jobs, want_src: bool = False):
+    """Flood values of several clouds in one batched call.
+
+    jobs: list of (grid, L, DeviceComplex, m). Returns a list of (values, src).
+    Each cloud's results equal those of filtration() on it alone, bit for bit.
+    """
+    if not jobs:
+        return []
+    dev = jobs[0][1].device
+    arr = (_lib.FiltrationJob * len(jobs))()
+    outs, keep = [], []
+    for i, (grid, L, cx, m) in enumerate(jobs):
+        L = _points(L, "L")
+        keep.append(L)
+        s, f, n = cx.arrays()
+        vals = [torch.empty(c, dtype=torch.float32, device=dev) for c in cx.counts]
+        srcs = [torch.empty((c, 2), dtype=torch.int32, device=dev) for c in cx.counts] if want_src else None
+        j = arr[i]
+        j.grid = grid.handle
+        j.L = L.data_ptr()
+        j.n_landmarks = L.shape[0]
+        j.m = int(m)
+        for k in range(4):
+            j.simplices[k] = s[k]
+            j.facets[k] = f[k]
+            j.n_simplices[k] = n[k]
+            j.values[k] = vals[k].data_ptr() if k < len(vals) and vals[k].numel() else 0
+            j.src[k] = srcs[k].data_ptr() if want_src and k < len(srcs) and srcs[k].numel() else 0
+        outs.append((vals, srcs))
+    with torch.cuda.device(dev):
+        st = _lib.get().flood_filtration_batch(arr, len(jobs), _stream_ptr(dev))
+    _lib.check(st, "flood_filtration_batch")
+    return outs
 
 
 def last_filtration_stats() -> dict:

@@ -183,6 +183,34 @@ def test_values_bitwise_invariant_to_cell_size():
             assert np.array_equal(s[k], runs[0][1][k])
 
 
+def test_batched_filtration_equals_each_cloud_alone():
+    """Clouds sharing one batched flood launch get exactly their alone results."""
+    ops = _ops()
+    dev = _dev()
+    jobs, alone = [], []
+    for i, (gen, n, n_l, m) in enumerate([(data.torus_cloud, 30_000, 60, 8), (data.sphere_cloud, 5_000, 40, 6),
+                                          (data.shape_mix_cloud, 50_000, 120, 8), (data.sphere_cloud, 800, 12, 5)]):
+        X = gen(n, seed=100 + i)
+        idx, _ = oracle.fps(X, n_l, 0)
+        L = X[idx]
+        cx = delaunay_complex(L)
+        Xd = torch.from_numpy(X).to(dev)
+        grid = ops.build_grid(Xd)
+        dcx = ops.to_device(cx, dev)
+        Ld = torch.from_numpy(L).to(dev)
+        v, s = ops.filtration(grid, Ld, dcx, m)
+        alone.append(([a.cpu().numpy() for a in v], [b.cpu().numpy() for b in s]))
+        jobs.append((grid, Ld, dcx, m))
+        if i == 0:
+            ref = oracle.flood_values(X, L, cx.simplices, m, method="kdtree")
+            assert_close(alone[0][0], ref.values, X, "batch member")
+    outs = ops.filtration_batch(jobs, want_src=True)
+    for (v, s), (va, sa) in zip(outs, alone):
+        for k in range(4):
+            assert np.array_equal(v[k].cpu().numpy().view(np.uint32), va[k].view(np.uint32))
+            assert np.array_equal(s[k].cpu().numpy(), sa[k])
+
+
 def test_src_points_at_attaining_sample():
     X = data.torus_cloud(8000, seed=5)
     m = 6
