@@ -247,6 +247,85 @@ int flood_filtration_backward(const flood_grid* grid, const float* L, int32_t n_
                               const float* const grad_values[4],
                               float* grad_X, float* grad_L, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of many point clouds on one GPU.
+ *
+ * Not in the paper, which runs one cloud at a time; this is the request
+ * loop around the same computation. A submitted cloud is admitted when an
+ * in-flight slot is free and its estimated device memory fits the budget
+ * (FIFO); it then runs FPS and the grid build on its own stream, is
+ * triangulated on the host by the caller's callback, and joins the next
+ * batched filtration (flood_filtration_batch) with every other cloud that is
+ * ready at that moment. Requests arriving while others run are admitted as
+ * slots and memory free up, and their work overlaps on the device. Each
+ * result equals what the one-cloud path computes on that cloud, bit for bit.
+ * ------------------------------------------------------------------------ */
+typedef struct flood_server flood_server;
+
+/* Simplex lists returned by the triangulation callback (host memory, layout
+ * of flood_filtration's simplices/facets). The arrays must stay valid until
+ * the library calls release(user, owner), which it does after copying them. */
+typedef struct flood_host_complex {
+    int64_t n_simplices[4];
+    const int32_t* simplices[4];
+    const int32_t* facets[4];
+    void* owner;
+} flood_host_complex;
+
+/* Triangulate the landmarks (host, (n, 3) float32). Returns 0 on success;
+ * any other value fails that request only. Called from library threads. */
+typedef int (*flood_triangulate_fn)(void* user, const float* landmarks, int32_t n_landmarks,
+                                    flood_host_complex* out);
+typedef void (*flood_release_fn)(void* user, void* owner);
+
+typedef struct flood_serve_config {
+    int64_t device_budget_bytes;    /* admission budget for in-flight clouds (> 0) */
+    int32_t max_inflight;           /* clouds admitted at once (>= 1) */
+    int32_t max_batch;              /* clouds per batched filtration (>= 1; 1 = per-cloud path) */
+    int32_t gpu_workers;            /* host threads driving FPS + grid (>= 1) */
+    int32_t triangulation_workers;  /* host threads calling triangulate (>= 1) */
+    float landmark_fraction;        /* n_landmarks when a request passes 0: round(fraction * N), >= 4 */
+    float cell_factor;              /* grid cell = cell_factor * FPS covering radius (> 0) */
+    flood_triangulate_fn triangulate;
+    flood_release_fn release;       /* may be NULL */
+    void* user;
+} flood_serve_config;
+
+typedef struct flood_result {
+    int32_t status;                 /* FLOOD_OK or this request's error */
+    int32_t n_landmarks;
+    int64_t n_simplices[4];
+    const float* values[4];         /* host, owned by the server until flood_serve_release */
+    const int64_t* landmarks;       /* host, n_landmarks rows of X (FPS order) */
+    double latency_ms;              /* submit -> values on the host */
+} flood_result;
+
+typedef struct flood_serve_stats_t {
+    int64_t submitted, completed, failed, inflight;
+    int64_t batches;                /* batched filtration calls */
+    double mean_batch;              /* clouds per batched call */
+    double clouds_per_s;            /* completed / (last completion - first submission) */
+    double p50_ms, p99_ms, mean_ms; /* latency over completed requests */
+    int64_t device_bytes_in_use;
+    int64_t device_bytes_peak;
+} flood_serve_stats_t;
+
+/* Start the server's threads. Errors: FLOOD_EINVAL (config), FLOOD_ENOMEM. */
+int flood_serve_create(const flood_serve_config* config, flood_server** out);
+/* Queue a cloud (X_host: host (N, 3) float32, copied before returning).
+ * n_landmarks = 0 uses the configured fraction; m is the grid resolution.
+ * Errors: FLOOD_EINVAL; FLOOD_ECAPACITY if the cloud alone exceeds the budget. */
+int flood_serve_submit(flood_server* server, const float* X_host, int64_t n_points, int32_t n_landmarks,
+                       int32_t m, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a result. FLOOD_ETIMEOUT if not
+ * done yet; otherwise *out describes it (out->status is its own outcome). */
+int flood_serve_poll(flood_server* server, uint64_t ticket, int32_t timeout_ms, flood_result* out);
+/* Free a finished request's host result. */
+int flood_serve_release(flood_server* server, uint64_t ticket);
+int flood_serve_stats(flood_server* server, flood_serve_stats_t* out);
+/* Stop the threads (waiting for in-flight work) and free everything. */
+void flood_serve_destroy(flood_server* server);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* flood_last_error(void);
 

@@ -53,6 +53,46 @@ class FiltrationJob(C.Structure):
         ("values", C.c_void_p * 4), ("src", C.c_void_p * 4),
     ]
 
+class HostComplex(C.Structure):
+    _fields_ = [("n_simplices", C.c_int64 * 4), ("simplices", C.c_void_p * 4), ("facets", C.c_void_p * 4),
+                ("owner", C.c_void_p)]
+
+
+TRIANGULATE = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(HostComplex))
+RELEASE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("device_budget_bytes", C.c_int64), ("max_inflight", C.c_int32), ("max_batch", C.c_int32),
+                ("gpu_workers", C.c_int32), ("triangulation_workers", C.c_int32),
+                ("landmark_fraction", C.c_float), ("cell_factor", C.c_float),
+                ("triangulate", TRIANGULATE), ("release", RELEASE), ("user", C.c_void_p)]
+
+
+class ServeResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_landmarks", C.c_int32), ("n_simplices", C.c_int64 * 4),
+                ("values", C.POINTER(C.c_float) * 4), ("landmarks", C.POINTER(C.c_int64)),
+                ("latency_ms", C.c_double)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("inflight", C.c_int64),
+                ("batches", C.c_int64), ("mean_batch", C.c_double), ("clouds_per_s", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("device_bytes_in_use", C.c_int64), ("device_bytes_peak", C.c_int64)]
+
+
+_SERVE_SIGNATURES = {
+    "flood_serve_create": (C.c_int, [C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]),
+    "flood_serve_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                                     C.POINTER(C.c_uint64)]),
+    "flood_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(ServeResult)]),
+    "flood_serve_release": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "flood_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(ServeStats)]),
+    "flood_serve_destroy": (None, [C.c_void_p]),
+}
+
+
 _SIGNATURES = {
     "flood_fps": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "flood_fps_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
@@ -70,6 +110,7 @@ _SIGNATURES = {
     "flood_version": (C.c_char_p, []),
     "flood_kernel_launches": (C.c_int64, []),
 }
+_SIGNATURES.update(_SERVE_SIGNATURES)
 
 _lock = threading.Lock()
 _lib = None

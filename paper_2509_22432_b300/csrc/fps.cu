@@ -198,6 +198,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_fps(FpsArgs a) {
 constexpr int kResidentThreads = 1024;
 constexpr int kStreamThreads = 512;
 
+// The grid holds just enough blocks for the points (at most all co-resident
+// blocks): small clouds synchronise fewer blocks and leave the rest of the
+// GPU to other work.
 template <int K, bool RESIDENT, int THREADS>
 int launch_fps(const FpsArgs& a, cudaStream_t s) {
     int per_sm = 0;
@@ -206,7 +209,8 @@ int launch_fps(const FpsArgs& a, cudaStream_t s) {
         set_error("flood_fps: kernel does not fit on an SM");
         return FLOOD_EINTERNAL;
     }
-    const int nb = device_sm_count() * per_sm;
+    const int64_t needed = ceil_div(a.n, int64_t(THREADS) * K);
+    const int nb = static_cast<int>(std::min<int64_t>(int64_t(device_sm_count()) * per_sm, std::max<int64_t>(needed, 1)));
     if (nb > 4096) {
         set_error("flood_fps: too many co-resident blocks (%d)", nb);
         return FLOOD_EINTERNAL;
