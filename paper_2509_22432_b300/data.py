@@ -26,6 +26,7 @@ __all__ = [
     "shape_mix_cloud",
     "swisscheese_cloud",
     "serving_sizes",
+    "poisson_arrivals",
     "jitter",
     "upstream_gradients",
 ]
