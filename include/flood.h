@@ -79,6 +79,24 @@ int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t sta
               int64_t* out_idx, float* out_key, void* stream);
 
 /* ------------------------------------------------------------------------
+ * flood_fps_blocks — flood_fps with an explicit launch width.
+ *
+ * Same picks as flood_fps (bit-exact whatever the width). n_blocks is the
+ * number of co-resident 1024-thread blocks (one per SM) the persistent FPS
+ * launch may use:
+ *   0   automatic (what flood_fps does): the fewest blocks whose registers
+ *       and shared memory hold every point (15,872 points per block; one
+ *       block needs no grid-wide exchange per pick), else every SM with
+ *       points streamed from memory;
+ *   1   one block: leaves the other SMs to concurrent work (many small
+ *       clouds at once); points stream from memory above 15,872;
+ *   k   k blocks (clamped to the SM count and to 160).
+ * Errors: as flood_fps; FLOOD_EINVAL also for n_blocks < 0.
+ * ------------------------------------------------------------------------ */
+int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,
+                     int32_t n_blocks, int64_t* out_idx, float* out_key, void* stream);
+
+/* ------------------------------------------------------------------------
  * flood_fps_noalloc — flood_fps without any device allocation.
  *
  * The paper has no counterpart: this is a deployment variant. It is for
@@ -87,9 +105,9 @@ int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t sta
  * loop that forbids allocator calls after start-up, or a plugin whose host
  * framework forbids its extensions from allocating. It computes exactly what
  * flood_fps computes (same kernels, same bit-exact picks) but takes all of
- * its scratch from one fixed-size array compiled into the library (about
- * 16 MiB of device memory, held by every GPU that loads the library until the
- * process exits) and calls no allocating routine.
+ * its scratch from one fixed-size array compiled into the library (26 MiB of
+ * device memory, held by every GPU that loads the library until the process
+ * exits) and calls no allocating routine.
  *
  *   Arguments, outputs and errors as flood_fps, plus:
  *   n_points   at most 1,048,576 (2^20); larger inputs are rejected with

@@ -95,6 +95,8 @@ _SERVE_SIGNATURES = {
 
 _SIGNATURES = {
     "flood_fps": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flood_fps_blocks": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]),
     "flood_fps_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
     "flood_build_grid": (C.c_int, [C.c_void_p, C.c_int64, C.c_float, C.POINTER(C.c_void_p), C.c_void_p]),

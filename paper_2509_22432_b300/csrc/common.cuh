@@ -67,6 +67,28 @@ struct Scratch {
     }
 };
 
+// Scratch carved from a caller-owned device buffer (no allocation): the same
+// alloc() interface as Scratch, 256-byte aligned pieces, FLOOD_ECAPACITY when
+// the buffer is exhausted.
+struct Bump {
+    unsigned char* p;
+    size_t left;
+    template <class T>
+    int alloc(T** out, size_t count) {
+        if (count == 0) count = 1;
+        const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (bytes > left) {
+            *out = nullptr;
+            set_error("fixed scratch exhausted (%zu bytes requested, %zu left)", bytes, left);
+            return FLOOD_ECAPACITY;
+        }
+        *out = reinterpret_cast<T*>(p);
+        p += bytes;
+        left -= bytes;
+        return FLOOD_OK;
+    }
+};
+
 // Wait for `stream`, then turn the device status word into a flood_status.
 int finish(cudaStream_t stream, const uint32_t* d_flags, const char* where);
 
@@ -137,6 +159,21 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Four relaxed 64-bit words at a 32-byte aligned address (one 256-bit access);
+// each word is single-copy atomic on its own (no atomicity across words).
+__device__ __forceinline__ void ld_relaxed_v4_u64(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c,
+                                                  uint64_t& d) {
+    asm volatile("ld.relaxed.gpu.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+                 : "l"(p)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_v4_u64(uint64_t* p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    asm volatile("st.relaxed.gpu.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
+                 : "memory");
 }
 
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int mask) {

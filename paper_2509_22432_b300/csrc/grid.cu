@@ -9,6 +9,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include "bbox.cuh"
 #include "geometry.cuh"
 #include "scan.cuh"
 
@@ -18,58 +19,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int64_t kMaxCells = int64_t(1) << 27;
-
-__device__ __forceinline__ uint32_t ordered_bits(float f) {
-    const uint32_t b = __float_as_uint(f);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-__host__ __device__ inline float from_ordered(uint32_t u) {
-    const uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
-    float f;
-    memcpy(&f, &b, 4);
-    return f;
-}
-
-// box[0..2] = ordered min, box[3..5] = ordered max.
-__global__ void __launch_bounds__(kThreads) k_bbox(const float* X, int64_t n, uint32_t* box, uint32_t* flags) {
-    uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
-    bool bad = false;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float v = X[3 * i + c];
-            if (!isfinite(v)) {
-                bad = true;
-                continue;
-            }
-            const uint32_t o = ordered_bits(v);
-            mn[c] = min(mn[c], o);
-            mx[c] = max(mx[c], o);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        for (int off = 16; off > 0; off >>= 1) {
-            mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
-            mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
-        }
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            atomicMin(&box[c], mn[c]);
-            atomicMax(&box[3 + c], mx[c]);
-        }
-    }
-    if (bad) atomicOr(flags, FLAG_NONFINITE);
-}
-
-__global__ void k_box_init(uint32_t* box, uint32_t* flags) {
-    box[0] = box[1] = box[2] = 0xffffffffu;
-    box[3] = box[4] = box[5] = 0u;
-    *flags = 0;
-}
 
 __global__ void __launch_bounds__(kThreads) k_cell_ids(const float* X, int64_t n, GridView g, int32_t* cell,
                                                       int32_t* count) {
@@ -160,8 +109,8 @@ extern "C" int flood_build_grid(const float* X, int64_t n_points, float cell_siz
     if (rc) return rc;
     k_box_init<<<1, 1, 0, s>>>(d_box, d_box + 6); note_launch();
     const int sms = device_sm_count();
-    const int64_t blocks = std::min<int64_t>(ceil_div(n_points, kThreads), int64_t(sms) * 8);
-    k_bbox<<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(X, n_points, d_box, d_box + 6); note_launch();
+    const int64_t blocks = std::min<int64_t>(ceil_div(n_points, kBoxThreads), int64_t(sms) * 8);
+    k_bbox<<<static_cast<unsigned>(blocks), kBoxThreads, 0, s>>>(X, n_points, d_box, d_box + 6); note_launch();
     FLOOD_CUDA(cudaGetLastError());
     uint32_t h_box[8];
     FLOOD_CUDA(cudaMemcpyAsync(h_box, d_box, sizeof(uint32_t) * 7, cudaMemcpyDeviceToHost, s));

@@ -72,7 +72,8 @@ __global__ void k_set_total(const int32_t* in, int32_t* out, int64_t n) {
     out[n] = (n > 0) ? out[n - 1] + in[n - 1] : 0;
 }
 
-int scan_rec(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch& scr) {
+template <class Alloc>
+int scan_rec(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Alloc& scr) {
     if (n <= 0) return FLOOD_OK;
     const int64_t tiles = ceil_div(n, kScanTile);
     if (tiles == 1) {
@@ -94,14 +95,23 @@ int scan_rec(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch
     return FLOOD_OK;
 }
 
-}  // namespace
-
-int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch& scr) {
+template <class Alloc>
+int scan_total(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Alloc& scr) {
     int rc = scan_rec(in, out, n, s, scr);
     if (rc) return rc;
     k_set_total<<<1, 1, 0, s>>>(in, out, n); note_launch();
     FLOOD_CUDA(cudaGetLastError());
     return FLOOD_OK;
+}
+
+}  // namespace
+
+int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch& scr) {
+    return scan_total(in, out, n, s, scr);
+}
+
+int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Bump& scr) {
+    return scan_total(in, out, n, s, scr);
 }
 
 }  // namespace flood

@@ -5,4 +5,5 @@ namespace flood {
 // out[i] = sum_{j<i} in[j] for i in [0, n], so out has n+1 entries (out[n] = total).
 // in and out may not alias. Totals must fit in int32.
 int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch& scr);
+int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Bump& scr);
 }  // namespace flood

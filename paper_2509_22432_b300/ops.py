@@ -37,14 +37,18 @@ def _points(X: torch.Tensor, name: str) -> torch.Tensor:
     return X.contiguous()
 
 
-def fps(X: torch.Tensor, n_landmarks: int, start: int = 0):
-    """Farthest point sampling (§3.2). Returns (idx int64[n], key float32[n])."""
+def fps(X: torch.Tensor, n_landmarks: int, start: int = 0, n_blocks: int = 0):
+    """Farthest point sampling (§3.2). Returns (idx int64[n], key float32[n]).
+
+    n_blocks: launch width (0 automatic, 1 one SM, k blocks); the picks are
+    the same for every width.
+    """
     X = _points(X, "X")
     idx = torch.empty(n_landmarks, dtype=torch.int64, device=X.device)
     key = torch.empty(n_landmarks, dtype=torch.float32, device=X.device)
     with torch.cuda.device(X.device):
-        st = _lib.get().flood_fps(_ptr(X), X.shape[0], int(n_landmarks), int(start), _ptr(idx), _ptr(key),
-                                  _stream_ptr(X.device))
+        st = _lib.get().flood_fps_blocks(_ptr(X), X.shape[0], int(n_landmarks), int(start), int(n_blocks), _ptr(idx),
+                                         _ptr(key), _stream_ptr(X.device))
     _lib.check(st, "flood_fps")
     return idx, key
 

@@ -73,6 +73,57 @@ def test_fps_ties_and_duplicates():
     assert np.array_equal(idx.cpu().numpy(), ri)
 
 
+# Every launch shape of the persistent FPS kernel gives the same picks: one
+# block holding its points on chip (n <= 15,872), several such blocks, one
+# block streaming chunks from memory, several streaming blocks.
+@pytest.mark.parametrize("n,n_l,blocks,seed", [
+    (5_000, 200, 0, 11), (5_000, 200, 3, 12),
+    (30_000, 300, 0, 13), (30_000, 300, 4, 14), (30_000, 300, 1, 15),
+    (100_000, 500, 0, 16), (100_000, 500, 1, 17), (100_000, 500, 5, 18)])
+def test_fps_launch_shapes_bit_exact(n, n_l, blocks, seed):
+    X = data.shape_mix_cloud(n, seed=seed)
+    idx, key = _ops().fps(torch.from_numpy(X).to(_dev()), n_l, 0, n_blocks=blocks)
+    ri, rk = oracle.fps(X, n_l, 0)
+    assert np.array_equal(idx.cpu().numpy(), ri)
+    assert np.array_equal(key.cpu().numpy().view(np.uint32), rk.view(np.uint32))
+
+
+def test_fps_ties_in_spatial_order():
+    # A shuffled 40^3 integer lattice (plus duplicates): keys are small
+    # integers, so nearly every pick is a many-way exact tie that must go to
+    # the lowest original row although points are processed in Morton order.
+    g = np.stack(np.meshgrid(np.arange(40), np.arange(40), np.arange(40), indexing="ij"), -1).reshape(-1, 3)
+    g = g[np.random.default_rng(21).permutation(g.shape[0])]
+    X = np.concatenate([g, g[:500]]).astype(np.float32)
+    ri, rk = oracle.fps(X, 400, 7)
+    for blocks in (0, 1, 3, 9):
+        idx, key = _ops().fps(torch.from_numpy(X).to(_dev()), 400, 7, n_blocks=blocks)
+        assert np.array_equal(idx.cpu().numpy(), ri), blocks
+        assert np.array_equal(key.cpu().numpy(), rk), blocks
+
+
+def test_fps_rejects_nonfinite_in_sorted_path_and_bad_width():
+    ops = _ops()
+    Y = data.sphere_cloud(20_000)
+    Y[12_345, 2] = np.inf
+    with pytest.raises(FloodError) as e:
+        ops.fps(torch.from_numpy(Y).to(_dev()), 5, 0)
+    assert e.value.name == "FLOOD_EINVAL"
+    with pytest.raises(FloodError) as e:
+        ops.fps(torch.from_numpy(data.sphere_cloud(100)).to(_dev()), 5, 0, n_blocks=-1)
+    assert e.value.name == "FLOOD_EINVAL"
+
+
+@pytest.mark.slow
+def test_fps_one_block_enlarged_chunks():
+    """1.3M points on one block: chunks grow to 320 points so their metadata fits shared memory."""
+    X = data.torus_cloud(1_300_000, seed=19)
+    idx, key = _ops().fps(torch.from_numpy(X).to(_dev()), 64, 0, n_blocks=1)
+    ri, rk = oracle.fps(X, 64, 0)
+    assert np.array_equal(idx.cpu().numpy(), ri)
+    assert np.array_equal(key.cpu().numpy(), rk)
+
+
 def test_fps_degenerate_and_invalid():
     ops = _ops()
     X = np.zeros((10, 3), np.float32)
