@@ -7,7 +7,7 @@
   sampled simplices against the FP64 k-d tree oracle.
 * 1,000,000-point jittered torus, 2,000 landmarks, m = 10, upstream
   gradients ~ N(0,1): backward against the oracle's analytic subgradient and
-  central differences (h = 1e-3) on 1,000 coordinates.
+  central differences (h = 1e-5) on 1,000 coordinates.
 """
 import numpy as np
 import pytest
@@ -129,11 +129,13 @@ def test_backward_1m_central_differences(torus_grad):
     probes = [("X", int(a), int(b)) for a, b in nzX[rng.choice(len(nzX), 500, replace=False)]]
     probes += [("L", int(a), int(rng.integers(3))) for a in rng.choice(L.shape[0], 250, replace=False)]
     probes += [("X", int(a), int(rng.integers(3))) for a in rng.choice(X.shape[0], 250, replace=False)]
-    fd, kink, _ = oracle.finite_difference(X, L, cx.simplices, m, gamma, probes, h=1e-3, method="kdtree")
+    # h = 1e-5: the central-difference error of f = |p* - x*| is O((h / f)^2),
+    # and flood values here go down to ~5e-3 (1.5 point spacings)
+    fd, kink, _ = oracle.finite_difference(X, L, cx.simplices, m, gamma, probes, h=1e-5, method="kdtree")
     an = np.array([gX[r, c] if w == "X" else gL[r, c] for (w, r, c) in probes])
     ok = ~kink
     # probes whose attaining (sample, point) pair changes within +-h are kinks:
-    # counted, not compared (the point spacing here is only ~3h)
-    assert ok.sum() >= 250, ok.sum()
+    # counted, not compared
+    assert ok.sum() >= 800, ok.sum()
     close = np.isclose(an[ok], fd[ok], rtol=1e-2, atol=1e-3)
     assert close.mean() >= 0.99, (close.mean(), ok.sum())
