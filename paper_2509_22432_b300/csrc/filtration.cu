@@ -776,12 +776,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             }
         }
         __syncthreads();
-        if (tid < n_valid) s_u[tid] = fminf(s_u[tid], __fsqrt_ru(__uint_as_float(s_ub2[tid])) * (1.0f + 1.0f / 65536.0f));
+        // A sample whose tightened bound cannot exceed the facet maximum (with a
+        // margin far above the rounding of the distances the scan would
+        // compute) can neither raise the simplex's value nor attain it, so it
+        // leaves the group before the scan: s_min = 0 marks it dominated.
+        if (tid < n_valid) {
+            const float u = fminf(s_u[tid], __fsqrt_ru(__uint_as_float(s_ub2[tid])) * (1.0f + 1.0f / 65536.0f));
+            s_u[tid] = u;
+            if (__fadd_rn(__fmul_rn(u, 1.0f + 1.0f / 4096.0f), a.shell_slack) <= s_lb[tid]) {
+                s_live[tid] = 0;
+                s_min[tid] = 0u;
+            }
+        }
         __syncthreads();
         R = 0.0f;
-        for (int i = 0; i < n_valid; ++i) R = fmaxf(R, s_u[i]);
+        bool any_live = false;
+        for (int i = 0; i < n_valid; ++i)
+            if (s_live[i]) {
+                R = fmaxf(R, s_u[i]);
+                any_live = true;
+            }
         const int dmax = max(g.dx, max(g.dy, g.dz));
-        const int s_max = min(static_cast<int>(ceilf((R + a.shell_slack) / a.shell_h)) + 1, dmax);
+        const int s_max = any_live ? min(static_cast<int>(ceilf((R + a.shell_slack) / a.shell_h)) + 1, dmax) : -1;
         Shell sh;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
