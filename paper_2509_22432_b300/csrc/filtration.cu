@@ -650,8 +650,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
 
 // ---------------------------------------------------------------- heavy groups
 // Groups whose vertex bound allows many shells (samples in empty regions)
-// scan far and long; one whole CTA takes each of them. Warp 0 fills large
-// shared tiles while all eight warps evaluate them; the thread layout is the
+// scan far and long; one whole CTA takes each of them. All threads enumerate
+// a shell's rows together (the walk over the cell table, not the arithmetic,
+// bounds these groups) and fill one shared tile by bulk copies; the layout is the
 // warp kernel's (W sample lanes x 256/W point streams) stretched over the CTA,
 // and per-sample minima are combined in shared memory.
 constexpr int kHeavyTile = 2048;
@@ -674,13 +675,14 @@ __device__ __forceinline__ void heavy_tile(const float4* buf, int n, int gs, int
 
 __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs, int n_jobs,
                                                              const int32_t* heavy_off, Ctl* ctl, int k) {
-    extern __shared__ __align__(128) float4 s_tiles[];  // 2 x kHeavyTile
+    extern __shared__ __align__(128) float4 s_tiles[];  // kHeavyTile points
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_min[kGroup];
     __shared__ int s_live[kGroup];
     __shared__ float s_u[kGroup], s_lb[kGroup];
     __shared__ uint32_t s_ub2[kGroup];
-    __shared__ int s_item, s_n[2], s_done, s_abort;
+    __shared__ int s_item, s_abort;
+    __shared__ int32_t s_wsum[kWarps];
     __shared__ float s_T2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -841,49 +843,68 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             fold();
             sh.T2 = s_T2;
             ++n_shells;
-            if (sh.rows > 0) {
-                Cursor cur{0, 0, 0};
-                if (warp == 0) produce_shell_tile(g, sh, cur, kHeavyTile, s_tiles, &s_bar[0], lane, &s_n[0]);
-                int b = 0;
-                for (;;) {
-                    if (!mbar_wait(&s_bar[b], (phases >> b) & 1u, &a.ctl->flags)) s_abort = 1;
-                    phases ^= 1u << b;
-                    const int n = s_n[b];
-                    __syncthreads();  // every thread has read s_n[b] and any timeout is visible
-                    if (n == 0 || s_abort) break;
-                    if (warp == 0) {
-                        const int more_all = cur.row < sh.rows;
-                        if (more_all)
-                            produce_shell_tile(g, sh, cur, kHeavyTile, s_tiles + (b ^ 1) * kHeavyTile, &s_bar[b ^ 1],
-                                               lane, &s_n[b ^ 1]);
-                        if (lane == 0) s_done = more_all;
-                    }
-                    float4* buf = s_tiles + b * kHeavyTile;
-                    for (int e = tid; e < n; e += kThreads) {
-                        float4 p = buf[e];
+            // All threads enumerate the shell's rows, 256 at a time: each
+            // thread finds its row's point ranges, a block scan places them,
+            // and the owners bulk-copy them into the tile window by window.
+            for (int row0 = 0; row0 < sh.rows && !s_abort; row0 += kThreads) {
+                int32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
+                if (row0 + tid < sh.rows) shell_row(g, sh, row0 + tid, b1, l1, b2, l2);
+                const int32_t len = l1 + l2;
+                int32_t incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane == 31) s_wsum[warp] = incl;
+                __syncthreads();
+                int32_t before = 0, total = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    const int32_t v = s_wsum[w];
+                    before += w < warp ? v : 0;
+                    total += v;
+                }
+                const int32_t off = before + incl - len;  // stream position of this row
+                for (int32_t w0 = 0; w0 < total; w0 += kHeavyTile) {
+                    const int32_t cnt = min(kHeavyTile, total - w0);
+                    if (tid == 0) mbar_arrive_expect_tx(&s_bar[0], static_cast<uint32_t>(cnt) * 16u);
+                    __syncthreads();
+                    const int32_t o1lo = max(off, w0), o1hi = min(off + l1, w0 + cnt);
+                    const int32_t o2lo = max(off + l1, w0), o2hi = min(off + len, w0 + cnt);
+                    if (o1hi > o1lo)
+                        bulk_copy_g2s(s_tiles + (o1lo - w0), g.pts + b1 + (o1lo - off),
+                                      static_cast<uint32_t>(o1hi - o1lo) * 16u, &s_bar[0]);
+                    if (o2hi > o2lo)
+                        bulk_copy_g2s(s_tiles + (o2lo - w0), g.pts + b2 + (o2lo - off - l1),
+                                      static_cast<uint32_t>(o2hi - o2lo) * 16u, &s_bar[0]);
+                    if (!mbar_wait(&s_bar[0], phases & 1u, &a.ctl->flags)) s_abort = 1;
+                    phases ^= 1u;
+                    __syncthreads();  // any timeout is visible to every thread
+                    if (s_abort) break;
+                    for (int e = tid; e < cnt; e += kThreads) {
+                        float4 p = s_tiles[e];
                         p.x = __fsub_rn(p.x, ox);
                         p.y = __fsub_rn(p.y, oy);
                         p.z = __fsub_rn(p.z, oz);
                         p.w = __fmaf_rn(p.x, p.x, __fmaf_rn(p.y, p.y, __fmul_rn(p.z, p.z)));
-                        buf[e] = p;
+                        s_tiles[e] = p;
                     }
                     __syncthreads();
                     if (nsl == 1)
-                        heavy_tile<1>(buf, n, gs, G, ax, ay, az, mn);
+                        heavy_tile<1>(s_tiles, cnt, gs, G, ax, ay, az, mn);
                     else if (nsl == 2)
-                        heavy_tile<2>(buf, n, gs, G, ax, ay, az, mn);
+                        heavy_tile<2>(s_tiles, cnt, gs, G, ax, ay, az, mn);
                     else if (nsl <= 4)
-                        heavy_tile<4>(buf, n, gs, G, ax, ay, az, mn);
+                        heavy_tile<4>(s_tiles, cnt, gs, G, ax, ay, az, mn);
                     else
-                        heavy_tile<kNS>(buf, n, gs, G, ax, ay, az, mn);
-                    pairs += tid == 0 ? static_cast<unsigned long long>(n) * n_valid : 0ull;
+                        heavy_tile<kNS>(s_tiles, cnt, gs, G, ax, ay, az, mn);
+                    pairs += tid == 0 ? static_cast<unsigned long long>(cnt) * n_valid : 0ull;
                     n_tiles += tid == 0;
                     fence_proxy_async_smem();
-                    __syncthreads();
-                    const int cont = s_done;
-                    if (!cont) break;
-                    b ^= 1;
+                    __syncthreads();  // the tile is free for the next window's copies
                 }
+                __syncthreads();  // s_wsum is free for the next rows
             }
             if (s_abort) break;
             fold();
@@ -974,7 +995,7 @@ __global__ void k_facemax(int k, int64_t n, const int32_t* simplices, const int3
 // ---------------------------------------------------------------- host side
 int launch_flood_heavy(const DimArgs* jobs, int n_jobs, const int32_t* heavy_off, Ctl* ctl, int k,
                        cudaStream_t s) {
-    const size_t smem = size_t(2) * kHeavyTile * sizeof(float4);
+    const size_t smem = size_t(kHeavyTile) * sizeof(float4);
     FLOOD_CUDA(cudaFuncSetAttribute(k_flood_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
     FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood_heavy, kThreads, smem));
