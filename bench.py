@@ -53,13 +53,14 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []       # (arrival time, csv line)
+        self.window = None    # (start, end) of the timed region, monotonic seconds
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -68,7 +69,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self, start: float, end: float):
+        """Keep only the samples that arrived inside [start, end]."""
+        self.window = (start, end)
 
     def __exit__(self, *a):
         if self.proc:
@@ -81,7 +86,9 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if self.window and not (self.window[0] <= t <= self.window[1]):
+                continue
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -216,7 +223,7 @@ def run_reference(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus-1M", choices=sorted(WORKLOADS))
@@ -288,6 +295,7 @@ def main():
         grid.close()
         return idx, vals
 
+    clocks = ClockSampler(local).__enter__()  # running before the timed region; samples filtered to it
     for _ in range(args.warmup):
         idx, vals = step()
     assert torch.equal(idx, idx0), "FPS must be deterministic"
@@ -299,7 +307,9 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+    time.sleep(0.3)  # the sampler's first lines arrive after a short start-up
+    t_region0 = time.monotonic()
+    try:
         for _ in range(args.steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -310,6 +320,9 @@ def main():
             times.append(e0.elapsed_time(e1))
             flood_ms.append(sum(ops.last_filtration_stats()["flood_kernel_ms"]))
         torch.cuda.synchronize()
+    finally:
+        clocks.mark(t_region0, time.monotonic())
+        clocks.__exit__(None, None, None)
     launches = ops.kernel_launches() - launches0
     ms, total_simplices = aggregate(float(np.mean(times)), float(n_simp), dev)
 

@@ -85,12 +85,12 @@ int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t sta
  * number of co-resident 1024-thread blocks (one per SM) the persistent FPS
  * launch may use:
  *   0   automatic (what flood_fps does): the fewest blocks whose registers
- *       and shared memory hold every point (15,872 points per block, so up
- *       to 1,015,808 points on 64 blocks; one block needs no grid-wide
- *       exchange), else 64 blocks with points streamed from memory;
+ *       and shared memory hold every point (15,360 points per block, so up
+ *       to 1,228,800 points on 80 blocks; one block needs no grid-wide
+ *       exchange), else 80 blocks with points streamed from memory;
  *   1   one block: leaves the other SMs to concurrent work (many small
- *       clouds at once); points stream from memory above 15,872;
- *   k   k blocks (clamped to the SM count and to 64).
+ *       clouds at once); points stream from memory above 15,360;
+ *   k   k blocks (clamped to the SM count and to 80).
  * Errors: as flood_fps; FLOOD_EINVAL also for n_blocks < 0.
  * ------------------------------------------------------------------------ */
 int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,

@@ -14,8 +14,8 @@
 //   between l and the box. A chunk whose gap is >= its largest d_i is
 //   therefore provably unchanged and skipped, bit-exactly; after the first few
 //   hundred picks almost every chunk is skipped.
-// * One warp of each 1024-thread block runs the grid-wide exchange, once per
-//   round: each block publishes its two best candidates with coordinates and
+// * Two warps of each 1024-thread block run the grid-wide exchange, once per
+//   round: each block publishes its four best candidates with coordinates and
 //   a bound on the rest in tagged words, and polls every block's words until
 //   all carry the round's tag. That one pass synchronises the grid and
 //   delivers the next pick with its coordinates (no dependent load follows),
@@ -39,11 +39,11 @@ namespace {
 
 constexpr int kThreads = 1024;  // one block per SM
 constexpr int kWarps = kThreads / 32;
-constexpr int kComputeWarps = kWarps - 1;  // the last warp runs the exchange
+constexpr int kComputeWarps = kWarps - 2;  // the last two warps run the exchange
 constexpr int kLanePts = 8;                // points per lane of a chunk
 constexpr int kChunk = 32 * kLanePts;      // points per chunk (resident kernel)
 constexpr int64_t kBlockPts = 2 * int64_t(kComputeWarps) * kChunk;  // points a resident block holds
-constexpr int kMaxBlocks = 64;             // blocks one exchange warp polls in 4 loads per lane
+constexpr int kMaxBlocks = 80;             // two exchange warps poll 40 blocks each in 5 loads per lane
 constexpr int kSlotStride = 16;            // uint64 words per slot line (128 bytes; 8 used)
 constexpr int64_t kSortMin = 16384;        // smaller clouds keep their input order
 constexpr int kGlobalBatch = 5;            // global kernel: points per lane loaded at once
@@ -183,37 +183,44 @@ struct FpsArgs {
 };
 
 // ---------------------------------------------------------------- rounds
-// A round folds the previous round's picks (one or two landmarks) into every
+// A round folds the previous round's picks (one to four landmarks) into every
 // chunk, then selects the next picks with one grid-wide exchange:
 //
-// * Each block reports its two best entries (an entry is a chunk candidate:
+// * Each block reports its four best entries (an entry is a chunk candidate:
 //   the chunk's largest running minimum, ties to the lowest original row, with
 //   the point's coordinates; the global kernel reports one entry per warp) and
-//   a bound U_b on every other point of the block: the larger of its third
+//   a bound U_b on every other point of the block: the larger of its fifth
 //   entry and the largest "second" of any entry (the second-largest minimum
 //   of the entry's chunk, or of all of the warp's other points).
-// * The best entry E1 over all blocks is the next pick, as in plain FPS. The
-//   second entry E2 is also picked, right after E1, when its key is positive,
-//   strictly above U = max_b U_b, and not lowered by E1 (kappa(E2, E1) >=
-//   key(E2)): every running minimum only decreases, every point other than
-//   E1 and E2 is below E2 in (key, lowest row) order, and E2's own minimum is
-//   unchanged by E1, so plain FPS picks E2 next. Both are folded in the next
-//   round. On the 1M-point torus with 2,000 picks this holds in ~84% of the
-//   rounds, which nearly halves the number of exchanges.
-constexpr int kTop = 2;
-static_assert(kTop == 2, "the slot writer and the resident kernel's hit bits are written for two entries");
+// * The best entry E1 over all blocks is the next pick, as in plain FPS.
+//   Entry E_k (k = 2..4) is picked right after E_(k-1) when E_2..E_(k-1) were,
+//   its key is positive and strictly above U = max_b U_b, and no earlier pick
+//   of the round lowers it (kappa(E_k, E_i) >= key(E_k), i < k): running
+//   minima only decrease, every point outside E_1..E_k is below E_k in (key,
+//   lowest row) order, and E_k's own minimum is unchanged by the earlier
+//   picks, so plain FPS picks E_k next. All are folded in the next round. On
+//   the 1M-point torus with 2,000 picks a round makes 2.9 picks on average.
+constexpr int kTop = 4;
 
-// Named barriers of a round (all 1024 threads counted): compute warps arrive
-// at kBarCands once their entries are written and wait at kBarPicks; the
-// exchange warp waits at kBarCands and arrives at kBarPicks once the picks
-// are written. An arrival releases the arriving thread's earlier
-// shared-memory writes to the threads that complete the wait.
-constexpr int kBarCands = 1, kBarPicks = 2;
-__device__ __forceinline__ void bar_arrive(int id) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kThreads) : "memory");
+// Two exchange warps: warp 30 (X0) reduces the block's entries, publishes
+// them and polls the first half of the blocks; warp 31 (X1) polls the second
+// half and hands its best entries to X0, which merges and selects the picks.
+// Named barriers per round: compute warps arrive at kBarCands (X0 waits),
+// X0 arrives at kBarPub once the block's slot is published (X1 waits: its
+// polling loads would otherwise slow X0's shared-memory loads and shuffles,
+// which share the SM's memory pipe), X1 arrives at kBarHalf (X0 waits), X0
+// arrives at kBarPicks (everyone else waits). An arrival releases the
+// arriving thread's earlier shared-memory writes to the threads that
+// complete the wait.
+constexpr int kX0 = kComputeWarps;  // warp kComputeWarps + 1 is X1
+constexpr int kBarCands = 1, kBarPicks = 2, kBarHalf = 3, kBarPub = 4;
+constexpr int kCandsCount = (kComputeWarps + 1) * 32;
+constexpr int kHalfCount = 64;
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
-__device__ __forceinline__ void bar_wait(int id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kThreads) : "memory");
+__device__ __forceinline__ void bar_wait(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 struct FpsShared {
@@ -223,6 +230,10 @@ struct FpsShared {
     uint64_t pick[kTop];        // this round's picks
     float px[kTop], py[kTop], pz[kTop];
     int n_pick;                 // picks of the round; -1 = stop (timeout)
+    uint64_t half[2][kTop];     // best entries of each half of the blocks (X0's, X1's)
+    float hx[2][kTop], hy[2][kTop], hz[2][kTop];
+    float hbound;               // X1's half: bound on everything else
+    int hstop;
 };
 
 __device__ __forceinline__ void shared_init(FpsShared& s) {
@@ -233,15 +244,10 @@ __device__ __forceinline__ void shared_init(FpsShared& s) {
     }
 }
 
-// Two best entries of the block (exchange warp) and the bound on the rest.
-struct BlockTop {
-    uint64_t e[kTop];
-    float x[kTop], y[kTop], z[kTop];
-    float bound;
-};
-
-__device__ __forceinline__ BlockTop block_top(const FpsShared& s, int lane) {
-    BlockTop t;
+// Block reduction (X0): lane l holds entries l and 32 + l; lane k < kTop
+// receives the k-th best entry. Returns the bound on every other point.
+__device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_t& me, float& mx, float& my,
+                                           float& mz) {
     uint64_t a = s.cand[lane], b = s.cand[kWarps + lane];
     int ia = lane, ib = kWarps + lane;
     if (b > a) {
@@ -252,25 +258,28 @@ __device__ __forceinline__ BlockTop block_top(const FpsShared& s, int lane) {
         ia = ib;
         ib = ti;
     }
+    me = 0ull;
+    mx = my = mz = 0.0f;
 #pragma unroll
     for (int k = 0; k < kTop; ++k) {
         const uint64_t m = warp_max_u64(a);
         const int o = __ffs(__ballot_sync(0xffffffffu, a == m)) - 1;
         const int oi = __shfl_sync(0xffffffffu, ia, o);
-        t.e[k] = m;
-        t.x[k] = s.cx[oi];
-        t.y[k] = s.cy[oi];
-        t.z[k] = s.cz[oi];
+        if (lane == k) {
+            me = m;
+            mx = s.cx[oi];
+            my = s.cy[oi];
+            mz = s.cz[oi];
+        }
         if (lane == o) {
             a = b;
             ia = ib;
             b = 0ull;
         }
     }
-    const float third = cand_key(warp_max_u64(a));
+    const float next = cand_key(warp_max_u64(a));
     const float sec = warp_max_f(fmaxf(s.sec[lane], s.sec[kWarps + lane]));
-    t.bound = fmaxf(fmaxf(third, sec), 0.0f);
-    return t;
+    return fmaxf(fmaxf(next, sec), 0.0f);
 }
 
 // Bound packed into 30 bits: rounded up to a multiple of 4 in its bit
@@ -286,132 +295,165 @@ __device__ __forceinline__ float bound_from30(uint32_t v) { return __uint_as_flo
 // A reader accepts a block once all its words carry round r, so every word is
 // read atomically and no order between them is needed; a block cannot publish
 // round r + 2 (same parity) before every block has finished reading r + 1.
-// In poll load l, lane 2 i + q reads entry q of block 16 l + i: one 32-byte
-// access per lane, 16 blocks per load, 4 loads for 64 blocks.
+// Exchange warp h polls blocks [40 h, 40 h + 40): in load l, lane 4 i + q
+// reads entry q of block 40 h + 8 l + i (one 32-byte access per lane).
 constexpr int kBlocksPerLoad = 32 / kTop;
-constexpr int kPollLoads = kMaxBlocks / kBlocksPerLoad;
+constexpr int kPollLoads = 5;
+constexpr int kHalfBlocks = kBlocksPerLoad * kPollLoads;
+static_assert(2 * kHalfBlocks == kMaxBlocks, "two exchange warps cover every block");
 
+// Poll one half of the blocks until all carry round r; its best kTop entries
+// go to s.half[h] (each written by the lane holding it). Returns the half's
+// bound on every other point.
+__device__ __forceinline__ float poll_half(const FpsArgs& a, FpsShared& s, int r, int h, int lane, bool& stop) {
+    const uint64_t tag = static_cast<uint64_t>(r & 3) << 62;
+    const uint64_t* buf = a.slots + static_cast<size_t>(r & 1) * kMaxBlocks * kSlotStride;
+    const int nb = gridDim.x, q = lane % kTop, bi = lane / kTop;
+    uint64_t w0[kPollLoads], w1[kPollLoads], w2[kPollLoads], w3[kPollLoads];
+    for (uint32_t polls = 0;;) {
+#pragma unroll
+        for (int l = 0; l < kPollLoads; ++l) {
+            const int b = h * kHalfBlocks + l * kBlocksPerLoad + bi;
+            if (b < nb) {
+                ld_relaxed_v4_u64(buf + static_cast<size_t>(b) * kSlotStride + 4 * q, w0[l], w1[l], w2[l], w3[l]);
+            } else {
+                w0[l] = w1[l] = w2[l] = w3[l] = tag;
+            }
+        }
+        uint64_t stale = 0ull;
+#pragma unroll
+        for (int l = 0; l < kPollLoads; ++l) stale |= (w0[l] ^ tag) | (w1[l] ^ tag) | (w2[l] ^ tag) | (w3[l] ^ tag);
+        if (__all_sync(0xffffffffu, (stale >> 62) == 0ull)) break;
+        if (++polls > kWaitPolls) {
+            stop = true;
+            if (lane == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+            break;
+        }
+    }
+    uint32_t u30 = 0u;
+    uint64_t c[kPollLoads];
+    uint32_t cxb[kPollLoads], cyb[kPollLoads], czb[kPollLoads];
+#pragma unroll
+    for (int l = 0; l < kPollLoads; ++l) {
+        if (q == 0) u30 = max(u30, static_cast<uint32_t>(w1[l] >> 32) & 0x3fffffffu);
+        c[l] = w0[l] & kCandMask;
+        cxb[l] = static_cast<uint32_t>(w1[l]);
+        cyb[l] = static_cast<uint32_t>(w2[l]);
+        czb[l] = static_cast<uint32_t>(w3[l]);
+    }
+#pragma unroll
+    for (int k = 0; k < kTop; ++k) {
+        uint64_t v = 0ull;
+        int vl = 0;
+#pragma unroll
+        for (int l = 0; l < kPollLoads; ++l)
+            if (c[l] > v) {
+                v = c[l];
+                vl = l;
+            }
+        const uint64_t m = warp_max_u64(v);
+        const int o = __ffs(__ballot_sync(0xffffffffu, v == m)) - 1;
+        if (lane == o) {
+            uint32_t ex = 0u, ey = 0u, ez = 0u;
+#pragma unroll
+            for (int l = 0; l < kPollLoads; ++l)
+                if (l == vl) {
+                    ex = cxb[l];
+                    ey = cyb[l];
+                    ez = czb[l];
+                    c[l] = 0ull;
+                }
+            s.half[h][k] = m;
+            s.hx[h][k] = __uint_as_float(ex);
+            s.hy[h][k] = __uint_as_float(ey);
+            s.hz[h][k] = __uint_as_float(ez);
+        }
+    }
+    return bound_from30(__reduce_max_sync(0xffffffffu, u30));
+}
+
+// X0, one round: block reduction, publication, its half of the polling, the
+// merge with X1's half, and the picks.
 __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, int r, int picks_left, int lane) {
-    const BlockTop t = block_top(s, lane);
-    uint64_t e1 = t.e[0], e2 = t.e[1];
-    float x1 = t.x[0], y1 = t.y[0], z1 = t.z[0], x2 = t.x[1], y2 = t.y[1], z2 = t.z[1];
-    float bound = t.bound;
+    uint64_t me;
+    float mx, my, mz;
+    float bound = block_top(s, lane, me, mx, my, mz);
     bool stop = false;
-    const int nb = gridDim.x;
-    if (nb > 1) {
+    if (gridDim.x > 1) {
         const uint64_t tag = static_cast<uint64_t>(r & 3) << 62;
         uint64_t* buf = a.slots + static_cast<size_t>(r & 1) * kMaxBlocks * kSlotStride;
         if (lane < kTop) {
-            const bool f = lane == 0;
-            const uint64_t hi = f ? static_cast<uint64_t>(bound_up30(bound)) << 32 : 0ull;
-            st_relaxed_v4_u64(buf + static_cast<size_t>(blockIdx.x) * kSlotStride + 4 * lane, tag | (f ? e1 : e2),
-                              tag | hi | __float_as_uint(f ? x1 : x2), tag | __float_as_uint(f ? y1 : y2),
-                              tag | __float_as_uint(f ? z1 : z2));
+            const uint64_t hi = lane == 0 ? static_cast<uint64_t>(bound_up30(bound)) << 32 : 0ull;
+            st_relaxed_v4_u64(buf + static_cast<size_t>(blockIdx.x) * kSlotStride + 4 * lane, tag | me,
+                              tag | hi | __float_as_uint(mx), tag | __float_as_uint(my), tag | __float_as_uint(mz));
         }
-        const int q = lane & 1, bi = lane >> 1;
-        uint64_t w0[kPollLoads], w1[kPollLoads], w2[kPollLoads], w3[kPollLoads];
-        for (uint32_t polls = 0;;) {
-#pragma unroll
-            for (int l = 0; l < kPollLoads; ++l) {
-                const int b = l * kBlocksPerLoad + bi;
-                if (b < nb) {
-                    ld_relaxed_v4_u64(buf + static_cast<size_t>(b) * kSlotStride + 4 * q, w0[l], w1[l], w2[l], w3[l]);
-                } else {
-                    w0[l] = w1[l] = w2[l] = w3[l] = tag;
-                }
-            }
-            uint64_t stale = 0ull;
-#pragma unroll
-            for (int l = 0; l < kPollLoads; ++l) stale |= (w0[l] ^ tag) | (w1[l] ^ tag) | (w2[l] ^ tag) | (w3[l] ^ tag);
-            if (__all_sync(0xffffffffu, (stale >> 62) == 0ull)) break;
-            if (++polls > kWaitPolls) {
-                stop = true;
-                if (lane == 0) atomicOr(a.flags, FLAG_TIMEOUT);
-                break;
-            }
+        bar_arrive(kBarPub, kHalfCount);
+        bound = poll_half(a, s, r, 0, lane, stop);
+        bar_wait(kBarHalf, kHalfCount);
+        __syncwarp();
+        // merge: lanes 0..3 hold X0's half, lanes 4..7 X1's
+        uint64_t v = 0ull;
+        float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+        if (lane < 2 * kTop) {
+            const int hh = lane / kTop, kk = lane % kTop;
+            v = s.half[hh][kk];
+            vx = s.hx[hh][kk];
+            vy = s.hy[hh][kk];
+            vz = s.hz[hh][kk];
         }
-        // global bound, then the two best entries over all blocks
-        uint32_t u30 = 0u;
-#pragma unroll
-        for (int l = 0; l < kPollLoads; ++l)
-            if (q == 0) u30 = max(u30, static_cast<uint32_t>(w1[l] >> 32) & 0x3fffffffu);
-        bound = bound_from30(__reduce_max_sync(0xffffffffu, u30));
-        uint64_t c[kPollLoads];
-#pragma unroll
-        for (int l = 0; l < kPollLoads; ++l) c[l] = w0[l] & kCandMask;
+        bound = fmaxf(bound, s.hbound);
+        stop = stop || s.hstop;
 #pragma unroll
         for (int k = 0; k < kTop; ++k) {
-            uint64_t v = 0ull;
-            uint32_t ex = 0u, ey = 0u, ez = 0u;
-            int vl = 0;
-#pragma unroll
-            for (int l = 0; l < kPollLoads; ++l) {
-                if (c[l] > v) {
-                    v = c[l];
-                    vl = l;
-                    ex = static_cast<uint32_t>(w1[l]);
-                    ey = static_cast<uint32_t>(w2[l]);
-                    ez = static_cast<uint32_t>(w3[l]);
-                }
-            }
             const uint64_t m = warp_max_u64(v);
             const int o = __ffs(__ballot_sync(0xffffffffu, v == m)) - 1;
-            const float fx = __uint_as_float(__shfl_sync(0xffffffffu, ex, o));
-            const float fy = __uint_as_float(__shfl_sync(0xffffffffu, ey, o));
-            const float fz = __uint_as_float(__shfl_sync(0xffffffffu, ez, o));
             if (lane == o) {
-#pragma unroll
-                for (int l = 0; l < kPollLoads; ++l)
-                    if (l == vl) c[l] = 0ull;
-            }
-            if (k == 0) {
-                e1 = m;
-                x1 = fx;
-                y1 = fy;
-                z1 = fz;
-            } else {
-                e2 = m;
-                x2 = fx;
-                y2 = fy;
-                z2 = fz;
+                s.pick[k] = m;
+                s.px[k] = vx;
+                s.py[k] = vy;
+                s.pz[k] = vz;
+                v = 0ull;
             }
         }
+    } else if (lane < kTop) {
+        s.pick[lane] = me;
+        s.px[lane] = mx;
+        s.py[lane] = my;
+        s.pz[lane] = mz;
     }
-    int n = -1;
-    if (!stop) {
-        const float k2 = cand_key(e2);
-        n = (picks_left >= 2 && e2 != 0ull && k2 > 0.0f && k2 > bound && fps_key(x2, y2, z2, x1, y1, z1) >= k2) ? 2
-                                                                                                              : 1;
+    __syncwarp();
+    // lane k in 1..3 checks whether entry k may follow the picks before it
+    bool ok = false;
+    if (lane >= 1 && lane < kTop) {
+        const uint64_t ek = s.pick[lane];
+        const float key = cand_key(ek);
+        const float x = s.px[lane], y = s.py[lane], z = s.pz[lane];
+        ok = picks_left > lane && ek != 0ull && key > 0.0f && key > bound;
+#pragma unroll
+        for (int i = 0; i < kTop - 1; ++i)
+            if (i < lane) ok = ok && fps_key(x, y, z, s.px[i], s.py[i], s.pz[i]) >= key;
     }
-    if (lane == 0) {
-        s.pick[0] = e1;
-        s.px[0] = x1;
-        s.py[0] = y1;
-        s.pz[0] = z1;
-        s.pick[1] = e2;
-        s.px[1] = x2;
-        s.py[1] = y2;
-        s.pz[1] = z2;
-        s.n_pick = n;
-    }
+    const uint32_t okm = __ballot_sync(0xffffffffu, ok) >> 1;  // bit k - 1: entry k
+    if (lane == 0) s.n_pick = stop ? -1 : __ffs(~okm);         // 1 + leading accepted entries
 }
 
-// After the second barrier of a round: record the picks (block 0) and return
-// how many were made; 0 tells every thread to stop (timeout, or no point left
-// with a positive key).
+// After the round's last barrier: how many picks the round made; 0 tells
+// every thread to stop (timeout, or no point left with a positive key).
+// Block 0's X1 records the picks: a barrier arrival waits for the arriving
+// thread's earlier global stores, and X1 arrives next only after a whole
+// round of polling, so the stores stay off the critical path.
 __device__ __forceinline__ int take_picks(const FpsArgs& a, const FpsShared& s, int j) {
     const int n = s.n_pick;
     if (n < 1) return 0;
     const uint64_t e1 = s.pick[0];
     if (e1 == 0ull || !(cand_key(e1) > 0.0f)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.flags, FLAG_DEGENERATE);
+        if (blockIdx.x == 0 && threadIdx.x == (kX0 + 1) * 32) atomicOr(a.flags, FLAG_DEGENERATE);
         return 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int t = 0; t < n; ++t) {
-            a.out_idx[j + t] = cand_row(s.pick[t]);
-            if (a.out_key) a.out_key[j + t] = cand_key(s.pick[t]);
-        }
+    const int t = static_cast<int>(threadIdx.x) - (kX0 + 1) * 32;  // lane of X1
+    if (blockIdx.x == 0 && t >= 0 && t < n) {
+        a.out_idx[j + t] = cand_row(s.pick[t]);
+        if (a.out_key) a.out_key[j + t] = cand_key(s.pick[t]);
     }
     return n;
 }
@@ -430,15 +472,31 @@ __device__ __forceinline__ void start_round(const FpsArgs& a, FpsShared& s) {
     }
 }
 
-// The exchange warp's loop (shared by both kernels): it waits where the
-// compute warps arrive and arrives where they wait, the exchange in between.
-__device__ __forceinline__ void exchange_loop(const FpsArgs& a, FpsShared& s, int lane) {
+// The exchange warps' loops (shared by both kernels): X0 waits where the
+// compute warps arrive and arrives where they wait; X1 polls its half and
+// hands it over.
+__device__ __forceinline__ void exchange_loop(const FpsArgs& a, FpsShared& s, int warp, int lane) {
     int r = 1;
     for (int j = 1; j < a.n_landmarks; ++r) {
-        bar_wait(kBarCands);
-        exchange_step(a, s, r, a.n_landmarks - j, lane);
-        __syncwarp();
-        bar_arrive(kBarPicks);
+        if (warp == kX0) {
+            bar_wait(kBarCands, kCandsCount);
+            exchange_step(a, s, r, a.n_landmarks - j, lane);
+            __syncwarp();
+            bar_arrive(kBarPicks, kThreads);
+        } else {
+            if (gridDim.x > 1) {
+                bool stop = false;
+                bar_wait(kBarPub, kHalfCount);
+                const float hb = poll_half(a, s, r, 1, lane, stop);
+                if (lane == 0) {
+                    s.hbound = hb;
+                    s.hstop = stop;
+                }
+                __syncwarp();
+                bar_arrive(kBarHalf, kHalfCount);
+            }
+            bar_wait(kBarPicks, kThreads);
+        }
         const int n = take_picks(a, s, j);
         if (n == 0) break;
         j += n;
@@ -502,9 +560,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     shared_init(s);
     start_round(a, s);
-    if (warp == kComputeWarps) {
+    if (warp >= kComputeWarps) {
         __syncthreads();
-        exchange_loop(a, s, lane);
+        exchange_loop(a, s, warp, lane);
         return;
     }
     const int64_t base = (static_cast<int64_t>(2 * warp) * gridDim.x + blockIdx.x) * kChunk;  // chunk A
@@ -603,19 +661,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                              s_bm[(f + 4) * kWarps + warp], s_bm[(f + 5) * kWarps + warp]) >= md);
         }
         const uint32_t hb = __ballot_sync(0xffffffffu, hit);
-        const uint32_t hit_a = (hb & 1u) | ((hb >> 1) & 2u);
-        const uint32_t hit_b = ((hb >> 1) & 1u) | ((hb >> 2) & 2u);
+        uint32_t hit_a = 0u, hit_b = 0u;
+#pragma unroll
+        for (int t = 0; t < kTop; ++t) {
+            hit_a |= ((hb >> (2 * t)) & 1u) << t;
+            hit_b |= ((hb >> (2 * t + 1)) & 1u) << t;
+        }
         if (hit_a) {
+#pragma unroll 1
+            for (int t = 0; t < kTop; ++t) {
+                if (!(hit_a & (1u << t))) continue;
+                const float qx = s.px[t], qy = s.py[t], qz = s.pz[t];
+#pragma unroll
+                for (int k = 0; k < kLanePts; ++k) pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], qx, qy, qz));
+            }
             float t1 = -1.0f, t2 = -1.0f;
 #pragma unroll
             for (int k = 0; k < kLanePts; ++k) {
-                float d = pd[k];
-#pragma unroll
-                for (int t = 0; t < kTop; ++t)
-                    if (hit_a & (1u << t)) d = fminf(d, fps_key(px[k], py[k], pz[k], s.px[t], s.py[t], s.pz[t]));
-                pd[k] = d;
-                t2 = fmaxf(t2, fminf(t1, d));
-                t1 = fmaxf(t1, d);
+                t2 = fmaxf(t2, fminf(t1, pd[k]));
+                t1 = fmaxf(t1, pd[k]);
             }
             const float wm = warp_max_f(t1);
             uint32_t cid = 0xffffffffu;
@@ -646,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                 const int o = lane + 32 * k;
                 const float qx = s_pts[wo + o], qy = s_pts[kPlane + wo + o], qz = s_pts[2 * kPlane + wo + o];
                 float d = s_pts[3 * kPlane + wo + o];
-#pragma unroll
+#pragma unroll 1
                 for (int t = 0; t < kTop; ++t)
                     if (hit_b & (1u << t)) d = fminf(d, fps_key(qx, qy, qz, s.px[t], s.py[t], s.pz[t]));
                 s_pts[3 * kPlane + wo + o] = d;
@@ -677,8 +741,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                 s_bm[6 * kWarps + warp] = wm;
             }
         }
-        bar_arrive(kBarCands);
-        bar_wait(kBarPicks);
+        bar_arrive(kBarCands, kCandsCount);
+        bar_wait(kBarPicks, kThreads);
         const int n = take_picks(a, s, j);
         if (n == 0) break;
         j += n;
@@ -761,9 +825,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_global(FpsArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     shared_init(s);
     start_round(a, s);
-    if (warp == kComputeWarps) {
+    if (warp >= kComputeWarps) {
         __syncthreads();
-        exchange_loop(a, s, lane);
+        exchange_loop(a, s, warp, lane);
         return;
     }
     const int cb = a.chunks_per_block;
@@ -862,8 +926,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_global(FpsArgs a) {
                 s.sec[warp] = bound;
             }
         }
-        bar_arrive(kBarCands);
-        bar_wait(kBarPicks);
+        bar_arrive(kBarCands, kCandsCount);
+        bar_wait(kBarPicks, kThreads);
         const int n = take_picks(a, s, j);
         if (n == 0) break;
         j += n;
@@ -883,7 +947,7 @@ struct FpsPlan {
 int max_fps_blocks() { return std::min(device_sm_count(), kMaxBlocks); }
 
 // Launch shape: n_blocks = 0 picks the fewest blocks whose registers and
-// shared memory hold every point (15,872 per block), else 64 blocks (or the SM
+// shared memory hold every point (15,360 per block), else 80 blocks (or the SM
 // count, if smaller) with chunks streamed from global memory; n_blocks = k
 // uses k blocks, resident when they hold every point.
 int plan_fps(int64_t n, int n_blocks, FpsPlan* p) {

@@ -74,7 +74,7 @@ def test_fps_ties_and_duplicates():
 
 
 # Every launch shape of the persistent FPS kernel gives the same picks: one
-# block holding its points on chip (n <= 15,872), several such blocks, one
+# block holding its points on chip (n <= 15,360), several such blocks, one
 # block streaming chunks from memory, several streaming blocks.
 @pytest.mark.parametrize("n,n_l,blocks,seed", [
     (5_000, 200, 0, 11), (5_000, 200, 3, 12),
