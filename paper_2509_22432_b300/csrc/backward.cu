@@ -158,12 +158,7 @@ extern "C" int flood_filtration_backward(const flood_grid* grid, const float* L,
         }
         tables[k] = interior_table(m, k);
         a.I[k] = static_cast<int>(tables[k].size() / (k + 1));
-        if (a.I[k] > 0) {
-            uint8_t* comp;
-            if ((rc = scr.alloc(&comp, tables[k].size()))) return rc;
-            FLOOD_CUDA(cudaMemcpyAsync(comp, tables[k].data(), tables[k].size(), cudaMemcpyHostToDevice, s));
-            a.comp[k] = comp;
-        }
+        if (a.I[k] > 0 && (rc = device_interior_table(m, k, tables[k], &a.comp[k]))) return rc;
     }
     for (int k = 1; k <= 3; ++k) {
         if (n_simplices[k] <= 0 || !grad_values[k]) continue;

@@ -1,6 +1,7 @@
 // Status plumbing shared by every entry point of libflood.
 #include <stdarg.h>
 #include <atomic>
+#include <mutex>
 #include <stdio.h>
 
 #include "common.cuh"
@@ -65,6 +66,28 @@ int device_sm_count() {
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
+}
+
+// Stream-ordered allocations come from the device's default memory pool. With
+// the pool's default release threshold of 0, every synchronisation hands
+// freed memory back to the driver and the next allocation maps it again; the
+// library keeps up to 4 GiB cached instead (once per device, process-wide).
+void keep_pool_warm() {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return;
+    done[dev] = true;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    uint64_t threshold = uint64_t(4) << 30;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold) != cudaSuccess) cudaGetLastError();
 }
 
 }  // namespace flood

@@ -41,11 +41,15 @@ int cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::flood::cuda_fail(e_, #call); \
     } while (0)
 
+// Keep the device's default memory pool from returning freed memory to the
+// driver at every synchronisation (up to 4 GiB stays cached; once per device).
+void keep_pool_warm();
+
 // Stream-ordered scratch that is returned on scope exit.
 struct Scratch {
     cudaStream_t stream;
     std::vector<void*> ptrs;
-    explicit Scratch(cudaStream_t s) : stream(s) {}
+    explicit Scratch(cudaStream_t s) : stream(s) { keep_pool_warm(); }
     ~Scratch() {
         for (void* p : ptrs) cudaFreeAsync(p, stream);
     }

@@ -37,6 +37,9 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "geometry.cuh"
@@ -510,7 +513,9 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
         const float T = t * (1.0f + 1.0f / 1024.0f) + sh.slack;
         return T * T;
     };
-    for (int s = 0; s <= s_max; ++s) {
+    // shells below s0 hold no point (block distance field)
+    const int s0 = min(first_shell(g, lo, hi), s_max);
+    for (int s = s0; s <= s_max; ++s) {
         sh.s = s;
         shell_setup(g, sh);
         sh.T2 = search_radius2();
@@ -587,7 +592,8 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
     }
 }
 
-constexpr int kNS = 8;  // samples per lane
+constexpr int kNS = 8;       // samples per lane (light groups)
+constexpr int kHeavyNS = 8;  // samples per thread slot (heavy groups)
 
 // Largest j with off[j] <= item (off has n + 1 non-decreasing entries).
 __device__ __forceinline__ int job_of(const int32_t* off, int n, int32_t item) {
@@ -637,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
         const float oy = __fadd_rn(a.lat.oy, static_cast<float>(byi) * a.lat.B);
         const float oz = __fadd_rn(a.lat.oz, static_cast<float>(bzi) * a.lat.B);
         const int n = s_end - s_begin;
-        const int W = n <= kNS ? 1 : n <= 2 * kNS ? 2 : n <= 4 * kNS ? 4 : 8;
+        const int W = n <= kNS ? 1 : n <= 2 * kNS ? 2 : n <= 4 * kNS ? 4 : n <= 8 * kNS ? 8 : 16;
         process_group<kNS>(a, gv, W, s_begin, s_end, ox, oy, oz, tiles, bar, s_ub[warp][0], s_ub[warp][1], phases,
                            abort, cnt, lane);
     }
@@ -658,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
 constexpr int kHeavyTile = 2048;
 constexpr int kHeavyShells = 8;  // class threshold: groups with >= this many shells are heavy
 
-// Evaluate the NSL used sample slots of one tile (NSL <= kNS).
+// Evaluate the NSL used sample slots of one tile (NSL <= kHeavyNS).
 template <int NSL>
 __device__ __forceinline__ void heavy_tile(const float4* buf, int n, int gs, int G, const float* ax, const float* ay,
                                            const float* az, float* mn) {
@@ -711,12 +717,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         const float ox = __fadd_rn(a.lat.ox, static_cast<float>(bxi) * a.lat.B);
         const float oy = __fadd_rn(a.lat.oy, static_cast<float>(byi) * a.lat.B);
         const float oz = __fadd_rn(a.lat.oz, static_cast<float>(bzi) * a.lat.B);
-        const int W = n_valid <= kNS ? 1 : n_valid <= 2 * kNS ? 2 : n_valid <= 4 * kNS ? 4 : 8;
+        const int W = n_valid <= kHeavyNS ? 1 : n_valid <= 2 * kHeavyNS ? 2 : n_valid <= 4 * kHeavyNS ? 4 : 8;
         const int G = kThreads / W;
         const int gs = tid / W, lw = tid % W;
         const int nsl = (n_valid + W - 1) / W;  // sample slots in use per thread
-        float ax[kNS], ay[kNS], az[kNS], pp[kNS], mn[kNS];
-        bool val[kNS];
+        float ax[kHeavyNS], ay[kHeavyNS], az[kHeavyNS], pp[kHeavyNS], mn[kHeavyNS];
+        bool val[kHeavyNS];
         // group geometry (every thread reads the same records: cached loads)
         int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
         float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -741,7 +747,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             hi[2] = max(hi[2], cz);
         }
 #pragma unroll
-        for (int q = 0; q < kNS; ++q) {
+        for (int q = 0; q < kHeavyNS; ++q) {
             const int32_t i = s_begin + q * W + lw;
             val[q] = i < s_end;
             ax[q] = ay[q] = az[q] = pp[q] = 0.0f;
@@ -813,7 +819,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         // order like their bit patterns) and recompute the search radius.
         auto fold = [&]() {
 #pragma unroll
-            for (int q = 0; q < kNS; ++q) {
+            for (int q = 0; q < kHeavyNS; ++q) {
                 float m = mn[q];
                 for (int o = W; o < 32; o <<= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
                 if (val[q] && gs % (32 / W) == 0 && m < INFINITY)
@@ -836,7 +842,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             }
             __syncthreads();
         };
-        for (int s = 0; s <= s_max; ++s) {
+        const int s0 = min(first_shell(g, lo, hi), s_max);  // shells below s0 hold no point
+        for (int s = s0; s <= s_max; ++s) {
             sh.s = s;
             shell_setup(g, sh);
             sh.T2 = s_T2 = 0.0f;
@@ -898,7 +905,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
                     else if (nsl <= 4)
                         heavy_tile<4>(s_tiles, cnt, gs, G, ax, ay, az, mn);
                     else
-                        heavy_tile<kNS>(s_tiles, cnt, gs, G, ax, ay, az, mn);
+                        heavy_tile<kHeavyNS>(s_tiles, cnt, gs, G, ax, ay, az, mn);
                     pairs += tid == 0 ? static_cast<unsigned long long>(cnt) * n_valid : 0ull;
                     n_tiles += tid == 0;
                     fence_proxy_async_smem();
@@ -1092,6 +1099,30 @@ std::vector<uint8_t> interior_table(int m, int k) {
     return out;
 }
 
+// Device copy of interior_table(m, k), uploaded once per device and kept for
+// the life of the process (at most C(63, 3) x 4 bytes per (m, k)).
+int device_interior_table(int m, int k, const std::vector<uint8_t>& host, const uint8_t** out) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, uint8_t*> cache;
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    uint8_t*& p = cache[std::make_tuple(dev, m, k)];
+    if (!p) {
+        uint8_t* q = nullptr;
+        FLOOD_CUDA(cudaMalloc(&q, host.size()));
+        const cudaError_t e = cudaMemcpy(q, host.data(), host.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(q);
+            return cuda_fail(e, "interior table upload");
+        }
+        p = q;
+    }
+    *out = p;
+    return FLOOD_OK;
+}
+
+
 }  // namespace flood
 
 using namespace flood;
@@ -1118,7 +1149,7 @@ struct JobState {
     Lattice lat;
     int64_t n_coarse, n_buckets, max_samples, max_n, max_groups;
     std::vector<uint8_t> tables[4];
-    uint8_t* comp[4];
+    const uint8_t* comp[4];
     int32_t *bcount, *bstart, *bfill, *goff, *g_arg, *cls;
     int2 *groups, *groups_sorted;
     SampleRec* recs;
@@ -1195,11 +1226,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s)
             J.max_samples = std::max(J.max_samples, J.nk[k] * J.I[k]);
             J.max_n = std::max(J.max_n, J.nk[k]);
             total_samples += J.nk[k] * J.I[k];
-            if (J.I[k] > 0) {
-                if ((rc = scr.alloc(&J.comp[k], J.tables[k].size()))) return rc;
-                FLOOD_CUDA(cudaMemcpyAsync(J.comp[k], J.tables[k].data(), J.tables[k].size(), cudaMemcpyHostToDevice,
-                                           s));
-            }
+            if (J.I[k] > 0 && (rc = device_interior_table(J.in.m, k, J.tables[k], &J.comp[k]))) return rc;
         }
         J.lat = make_lattice(grid, total_samples);
         J.n_coarse = int64_t(J.lat.bx) * J.lat.by * J.lat.bz;

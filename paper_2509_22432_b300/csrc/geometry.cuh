@@ -23,6 +23,7 @@ struct flood_grid {
     float4* pts;          // points sorted by cell: (x, y, z, original row as int bits)
     int32_t* cell_start;  // n_cells + 1 offsets into pts
     uint32_t* occupied;   // one bit per block of 4 x 4 x 4 cells that holds any point
+    uint8_t* bdist;       // per block: Chebyshev distance in blocks to the nearest occupied one (capped, a lower bound)
     int32_t bdims[3];     // blocks per axis
     int64_t device_bytes;
 };
@@ -32,11 +33,14 @@ namespace flood {
 // Interior compositions of m into k+1 parts >= 1 (barycentric c_i with
 // lambda_i = c_i / m, Lemma 1), lexicographic in (c_0, ..., c_k), as bytes.
 std::vector<uint8_t> interior_table(int m, int k);
+// Device copy of interior_table(m, k) (host: that table), cached per device.
+int device_interior_table(int m, int k, const std::vector<uint8_t>& host, const uint8_t** out);
 
 struct GridView {
     const float4* pts;
     const int32_t* cell_start;
     const uint32_t* occupied;
+    const uint8_t* bdist;
     int dx, dy, dz;
     int bx, by, bz;
     float ox, oy, oz;
@@ -49,6 +53,7 @@ inline GridView view_of(const flood_grid* g) {
     v.pts = g->pts;
     v.cell_start = g->cell_start;
     v.occupied = g->occupied;
+    v.bdist = g->bdist;
     v.bx = g->bdims[0];
     v.by = g->bdims[1];
     v.bz = g->bdims[2];
@@ -80,6 +85,22 @@ __device__ __forceinline__ bool row_occupied(const GridView& g, int cy, int cz, 
         if (g.occupied[bit >> 5] & (1u << (bit & 31))) return true;
     }
     return false;
+}
+
+// First shell (Chebyshev distance in cells from the box [lo, hi]) that can
+// hold a point: if every 4 x 4 x 4 block touching the box is D >= 1 blocks
+// from the nearest occupied block, no point lies within 4 (D - 1) cells of
+// the box, so shells 0 .. 4 (D - 1) are empty. Boxes over more than 64
+// blocks start at shell 0.
+__device__ __forceinline__ int first_shell(const GridView& g, const int lo[3], const int hi[3]) {
+    const int x0 = lo[0] >> 2, x1 = hi[0] >> 2, y0 = lo[1] >> 2, y1 = hi[1] >> 2, z0 = lo[2] >> 2, z1 = hi[2] >> 2;
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1) > 64) return 0;
+    int d = 255;
+    for (int z = z0; z <= z1; ++z)
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x)
+                d = min(d, static_cast<int>(g.bdist[(static_cast<int64_t>(z) * g.by + y) * g.bx + x]));
+    return d >= 1 ? 4 * (d - 1) + 1 : 0;
 }
 
 // Vertex coordinates of a k-simplex: origin v0 and edge vectors e_j = v_j - v0.

@@ -58,6 +58,42 @@ __global__ void k_block_bits(GridView g, uint32_t* bits) {
     if (any) atomicOr(&bits[b >> 5], 1u << (b & 31));
 }
 
+// Chebyshev distance transform of the block occupancy, in three separable
+// passes (distance along x to an occupied block, then the max-min combination
+// along y and along z), each over a window of +-kBdistCap blocks. Distances
+// are capped at kBdistCap, so every stored value is a lower bound.
+constexpr int kBdistCap = 15;
+
+__global__ void k_bdist_x(GridView g, uint8_t* out) {
+    const int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t nb = int64_t(g.bx) * g.by * g.bz;
+    if (b >= nb) return;
+    const int bx = static_cast<int>(b % g.bx);
+    const int64_t row = b - bx;
+    int d = kBdistCap;
+    for (int dx = -kBdistCap; dx <= kBdistCap; ++dx) {
+        const int x = bx + dx;
+        if (x < 0 || x >= g.bx) continue;
+        const int64_t bit = row + x;
+        if (g.occupied[bit >> 5] & (1u << (bit & 31))) d = min(d, abs(dx));
+    }
+    out[b] = static_cast<uint8_t>(d);
+}
+
+// stride: blocks between neighbours along the axis; extent: blocks along it.
+__global__ void k_bdist_pass(const uint8_t* in, uint8_t* out, int64_t nb, int64_t stride, int extent) {
+    const int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (b >= nb) return;
+    const int c = static_cast<int>((b / stride) % extent);
+    int d = kBdistCap;
+    for (int dc = -kBdistCap; dc <= kBdistCap; ++dc) {
+        const int cc = c + dc;
+        if (cc < 0 || cc >= extent) continue;
+        d = min(d, max(abs(dc), static_cast<int>(in[b + dc * stride])));
+    }
+    out[b] = static_cast<uint8_t>(d);
+}
+
 }  // namespace
 
 // Default edge length: the cube root of the volume per point times 2, with
@@ -152,20 +188,25 @@ extern "C" int flood_build_grid(const float* X, int64_t n_points, float cell_siz
     for (int c = 0; c < 3; ++c) g->bdims[c] = (g->dims[c] + 3) / 4;
     const int64_t n_blocks = int64_t(g->bdims[0]) * g->bdims[1] * g->bdims[2];
     const int64_t n_words = (n_blocks + 31) / 32;
-    cudaError_t e1 = cudaMalloc(&g->pts, sizeof(float4) * n_points);
-    cudaError_t e2 = cudaMalloc(&g->cell_start, sizeof(int32_t) * (g->n_cells + 1));
-    cudaError_t e3 = cudaMalloc(&g->occupied, sizeof(uint32_t) * n_words);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    // from the stream-ordered pool (cheap once warm); flood_grid_destroy's
+    // cudaFree waits for all work before releasing them
+    cudaError_t e1 = cudaMallocAsync(&g->pts, sizeof(float4) * n_points, s);
+    cudaError_t e2 = cudaMallocAsync(&g->cell_start, sizeof(int32_t) * (g->n_cells + 1), s);
+    cudaError_t e3 = cudaMallocAsync(&g->occupied, sizeof(uint32_t) * n_words, s);
+    cudaError_t e4 = cudaMallocAsync(&g->bdist, static_cast<size_t>(n_blocks), s);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
         cudaGetLastError();
         flood_grid_destroy(g);
         set_error("flood_build_grid: device allocation failed");
         return FLOOD_ENOMEM;
     }
     g->device_bytes = int64_t(sizeof(float4)) * n_points + int64_t(sizeof(int32_t)) * (g->n_cells + 1) +
-                      int64_t(sizeof(uint32_t)) * n_words;
+                      int64_t(sizeof(uint32_t)) * n_words + n_blocks;
 
     int32_t *d_cell = nullptr, *d_count = nullptr;
-    if ((rc = scr.alloc(&d_cell, n_points)) || (rc = scr.alloc(&d_count, g->n_cells))) {
+    uint8_t* d_bd = nullptr;
+    if ((rc = scr.alloc(&d_cell, n_points)) || (rc = scr.alloc(&d_count, g->n_cells)) ||
+        (rc = scr.alloc(&d_bd, n_blocks))) {
         flood_grid_destroy(g);
         return rc;
     }
@@ -178,8 +219,13 @@ extern "C" int flood_build_grid(const float* X, int64_t n_points, float cell_siz
         cudaMemsetAsync(d_count, 0, sizeof(int32_t) * g->n_cells, s);
         k_scatter<<<nb, kThreads, 0, s>>>(X, n_points, d_cell, g->cell_start, d_count, g->pts); note_launch();
         cudaMemsetAsync(g->occupied, 0, sizeof(uint32_t) * n_words, s);
-        k_block_bits<<<static_cast<unsigned>(ceil_div(n_blocks, kThreads)), kThreads, 0, s>>>(view_of(g), g->occupied);
-        note_launch();
+        const unsigned nbb = static_cast<unsigned>(ceil_div(n_blocks, kThreads));
+        k_block_bits<<<nbb, kThreads, 0, s>>>(view_of(g), g->occupied);
+        k_bdist_x<<<nbb, kThreads, 0, s>>>(view_of(g), g->bdist);
+        k_bdist_pass<<<nbb, kThreads, 0, s>>>(g->bdist, d_bd, n_blocks, g->bdims[0], g->bdims[1]);
+        k_bdist_pass<<<nbb, kThreads, 0, s>>>(d_bd, g->bdist, n_blocks, int64_t(g->bdims[0]) * g->bdims[1],
+                                              g->bdims[2]);
+        note_launch(4);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "flood_build_grid kernels");
     }
@@ -218,5 +264,6 @@ extern "C" void flood_grid_destroy(flood_grid* g) {
     if (g->pts) cudaFree(g->pts);
     if (g->cell_start) cudaFree(g->cell_start);
     if (g->occupied) cudaFree(g->occupied);
+    if (g->bdist) cudaFree(g->bdist);
     free(g);
 }
