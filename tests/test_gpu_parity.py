@@ -234,6 +234,25 @@ def test_values_bitwise_invariant_to_cell_size():
             assert np.array_equal(s[k], runs[0][1][k])
 
 
+def test_voids_heavy_groups_and_empty_shells():
+    """A swisscheese-like cloud (§5.3 synthetic data: uniform points minus balls) at several cell
+    sizes: samples inside the voids are far from every point, so they run in the heavy-group kernel,
+    many are dropped by the nearest-landmark bound and scans start past empty shells. Values must
+    match the oracle and stay bitwise identical across cell sizes."""
+    X = data.swisscheese_cloud(30_000, n_holes=6, seed=17)
+    idx, _ = oracle.fps(X, 150, 0)
+    L = X[idx]
+    cx = delaunay_complex(L)
+    ref = oracle.flood_values(X, L, cx.simplices, 8, method="kdtree")
+    runs = [gpu_flood(X, L, cx, 8, cell_size=h, want_src=True) for h in (0.0, 0.02, 0.08, 0.5)]
+    for v, _, _ in runs:
+        assert_close(v, ref.values, X, "voids")
+    for v, s, _ in runs[1:]:
+        for k in range(4):
+            assert np.array_equal(v[k].view(np.uint32), runs[0][0][k].view(np.uint32))
+            assert np.array_equal(s[k], runs[0][1][k])
+
+
 def test_batched_filtration_equals_each_cloud_alone():
     """Clouds sharing one batched flood launch get exactly their alone results."""
     ops = _ops()
