@@ -33,6 +33,24 @@ WORKLOADS = {
 }
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
 FLOPS_PER_PAIR = 6               # one pair = 3 FMAs: |x'|^2 - 2 p'.x'
+# DRAM bytes (read + write) of one k_fps_resident launch on torus-1M, from one
+# ncu capture (profiles/k_fps_resident_torus-1M.md), valid only while the FPS
+# source is the one captured: reported as null once fps.cu changes.
+FPS_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 16_063_488 + 1_536,
+                    "fps_cu_sha256": "912f4a8234893e0acdcf9e0ae416420e2ea4b51db62eac8ba00829e089fd0138"}
+
+
+def _fps_traffic(workload: str):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_2509_22432_b300", "csrc", "fps.cu"), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    cap = FPS_DRAM_CAPTURE
+    if workload != cap["workload"] or digest != cap["fps_cu_sha256"]:
+        return None
+    return float(cap["bytes"])
 
 
 def _peaks():
@@ -398,7 +416,8 @@ def main():
                      "filtration": float(np.mean([e[2].elapsed_time(e[3]) for e in phase_events])),
                      "flood_kernels": fk},
         "roofline": {"bound": "hbm", "achieved": fps_gbs, "peak": hbm, "unit": "GB/s", "frac": fps_gbs / hbm,
-                     "traffic": None, "kernel": "k_fps_resident (FPS, dominant by time)", "effective": True,
+                     "traffic": _fps_traffic(args.workload), "traffic_unit": "bytes per launch",
+                     "kernel": "k_fps_resident (FPS, dominant by time)", "effective": True,
                      "algorithmic_bytes": "20 N per pick (12N coordinates + 8N running minima) of the streaming "
                                           "algorithm; effective: points stay on chip and chunks whose minima "
                                           "provably cannot change are skipped (exact)",
