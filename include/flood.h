@@ -85,11 +85,11 @@ int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t sta
  * number of co-resident 1024-thread blocks (one per SM) the persistent FPS
  * launch may use:
  *   0   automatic (what flood_fps does): the fewest blocks whose registers
- *       and shared memory hold every point (15,360 points per block, so up
- *       to 1,228,800 points on 80 blocks; one block needs no grid-wide
+ *       and shared memory hold every point (14,336 points per block, so up
+ *       to 1,146,880 points on 80 blocks; one block needs no grid-wide
  *       exchange), else 80 blocks with points streamed from memory;
  *   1   one block: leaves the other SMs to concurrent work (many small
- *       clouds at once); points stream from memory above 15,360;
+ *       clouds at once); points stream from memory above 14,336;
  *   k   k blocks (clamped to the SM count and to 80).
  * Errors: as flood_fps; FLOOD_EINVAL also for n_blocks < 0.
  * ------------------------------------------------------------------------ */
@@ -105,7 +105,7 @@ int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_landmarks, int6
  * loop that forbids allocator calls after start-up, or a plugin whose host
  * framework forbids its extensions from allocating. It computes exactly what
  * flood_fps computes (same kernels, same bit-exact picks) but takes all of
- * its scratch from one fixed-size array compiled into the library (26 MiB of
+ * its scratch from one fixed-size array compiled into the library (27 MiB of
  * device memory, held by every GPU that loads the library until the process
  * exits) and calls no allocating routine.
  *

@@ -14,12 +14,12 @@
 //   between l and the box. A chunk whose gap is >= its largest d_i is
 //   therefore provably unchanged and skipped, bit-exactly; after the first few
 //   hundred picks almost every chunk is skipped.
-// * Two warps of each 1024-thread block run the grid-wide exchange, once per
-//   round: each block publishes its four best candidates with coordinates and
-//   a bound on the rest in tagged words, and polls every block's words until
-//   all carry the round's tag. That one pass synchronises the grid and
+// * Four warps of each 1024-thread block run the grid-wide exchange, once per
+//   round: each block publishes its eight best candidates with coordinates
+//   and a bound on the rest in tagged words, and polls every block's words
+//   until all carry the round's tag. That one pass synchronises the grid and
 //   delivers the next pick with its coordinates (no dependent load follows),
-//   and often the pick after it as well (see "rounds" below).
+//   and usually several picks after it as well (see "rounds" below).
 //
 // The key is the binary32 squared distance with each operation rounded on its
 // own (__fsub_rn/__fmul_rn/__fadd_rn are never contracted into FMAs), which
@@ -39,12 +39,13 @@ namespace {
 
 constexpr int kThreads = 1024;  // one block per SM
 constexpr int kWarps = kThreads / 32;
-constexpr int kComputeWarps = kWarps - 2;  // the last two warps run the exchange
+constexpr int kPollers = 4;                // the last four warps run the exchange
+constexpr int kComputeWarps = kWarps - kPollers;
 constexpr int kLanePts = 8;                // points per lane of a chunk
 constexpr int kChunk = 32 * kLanePts;      // points per chunk (resident kernel)
 constexpr int64_t kBlockPts = 2 * int64_t(kComputeWarps) * kChunk;  // points a resident block holds
-constexpr int kMaxBlocks = 80;             // two exchange warps poll 40 blocks each in 5 loads per lane
-constexpr int kSlotStride = 16;            // uint64 words per slot line (128 bytes; 8 used)
+constexpr int kMaxBlocks = 80;             // four exchange warps poll 20 blocks each in 5 loads per lane
+constexpr int kSlotStride = 32;            // uint64 words per block slot (256 bytes)
 constexpr int64_t kSortMin = 16384;        // smaller clouds keep their input order
 constexpr int kGlobalBatch = 5;            // global kernel: points per lane loaded at once
 constexpr int kMetaBytes = 8 + 10 * 4;     // per chunk in shared memory: candidate, box, coordinates, second
@@ -183,39 +184,44 @@ struct FpsArgs {
 };
 
 // ---------------------------------------------------------------- rounds
-// A round folds the previous round's picks (one to four landmarks) into every
-// chunk, then selects the next picks with one grid-wide exchange:
+// A round folds the previous round's picks (1 to kMaxPicks landmarks) into
+// every chunk, then selects the next picks with one grid-wide exchange:
 //
-// * Each block reports its four best entries (an entry is a chunk candidate:
+// * Each block reports its eight best entries (an entry is a chunk candidate:
 //   the chunk's largest running minimum, ties to the lowest original row, with
 //   the point's coordinates; the global kernel reports one entry per warp) and
-//   a bound U_b on every other point of the block: the larger of its fifth
+//   a bound U_b on every other point of the block: the larger of its ninth
 //   entry and the largest "second" of any entry (the second-largest minimum
 //   of the entry's chunk, or of all of the warp's other points).
-// * The best entry E1 over all blocks is the next pick, as in plain FPS.
-//   Entry E_k (k = 2..4) is picked right after E_(k-1) when E_2..E_(k-1) were,
-//   its key is positive and strictly above U = max_b U_b, and no earlier pick
-//   of the round lowers it (kappa(E_k, E_i) >= key(E_k), i < k): running
-//   minima only decrease, every point outside E_1..E_k is below E_k in (key,
-//   lowest row) order, and E_k's own minimum is unchanged by the earlier
-//   picks, so plain FPS picks E_k next. All are folded in the next round. On
-//   the 1M-point torus with 2,000 picks a round makes 2.9 picks on average.
-constexpr int kTop = 4;
+// * Each exchange warp keeps the eight best entries of its quarter of the
+//   blocks; the bound U is the largest U_b and the largest ninth entry of a
+//   quarter, so every point outside the 32 kept entries has a running
+//   minimum <= U, now and after any pick (minima only decrease).
+// * The kept entries carry their points' exact running minima. Plain FPS
+//   picks the point with the largest minimum (ties to the lowest row), so
+//   the best kept entry is the next pick; after it, the kept entries' minima
+//   are lowered by that pick (kappa to it), and the best of them is the pick
+//   after, as long as its minimum is positive and strictly above U (then no
+//   point outside the entries can beat or tie it). Repeating this selects
+//   several picks per round with the result of plain FPS, bit for bit: on the
+//   1M-point torus with 2,000 picks a round makes about four picks.
+constexpr int kTop = 8;        // entries a block publishes
+constexpr int kMaxPicks = 16;  // picks per round (one box-test lane per pick and chunk)
 
-// Two exchange warps: warp 30 (X0) reduces the block's entries, publishes
-// them and polls the first half of the blocks; warp 31 (X1) polls the second
-// half and hands its best entries to X0, which merges and selects the picks.
-// Named barriers per round: compute warps arrive at kBarCands (X0 waits),
-// X0 arrives at kBarPub once the block's slot is published (X1 waits: its
-// polling loads would otherwise slow X0's shared-memory loads and shuffles,
-// which share the SM's memory pipe), X1 arrives at kBarHalf (X0 waits), X0
-// arrives at kBarPicks (everyone else waits). An arrival releases the
-// arriving thread's earlier shared-memory writes to the threads that
-// complete the wait.
-constexpr int kX0 = kComputeWarps;  // warp kComputeWarps + 1 is X1
-constexpr int kBarCands = 1, kBarPicks = 2, kBarHalf = 3, kBarPub = 4;
+// Exchange warps X0..X3 (warps kComputeWarps..kWarps - 1): X0 reduces the
+// block's entries, publishes them and polls the first quarter of the blocks;
+// X1..X3 poll the other quarters and hand their best entries to X0, which
+// merges and selects the picks. Named barriers per round: compute warps
+// arrive at kBarCands (X0 waits), X0 arrives at kBarPub once the block's slot
+// is published (X1..X3 wait: polling loads would otherwise slow X0's
+// shared-memory loads and shuffles, which share the SM's memory pipe),
+// X1..X3 arrive at kBarQuarters (X0 waits), X0 arrives at kBarPicks
+// (everyone else waits). An arrival releases the arriving thread's earlier
+// shared-memory writes to the threads that complete the wait.
+constexpr int kX0 = kComputeWarps;  // warp kX0 + 1 is X1 (it records the picks)
+constexpr int kBarCands = 1, kBarPicks = 2, kBarQuarters = 3, kBarPub = 4;
 constexpr int kCandsCount = (kComputeWarps + 1) * 32;
-constexpr int kHalfCount = 64;
+constexpr int kPollCount = kPollers * 32;
 __device__ __forceinline__ void bar_arrive(int id, int count) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
@@ -227,13 +233,13 @@ struct FpsShared {
     uint64_t cand[2 * kWarps];  // entries (resident kernel: w = chunk A, 32 + w = chunk B of warp w)
     float cx[2 * kWarps], cy[2 * kWarps], cz[2 * kWarps];
     float sec[2 * kWarps];      // bound on the entry's other points (-1: none)
-    uint64_t pick[kTop];        // this round's picks
-    float px[kTop], py[kTop], pz[kTop];
+    uint64_t pick[kMaxPicks];   // this round's picks (candidate words with the minimum at the pick)
+    float px[kMaxPicks], py[kMaxPicks], pz[kMaxPicks];
     int n_pick;                 // picks of the round; -1 = stop (timeout)
-    uint64_t half[2][kTop];     // best entries of each half of the blocks (X0's, X1's)
-    float hx[2][kTop], hy[2][kTop], hz[2][kTop];
-    float hbound;               // X1's half: bound on everything else
-    int hstop;
+    uint64_t qc[kPollers][kTop];  // best entries of each quarter of the blocks
+    float qx[kPollers][kTop], qy[kPollers][kTop], qz[kPollers][kTop];
+    float qbound[kPollers];     // each quarter's bound on everything else
+    int qstop[kPollers];
 };
 
 __device__ __forceinline__ void shared_init(FpsShared& s) {
@@ -288,32 +294,35 @@ __device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_
 __device__ __forceinline__ uint32_t bound_up30(float u) { return ((__float_as_uint(u) + 3u) & ~3u) >> 2; }
 __device__ __forceinline__ float bound_from30(uint32_t v) { return __uint_as_float(v << 2); }
 
-// Slot of block b for round r (parity r & 1): its own 128-byte line holding
-// kTop entries of four words, each word tagged with r & 3 in its top bits:
+// Slot of block b for round r (parity r & 1): 256 bytes holding kTop
+// entries of four words, each word tagged with r & 3 in its top bits:
 //   w0 = tag | candidate
 //   w1 = tag | U30 << 32 (first entry only) | bits of x;  w2 = tag | y;  w3 = tag | z.
 // A reader accepts a block once all its words carry round r, so every word is
 // read atomically and no order between them is needed; a block cannot publish
 // round r + 2 (same parity) before every block has finished reading r + 1.
-// Exchange warp h polls blocks [40 h, 40 h + 40): in load l, lane 4 i + q
-// reads entry q of block 40 h + 8 l + i (one 32-byte access per lane).
+// Exchange warp h polls blocks [20 h, 20 h + 20): in load l, lane 8 i + q
+// reads entry q of block 20 h + 4 l + i (one 32-byte access per lane).
 constexpr int kBlocksPerLoad = 32 / kTop;
 constexpr int kPollLoads = 5;
-constexpr int kHalfBlocks = kBlocksPerLoad * kPollLoads;
-static_assert(2 * kHalfBlocks == kMaxBlocks, "two exchange warps cover every block");
+constexpr int kQuarterBlocks = kBlocksPerLoad * kPollLoads;
+static_assert(kPollers * kQuarterBlocks == kMaxBlocks, "the exchange warps cover every block");
+static_assert(kPollers * kTop == 32, "X0 merges one kept entry per lane");
+static_assert(2 * kMaxPicks <= 32, "one box-test lane per pick and chunk");
 
-// Poll one half of the blocks until all carry round r; its best kTop entries
-// go to s.half[h] (each written by the lane holding it). Returns the half's
-// bound on every other point.
-__device__ __forceinline__ float poll_half(const FpsArgs& a, FpsShared& s, int r, int h, int lane, bool& stop) {
+// Poll quarter h of the blocks until all carry round r; its best kTop entries
+// go to s.qc[h] etc. (each written by the lane holding it) and its bound on
+// every other point to s.qbound[h].
+__device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int r, int h, int lane) {
     const uint64_t tag = static_cast<uint64_t>(r & 3) << 62;
     const uint64_t* buf = a.slots + static_cast<size_t>(r & 1) * kMaxBlocks * kSlotStride;
     const int nb = gridDim.x, q = lane % kTop, bi = lane / kTop;
     uint64_t w0[kPollLoads], w1[kPollLoads], w2[kPollLoads], w3[kPollLoads];
+    bool stop = false;
     for (uint32_t polls = 0;;) {
 #pragma unroll
         for (int l = 0; l < kPollLoads; ++l) {
-            const int b = h * kHalfBlocks + l * kBlocksPerLoad + bi;
+            const int b = h * kQuarterBlocks + l * kBlocksPerLoad + bi;
             if (b < nb) {
                 ld_relaxed_v4_u64(buf + static_cast<size_t>(b) * kSlotStride + 4 * q, w0[l], w1[l], w2[l], w3[l]);
             } else {
@@ -341,8 +350,9 @@ __device__ __forceinline__ float poll_half(const FpsArgs& a, FpsShared& s, int r
         cyb[l] = static_cast<uint32_t>(w2[l]);
         czb[l] = static_cast<uint32_t>(w3[l]);
     }
+    u30 = __reduce_max_sync(0xffffffffu, u30);
 #pragma unroll
-    for (int k = 0; k < kTop; ++k) {
+    for (int k = 0; k <= kTop; ++k) {
         uint64_t v = 0ull;
         int vl = 0;
 #pragma unroll
@@ -352,6 +362,13 @@ __device__ __forceinline__ float poll_half(const FpsArgs& a, FpsShared& s, int r
                 vl = l;
             }
         const uint64_t m = warp_max_u64(v);
+        if (k == kTop) {  // the best entry left out
+            if (lane == 0) {
+                s.qbound[h] = fmaxf(bound_from30(u30), cand_key(m));
+                s.qstop[h] = stop;
+            }
+            break;
+        }
         const int o = __ffs(__ballot_sync(0xffffffffu, v == m)) - 1;
         if (lane == o) {
             uint32_t ex = 0u, ey = 0u, ez = 0u;
@@ -363,17 +380,16 @@ __device__ __forceinline__ float poll_half(const FpsArgs& a, FpsShared& s, int r
                     ez = czb[l];
                     c[l] = 0ull;
                 }
-            s.half[h][k] = m;
-            s.hx[h][k] = __uint_as_float(ex);
-            s.hy[h][k] = __uint_as_float(ey);
-            s.hz[h][k] = __uint_as_float(ez);
+            s.qc[h][k] = m;
+            s.qx[h][k] = __uint_as_float(ex);
+            s.qy[h][k] = __uint_as_float(ey);
+            s.qz[h][k] = __uint_as_float(ez);
         }
     }
-    return bound_from30(__reduce_max_sync(0xffffffffu, u30));
 }
 
-// X0, one round: block reduction, publication, its half of the polling, the
-// merge with X1's half, and the picks.
+// X0, one round: block reduction, publication, its quarter of the polling,
+// the merge with the other quarters, and the picks.
 __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, int r, int picks_left, int lane) {
     uint64_t me;
     float mx, my, mz;
@@ -387,54 +403,47 @@ __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, in
             st_relaxed_v4_u64(buf + static_cast<size_t>(blockIdx.x) * kSlotStride + 4 * lane, tag | me,
                               tag | hi | __float_as_uint(mx), tag | __float_as_uint(my), tag | __float_as_uint(mz));
         }
-        bar_arrive(kBarPub, kHalfCount);
-        bound = poll_half(a, s, r, 0, lane, stop);
-        bar_wait(kBarHalf, kHalfCount);
+        bar_arrive(kBarPub, kPollCount);
+        poll_quarter(a, s, r, 0, lane);
+        bar_wait(kBarQuarters, kPollCount);
         __syncwarp();
-        // merge: lanes 0..3 hold X0's half, lanes 4..7 X1's
-        uint64_t v = 0ull;
-        float vx = 0.0f, vy = 0.0f, vz = 0.0f;
-        if (lane < 2 * kTop) {
-            const int hh = lane / kTop, kk = lane % kTop;
-            v = s.half[hh][kk];
-            vx = s.hx[hh][kk];
-            vy = s.hy[hh][kk];
-            vz = s.hz[hh][kk];
+        // lane 8 h + k holds entry k of quarter h
+        const int hh = lane / kTop, kk = lane % kTop;
+        me = s.qc[hh][kk];
+        mx = s.qx[hh][kk];
+        my = s.qy[hh][kk];
+        mz = s.qz[hh][kk];
+        bound = fmaxf(fmaxf(s.qbound[0], s.qbound[1]), fmaxf(s.qbound[2], s.qbound[3]));
+        stop = (s.qstop[0] | s.qstop[1] | s.qstop[2] | s.qstop[3]) != 0;
+    }
+    // Picks: the best live entry while its minimum stays positive and above
+    // the bound (the first one unconditionally); each pick lowers the others.
+    const int cap = min(picks_left, kMaxPicks);
+    const uint32_t row = cand_row(me);
+    float cur = cand_key(me);
+    bool live = me != 0ull;
+    int np = 0;
+    while (np < cap) {
+        const uint64_t v = live ? pack_cand(cur, row) : 0ull;
+        const uint64_t m = warp_max_u64(v);
+        if (np > 0 && !(m != 0ull && cand_key(m) > 0.0f && cand_key(m) > bound)) break;
+        const uint32_t own = __ballot_sync(0xffffffffu, v == m);
+        const int o = m != 0ull ? __ffs(own) - 1 : 0;
+        const float qx = __shfl_sync(0xffffffffu, mx, o), qy = __shfl_sync(0xffffffffu, my, o),
+                    qz = __shfl_sync(0xffffffffu, mz, o);
+        if (lane == o) {
+            s.pick[np] = m;
+            s.px[np] = qx;
+            s.py[np] = qy;
+            s.pz[np] = qz;
+            live = false;
         }
-        bound = fmaxf(bound, s.hbound);
-        stop = stop || s.hstop;
-#pragma unroll
-        for (int k = 0; k < kTop; ++k) {
-            const uint64_t m = warp_max_u64(v);
-            const int o = __ffs(__ballot_sync(0xffffffffu, v == m)) - 1;
-            if (lane == o) {
-                s.pick[k] = m;
-                s.px[k] = vx;
-                s.py[k] = vy;
-                s.pz[k] = vz;
-                v = 0ull;
-            }
-        }
-    } else if (lane < kTop) {
-        s.pick[lane] = me;
-        s.px[lane] = mx;
-        s.py[lane] = my;
-        s.pz[lane] = mz;
+        ++np;
+        if (m == 0ull) break;
+        cur = fminf(cur, fps_key(mx, my, mz, qx, qy, qz));
     }
     __syncwarp();
-    // lane k in 1..3 checks whether entry k may follow the picks before it
-    bool ok = false;
-    if (lane >= 1 && lane < kTop) {
-        const uint64_t ek = s.pick[lane];
-        const float key = cand_key(ek);
-        const float x = s.px[lane], y = s.py[lane], z = s.pz[lane];
-        ok = picks_left > lane && ek != 0ull && key > 0.0f && key > bound;
-#pragma unroll
-        for (int i = 0; i < kTop - 1; ++i)
-            if (i < lane) ok = ok && fps_key(x, y, z, s.px[i], s.py[i], s.pz[i]) >= key;
-    }
-    const uint32_t okm = __ballot_sync(0xffffffffu, ok) >> 1;  // bit k - 1: entry k
-    if (lane == 0) s.n_pick = stop ? -1 : __ffs(~okm);         // 1 + leading accepted entries
+    if (lane == 0) s.n_pick = stop ? -1 : np;
 }
 
 // After the round's last barrier: how many picks the round made; 0 tells
@@ -473,8 +482,8 @@ __device__ __forceinline__ void start_round(const FpsArgs& a, FpsShared& s) {
 }
 
 // The exchange warps' loops (shared by both kernels): X0 waits where the
-// compute warps arrive and arrives where they wait; X1 polls its half and
-// hands it over.
+// compute warps arrive and arrives where they wait; X1..X3 poll their
+// quarters and hand them over.
 __device__ __forceinline__ void exchange_loop(const FpsArgs& a, FpsShared& s, int warp, int lane) {
     int r = 1;
     for (int j = 1; j < a.n_landmarks; ++r) {
@@ -485,15 +494,10 @@ __device__ __forceinline__ void exchange_loop(const FpsArgs& a, FpsShared& s, in
             bar_arrive(kBarPicks, kThreads);
         } else {
             if (gridDim.x > 1) {
-                bool stop = false;
-                bar_wait(kBarPub, kHalfCount);
-                const float hb = poll_half(a, s, r, 1, lane, stop);
-                if (lane == 0) {
-                    s.hbound = hb;
-                    s.hstop = stop;
-                }
+                bar_wait(kBarPub, kPollCount);
+                poll_quarter(a, s, r, warp - kX0, lane);
                 __syncwarp();
-                bar_arrive(kBarHalf, kHalfCount);
+                bar_arrive(kBarQuarters, kPollCount);
             }
             bar_wait(kBarPicks, kThreads);
         }
@@ -508,10 +512,19 @@ __device__ __forceinline__ void exchange_loop(const FpsArgs& a, FpsShared& s, in
 __device__ __forceinline__ uint32_t box_hits(const FpsShared& s, int np, float lox, float loy, float loz, float hix,
                                              float hiy, float hiz, float maxd) {
     uint32_t hit = 0u;
-#pragma unroll
-    for (int t = 0; t < kTop; ++t)
-        if (t < np && !(box_gap2(s.px[t], s.py[t], s.pz[t], lox, loy, loz, hix, hiy, hiz) >= maxd)) hit |= 1u << t;
+    for (int t = 0; t < np; ++t)
+        if (!(box_gap2(s.px[t], s.py[t], s.pz[t], lox, loy, loz, hix, hiy, hiz) >= maxd)) hit |= 1u << t;
     return hit;
+}
+
+// Even bits of v (bit 2 t moves to bit t).
+__device__ __forceinline__ uint32_t even_bits(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0f0f0f0fu;
+    v = (v | (v >> 4)) & 0x00ff00ffu;
+    v = (v | (v >> 8)) & 0x0000ffffu;
+    return v;
 }
 
 // Candidate of a chunk after its update: warp maximum wm of the minima, ties
@@ -542,8 +555,8 @@ __device__ __forceinline__ int publish_chunk(FpsShared& s, int slot, float wm, u
 // k < 8) and chunk B = A + nb in shared memory; boxes and chunk B's largest
 // minimum in shared memory, chunk A's in a register.
 // Dynamic shared memory:
-//   ids  int32 [2][31][256]  original rows of chunks A and B
-//   pts  float [4][31][256]  chunk B: x, y, z, running minimum
+//   ids  int32 [2][28][256]  original rows of chunks A and B
+//   pts  float [4][28][256]  chunk B: x, y, z, running minimum
 //   meta float [13][32]      chunk B: box lo x/y/z, hi x/y/z, largest minimum;
 //                            chunk A: box lo x/y/z, hi x/y/z
 constexpr int kResIds = 0;
@@ -653,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
     for (int j = 1; j < a.n_landmarks;) {
         // lanes 2 t + c test pick t against chunk c (0 = A, 1 = B)
         bool hit = false;
-        if (lane < 2 * kTop && (lane >> 1) < s.n_pick) {
+        if ((lane >> 1) < s.n_pick) {
             const int t = lane >> 1, f = (lane & 1) ? 0 : 7;
             const float md = (lane & 1) ? s_bm[6 * kWarps + warp] : maxd;
             hit = !(box_gap2(s.px[t], s.py[t], s.pz[t], s_bm[f * kWarps + warp], s_bm[(f + 1) * kWarps + warp],
@@ -661,16 +674,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                              s_bm[(f + 4) * kWarps + warp], s_bm[(f + 5) * kWarps + warp]) >= md);
         }
         const uint32_t hb = __ballot_sync(0xffffffffu, hit);
-        uint32_t hit_a = 0u, hit_b = 0u;
-#pragma unroll
-        for (int t = 0; t < kTop; ++t) {
-            hit_a |= ((hb >> (2 * t)) & 1u) << t;
-            hit_b |= ((hb >> (2 * t + 1)) & 1u) << t;
-        }
+        const uint32_t hit_a = even_bits(hb), hit_b = even_bits(hb >> 1);
         if (hit_a) {
 #pragma unroll 1
-            for (int t = 0; t < kTop; ++t) {
-                if (!(hit_a & (1u << t))) continue;
+            for (uint32_t mt = hit_a; mt; mt &= mt - 1) {
+                const int t = __ffs(mt) - 1;
                 const float qx = s.px[t], qy = s.py[t], qz = s.pz[t];
 #pragma unroll
                 for (int k = 0; k < kLanePts; ++k) pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], qx, qy, qz));
@@ -711,8 +719,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                 const float qx = s_pts[wo + o], qy = s_pts[kPlane + wo + o], qz = s_pts[2 * kPlane + wo + o];
                 float d = s_pts[3 * kPlane + wo + o];
 #pragma unroll 1
-                for (int t = 0; t < kTop; ++t)
-                    if (hit_b & (1u << t)) d = fminf(d, fps_key(qx, qy, qz, s.px[t], s.py[t], s.pz[t]));
+                for (uint32_t mt = hit_b; mt; mt &= mt - 1) {
+                    const int t = __ffs(mt) - 1;
+                    d = fminf(d, fps_key(qx, qy, qz, s.px[t], s.py[t], s.pz[t]));
+                }
                 s_pts[3 * kPlane + wo + o] = d;
                 t2 = fmaxf(t2, fminf(t1, d));
                 t1 = fmaxf(t1, d);
@@ -791,9 +801,11 @@ __device__ __forceinline__ void update_chunk(const FpsArgs& a, const FpsShared& 
             const int64_t i = base + lane + 32 * (q + k);
             if (i < a.n) {
                 float nd = d[k];
-#pragma unroll
-                for (int t = 0; t < kTop; ++t)
-                    if (hit & (1u << t)) nd = fminf(nd, fps_key(x[k], y[k], z[k], s.px[t], s.py[t], s.pz[t]));
+#pragma unroll 1
+                for (uint32_t mt = hit; mt; mt &= mt - 1) {
+                    const int t = __ffs(mt) - 1;
+                    nd = fminf(nd, fps_key(x[k], y[k], z[k], s.px[t], s.py[t], s.pz[t]));
+                }
                 if (nd != d[k]) a.d[i] = nd;
                 t2 = fmaxf(t2, fminf(t1, nd));
                 t1 = fmaxf(t1, nd);
@@ -947,7 +959,7 @@ struct FpsPlan {
 int max_fps_blocks() { return std::min(device_sm_count(), kMaxBlocks); }
 
 // Launch shape: n_blocks = 0 picks the fewest blocks whose registers and
-// shared memory hold every point (15,360 per block), else 80 blocks (or the SM
+// shared memory hold every point (14,336 per block), else 80 blocks (or the SM
 // count, if smaller) with chunks streamed from global memory; n_blocks = k
 // uses k blocks, resident when they hold every point.
 int plan_fps(int64_t n, int n_blocks, FpsPlan* p) {
@@ -1104,14 +1116,14 @@ extern "C" int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, 
 // flood_fps but takes its scratch (point order, structure-of-arrays copy,
 // running minima, sort histogram, exchange slots, control words) from one
 // file-scope device array of fixed size that is part of the loaded module.
-// Every GPU that loads this library holds that array (26 MiB) until the
+// Every GPU that loads this library holds that array (27 MiB) until the
 // process exits.
 // ---------------------------------------------------------------------------
 namespace flood {
 namespace {
 
 constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 20;  // 1,048,576 points
-constexpr size_t kNoAllocBytes = size_t(26) << 20;      // holds run_fps's pieces for 2^20 points
+constexpr size_t kNoAllocBytes = size_t(27) << 20;      // holds run_fps's pieces for 2^20 points
 
 // The scratch itself. Host code must not use this name as a pointer: on the
 // host it is only a stand-in for the symbol, so its device address is looked
