@@ -164,6 +164,12 @@ __device__ __forceinline__ float warp_max_f(float v) {
     return from_ordered(__reduce_max_sync(0xffffffffu, ordered_bits(v)));
 }
 
+// Lowest lane whose predicate holds (32 if none): one redux, shorter than a
+// ballot followed by a find-first-set.
+__device__ __forceinline__ int first_lane(bool pred, int lane) {
+    return static_cast<int>(__reduce_min_sync(0xffffffffu, pred ? static_cast<uint32_t>(lane) : 32u));
+}
+
 struct FpsArgs {
     const float* X;    // (n, 3) input rows (start point)
     const float* x;    // points in processing order, structure of arrays
@@ -229,10 +235,15 @@ __device__ __forceinline__ void bar_wait(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Entries of compute warp w: w and 32 + w are the best points of its chunks
+// A and B, 64 + w and 96 + w their second best (resident kernel; the global
+// kernel fills w only).
+constexpr int kEntries = 4 * kWarps;
+
 struct FpsShared {
-    uint64_t cand[2 * kWarps];  // entries (resident kernel: w = chunk A, 32 + w = chunk B of warp w)
-    float cx[2 * kWarps], cy[2 * kWarps], cz[2 * kWarps];
-    float sec[2 * kWarps];      // bound on the entry's other points (-1: none)
+    uint64_t cand[kEntries];
+    float cx[kEntries], cy[kEntries], cz[kEntries];
+    float sec[2 * kWarps];      // bound on every other point of chunk A (w) or B (32 + w); -1: none
     uint64_t pick[kMaxPicks];   // this round's picks (candidate words with the minimum at the pick)
     float px[kMaxPicks], py[kMaxPicks], pz[kMaxPicks];
     int n_pick;                 // picks of the round; -1 = stop (timeout)
@@ -243,19 +254,14 @@ struct FpsShared {
 };
 
 __device__ __forceinline__ void shared_init(FpsShared& s) {
-    if (threadIdx.x < 2 * kWarps) {
+    if (threadIdx.x < kEntries) {
         s.cand[threadIdx.x] = 0ull;
         s.cx[threadIdx.x] = s.cy[threadIdx.x] = s.cz[threadIdx.x] = 0.0f;
-        s.sec[threadIdx.x] = -1.0f;
     }
+    if (threadIdx.x < 2 * kWarps) s.sec[threadIdx.x] = -1.0f;
 }
 
-// Block reduction (X0): lane l holds entries l and 32 + l; lane k < kTop
-// receives the k-th best entry. Returns the bound on every other point.
-__device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_t& me, float& mx, float& my,
-                                           float& mz) {
-    uint64_t a = s.cand[lane], b = s.cand[kWarps + lane];
-    int ia = lane, ib = kWarps + lane;
+__device__ __forceinline__ void order2(uint64_t& a, int& ia, uint64_t& b, int& ib) {
     if (b > a) {
         const uint64_t tv = a;
         a = b;
@@ -264,13 +270,28 @@ __device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_
         ia = ib;
         ib = ti;
     }
+}
+
+// Block reduction (X0): lane l holds entries l + 32 i (i < 4), sorted; lane
+// k < kTop receives the k-th best entry. Returns the bound on every other
+// point.
+__device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_t& me, float& mx, float& my,
+                                           float& mz) {
+    uint64_t e0 = s.cand[lane], e1 = s.cand[kWarps + lane], e2 = s.cand[2 * kWarps + lane],
+             e3 = s.cand[3 * kWarps + lane];
+    int i0 = lane, i1 = kWarps + lane, i2 = 2 * kWarps + lane, i3 = 3 * kWarps + lane;
+    order2(e0, i0, e1, i1);
+    order2(e2, i2, e3, i3);
+    order2(e0, i0, e2, i2);
+    order2(e1, i1, e3, i3);
+    order2(e1, i1, e2, i2);
     me = 0ull;
     mx = my = mz = 0.0f;
 #pragma unroll
     for (int k = 0; k < kTop; ++k) {
-        const uint64_t m = warp_max_u64(a);
-        const int o = __ffs(__ballot_sync(0xffffffffu, a == m)) - 1;
-        const int oi = __shfl_sync(0xffffffffu, ia, o);
+        const uint64_t m = warp_max_u64(e0);
+        const int o = first_lane(e0 == m, lane);
+        const int oi = __shfl_sync(0xffffffffu, i0, o);
         if (lane == k) {
             me = m;
             mx = s.cx[oi];
@@ -278,12 +299,16 @@ __device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_
             mz = s.cz[oi];
         }
         if (lane == o) {
-            a = b;
-            ia = ib;
-            b = 0ull;
+            e0 = e1;
+            i0 = i1;
+            e1 = e2;
+            i1 = i2;
+            e2 = e3;
+            i2 = i3;
+            e3 = 0ull;
         }
     }
-    const float next = cand_key(warp_max_u64(a));
+    const float next = cand_key(warp_max_u64(e0));
     const float sec = warp_max_f(fmaxf(s.sec[lane], s.sec[kWarps + lane]));
     return fmaxf(fmaxf(next, sec), 0.0f);
 }
@@ -369,7 +394,7 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
             }
             break;
         }
-        const int o = __ffs(__ballot_sync(0xffffffffu, v == m)) - 1;
+        const int o = first_lane(v == m, lane);
         if (lane == o) {
             uint32_t ex = 0u, ey = 0u, ez = 0u;
 #pragma unroll
@@ -427,8 +452,7 @@ __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, in
         const uint64_t v = live ? pack_cand(cur, row) : 0ull;
         const uint64_t m = warp_max_u64(v);
         if (np > 0 && !(m != 0ull && cand_key(m) > 0.0f && cand_key(m) > bound)) break;
-        const uint32_t own = __ballot_sync(0xffffffffu, v == m);
-        const int o = m != 0ull ? __ffs(own) - 1 : 0;
+        const int o = m != 0ull ? first_lane(v == m, lane) : 0;
         const float qx = __shfl_sync(0xffffffffu, mx, o), qy = __shfl_sync(0xffffffffu, my, o),
                     qz = __shfl_sync(0xffffffffu, mz, o);
         if (lane == o) {
@@ -527,24 +551,31 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t v) {
     return v;
 }
 
-// Candidate of a chunk after its update: warp maximum wm of the minima, ties
-// to the lowest original row cid (lanes pass their lowest row holding wm, or
-// ~0), written to entry `slot` by one lane; returns that lane (-1: none).
-__device__ __forceinline__ int publish_chunk(FpsShared& s, int slot, float wm, uint32_t cid, float cx, float cy,
-                                             float cz, int lane) {
-    uint32_t have = __ballot_sync(0xffffffffu, cid != 0xffffffffu);
-    if (__popc(have) > 1) {
-        const uint32_t m = __reduce_min_sync(0xffffffffu, cid);
-        have = __ballot_sync(0xffffffffu, cid == m);
-    }
-    const int owner = have ? __ffs(have) - 1 : -1;
-    if (lane == owner) {
+// Entry of a chunk after its update: the point with minimum wm and the lowest
+// original row (lanes pass their lowest row holding wm, or ~0; rows are
+// distinct, so one lane holds the smallest), written to entry `slot` by that
+// lane (entry 0 if no lane has one). Returns the row (~0: none) and sets
+// `owner` on the lane that wrote it.
+__device__ __forceinline__ uint32_t publish_chunk(FpsShared& s, int slot, float wm, uint32_t cid, float cx,
+                                                  float cy, float cz, int lane, bool& owner) {
+    const uint32_t m = __reduce_min_sync(0xffffffffu, cid);
+    owner = m != 0xffffffffu && cid == m;
+    if (owner) {
         s.cand[slot] = pack_cand(wm, cid);
         s.cx[slot] = cx;
         s.cy[slot] = cy;
         s.cz[slot] = cz;
+    } else if (m == 0xffffffffu && lane == 0) {
+        s.cand[slot] = 0ull;
     }
-    return owner;
+    return m;
+}
+
+// Running top three of a lane's minima (t1 >= t2 >= t3, as a multiset).
+__device__ __forceinline__ void top3_insert(float v, float& t1, float& t2, float& t3) {
+    t3 = fmaxf(t3, fminf(t2, v));
+    t2 = fmaxf(t2, fminf(t1, v));
+    t1 = fmaxf(t1, v);
 }
 
 // ---------------------------------------------------------------- resident kernel
@@ -665,8 +696,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
     __syncthreads();
     for (int j = 1; j < a.n_landmarks;) {
         // lanes 2 t + c test pick t against chunk c (0 = A, 1 = B)
+        const int np = s.n_pick;
         bool hit = false;
-        if ((lane >> 1) < s.n_pick) {
+        if ((lane >> 1) < np) {
             const int t = lane >> 1, f = (lane & 1) ? 0 : 7;
             const float md = (lane & 1) ? s_bm[6 * kWarps + warp] : maxd;
             hit = !(box_gap2(s.px[t], s.py[t], s.pz[t], s_bm[f * kWarps + warp], s_bm[(f + 1) * kWarps + warp],
@@ -683,12 +715,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
 #pragma unroll
                 for (int k = 0; k < kLanePts; ++k) pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], qx, qy, qz));
             }
-            float t1 = -1.0f, t2 = -1.0f;
+            float t1 = -1.0f, t2 = -1.0f, t3 = -1.0f;
 #pragma unroll
-            for (int k = 0; k < kLanePts; ++k) {
-                t2 = fmaxf(t2, fminf(t1, pd[k]));
-                t1 = fmaxf(t1, pd[k]);
-            }
+            for (int k = 0; k < kLanePts; ++k) top3_insert(pd[k], t1, t2, t3);
+            // best point of the chunk, then the best of the others
             const float wm = warp_max_f(t1);
             uint32_t cid = 0xffffffffu;
             float cx = 0.0f, cy = 0.0f, cz = 0.0f;
@@ -706,13 +736,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                     }
                 }
             }
-            const int owner = publish_chunk(s, warp, wm, cid, cx, cy, cz, lane);
-            const float sec = warp_max_f(lane == owner ? t2 : t1);
+            bool own1, own2;
+            const uint32_t r1 = publish_chunk(s, warp, wm, cid, cx, cy, cz, lane, own1);
+            const float v2 = own1 ? t2 : t1;
+            const float wm2 = warp_max_f(v2);
+            cid = 0xffffffffu;
+            if (wm2 >= 0.0f && v2 == wm2) {
+#pragma unroll
+                for (int k = 0; k < kLanePts; ++k) {
+                    if (pd[k] == wm2) {
+                        const uint32_t id = static_cast<uint32_t>(s_ids[wo + lane + 32 * k]);
+                        if (id != r1 && id < cid) {
+                            cid = id;
+                            cx = px[k];
+                            cy = py[k];
+                            cz = pz[k];
+                        }
+                    }
+                }
+            }
+            publish_chunk(s, 2 * kWarps + warp, wm2, cid, cx, cy, cz, lane, own2);
+            const float sec = warp_max_f(own1 ? (own2 ? t3 : t2) : (own2 ? t2 : t1));
             if (lane == 0) s.sec[warp] = sec;
             maxd = wm;
         }
         if (hit_b) {
-            float t1 = -1.0f, t2 = -1.0f;
+            float t1 = -1.0f, t2 = -1.0f, t3 = -1.0f;
 #pragma unroll 4
             for (int k = 0; k < kLanePts; ++k) {
                 const int o = lane + 32 * k;
@@ -724,8 +773,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                     d = fminf(d, fps_key(qx, qy, qz, s.px[t], s.py[t], s.pz[t]));
                 }
                 s_pts[3 * kPlane + wo + o] = d;
-                t2 = fmaxf(t2, fminf(t1, d));
-                t1 = fmaxf(t1, d);
+                top3_insert(d, t1, t2, t3);
             }
             const float wm = warp_max_f(t1);
             uint32_t cid = 0xffffffffu;
@@ -744,8 +792,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                     }
                 }
             }
-            const int owner = publish_chunk(s, kWarps + warp, wm, cid, cx, cy, cz, lane);
-            const float sec = warp_max_f(lane == owner ? t2 : t1);
+            bool own1, own2;
+            const uint32_t r1 = publish_chunk(s, kWarps + warp, wm, cid, cx, cy, cz, lane, own1);
+            const float v2 = own1 ? t2 : t1;
+            const float wm2 = warp_max_f(v2);
+            cid = 0xffffffffu;
+            if (wm2 >= 0.0f && v2 == wm2) {
+                for (int k = 0; k < kLanePts; ++k) {
+                    const int o = lane + 32 * k;
+                    if (s_pts[3 * kPlane + wo + o] == wm2) {
+                        const uint32_t id = static_cast<uint32_t>(s_ids[kPlane + wo + o]);
+                        if (id != r1 && id < cid) {
+                            cid = id;
+                            cx = s_pts[wo + o];
+                            cy = s_pts[kPlane + wo + o];
+                            cz = s_pts[2 * kPlane + wo + o];
+                        }
+                    }
+                }
+            }
+            publish_chunk(s, 3 * kWarps + warp, wm2, cid, cx, cy, cz, lane, own2);
+            const float sec = warp_max_f(own1 ? (own2 ? t3 : t2) : (own2 ? t2 : t1));
             if (lane == 0) {
                 s.sec[kWarps + warp] = sec;
                 s_bm[6 * kWarps + warp] = wm;
