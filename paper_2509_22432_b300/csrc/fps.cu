@@ -164,11 +164,6 @@ __device__ __forceinline__ float warp_max_f(float v) {
     return from_ordered(__reduce_max_sync(0xffffffffu, ordered_bits(v)));
 }
 
-// Lowest lane whose predicate holds (32 if none): one redux, shorter than a
-// ballot followed by a find-first-set.
-__device__ __forceinline__ int first_lane(bool pred, int lane) {
-    return static_cast<int>(__reduce_min_sync(0xffffffffu, pred ? static_cast<uint32_t>(lane) : 32u));
-}
 
 struct FpsArgs {
     const float* X;    // (n, 3) input rows (start point)
@@ -251,6 +246,7 @@ struct FpsShared {
     float qx[kPollers][kTop], qy[kPollers][kTop], qz[kPollers][kTop];
     float qbound[kPollers];     // each quarter's bound on everything else
     int qstop[kPollers];
+    int top[kTop];              // entry indices of the block's best entries (block_top)
 };
 
 __device__ __forceinline__ void shared_init(FpsShared& s) {
@@ -272,10 +268,10 @@ __device__ __forceinline__ void order2(uint64_t& a, int& ia, uint64_t& b, int& i
     }
 }
 
-// Block reduction (X0): lane l holds entries l + 32 i (i < 4), sorted; lane
-// k < kTop receives the k-th best entry. Returns the bound on every other
-// point.
-__device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_t& me, float& mx, float& my,
+// Block reduction (X0): lane l holds entries l + 32 i (i < 4), sorted; the
+// lane holding the k-th best entry records its index in s.top[k], and lane
+// k < kTop receives it. Returns the bound on every other point.
+__device__ __forceinline__ float block_top(FpsShared& s, int lane, uint64_t& me, float& mx, float& my,
                                            float& mz) {
     uint64_t e0 = s.cand[lane], e1 = s.cand[kWarps + lane], e2 = s.cand[2 * kWarps + lane],
              e3 = s.cand[3 * kWarps + lane];
@@ -285,20 +281,11 @@ __device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_
     order2(e0, i0, e2, i2);
     order2(e1, i1, e3, i3);
     order2(e1, i1, e2, i2);
-    me = 0ull;
-    mx = my = mz = 0.0f;
 #pragma unroll
     for (int k = 0; k < kTop; ++k) {
         const uint64_t m = warp_max_u64(e0);
-        const int o = first_lane(e0 == m, lane);
-        const int oi = __shfl_sync(0xffffffffu, i0, o);
-        if (lane == k) {
-            me = m;
-            mx = s.cx[oi];
-            my = s.cy[oi];
-            mz = s.cz[oi];
-        }
-        if (lane == o) {
+        if (e0 == m) {  // one lane, unless m == 0 (no entry left: any of them may record it)
+            s.top[k] = m != 0ull ? i0 : -1;
             e0 = e1;
             i0 = i1;
             e1 = e2;
@@ -310,6 +297,18 @@ __device__ __forceinline__ float block_top(const FpsShared& s, int lane, uint64_
     }
     const float next = cand_key(warp_max_u64(e0));
     const float sec = warp_max_f(fmaxf(s.sec[lane], s.sec[kWarps + lane]));
+    __syncwarp();
+    me = 0ull;
+    mx = my = mz = 0.0f;
+    if (lane < kTop) {
+        const int i = s.top[lane];
+        if (i >= 0) {
+            me = s.cand[i];
+            mx = s.cx[i];
+            my = s.cy[i];
+            mz = s.cz[i];
+        }
+    }
     return fmaxf(fmaxf(next, sec), 0.0f);
 }
 
@@ -394,8 +393,7 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
             }
             break;
         }
-        const int o = first_lane(v == m, lane);
-        if (lane == o) {
+        if (v == m) {  // one lane, unless m == 0 (then every writer stores an empty entry)
             uint32_t ex = 0u, ey = 0u, ez = 0u;
 #pragma unroll
             for (int l = 0; l < kPollLoads; ++l)
@@ -443,27 +441,39 @@ __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, in
     }
     // Picks: the best live entry while its minimum stays positive and above
     // the bound (the first one unconditionally); each pick lowers the others.
+    // The best is found with two 32-bit reductions: the largest minimum, then
+    // among the lanes holding it the lowest row, through the rank of each
+    // lane's row among the entries (rows are distinct) packed with the lane.
     const int cap = min(picks_left, kMaxPicks);
     const uint32_t row = cand_row(me);
     float cur = cand_key(me);
     bool live = me != 0ull;
+    uint32_t rank = 0u;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) rank += __shfl_sync(0xffffffffu, row, i) < row;
+    const uint32_t tag = (rank << 5) | static_cast<uint32_t>(lane);
     int np = 0;
     while (np < cap) {
-        const uint64_t v = live ? pack_cand(cur, row) : 0ull;
-        const uint64_t m = warp_max_u64(v);
-        if (np > 0 && !(m != 0ull && cand_key(m) > 0.0f && cand_key(m) > bound)) break;
-        const int o = m != 0ull ? first_lane(v == m, lane) : 0;
+        const uint32_t kb = live ? __float_as_uint(cur) : 0u;  // minima are >= +0: bits order like values
+        const uint32_t mh = __reduce_max_sync(0xffffffffu, kb);
+        if (np > 0 && !(__uint_as_float(mh) > 0.0f && __uint_as_float(mh) > bound)) break;
+        const uint32_t sel = __reduce_min_sync(0xffffffffu, live && kb == mh ? tag : 0xffffffffu);
+        if (sel == 0xffffffffu) {  // no entry at all: an empty pick (reported as degenerate)
+            if (lane == 0) s.pick[np] = 0ull;
+            ++np;
+            break;
+        }
+        const int o = static_cast<int>(sel & 31u);
         const float qx = __shfl_sync(0xffffffffu, mx, o), qy = __shfl_sync(0xffffffffu, my, o),
                     qz = __shfl_sync(0xffffffffu, mz, o);
         if (lane == o) {
-            s.pick[np] = m;
-            s.px[np] = qx;
-            s.py[np] = qy;
-            s.pz[np] = qz;
+            s.pick[np] = pack_cand(cur, row);
+            s.px[np] = mx;
+            s.py[np] = my;
+            s.pz[np] = mz;
             live = false;
         }
         ++np;
-        if (m == 0ull) break;
         cur = fminf(cur, fps_key(mx, my, mz, qx, qy, qz));
     }
     __syncwarp();
