@@ -236,11 +236,11 @@ __device__ __forceinline__ void bar_wait(int id, int count) {
 constexpr int kEntries = 4 * kWarps;
 
 struct FpsShared {
+    float4 pxyz[kMaxPicks];     // this round's picks: coordinates (w unused)
     uint64_t cand[kEntries];
     float cx[kEntries], cy[kEntries], cz[kEntries];
     float sec[2 * kWarps];      // bound on every other point of chunk A (w) or B (32 + w); -1: none
     uint64_t pick[kMaxPicks];   // this round's picks (candidate words with the minimum at the pick)
-    float px[kMaxPicks], py[kMaxPicks], pz[kMaxPicks];
     int n_pick;                 // picks of the round; -1 = stop (timeout)
     uint64_t qc[kPollers][kTop];  // best entries of each quarter of the blocks
     float qx[kPollers][kTop], qy[kPollers][kTop], qz[kPollers][kTop];
@@ -468,9 +468,7 @@ __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, in
                     qz = __shfl_sync(0xffffffffu, mz, o);
         if (lane == o) {
             s.pick[np] = pack_cand(cur, row);
-            s.px[np] = mx;
-            s.py[np] = my;
-            s.pz[np] = mz;
+            s.pxyz[np] = make_float4(mx, my, mz, 0.0f);
             live = false;
         }
         ++np;
@@ -508,9 +506,7 @@ __device__ __forceinline__ void start_round(const FpsArgs& a, FpsShared& s) {
             a.out_idx[0] = a.start;
             if (a.out_key) a.out_key[0] = __int_as_float(0x7f800000);
         }
-        s.px[0] = a.X[3 * a.start + 0];
-        s.py[0] = a.X[3 * a.start + 1];
-        s.pz[0] = a.X[3 * a.start + 2];
+        s.pxyz[0] = make_float4(a.X[3 * a.start + 0], a.X[3 * a.start + 1], a.X[3 * a.start + 2], 0.0f);
         s.n_pick = 1;
     }
 }
@@ -546,8 +542,10 @@ __device__ __forceinline__ void exchange_loop(const FpsArgs& a, FpsShared& s, in
 __device__ __forceinline__ uint32_t box_hits(const FpsShared& s, int np, float lox, float loy, float loz, float hix,
                                              float hiy, float hiz, float maxd) {
     uint32_t hit = 0u;
-    for (int t = 0; t < np; ++t)
-        if (!(box_gap2(s.px[t], s.py[t], s.pz[t], lox, loy, loz, hix, hiy, hiz) >= maxd)) hit |= 1u << t;
+    for (int t = 0; t < np; ++t) {
+        const float4 q = s.pxyz[t];
+        if (!(box_gap2(q.x, q.y, q.z, lox, loy, loz, hix, hiy, hiz) >= maxd)) hit |= 1u << t;
+    }
     return hit;
 }
 
@@ -596,21 +594,21 @@ __device__ __forceinline__ void top3_insert(float v, float& t1, float& t2, float
 // k < 8) and chunk B = A + nb in shared memory; boxes and chunk B's largest
 // minimum in shared memory, chunk A's in a register.
 // Dynamic shared memory:
-//   ids  int32 [2][28][256]  original rows of chunks A and B
-//   pts  float [4][28][256]  chunk B: x, y, z, running minimum
-//   meta float [13][32]      chunk B: box lo x/y/z, hi x/y/z, largest minimum;
-//                            chunk A: box lo x/y/z, hi x/y/z
+//   ids  int32  [2][28][256]  original rows of chunks A and B
+//   pts  float  [4][28][256]  chunk B: x, y, z, running minimum
+//   box  float4 [32][2][2]    per warp and chunk (A, B): (lo x/y/z, largest
+//                             minimum: chunk B only), (hi x/y/z, unused)
 constexpr int kResIds = 0;
 constexpr int kResPts = kResIds + 2 * kComputeWarps * kChunk * 4;
 constexpr int kResMeta = kResPts + 4 * kComputeWarps * kChunk * 4;
-constexpr int kResidentSmem = kResMeta + 13 * kWarps * 4;
+constexpr int kResidentSmem = kResMeta + kWarps * 2 * 2 * 16;
 
 __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
     __shared__ FpsShared s;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     int32_t* s_ids = reinterpret_cast<int32_t*>(s_dyn + kResIds);
     float* s_pts = reinterpret_cast<float*>(s_dyn + kResPts);
-    float* s_bm = reinterpret_cast<float*>(s_dyn + kResMeta);
+    float4* s_box = reinterpret_cast<float4*>(s_dyn + kResMeta);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     shared_init(s);
     start_round(a, s);
@@ -655,13 +653,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
         bhiy = warp_max_f(bhiy);
         bhiz = warp_max_f(bhiz);
         if (lane == 0) {
-            s_bm[0 * kWarps + warp] = blox;
-            s_bm[1 * kWarps + warp] = bloy;
-            s_bm[2 * kWarps + warp] = bloz;
-            s_bm[3 * kWarps + warp] = bhix;
-            s_bm[4 * kWarps + warp] = bhiy;
-            s_bm[5 * kWarps + warp] = bhiz;
-            s_bm[6 * kWarps + warp] = base_b < a.n ? inf : -1.0f;
+            s_box[(2 * warp + 1) * 2 + 0] = make_float4(blox, bloy, bloz, base_b < a.n ? inf : -1.0f);
+            s_box[(2 * warp + 1) * 2 + 1] = make_float4(bhix, bhiy, bhiz, 0.0f);
         }
     }
     float px[kLanePts], py[kLanePts], pz[kLanePts], pd[kLanePts];
@@ -693,12 +686,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
         hiy = warp_max_f(hiy);
         hiz = warp_max_f(hiz);
         if (lane == 0) {
-            s_bm[7 * kWarps + warp] = lox;
-            s_bm[8 * kWarps + warp] = loy;
-            s_bm[9 * kWarps + warp] = loz;
-            s_bm[10 * kWarps + warp] = hix;
-            s_bm[11 * kWarps + warp] = hiy;
-            s_bm[12 * kWarps + warp] = hiz;
+            s_box[(2 * warp + 0) * 2 + 0] = make_float4(lox, loy, loz, 0.0f);
+            s_box[(2 * warp + 0) * 2 + 1] = make_float4(hix, hiy, hiz, 0.0f);
         }
     }
     // Largest running minimum of chunk A (lane-replicated); -1 = no points.
@@ -709,11 +698,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
         const int np = s.n_pick;
         bool hit = false;
         if ((lane >> 1) < np) {
-            const int t = lane >> 1, f = (lane & 1) ? 0 : 7;
-            const float md = (lane & 1) ? s_bm[6 * kWarps + warp] : maxd;
-            hit = !(box_gap2(s.px[t], s.py[t], s.pz[t], s_bm[f * kWarps + warp], s_bm[(f + 1) * kWarps + warp],
-                             s_bm[(f + 2) * kWarps + warp], s_bm[(f + 3) * kWarps + warp],
-                             s_bm[(f + 4) * kWarps + warp], s_bm[(f + 5) * kWarps + warp]) >= md);
+            const int t = lane >> 1, c = lane & 1;
+            const float4 lo = s_box[(2 * warp + c) * 2], hi = s_box[(2 * warp + c) * 2 + 1], q = s.pxyz[t];
+            hit = !(box_gap2(q.x, q.y, q.z, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z) >= (c ? lo.w : maxd));
         }
         const uint32_t hb = __ballot_sync(0xffffffffu, hit);
         const uint32_t hit_a = even_bits(hb), hit_b = even_bits(hb >> 1);
@@ -721,9 +708,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
 #pragma unroll 1
             for (uint32_t mt = hit_a; mt; mt &= mt - 1) {
                 const int t = __ffs(mt) - 1;
-                const float qx = s.px[t], qy = s.py[t], qz = s.pz[t];
+                const float4 q = s.pxyz[t];
 #pragma unroll
-                for (int k = 0; k < kLanePts; ++k) pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], qx, qy, qz));
+                for (int k = 0; k < kLanePts; ++k) pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], q.x, q.y, q.z));
             }
             float t1 = -1.0f, t2 = -1.0f, t3 = -1.0f;
 #pragma unroll
@@ -780,7 +767,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
 #pragma unroll 1
                 for (uint32_t mt = hit_b; mt; mt &= mt - 1) {
                     const int t = __ffs(mt) - 1;
-                    d = fminf(d, fps_key(qx, qy, qz, s.px[t], s.py[t], s.pz[t]));
+                    const float4 q = s.pxyz[t];
+                    d = fminf(d, fps_key(qx, qy, qz, q.x, q.y, q.z));
                 }
                 s_pts[3 * kPlane + wo + o] = d;
                 top3_insert(d, t1, t2, t3);
@@ -825,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
             const float sec = warp_max_f(own1 ? (own2 ? t3 : t2) : (own2 ? t2 : t1));
             if (lane == 0) {
                 s.sec[kWarps + warp] = sec;
-                s_bm[6 * kWarps + warp] = wm;
+                reinterpret_cast<float*>(s_box + (2 * warp + 1) * 2)[3] = wm;
             }
         }
         bar_arrive(kBarCands, kCandsCount);
@@ -881,7 +869,8 @@ __device__ __forceinline__ void update_chunk(const FpsArgs& a, const FpsShared& 
 #pragma unroll 1
                 for (uint32_t mt = hit; mt; mt &= mt - 1) {
                     const int t = __ffs(mt) - 1;
-                    nd = fminf(nd, fps_key(x[k], y[k], z[k], s.px[t], s.py[t], s.pz[t]));
+                    const float4 l = s.pxyz[t];
+                    nd = fminf(nd, fps_key(x[k], y[k], z[k], l.x, l.y, l.z));
                 }
                 if (nd != d[k]) a.d[i] = nd;
                 t2 = fmaxf(t2, fminf(t1, nd));
