@@ -759,19 +759,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
         }
         if (hit_b) {
             float t1 = -1.0f, t2 = -1.0f, t3 = -1.0f;
-#pragma unroll 4
-            for (int k = 0; k < kLanePts; ++k) {
-                const int o = lane + 32 * k;
-                const float qx = s_pts[wo + o], qy = s_pts[kPlane + wo + o], qz = s_pts[2 * kPlane + wo + o];
-                float d = s_pts[3 * kPlane + wo + o];
+            // two halves of four points per lane, picks in the outer loop so
+            // that the four keys of a pick are independent
+#pragma unroll 1
+            for (int h = 0; h < kLanePts; h += kLanePts / 2) {
+                float bx[kLanePts / 2], by[kLanePts / 2], bz[kLanePts / 2], bd[kLanePts / 2];
+#pragma unroll
+                for (int k = 0; k < kLanePts / 2; ++k) {
+                    const int o = wo + lane + 32 * (h + k);
+                    bx[k] = s_pts[o];
+                    by[k] = s_pts[kPlane + o];
+                    bz[k] = s_pts[2 * kPlane + o];
+                    bd[k] = s_pts[3 * kPlane + o];
+                }
 #pragma unroll 1
                 for (uint32_t mt = hit_b; mt; mt &= mt - 1) {
-                    const int t = __ffs(mt) - 1;
-                    const float4 q = s.pxyz[t];
-                    d = fminf(d, fps_key(qx, qy, qz, q.x, q.y, q.z));
+                    const float4 q = s.pxyz[__ffs(mt) - 1];
+#pragma unroll
+                    for (int k = 0; k < kLanePts / 2; ++k)
+                        bd[k] = fminf(bd[k], fps_key(bx[k], by[k], bz[k], q.x, q.y, q.z));
                 }
-                s_pts[3 * kPlane + wo + o] = d;
-                top3_insert(d, t1, t2, t3);
+#pragma unroll
+                for (int k = 0; k < kLanePts / 2; ++k) {
+                    s_pts[3 * kPlane + wo + lane + 32 * (h + k)] = bd[k];
+                    top3_insert(bd[k], t1, t2, t3);
+                }
             }
             const float wm = warp_max_f(t1);
             uint32_t cid = 0xffffffffu;
