@@ -120,8 +120,10 @@ struct DimArgs {
 // ---------------------------------------------------------------- vertices
 // f(v) = d(v, X) = 0 for a landmark that is a point of X; anything else is an
 // input error (the vertex bound relies on L ⊂ X).
+// One warp per landmark: its lanes scan the landmark's cell together.
 __global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, int32_t* src, uint32_t* flags) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = static_cast<int>((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (v >= n_L) return;
     const float x = L[3 * v], y = L[3 * v + 1], z = L[3 * v + 2];
     bool found = false;
@@ -131,16 +133,25 @@ __global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, 
         const int cz = cell_coord(z, g.oz, g.inv_cell, g.dz);
         const int64_t c = (static_cast<int64_t>(cz) * g.dy + cy) * g.dx + cx;
         const int32_t b = g.cell_start[c], e = g.cell_start[c + 1];
-        for (int32_t i = b; i < e && !found; ++i) {
-            const float4 p = g.pts[i];
-            found = __float_as_uint(p.x) == __float_as_uint(x) && __float_as_uint(p.y) == __float_as_uint(y) &&
-                    __float_as_uint(p.z) == __float_as_uint(z);
+        for (int32_t i0 = b; i0 < e; i0 += 32) {
+            bool hit = false;
+            if (i0 + lane < e) {
+                const float4 p = g.pts[i0 + lane];
+                hit = __float_as_uint(p.x) == __float_as_uint(x) && __float_as_uint(p.y) == __float_as_uint(y) &&
+                      __float_as_uint(p.z) == __float_as_uint(z);
+            }
+            if (__any_sync(0xffffffffu, hit)) {
+                found = true;
+                break;
+            }
         }
     }
-    if (!found) atomicOr(flags, FLAG_NOT_SUBSET);
-    val[v] = found ? 0.0f : __int_as_float(0x7fc00000);
-    src[2 * v] = v;
-    src[2 * v + 1] = 0;
+    if (lane == 0) {
+        if (!found) atomicOr(flags, FLAG_NOT_SUBSET);
+        val[v] = found ? 0.0f : __int_as_float(0x7fc00000);
+        src[2 * v] = v;
+        src[2 * v + 1] = 0;
+    }
 }
 
 // ---------------------------------------------------------------- samples
@@ -1209,9 +1220,8 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s)
             if (!J.val[k] && (rc = scr.alloc(&J.val[k], J.nk[k]))) return rc;
             if (!J.src[k] && (rc = scr.alloc(&J.src[k], 2 * J.nk[k]))) return rc;
         }
-        k_vertices<<<static_cast<unsigned>(ceil_div(J.nk[0], 256)), 256, 0, s>>>(J.in.L, J.in.n_landmarks,
-                                                                                 view_of(grid), J.val[0], J.src[0],
-                                                                                 &ctl->flags);
+        const unsigned vblocks = static_cast<unsigned>(ceil_div(J.nk[0] * int64_t(32), 256));  // a warp per landmark
+        k_vertices<<<vblocks, 256, 0, s>>>(J.in.L, J.in.n_landmarks, view_of(grid), J.val[0], J.src[0], &ctl->flags);
         note_launch();
         FLOOD_CUDA(cudaGetLastError());
         J.max_samples = 1;

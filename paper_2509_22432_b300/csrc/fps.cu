@@ -1134,8 +1134,7 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
         if ((rc = al.alloc(&code, n)) || (rc = al.alloc(&count, codes)) || (rc = al.alloc(&cstart, codes + 1)))
             return rc;
         FLOOD_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * codes, s));
-        const int64_t bb = std::min<int64_t>(ceil_div(n, kBoxThreads), int64_t(device_sm_count()) * 8);
-        k_bbox<<<static_cast<unsigned>(bb), kBoxThreads, 0, s>>>(X, n, ctl + 1, ctl);
+        k_bbox<<<bbox_blocks(n, device_sm_count()), kBoxThreads, 0, s>>>(X, n, ctl + 1, ctl);
         k_morton_count<<<grid, 256, 0, s>>>(X, n, ctl + 1, bits, code, count);
         note_launch(2);
         FLOOD_CUDA(cudaGetLastError());

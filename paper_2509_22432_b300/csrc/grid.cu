@@ -145,8 +145,7 @@ extern "C" int flood_build_grid(const float* X, int64_t n_points, float cell_siz
     if (rc) return rc;
     k_box_init<<<1, 1, 0, s>>>(d_box, d_box + 6); note_launch();
     const int sms = device_sm_count();
-    const int64_t blocks = std::min<int64_t>(ceil_div(n_points, kBoxThreads), int64_t(sms) * 8);
-    k_bbox<<<static_cast<unsigned>(blocks), kBoxThreads, 0, s>>>(X, n_points, d_box, d_box + 6); note_launch();
+    k_bbox<<<bbox_blocks(n_points, sms), kBoxThreads, 0, s>>>(X, n_points, d_box, d_box + 6); note_launch();
     FLOOD_CUDA(cudaGetLastError());
     uint32_t h_box[8];
     FLOOD_CUDA(cudaMemcpyAsync(h_box, d_box, sizeof(uint32_t) * 7, cudaMemcpyDeviceToHost, s));
