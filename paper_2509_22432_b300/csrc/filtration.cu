@@ -317,9 +317,8 @@ __device__ __forceinline__ float slab_gap(float o, float h, int c, float lo, flo
 }
 
 // Row r of shell s as up to two point ranges. A row (or the part of it along
-// x) whose cells lie farther than sqrt(T2) from every sample of the group, or
-// whose 4x4x4 blocks are empty, contributes nothing; neither changes any
-// live sample's nearest distance.
+// x) whose cells lie farther than sqrt(T2) from every sample of the group
+// contributes nothing; it cannot change any live sample's nearest distance.
 __device__ __forceinline__ void shell_row(const GridView& g, const Shell& sh, int r, int32_t& b1, int32_t& l1,
                                           int32_t& b2, int32_t& l2) {
     const int s = sh.s;
@@ -337,19 +336,21 @@ __device__ __forceinline__ void shell_row(const GridView& g, const Shell& sh, in
     const int xb = cell_coord(sh.whi[0] + w, g.ox, g.inv_cell, g.dx);
     const int64_t base = (static_cast<int64_t>(cz) * g.dy + cy) * g.dx;
     const bool face = s == 0 || cy == sh.lo[1] - s || cy == sh.hi[1] + s || cz == sh.lo[2] - s || cz == sh.hi[2] + s;
+    // the cell table gives each range directly (empty ones have length 0),
+    // in one round of independent loads
     if (face) {
         const int x0 = max(max(sh.lo[0] - s, 0), xa), x1 = min(min(sh.hi[0] + s, g.dx - 1), xb);
-        if (x0 <= x1 && row_occupied(g, cy, cz, x0, x1)) {
+        if (x0 <= x1) {
             b1 = g.cell_start[base + x0];
             l1 = g.cell_start[base + x1 + 1] - b1;
         }
     } else {
         const int xl = sh.lo[0] - s, xr = sh.hi[0] + s;
-        if (xl >= 0 && xl >= xa && xl <= xb && row_occupied(g, cy, cz, xl, xl)) {
+        if (xl >= 0 && xl >= xa && xl <= xb) {
             b1 = g.cell_start[base + xl];
             l1 = g.cell_start[base + xl + 1] - b1;
         }
-        if (xr < g.dx && xr >= xa && xr <= xb && row_occupied(g, cy, cz, xr, xr)) {
+        if (xr < g.dx && xr >= xa && xr <= xb) {
             b2 = g.cell_start[base + xr];
             l2 = g.cell_start[base + xr + 1] - b2;
         }

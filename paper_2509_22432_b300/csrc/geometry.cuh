@@ -76,17 +76,6 @@ __device__ __forceinline__ int cell_coord(float v, float o, float inv_cell, int 
     return static_cast<int>(t);
 }
 
-// Whether any block of 4 x 4 x 4 cells along the row (cy, cz), cells
-// [x0, x1] of x, holds a point.
-__device__ __forceinline__ bool row_occupied(const GridView& g, int cy, int cz, int x0, int x1) {
-    const int64_t base = (static_cast<int64_t>(cz >> 2) * g.by + (cy >> 2)) * g.bx;
-    for (int b = x0 >> 2; b <= (x1 >> 2); ++b) {
-        const int64_t bit = base + b;
-        if (g.occupied[bit >> 5] & (1u << (bit & 31))) return true;
-    }
-    return false;
-}
-
 // First shell (Chebyshev distance in cells from the box [lo, hi]) that can
 // hold a point: if every 4 x 4 x 4 block touching the box is D >= 1 blocks
 // from the nearest occupied block, no point lies within 4 (D - 1) cells of
