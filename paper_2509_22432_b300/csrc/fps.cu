@@ -220,7 +220,7 @@ constexpr int kMaxPicks = 16;  // picks per round (one box-test lane per pick an
 // (everyone else waits). An arrival releases the arriving thread's earlier
 // shared-memory writes to the threads that complete the wait.
 constexpr int kX0 = kComputeWarps;  // warp kX0 + 1 is X1 (it records the picks)
-constexpr int kBarCands = 1, kBarPicks = 2, kBarQuarters = 3, kBarPub = 4;
+constexpr int kBarCands = 1, kBarPicks = 2, kBarQuarters = 3, kBarPub = 4, kBarHits = 5;
 constexpr int kCandsCount = (kComputeWarps + 1) * 32;
 constexpr int kPollCount = kPollers * 32;
 __device__ __forceinline__ void bar_arrive(int id, int count) {
@@ -247,6 +247,7 @@ struct FpsShared {
     float qbound[kPollers];     // each quarter's bound on everything else
     int qstop[kPollers];
     int top[kTop];              // entry indices of the block's best entries (block_top)
+    uint32_t hits[kWarps];      // resident kernel: each compute warp's pick masks (A | B << 16)
 };
 
 __device__ __forceinline__ void shared_init(FpsShared& s) {
@@ -704,6 +705,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
         }
         const uint32_t hb = __ballot_sync(0xffffffffu, hit);
         const uint32_t hit_a = even_bits(hb), hit_b = even_bits(hb >> 1);
+        // A warp whose two chunks both changed hands chunk B (shared memory,
+        // foldable by any warp) to a warp with nothing to fold: the i-th such
+        // warp to the i-th idle warp.
+        if (lane == 0) s.hits[warp] = hit_a | (hit_b << 16);
+        bar_wait(kBarHits, kComputeWarps * 32);
+        int bw = -1;  // owner of the chunk B this warp folds
+        uint32_t bmask = 0u;
+        {
+            const uint32_t hw = lane < kComputeWarps ? s.hits[lane] : 0u;
+            const uint32_t both = __ballot_sync(0xffffffffu, (hw & 0xffffu) && (hw >> 16));
+            const uint32_t idle = __ballot_sync(0xffffffffu, lane < kComputeWarps && hw == 0u);
+            const uint32_t below = (1u << warp) - 1u;
+            const int n_move = min(__popc(both), __popc(idle));
+            if (hit_b && !(hit_a && __popc(both & below) < n_move)) {
+                bw = warp;
+                bmask = hit_b;
+            } else if (!hit_a && !hit_b && __popc(idle & below) < n_move) {
+                uint32_t m = both;  // the (rank + 1)-th warp of `both`
+                for (int i = __popc(idle & below); i > 0; --i) m &= m - 1;
+                bw = __ffs(m) - 1;
+                bmask = s.hits[bw] >> 16;
+            }
+        }
         if (hit_a) {
 #pragma unroll 1
             for (uint32_t mt = hit_a; mt; mt &= mt - 1) {
@@ -757,7 +781,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
             if (lane == 0) s.sec[warp] = sec;
             maxd = wm;
         }
-        if (hit_b) {
+        if (bw >= 0) {
+            const int wb = bw * kChunk;
             float t1 = -1.0f, t2 = -1.0f, t3 = -1.0f;
             // two halves of four points per lane, picks in the outer loop so
             // that the four keys of a pick are independent
@@ -766,14 +791,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                 float bx[kLanePts / 2], by[kLanePts / 2], bz[kLanePts / 2], bd[kLanePts / 2];
 #pragma unroll
                 for (int k = 0; k < kLanePts / 2; ++k) {
-                    const int o = wo + lane + 32 * (h + k);
+                    const int o = wb + lane + 32 * (h + k);
                     bx[k] = s_pts[o];
                     by[k] = s_pts[kPlane + o];
                     bz[k] = s_pts[2 * kPlane + o];
                     bd[k] = s_pts[3 * kPlane + o];
                 }
 #pragma unroll 1
-                for (uint32_t mt = hit_b; mt; mt &= mt - 1) {
+                for (uint32_t mt = bmask; mt; mt &= mt - 1) {
                     const float4 q = s.pxyz[__ffs(mt) - 1];
 #pragma unroll
                     for (int k = 0; k < kLanePts / 2; ++k)
@@ -781,7 +806,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                 }
 #pragma unroll
                 for (int k = 0; k < kLanePts / 2; ++k) {
-                    s_pts[3 * kPlane + wo + lane + 32 * (h + k)] = bd[k];
+                    s_pts[3 * kPlane + wb + lane + 32 * (h + k)] = bd[k];
                     top3_insert(bd[k], t1, t2, t3);
                 }
             }
@@ -791,41 +816,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
             if (t1 == wm) {
                 for (int k = 0; k < kLanePts; ++k) {
                     const int o = lane + 32 * k;
-                    if (s_pts[3 * kPlane + wo + o] == wm) {
-                        const uint32_t id = static_cast<uint32_t>(s_ids[kPlane + wo + o]);
+                    if (s_pts[3 * kPlane + wb + o] == wm) {
+                        const uint32_t id = static_cast<uint32_t>(s_ids[kPlane + wb + o]);
                         if (id < cid) {
                             cid = id;
-                            cx = s_pts[wo + o];
-                            cy = s_pts[kPlane + wo + o];
-                            cz = s_pts[2 * kPlane + wo + o];
+                            cx = s_pts[wb + o];
+                            cy = s_pts[kPlane + wb + o];
+                            cz = s_pts[2 * kPlane + wb + o];
                         }
                     }
                 }
             }
             bool own1, own2;
-            const uint32_t r1 = publish_chunk(s, kWarps + warp, wm, cid, cx, cy, cz, lane, own1);
+            const uint32_t r1 = publish_chunk(s, kWarps + bw, wm, cid, cx, cy, cz, lane, own1);
             const float v2 = own1 ? t2 : t1;
             const float wm2 = warp_max_f(v2);
             cid = 0xffffffffu;
             if (wm2 >= 0.0f && v2 == wm2) {
                 for (int k = 0; k < kLanePts; ++k) {
                     const int o = lane + 32 * k;
-                    if (s_pts[3 * kPlane + wo + o] == wm2) {
-                        const uint32_t id = static_cast<uint32_t>(s_ids[kPlane + wo + o]);
+                    if (s_pts[3 * kPlane + wb + o] == wm2) {
+                        const uint32_t id = static_cast<uint32_t>(s_ids[kPlane + wb + o]);
                         if (id != r1 && id < cid) {
                             cid = id;
-                            cx = s_pts[wo + o];
-                            cy = s_pts[kPlane + wo + o];
-                            cz = s_pts[2 * kPlane + wo + o];
+                            cx = s_pts[wb + o];
+                            cy = s_pts[kPlane + wb + o];
+                            cz = s_pts[2 * kPlane + wb + o];
                         }
                     }
                 }
             }
-            publish_chunk(s, 3 * kWarps + warp, wm2, cid, cx, cy, cz, lane, own2);
+            publish_chunk(s, 3 * kWarps + bw, wm2, cid, cx, cy, cz, lane, own2);
             const float sec = warp_max_f(own1 ? (own2 ? t3 : t2) : (own2 ? t2 : t1));
             if (lane == 0) {
-                s.sec[kWarps + warp] = sec;
-                reinterpret_cast<float*>(s_box + (2 * warp + 1) * 2)[3] = wm;
+                s.sec[kWarps + bw] = sec;
+                reinterpret_cast<float*>(s_box + (2 * bw + 1) * 2)[3] = wm;
             }
         }
         bar_arrive(kBarCands, kCandsCount);
