@@ -698,6 +698,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
     __shared__ uint32_t s_min[kGroup];
     __shared__ int s_live[kGroup];
     __shared__ float s_u[kGroup], s_lb[kGroup];
+    __shared__ float s_x[kGroup], s_y[kGroup], s_z[kGroup];
     __shared__ uint32_t s_ub2[kGroup];
     __shared__ int s_item, s_abort;
     __shared__ int32_t s_wsum[kWarps];
@@ -735,22 +736,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         const int nsl = (n_valid + W - 1) / W;  // sample slots in use per thread
         float ax[kHeavyNS], ay[kHeavyNS], az[kHeavyNS], pp[kHeavyNS], mn[kHeavyNS];
         bool val[kHeavyNS];
-        // group geometry (every thread reads the same records: cached loads)
+        // the group's records, once, into shared memory
+        if (tid < kGroup) {
+            s_min[tid] = 0xffffffffu;
+            s_live[tid] = tid < n_valid;
+            s_ub2[tid] = 0x7f800000u;  // +inf
+            if (tid < n_valid) {
+                const SampleRec r = a.recs[s_begin + tid];
+                s_x[tid] = r.x;
+                s_y[tid] = r.y;
+                s_z[tid] = r.z;
+                s_u[tid] = r.u;
+                s_lb[tid] = r.lb;
+            }
+        }
+        __syncthreads();
+        // group geometry (every thread reads the same shared records)
         int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
         float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
         float R = 0.0f;
-        for (int32_t i = s_begin; i < s_end; ++i) {
-            const SampleRec r = a.recs[i];
-            R = fmaxf(R, r.u);
-            wlo[0] = fminf(wlo[0], r.x);
-            wlo[1] = fminf(wlo[1], r.y);
-            wlo[2] = fminf(wlo[2], r.z);
-            whi[0] = fmaxf(whi[0], r.x);
-            whi[1] = fmaxf(whi[1], r.y);
-            whi[2] = fmaxf(whi[2], r.z);
-            const int cx = cell_coord(r.x, g.ox, g.inv_cell, g.dx);
-            const int cy = cell_coord(r.y, g.oy, g.inv_cell, g.dy);
-            const int cz = cell_coord(r.z, g.oz, g.inv_cell, g.dz);
+        for (int i = 0; i < n_valid; ++i) {
+            const float rx = s_x[i], ry = s_y[i], rz = s_z[i];
+            R = fmaxf(R, s_u[i]);
+            wlo[0] = fminf(wlo[0], rx);
+            wlo[1] = fminf(wlo[1], ry);
+            wlo[2] = fminf(wlo[2], rz);
+            whi[0] = fmaxf(whi[0], rx);
+            whi[1] = fmaxf(whi[1], ry);
+            whi[2] = fmaxf(whi[2], rz);
+            const int cx = cell_coord(rx, g.ox, g.inv_cell, g.dx);
+            const int cy = cell_coord(ry, g.oy, g.inv_cell, g.dy);
+            const int cz = cell_coord(rz, g.oz, g.inv_cell, g.dz);
             lo[0] = min(lo[0], cx);
             lo[1] = min(lo[1], cy);
             lo[2] = min(lo[2], cz);
@@ -765,32 +781,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             ax[q] = ay[q] = az[q] = pp[q] = 0.0f;
             mn[q] = INFINITY;
             if (val[q]) {
-                const SampleRec r = a.recs[i];
-                const float px = __fsub_rn(r.x, ox), py = __fsub_rn(r.y, oy), pz = __fsub_rn(r.z, oz);
+                const int li = i - s_begin;
+                const float px = __fsub_rn(s_x[li], ox), py = __fsub_rn(s_y[li], oy), pz = __fsub_rn(s_z[li], oz);
                 ax[q] = -2.0f * px;
                 ay[q] = -2.0f * py;
                 az[q] = -2.0f * pz;
                 pp[q] = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
             }
         }
-        if (tid < kGroup) {
-            s_min[tid] = 0xffffffffu;
-            s_live[tid] = tid < n_valid;
-            if (tid < n_valid) {
-                s_u[tid] = a.recs[s_begin + tid].u;
-                s_lb[tid] = a.recs[s_begin + tid].lb;
-            }
-            s_ub2[tid] = 0x7f800000u;  // +inf
-        }
-        __syncthreads();
         // Every landmark is a point of X, so the distance to the nearest one is
         // also an upper bound of d(p, X), usually far tighter than the simplex's
         // own vertices for samples in empty space; it narrows the search radius.
         for (int l = tid; l < a.n_L; l += kThreads) {
             const float lx = a.L[3 * l], ly = a.L[3 * l + 1], lz = a.L[3 * l + 2];
             for (int i = 0; i < n_valid; ++i) {
-                const SampleRec& r = a.recs[s_begin + i];
-                const float dx = __fsub_rn(lx, r.x), dy = __fsub_rn(ly, r.y), dz = __fsub_rn(lz, r.z);
+                const float dx = __fsub_rn(lx, s_x[i]), dy = __fsub_rn(ly, s_y[i]), dz = __fsub_rn(lz, s_z[i]);
                 const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
                 if (d2 < s_u[i] * s_u[i]) atomicMin(reinterpret_cast<unsigned int*>(&s_ub2[i]), __float_as_uint(d2));
             }
@@ -855,11 +860,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             __syncthreads();
         };
         const int s0 = min(first_shell(g, lo, hi), s_max);  // shells below s0 hold no point
+        // fold only after tiles were evaluated: otherwise s_min is current and
+        // the previous radius (an upper bound of the new one) still prunes safely
+        bool dirty = true;
         for (int s = s0; s <= s_max; ++s) {
             sh.s = s;
             shell_setup(g, sh);
-            sh.T2 = s_T2 = 0.0f;
-            fold();
+            if (dirty) {
+                fold();
+                dirty = false;
+            }
             sh.T2 = s_T2;
             ++n_shells;
             // All threads enumerate the shell's rows, 256 at a time: each
@@ -920,13 +930,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
                         heavy_tile<kHeavyNS>(s_tiles, cnt, gs, G, ax, ay, az, mn);
                     pairs += tid == 0 ? static_cast<unsigned long long>(cnt) * n_valid : 0ull;
                     n_tiles += tid == 0;
+                    dirty = true;
                     fence_proxy_async_smem();
                     __syncthreads();  // the tile is free for the next window's copies
                 }
                 __syncthreads();  // s_wsum is free for the next rows
             }
             if (s_abort) break;
-            fold();
+            if (dirty) {
+                fold();
+                dirty = false;
+            }
             // termination: every sample exact (below the next shell) or dominated
             const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * a.shell_h, a.shell_slack), 0.0f);
             const float sl2 = __fmul_rn(sl, sl);
@@ -939,7 +953,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             }
             if (!__syncthreads_or(live)) break;
         }
-        fold();
+        if (dirty) fold();
         if (tid < n_valid) {
             const SampleRec r = a.recs[s_begin + tid];
             const float d2 = __uint_as_float(s_min[tid]);
