@@ -527,10 +527,16 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
     };
     // shells below s0 hold no point (block distance field)
     const int s0 = min(first_shell(g, lo, hi), s_max);
+    // minima to combine since the last combination; while none, the previous
+    // radius (an upper bound of a recomputed one) still prunes safely
+    bool dirty = true;
     for (int s = s0; s <= s_max; ++s) {
         sh.s = s;
         shell_setup(g, sh);
-        sh.T2 = search_radius2();
+        if (dirty) {
+            sh.T2 = search_radius2();
+            dirty = false;
+        }
         ++cnt.shells;
         if (sh.rows > 0) {
             Cursor cur{0, 0, 0};
@@ -566,9 +572,13 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
                 }
                 cnt.pairs += static_cast<unsigned long long>(n) * static_cast<unsigned long long>(n_valid);
                 ++cnt.tiles;
+                dirty = true;
                 // A row's length depends on the radius, so the radius may only
                 // tighten between rows, never inside a partly copied one.
-                if (cur.pos == cur.row_pos) sh.T2 = search_radius2();
+                if (cur.pos == cur.row_pos) {
+                    sh.T2 = search_radius2();
+                    dirty = false;
+                }
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (!more) break;
@@ -576,7 +586,10 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
             }
         }
         if (abort) break;
-        combine();
+        if (dirty) {
+            combine();
+            dirty = false;
+        }
         const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * a.shell_h, a.shell_slack), 0.0f);
         const float sl2 = __fmul_rn(sl, sl);
         bool done = true;
@@ -590,7 +603,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
         }
         if (__all_sync(0xffffffffu, done)) break;
     }
-    combine();
+    if (dirty) combine();
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         const int32_t i = slot(q);
