@@ -872,10 +872,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             }
             __syncthreads();
         };
-        const int s0 = min(first_shell(g, lo, hi), s_max);  // shells below s0 hold no point
+        // shells below s0 hold no point; a group with no live sample scans none
+        const int s0 = any_live ? min(first_shell(g, lo, hi), s_max) : 0;
         // fold only after tiles were evaluated: otherwise s_min is current and
         // the previous radius (an upper bound of the new one) still prunes safely
-        bool dirty = true;
+        bool dirty = any_live;
         for (int s = s0; s <= s_max; ++s) {
             sh.s = s;
             shell_setup(g, sh);
