@@ -805,8 +805,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         // Every landmark is a point of X, so the distance to the nearest one is
         // also an upper bound of d(p, X), usually far tighter than the simplex's
         // own vertices for samples in empty space; it narrows the search radius.
+        // (landmarks farther than R from the samples' box cannot tighten any
+        // bound and are skipped; skipping a landmark only loosens a bound)
+        const float R2 = R * R;
         for (int l = tid; l < a.n_L; l += kThreads) {
             const float lx = a.L[3 * l], ly = a.L[3 * l + 1], lz = a.L[3 * l + 2];
+            const float gx = fmaxf(fmaxf(wlo[0] - lx, lx - whi[0]), 0.0f);
+            const float gy = fmaxf(fmaxf(wlo[1] - ly, ly - whi[1]), 0.0f);
+            const float gz = fmaxf(fmaxf(wlo[2] - lz, lz - whi[2]), 0.0f);
+            if (!(gx * gx + gy * gy + gz * gz < R2)) continue;
             for (int i = 0; i < n_valid; ++i) {
                 const float dx = __fsub_rn(lx, s_x[i]), dy = __fsub_rn(ly, s_y[i]), dz = __fsub_rn(lz, s_z[i]);
                 const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
