@@ -418,6 +418,23 @@ __device__ __noinline__ int produce_shell_tile(const GridView& g, const Shell& s
 }
 
 // ---------------------------------------------------------------- flood kernel
+// Warp minimum / maximum of floats with one redux over order-preserving bit
+// patterns (a non-negative float keeps its bits with the sign set, a negative
+// one is complemented).
+__device__ __forceinline__ uint32_t float_order(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_float(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ float warp_min_of(float v) {
+    return order_float(__reduce_min_sync(0xffffffffu, float_order(v)));
+}
+__device__ __forceinline__ float warp_max_of(float v) {
+    return order_float(__reduce_max_sync(0xffffffffu, float_order(v)));
+}
+
 struct WarpCounters {
     unsigned long long pairs = 0ull, shells = 0ull, tiles = 0ull;
 };
@@ -441,11 +458,6 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
     const int G = 32 / W;  // point streams
     const int gs = lane / W, lw = lane % W;
     __syncwarp();  // the previous group's reads of s_u / s_lb are complete
-    for (int i = lane; i < s_end - s_begin; i += 32) {
-        s_u[i] = a.recs[s_begin + i].u;
-        s_lb[i] = a.recs[s_begin + i].lb;
-    }
-    __syncwarp();
     auto slot = [&](int q) { return s_begin + q * W + lw; };
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
@@ -476,21 +488,21 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
             hi[0] = max(hi[0], cx);
             hi[1] = max(hi[1], cy);
             hi[2] = max(hi[2], cz);
-        }
-    }
-    {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                lo[c] = min(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
-                hi[c] = max(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
-                wlo[c] = fminf(wlo[c], __shfl_xor_sync(0xffffffffu, wlo[c], o));
-                whi[c] = fmaxf(whi[c], __shfl_xor_sync(0xffffffffu, whi[c], o));
+            if (gs == 0) {  // one lane per sample keeps its bounds in shared memory
+                s_u[i - s_begin] = r.u;
+                s_lb[i - s_begin] = r.lb;
             }
         }
     }
+    R = warp_max_of(R);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = __reduce_min_sync(0xffffffffu, lo[c]);
+        hi[c] = __reduce_max_sync(0xffffffffu, hi[c]);
+        wlo[c] = warp_min_of(wlo[c]);
+        whi[c] = warp_max_of(whi[c]);
+    }
+    __syncwarp();  // s_u / s_lb written
     const int n_valid = s_end - s_begin;
     // Beyond shell s every point is at least s*h (less rounding slack) from
     // every sample; at max u_p no nearest point can lie farther out.
