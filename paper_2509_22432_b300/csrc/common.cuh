@@ -45,10 +45,16 @@ int cuda_fail(cudaError_t e, const char* what);
 // driver at every synchronisation (up to 4 GiB stays cached; once per device).
 void keep_pool_warm();
 
-// Stream-ordered scratch that is returned on scope exit.
+// Stream-ordered scratch that is returned on scope exit. Pieces (256-byte
+// aligned) are carved from chunks of at least 16 MiB taken from the
+// stream-ordered pool, so a call makes one or two pool requests instead of
+// one per buffer.
 struct Scratch {
+    static constexpr size_t kChunk = size_t(16) << 20;
     cudaStream_t stream;
-    std::vector<void*> ptrs;
+    std::vector<void*> ptrs;  // chunks
+    unsigned char* cur = nullptr;
+    size_t left = 0;
     explicit Scratch(cudaStream_t s) : stream(s) { keep_pool_warm(); }
     ~Scratch() {
         for (void* p : ptrs) cudaFreeAsync(p, stream);
@@ -57,16 +63,23 @@ struct Scratch {
     int alloc(T** out, size_t count) {
         *out = nullptr;
         if (count == 0) count = 1;
-        void* p = nullptr;
-        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), stream);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            set_error("device allocation of %zu bytes failed: %s", count * sizeof(T),
-                      cudaGetErrorString(e));
-            return FLOOD_ENOMEM;
+        const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (bytes > left) {
+            const size_t size = bytes > kChunk ? bytes : kChunk;
+            void* p = nullptr;
+            cudaError_t e = cudaMallocAsync(&p, size, stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation of %zu bytes failed: %s", size, cudaGetErrorString(e));
+                return FLOOD_ENOMEM;
+            }
+            ptrs.push_back(p);
+            cur = static_cast<unsigned char*>(p);
+            left = size;
         }
-        ptrs.push_back(p);
-        *out = static_cast<T*>(p);
+        *out = reinterpret_cast<T*>(cur);
+        cur += bytes;
+        left -= bytes;
         return FLOOD_OK;
     }
 };

@@ -1059,13 +1059,30 @@ __global__ void k_facemax(int k, int64_t n, const int32_t* simplices, const int3
 }
 
 // ---------------------------------------------------------------- host side
+// Resident CTAs per SM of a flood kernel at its shared-memory size, set up
+// once per device (the attribute call and the occupancy query are host
+// round trips worth skipping on every call).
+template <class K>
+int flood_kernel_per_sm(K kernel, size_t smem, int* cache) {
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    FLOOD_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int per_sm = 0;
+    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+    per_sm = std::max(per_sm, 1);
+    if (dev >= 0 && dev < 64) cache[dev] = per_sm;
+    return per_sm;
+}
+
 int launch_flood_heavy(const DimArgs* jobs, int n_jobs, const int32_t* heavy_off, Ctl* ctl, int k,
                        cudaStream_t s) {
     const size_t smem = size_t(kHeavyTile) * sizeof(float4);
-    FLOOD_CUDA(cudaFuncSetAttribute(k_flood_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    int per_sm = 0;
-    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood_heavy, kThreads, smem));
-    per_sm = std::max(per_sm, 1);
+    static int cache[64] = {};
+    const int per_sm = flood_kernel_per_sm(k_flood_heavy, smem, cache);
+    if (per_sm < 0) return per_sm;
     k_flood_heavy<<<static_cast<unsigned>(device_sm_count() * per_sm), kThreads, smem, s>>>(jobs, n_jobs, heavy_off,
                                                                                           ctl, k);
     note_launch();
@@ -1075,10 +1092,9 @@ int launch_flood_heavy(const DimArgs* jobs, int n_jobs, const int32_t* heavy_off
 
 int launch_flood(const DimArgs* jobs, int n_jobs, const int32_t* light_off, Ctl* ctl, int k, cudaStream_t s) {
     const size_t smem = size_t(kWarps) * 2 * kWTile * sizeof(float4);
-    FLOOD_CUDA(cudaFuncSetAttribute(k_flood, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    int per_sm = 0;
-    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flood, kThreads, smem));
-    per_sm = std::max(per_sm, 1);
+    static int cache[64] = {};
+    const int per_sm = flood_kernel_per_sm(k_flood, smem, cache);
+    if (per_sm < 0) return per_sm;
     const int64_t grid = int64_t(device_sm_count()) * per_sm;
     k_flood<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(jobs, n_jobs, light_off, ctl, k);
     note_launch();
