@@ -247,6 +247,53 @@ __global__ void k_group_fill(const int32_t* group_off, int64_t n_coarse, int2* g
     for (int32_t j = o; j < e; ++j) groups[j] = make_int2(static_cast<int>(c), j - o);
 }
 
+// The three steps above in one block, for lattices of up to 16 x 1024 coarse
+// cubes: thread t takes a run of consecutive cubes, a block scan of the runs'
+// group counts places them.
+constexpr int kGroupOffThreads = 1024;
+constexpr int64_t kGroupOffMaxCubes = int64_t(16) * kGroupOffThreads;
+
+__global__ void __launch_bounds__(kGroupOffThreads) k_group_offsets_one_block(const int32_t* bucket_start,
+                                                                             int64_t n_coarse, int32_t* group_off,
+                                                                             int2* groups) {
+    __shared__ int32_t s_warp[kGroupOffThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t per = (n_coarse + kGroupOffThreads - 1) / kGroupOffThreads;
+    const int64_t c0 = min(n_coarse, t * per), c1 = min(n_coarse, c0 + per);
+    auto groups_of = [&](int64_t c) {
+        const int32_t cnt = bucket_start[(c + 1) * kFine] - bucket_start[c * kFine];
+        return (cnt + kGroup - 1) / kGroup;
+    };
+    int32_t mine = 0;
+    for (int64_t c = c0; c < c1; ++c) mine += groups_of(c);
+    int32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int32_t off = (warp > 0 ? s_warp[warp - 1] : 0) + incl - mine;
+    for (int64_t c = c0; c < c1; ++c) {
+        const int32_t ng = groups_of(c);
+        group_off[c] = off;
+        for (int32_t j = 0; j < ng; ++j) groups[off + j] = make_int2(static_cast<int>(c), j);
+        off += ng;
+    }
+    if (t == kGroupOffThreads - 1) group_off[n_coarse] = s_warp[31];
+}
+
 // Longest-first queue: groups are counting-sorted by the number of shells
 // their vertex bound allows (descending), so the groups that may scan far
 // start first and the short ones fill in behind them.
@@ -267,13 +314,38 @@ __global__ void k_group_class_count(DimArgs a, const int32_t* n_groups, int32_t*
     atomicAdd(&class_count[group_class(a, a.groups[j])], 1);
 }
 
-__global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const int32_t* class_start,
-                                      int32_t* class_fill, int2* sorted) {
+// Every block takes the exclusive scan of the kClasses counts itself (block 0
+// also stores it: entry kClasses - kHeavyShells is the heavy prefix), then
+// places its groups.
+__global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const int32_t* class_count,
+                                      int32_t* class_start, int32_t* class_fill, int2* sorted) {
+    static_assert(kClasses == 64, "two lanes' worth of classes per lane of one warp");
+    __shared__ int32_t s_start[kClasses + 1];
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        const int32_t c0 = class_count[2 * l], c1 = class_count[2 * l + 1];
+        int32_t incl = c0 + c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (l >= o) incl += y;
+        }
+        const int32_t excl = incl - c0 - c1;
+        s_start[2 * l] = excl;
+        s_start[2 * l + 1] = excl + c0;
+        if (l == 31) s_start[kClasses] = incl;
+        if (blockIdx.x == 0) {
+            class_start[2 * l] = excl;
+            class_start[2 * l + 1] = excl + c0;
+            if (l == 31) class_start[kClasses] = incl;
+        }
+    }
+    __syncthreads();
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= *n_groups) return;
     const int2 gb = a.groups[j];
     const int c = group_class(a, gb);
-    sorted[class_start[c] + atomicAdd(&class_fill[c], 1)] = gb;
+    sorted[s_start[c] + atomicAdd(&class_fill[c], 1)] = gb;
 }
 
 // ---------------------------------------------------------------- shell streaming
@@ -1021,24 +1093,19 @@ __global__ void k_queue_offsets(const DimArgs* jobs, int n_jobs, int32_t* heavy_
 
 // Own maximum per simplex from the packed atomic maxima (0 when no sample can
 // exceed the facet maximum).
-__global__ void k_finalize(const unsigned long long* best, int64_t n, float* g2, int32_t* arg) {
-    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= n) return;
-    const unsigned long long b = best[i];
-    g2[i] = b ? __uint_as_float(static_cast<uint32_t>(b >> 32)) : 0.0f;
-    arg[i] = b ? static_cast<int32_t>(0xffffffffu - static_cast<uint32_t>(b)) : 0;
-}
-
 // ---------------------------------------------------------------- face-max
-// f(sigma) = max(sqrt(g2), f(facets)); the source of the maximum is the
-// lowest (dim << 28 | row, sample) among those attaining it.
+// f(sigma) = max(sqrt(g2), f(facets)), g2 and its sample from the simplex's
+// packed maximum (squared distance bits << 32 | ~sample; 0: no sample above
+// the facets); the source of the maximum is the lowest (dim << 28 | row,
+// sample) among those attaining it.
 __global__ void k_facemax(int k, int64_t n, const int32_t* simplices, const int32_t* facets, int64_t n_lower,
-                          const float* g2, const int32_t* arg, const float* val_lower, const int32_t* src_lower,
+                          const unsigned long long* own, const float* val_lower, const int32_t* src_lower,
                           float* val, int32_t* src, uint32_t* flags) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
-    float best = __fsqrt_rn(g2[i]);
-    int32_t s0 = (k << 28) | static_cast<int32_t>(i), s1 = arg[i];
+    const unsigned long long b = own[i];
+    float best = b ? __fsqrt_rn(__uint_as_float(static_cast<uint32_t>(b >> 32))) : 0.0f;
+    int32_t s0 = (k << 28) | static_cast<int32_t>(i), s1 = b ? static_cast<int32_t>(0xffffffffu - static_cast<uint32_t>(b)) : 0;
     for (int j = 0; j <= k; ++j) {
         const int32_t t = (k == 1) ? simplices[i * 2 + (1 - j)] : facets[i * (k + 1) + j];
         if (t < 0 || t >= n_lower) {
@@ -1225,11 +1292,10 @@ struct JobState {
     int64_t n_coarse, n_buckets, max_samples, max_n, max_groups;
     std::vector<uint8_t> tables[4];
     const uint8_t* comp[4];
-    int32_t *bcount, *bstart, *bfill, *goff, *g_arg, *cls;
+    int32_t *bcount, *bstart, *bfill, *goff, *cls;
     int2 *groups, *groups_sorted;
     SampleRec* recs;
     unsigned long long* best;
-    float* g_own;
     float shell_slack;
 };
 
@@ -1309,9 +1375,8 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s)
         if ((rc = scr.alloc(&J.bcount, J.n_buckets)) || (rc = scr.alloc(&J.bstart, J.n_buckets + 1)) ||
             (rc = scr.alloc(&J.bfill, J.n_buckets)) || (rc = scr.alloc(&J.goff, J.n_coarse + 1)) ||
             (rc = scr.alloc(&J.groups, J.max_groups)) || (rc = scr.alloc(&J.groups_sorted, J.max_groups)) ||
-            (rc = scr.alloc(&J.cls, 2 * (kClasses + 1))) || (rc = scr.alloc(&J.recs, J.max_samples)) ||
-            (rc = scr.alloc(&J.best, J.max_n)) || (rc = scr.alloc(&J.g_own, J.max_n)) ||
-            (rc = scr.alloc(&J.g_arg, J.max_n)))
+            (rc = scr.alloc(&J.cls, 3 * kClasses + 1)) || (rc = scr.alloc(&J.recs, J.max_samples)) ||
+            (rc = scr.alloc(&J.best, J.max_n)))
             return rc;
         const float emax = std::max(grid->bbox_hi[0] - grid->bbox_lo[0],
                                     std::max(grid->bbox_hi[1] - grid->bbox_lo[1], grid->bbox_hi[2] - grid->bbox_lo[2]));
@@ -1373,26 +1438,31 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s)
             if ((rc = exclusive_scan(J.bcount, J.bstart, J.n_buckets, s, scr))) return rc;
             k_samples<true><<<wb, 256, 0, s>>>(a);
             note_launch();
-            const unsigned bb = static_cast<unsigned>(ceil_div(J.n_coarse, 256));
-            k_group_counts<<<bb, 256, 0, s>>>(J.bstart, J.n_coarse, J.bcount);
-            note_launch();
-            if ((rc = exclusive_scan(J.bcount, J.goff, J.n_coarse, s, scr))) return rc;
-            k_group_fill<<<bb, 256, 0, s>>>(J.goff, J.n_coarse, J.groups);
-            note_launch();
+            if (J.n_coarse <= kGroupOffMaxCubes) {
+                k_group_offsets_one_block<<<1, kGroupOffThreads, 0, s>>>(J.bstart, J.n_coarse, J.goff, J.groups);
+                note_launch();
+            } else {
+                const unsigned bb = static_cast<unsigned>(ceil_div(J.n_coarse, 256));
+                k_group_counts<<<bb, 256, 0, s>>>(J.bstart, J.n_coarse, J.bcount);
+                note_launch();
+                if ((rc = exclusive_scan(J.bcount, J.goff, J.n_coarse, s, scr))) return rc;
+                k_group_fill<<<bb, 256, 0, s>>>(J.goff, J.n_coarse, J.groups);
+                note_launch();
+            }
             // longest-first order of this cloud's groups; the count stays on the device
             const int32_t* n_groups = J.goff + J.n_coarse;
-            FLOOD_CUDA(cudaMemsetAsync(J.cls, 0, sizeof(int32_t) * 2 * (kClasses + 1), s));
+            // cls: counts [0, kClasses), fill [kClasses, 2 kClasses), starts [2 kClasses, 3 kClasses + 1)
+            FLOOD_CUDA(cudaMemsetAsync(J.cls, 0, sizeof(int32_t) * 2 * kClasses, s));
             const unsigned gbk = static_cast<unsigned>(ceil_div(J.max_groups, 256));
             k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, J.cls);
             note_launch();
-            if ((rc = exclusive_scan(J.cls, J.cls + kClasses + 1, kClasses, s, scr))) return rc;
-            FLOOD_CUDA(cudaMemsetAsync(J.cls, 0, sizeof(int32_t) * kClasses, s));
-            k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, J.cls + kClasses + 1, J.cls, J.groups_sorted);
+            k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, J.cls, J.cls + 2 * kClasses, J.cls + kClasses,
+                                                      J.groups_sorted);
             note_launch();
             FLOOD_CUDA(cudaGetLastError());
             a.groups = J.groups_sorted;
             // heavy groups: shell bound >= kHeavyShells, i.e. classes [0, kClasses - kHeavyShells)
-            a.n_heavy = J.cls + kClasses + 1 + (kClasses - kHeavyShells);
+            a.n_heavy = J.cls + 2 * kClasses + (kClasses - kHeavyShells);
             FLOOD_CUDA(cudaMemcpyAsync(d_counts + i * 4 + k, n_groups, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
             h_jobs.push_back(a);
         }
@@ -1418,10 +1488,8 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s)
             JobState& J = js[i];
             const int64_t n = J.nk[k];
             if (n == 0) continue;
-            k_finalize<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(J.best, n, J.g_own, J.g_arg);
-            note_launch();
             k_facemax<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(
-                k, n, J.in.simplices[k], J.in.facets[k], J.nk[k - 1], J.g_own, J.g_arg, J.val[k - 1], J.src[k - 1],
+                k, n, J.in.simplices[k], J.in.facets[k], J.nk[k - 1], J.best, J.val[k - 1], J.src[k - 1],
                 J.val[k], J.src[k], &ctl->flags);
             note_launch();
             FLOOD_CUDA(cudaGetLastError());
