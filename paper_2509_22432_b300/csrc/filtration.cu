@@ -522,7 +522,10 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
                                               int32_t s_end, float ox, float oy, float oz, float4* tiles,
                                               uint64_t* bar, float* s_u, float* s_lb, uint32_t& phases, bool& abort,
                                               WarpCounters& cnt, int lane) {
-    float ax[NS], ay[NS], az[NS], pp[NS], mn[NS];
+    static_assert(NS % 2 == 0, "samples are evaluated in pairs");
+    // -2 p' per sample, paired over consecutive samples for packed FMAs
+    float2 ax[NS / 2], ay[NS / 2], az[NS / 2];
+    float pp[NS], mn[NS];
     bool live[NS];
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
     float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -535,14 +538,17 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
     for (int q = 0; q < NS; ++q) {
         const int32_t i = slot(q);
         live[q] = i < s_end;
-        ax[q] = ay[q] = az[q] = pp[q] = 0.0f;
+        float* const qx = (q & 1) ? &ax[q >> 1].y : &ax[q >> 1].x;
+        float* const qy = (q & 1) ? &ay[q >> 1].y : &ay[q >> 1].x;
+        float* const qz = (q & 1) ? &az[q >> 1].y : &az[q >> 1].x;
+        *qx = *qy = *qz = pp[q] = 0.0f;
         mn[q] = INFINITY;
         if (live[q]) {
             const SampleRec r = a.recs[i];
             const float px = __fsub_rn(r.x, ox), py = __fsub_rn(r.y, oy), pz = __fsub_rn(r.z, oz);
-            ax[q] = -2.0f * px;
-            ay[q] = -2.0f * py;
-            az[q] = -2.0f * pz;
+            *qx = -2.0f * px;
+            *qy = -2.0f * py;
+            *qz = -2.0f * pz;
             pp[q] = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
             R = fmaxf(R, r.u);
             wlo[0] = fminf(wlo[0], r.x);
@@ -645,13 +651,18 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
                     buf[e] = p;
                 }
                 __syncwarp();
+                // two samples per packed FMA chain: the same three rounded
+                // FMAs per pair as the scalar form, in the same order
 #pragma unroll 2
                 for (int j = gs; j < n; j += G) {
                     const float4 x = buf[j];
+                    const float2 xx = make_float2(x.x, x.x), xy = make_float2(x.y, x.y), xz = make_float2(x.z, x.z),
+                                 xw = make_float2(x.w, x.w);
 #pragma unroll
-                    for (int q = 0; q < NS; ++q) {
-                        const float t = __fmaf_rn(ax[q], x.x, __fmaf_rn(ay[q], x.y, __fmaf_rn(az[q], x.z, x.w)));
-                        mn[q] = fminf(mn[q], t);
+                    for (int q = 0; q < NS / 2; ++q) {
+                        const float2 t = __ffma2_rn(ax[q], xx, __ffma2_rn(ay[q], xy, __ffma2_rn(az[q], xz, xw)));
+                        mn[2 * q] = fminf(mn[2 * q], t.x);
+                        mn[2 * q + 1] = fminf(mn[2 * q + 1], t.y);
                     }
                 }
                 cnt.pairs += static_cast<unsigned long long>(n) * static_cast<unsigned long long>(n_valid);
