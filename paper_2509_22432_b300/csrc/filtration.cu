@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
 // bounds these groups) and fill one shared tile by bulk copies; the layout is the
 // warp kernel's (W sample lanes x 256/W point streams) stretched over the CTA,
 // and per-sample minima are combined in shared memory.
-constexpr int kHeavyTile = 2048;
+constexpr int kHeavyTile = 4096;
 constexpr int kHeavyShells = 8;  // class threshold: groups with >= this many shells are heavy
 
 // Evaluate the NSL used sample slots of one tile (NSL <= kHeavyNS).
