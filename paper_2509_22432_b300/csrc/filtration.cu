@@ -616,7 +616,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
         return T * T;
     };
     // shells below s0 hold no point (block distance field)
-    const int s0 = min(first_shell(g, lo, hi), s_max);
+    const int s0 = min(first_shell(g, lo, hi, lane), s_max);
     // minima to combine since the last combination; while none, the previous
     // radius (an upper bound of a recomputed one) still prunes safely
     bool dirty = true;
@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             __syncthreads();
         };
         // shells below s0 hold no point; a group with no live sample scans none
-        const int s0 = any_live ? min(first_shell(g, lo, hi), s_max) : 0;
+        const int s0 = any_live ? min(first_shell(g, lo, hi, lane), s_max) : 0;
         // fold only after tiles were evaluated: otherwise s_min is current and
         // the previous radius (an upper bound of the new one) still prunes safely
         bool dirty = any_live;

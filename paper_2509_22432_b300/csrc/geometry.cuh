@@ -80,15 +80,18 @@ __device__ __forceinline__ int cell_coord(float v, float o, float inv_cell, int 
 // hold a point: if every 4 x 4 x 4 block touching the box is D >= 1 blocks
 // from the nearest occupied block, no point lies within 4 (D - 1) cells of
 // the box, so shells 0 .. 4 (D - 1) are empty. Boxes over more than 64
-// blocks start at shell 0.
-__device__ __forceinline__ int first_shell(const GridView& g, const int lo[3], const int hi[3]) {
-    const int x0 = lo[0] >> 2, x1 = hi[0] >> 2, y0 = lo[1] >> 2, y1 = hi[1] >> 2, z0 = lo[2] >> 2, z1 = hi[2] >> 2;
-    if ((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1) > 64) return 0;
+// blocks start at shell 0. Warp-collective: the lanes read the (at most 64)
+// blocks' distances together.
+__device__ __forceinline__ int first_shell(const GridView& g, const int lo[3], const int hi[3], int lane) {
+    const int x0 = lo[0] >> 2, y0 = lo[1] >> 2, z0 = lo[2] >> 2;
+    const int nx = (hi[0] >> 2) - x0 + 1, ny = (hi[1] >> 2) - y0 + 1, nz = (hi[2] >> 2) - z0 + 1;
+    if (nx * ny * nz > 64) return 0;
     int d = 255;
-    for (int z = z0; z <= z1; ++z)
-        for (int y = y0; y <= y1; ++y)
-            for (int x = x0; x <= x1; ++x)
-                d = min(d, static_cast<int>(g.bdist[(static_cast<int64_t>(z) * g.by + y) * g.bx + x]));
+    for (int i = lane; i < nx * ny * nz; i += 32) {
+        const int x = x0 + i % nx, y = y0 + (i / nx) % ny, z = z0 + i / (nx * ny);
+        d = min(d, static_cast<int>(g.bdist[(static_cast<int64_t>(z) * g.by + y) * g.bx + x]));
+    }
+    d = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<uint32_t>(d)));
     return d >= 1 ? 4 * (d - 1) + 1 : 0;
 }
 
