@@ -230,10 +230,11 @@ __device__ __forceinline__ void bar_wait(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Entries of compute warp w: w and 32 + w are the best points of its chunks
-// A and B, 64 + w and 96 + w their second best (resident kernel; the global
-// kernel fills w only).
-constexpr int kEntries = 4 * kWarps;
+// Entries of compute warp w: 64 e + w and 64 e + 32 + w hold the (e + 1)-th
+// best point of its chunks A and B, e < kChunkEntries (resident kernel; the
+// global kernel fills w only).
+constexpr int kChunkEntries = 3;
+constexpr int kEntries = 2 * kChunkEntries * kWarps;
 
 struct FpsShared {
     float4 pxyz[kMaxPicks];     // this round's picks: coordinates (w unused)
@@ -269,19 +270,29 @@ __device__ __forceinline__ void order2(uint64_t& a, int& ia, uint64_t& b, int& i
     }
 }
 
-// Block reduction (X0): lane l holds entries l + 32 i (i < 4), sorted; the
+// Block reduction (X0): lane l holds entries l + 32 i (i < 6), sorted; the
 // lane holding the k-th best entry records its index in s.top[k], and lane
 // k < kTop receives it. Returns the bound on every other point.
 __device__ __forceinline__ float block_top(FpsShared& s, int lane, uint64_t& me, float& mx, float& my,
                                            float& mz) {
+    static_assert(kEntries == 6 * kWarps, "six entries per lane");
     uint64_t e0 = s.cand[lane], e1 = s.cand[kWarps + lane], e2 = s.cand[2 * kWarps + lane],
-             e3 = s.cand[3 * kWarps + lane];
-    int i0 = lane, i1 = kWarps + lane, i2 = 2 * kWarps + lane, i3 = 3 * kWarps + lane;
+             e3 = s.cand[3 * kWarps + lane], e4 = s.cand[4 * kWarps + lane], e5 = s.cand[5 * kWarps + lane];
+    int i0 = lane, i1 = kWarps + lane, i2 = 2 * kWarps + lane, i3 = 3 * kWarps + lane, i4 = 4 * kWarps + lane,
+        i5 = 5 * kWarps + lane;
+    // sorting network for six (descending)
+    order2(e0, i0, e5, i5);
+    order2(e1, i1, e3, i3);
+    order2(e2, i2, e4, i4);
+    order2(e1, i1, e2, i2);
+    order2(e3, i3, e4, i4);
+    order2(e0, i0, e3, i3);
+    order2(e2, i2, e5, i5);
     order2(e0, i0, e1, i1);
     order2(e2, i2, e3, i3);
-    order2(e0, i0, e2, i2);
-    order2(e1, i1, e3, i3);
+    order2(e4, i4, e5, i5);
     order2(e1, i1, e2, i2);
+    order2(e3, i3, e4, i4);
 #pragma unroll
     for (int k = 0; k < kTop; ++k) {
         const uint64_t m = warp_max_u64(e0);
@@ -293,7 +304,11 @@ __device__ __forceinline__ float block_top(FpsShared& s, int lane, uint64_t& me,
             i1 = i2;
             e2 = e3;
             i2 = i3;
-            e3 = 0ull;
+            e3 = e4;
+            i3 = i4;
+            e4 = e5;
+            i4 = i5;
+            e5 = 0ull;
         }
     }
     const float next = cand_key(warp_max_u64(e0));
@@ -560,31 +575,63 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t v) {
     return v;
 }
 
-// Entry of a chunk after its update: the point with minimum wm and the lowest
-// original row (lanes pass their lowest row holding wm, or ~0; rows are
-// distinct, so one lane holds the smallest), written to entry `slot` by that
-// lane (entry 0 if no lane has one). Returns the row (~0: none) and sets
-// `owner` on the lane that wrote it.
-__device__ __forceinline__ uint32_t publish_chunk(FpsShared& s, int slot, float wm, uint32_t cid, float cx,
-                                                  float cy, float cz, int lane, bool& owner) {
-    const uint32_t m = __reduce_min_sync(0xffffffffu, cid);
-    owner = m != 0xffffffffu && cid == m;
-    if (owner) {
-        s.cand[slot] = pack_cand(wm, cid);
-        s.cx[slot] = cx;
-        s.cy[slot] = cy;
-        s.cz[slot] = cz;
-    } else if (m == 0xffffffffu && lane == 0) {
-        s.cand[slot] = 0ull;
-    }
-    return m;
+// Running top four of a lane's minima (t[0] >= ... >= t[3], as a multiset).
+__device__ __forceinline__ void top4_insert(float v, float t[4]) {
+    t[3] = fmaxf(t[3], fminf(t[2], v));
+    t[2] = fmaxf(t[2], fminf(t[1], v));
+    t[1] = fmaxf(t[1], fminf(t[0], v));
+    t[0] = fmaxf(t[0], v);
 }
 
-// Running top three of a lane's minima (t1 >= t2 >= t3, as a multiset).
-__device__ __forceinline__ void top3_insert(float v, float& t1, float& t2, float& t3) {
-    t3 = fmaxf(t3, fminf(t2, v));
-    t2 = fmaxf(t2, fminf(t1, v));
-    t1 = fmaxf(t1, v);
+// Entries of a chunk after its update: its kChunkEntries best points in
+// (minimum desc, original row asc) order go to entries slot0 + 64 e, each
+// written by the lane holding it (0 if the chunk has fewer real points).
+// Each lane's best point not yet given is its (o + 1)-th minimum t[o], o the
+// entries it gave; rows already given are excluded from tie searches (rows
+// are distinct). Returns the bound on the chunk's other points (the largest
+// minimum left) and the chunk's largest minimum in wm.
+// val(k), row(k) and xyz(k, x, y, z) read this lane's point k.
+template <class Val, class Row, class Xyz>
+__device__ __forceinline__ float chunk_entries(FpsShared& s, const float t[4], int slot0, int lane, float& wm,
+                                               Val val, Row row, Xyz xyz) {
+    int o = 0;
+    uint32_t given[kChunkEntries - 1];
+#pragma unroll
+    for (int e = 0; e < kChunkEntries; ++e) {
+        const float v = o == 0 ? t[0] : o == 1 ? t[1] : o == 2 ? t[2] : t[3];
+        const float we = warp_max_f(v);
+        if (e == 0) wm = we;
+        uint32_t cid = 0xffffffffu;
+        float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+        if (we >= 0.0f && v == we) {  // padding holds -1
+#pragma unroll
+            for (int k = 0; k < kLanePts; ++k) {
+                if (val(k) == we) {
+                    const uint32_t id = row(k);
+                    bool fresh = id < cid;
+#pragma unroll
+                    for (int q = 0; q < e; ++q) fresh = fresh && id != given[q];
+                    if (fresh) {
+                        cid = id;
+                        xyz(k, cx, cy, cz);
+                    }
+                }
+            }
+        }
+        const uint32_t r = __reduce_min_sync(0xffffffffu, cid);
+        const int slot = slot0 + 2 * kWarps * e;
+        if (r != 0xffffffffu && cid == r) {
+            s.cand[slot] = pack_cand(we, r);
+            s.cx[slot] = cx;
+            s.cy[slot] = cy;
+            s.cz[slot] = cz;
+            ++o;
+        } else if (r == 0xffffffffu && lane == 0) {
+            s.cand[slot] = 0ull;
+        }
+        if (e < kChunkEntries - 1) given[e] = r;
+    }
+    return warp_max_f(o == 0 ? t[0] : o == 1 ? t[1] : o == 2 ? t[2] : t[3]);
 }
 
 // ---------------------------------------------------------------- resident kernel
@@ -736,54 +783,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
 #pragma unroll
                 for (int k = 0; k < kLanePts; ++k) pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], q.x, q.y, q.z));
             }
-            float t1 = -1.0f, t2 = -1.0f, t3 = -1.0f;
+            float t[4] = {-1.0f, -1.0f, -1.0f, -1.0f};
 #pragma unroll
-            for (int k = 0; k < kLanePts; ++k) top3_insert(pd[k], t1, t2, t3);
-            // best point of the chunk, then the best of the others
-            const float wm = warp_max_f(t1);
-            uint32_t cid = 0xffffffffu;
-            float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-            if (t1 == wm) {
-#pragma unroll
-                for (int k = 0; k < kLanePts; ++k) {
-                    if (pd[k] == wm) {
-                        const uint32_t id = static_cast<uint32_t>(s_ids[wo + lane + 32 * k]);
-                        if (id < cid) {
-                            cid = id;
-                            cx = px[k];
-                            cy = py[k];
-                            cz = pz[k];
-                        }
-                    }
-                }
-            }
-            bool own1, own2;
-            const uint32_t r1 = publish_chunk(s, warp, wm, cid, cx, cy, cz, lane, own1);
-            const float v2 = own1 ? t2 : t1;
-            const float wm2 = warp_max_f(v2);
-            cid = 0xffffffffu;
-            if (wm2 >= 0.0f && v2 == wm2) {
-#pragma unroll
-                for (int k = 0; k < kLanePts; ++k) {
-                    if (pd[k] == wm2) {
-                        const uint32_t id = static_cast<uint32_t>(s_ids[wo + lane + 32 * k]);
-                        if (id != r1 && id < cid) {
-                            cid = id;
-                            cx = px[k];
-                            cy = py[k];
-                            cz = pz[k];
-                        }
-                    }
-                }
-            }
-            publish_chunk(s, 2 * kWarps + warp, wm2, cid, cx, cy, cz, lane, own2);
-            const float sec = warp_max_f(own1 ? (own2 ? t3 : t2) : (own2 ? t2 : t1));
+            for (int k = 0; k < kLanePts; ++k) top4_insert(pd[k], t);
+            float wm;
+            const float sec = chunk_entries(
+                s, t, warp, lane, wm, [&](int k) { return pd[k]; },
+                [&](int k) { return static_cast<uint32_t>(s_ids[wo + lane + 32 * k]); },
+                [&](int k, float& x, float& y, float& z) {
+                    x = px[k];
+                    y = py[k];
+                    z = pz[k];
+                });
             if (lane == 0) s.sec[warp] = sec;
             maxd = wm;
         }
         if (bw >= 0) {
             const int wb = bw * kChunk;
-            float t1 = -1.0f, t2 = -1.0f, t3 = -1.0f;
+            float t[4] = {-1.0f, -1.0f, -1.0f, -1.0f};
             // two halves of four points per lane, picks in the outer loop so
             // that the four keys of a pick are independent
 #pragma unroll 1
@@ -807,47 +824,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
 #pragma unroll
                 for (int k = 0; k < kLanePts / 2; ++k) {
                     s_pts[3 * kPlane + wb + lane + 32 * (h + k)] = bd[k];
-                    top3_insert(bd[k], t1, t2, t3);
+                    top4_insert(bd[k], t);
                 }
             }
-            const float wm = warp_max_f(t1);
-            uint32_t cid = 0xffffffffu;
-            float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-            if (t1 == wm) {
-                for (int k = 0; k < kLanePts; ++k) {
-                    const int o = lane + 32 * k;
-                    if (s_pts[3 * kPlane + wb + o] == wm) {
-                        const uint32_t id = static_cast<uint32_t>(s_ids[kPlane + wb + o]);
-                        if (id < cid) {
-                            cid = id;
-                            cx = s_pts[wb + o];
-                            cy = s_pts[kPlane + wb + o];
-                            cz = s_pts[2 * kPlane + wb + o];
-                        }
-                    }
-                }
-            }
-            bool own1, own2;
-            const uint32_t r1 = publish_chunk(s, kWarps + bw, wm, cid, cx, cy, cz, lane, own1);
-            const float v2 = own1 ? t2 : t1;
-            const float wm2 = warp_max_f(v2);
-            cid = 0xffffffffu;
-            if (wm2 >= 0.0f && v2 == wm2) {
-                for (int k = 0; k < kLanePts; ++k) {
-                    const int o = lane + 32 * k;
-                    if (s_pts[3 * kPlane + wb + o] == wm2) {
-                        const uint32_t id = static_cast<uint32_t>(s_ids[kPlane + wb + o]);
-                        if (id != r1 && id < cid) {
-                            cid = id;
-                            cx = s_pts[wb + o];
-                            cy = s_pts[kPlane + wb + o];
-                            cz = s_pts[2 * kPlane + wb + o];
-                        }
-                    }
-                }
-            }
-            publish_chunk(s, 3 * kWarps + bw, wm2, cid, cx, cy, cz, lane, own2);
-            const float sec = warp_max_f(own1 ? (own2 ? t3 : t2) : (own2 ? t2 : t1));
+            float wm;
+            const float sec = chunk_entries(
+                s, t, kWarps + bw, lane, wm, [&](int k) { return s_pts[3 * kPlane + wb + lane + 32 * k]; },
+                [&](int k) { return static_cast<uint32_t>(s_ids[kPlane + wb + lane + 32 * k]); },
+                [&](int k, float& x, float& y, float& z) {
+                    const int o = wb + lane + 32 * k;
+                    x = s_pts[o];
+                    y = s_pts[kPlane + o];
+                    z = s_pts[2 * kPlane + o];
+                });
             if (lane == 0) {
                 s.sec[kWarps + bw] = sec;
                 reinterpret_cast<float*>(s_box + (2 * bw + 1) * 2)[3] = wm;
