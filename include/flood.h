@@ -85,12 +85,13 @@ int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t sta
  * number of co-resident 1024-thread blocks (one per SM) the persistent FPS
  * launch may use:
  *   0   automatic (what flood_fps does): the fewest blocks whose registers
- *       and shared memory hold every point (14,336 points per block, so up
- *       to 1,146,880 points on 80 blocks; one block needs no grid-wide
- *       exchange), else 80 blocks with points streamed from memory;
+ *       hold every point (7,168 points per block, one block per SM, so up
+ *       to 1,060,864 points on a 148-SM B300; one block needs no grid-wide
+ *       exchange), else as many blocks as SMs (at most 160) with points
+ *       streamed from memory;
  *   1   one block: leaves the other SMs to concurrent work (many small
- *       clouds at once); points stream from memory above 14,336;
- *   k   k blocks (clamped to the SM count and to 80).
+ *       clouds at once); points stream from memory above 7,168;
+ *   k   k blocks (clamped to the SM count and to 160).
  * Errors: as flood_fps; FLOOD_EINVAL also for n_blocks < 0.
  * ------------------------------------------------------------------------ */
 int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,

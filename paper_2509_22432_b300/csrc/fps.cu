@@ -43,9 +43,9 @@ constexpr int kPollers = 4;                // the last four warps run the exchan
 constexpr int kComputeWarps = kWarps - kPollers;
 constexpr int kLanePts = 8;                // points per lane of a chunk
 constexpr int kChunk = 32 * kLanePts;      // points per chunk (resident kernel)
-constexpr int64_t kBlockPts = 2 * int64_t(kComputeWarps) * kChunk;  // points a resident block holds
-constexpr int kMaxBlocks = 80;             // four exchange warps poll 20 blocks each in 5 loads per lane
-constexpr int kSlotStride = 32;            // uint64 words per block slot (256 bytes)
+constexpr int64_t kBlockPts = int64_t(kComputeWarps) * kChunk;  // points a resident block holds
+constexpr int kMaxBlocks = 160;            // four exchange warps poll 40 blocks each in 5 loads per lane
+constexpr int kSlotStride = 16;            // uint64 words per block slot (128 bytes)
 constexpr int64_t kSortMin = 16384;        // smaller clouds keep their input order
 constexpr int kGlobalBatch = 5;            // global kernel: points per lane loaded at once
 constexpr int kMetaBytes = 8 + 10 * 4;     // per chunk in shared memory: candidate, box, coordinates, second
@@ -206,8 +206,9 @@ struct FpsArgs {
 //   point outside the entries can beat or tie it). Repeating this selects
 //   several picks per round with the result of plain FPS, bit for bit: on the
 //   1M-point torus with 2,000 picks a round makes about four picks.
-constexpr int kTop = 8;        // entries a block publishes
-constexpr int kMaxPicks = 16;  // picks per round (one box-test lane per pick and chunk)
+constexpr int kTop = 4;        // entries a block publishes
+constexpr int kKeep = 8;       // entries each exchange warp keeps of its quarter of the blocks
+constexpr int kMaxPicks = 16;  // picks per round
 
 // Exchange warps X0..X3 (warps kComputeWarps..kWarps - 1): X0 reduces the
 // block's entries, publishes them and polls the first quarter of the blocks;
@@ -220,7 +221,7 @@ constexpr int kMaxPicks = 16;  // picks per round (one box-test lane per pick an
 // (everyone else waits). An arrival releases the arriving thread's earlier
 // shared-memory writes to the threads that complete the wait.
 constexpr int kX0 = kComputeWarps;  // warp kX0 + 1 is X1 (it records the picks)
-constexpr int kBarCands = 1, kBarPicks = 2, kBarQuarters = 3, kBarPub = 4, kBarHits = 5;
+constexpr int kBarCands = 1, kBarPicks = 2, kBarQuarters = 3, kBarPub = 4;
 constexpr int kCandsCount = (kComputeWarps + 1) * 32;
 constexpr int kPollCount = kPollers * 32;
 __device__ __forceinline__ void bar_arrive(int id, int count) {
@@ -230,25 +231,23 @@ __device__ __forceinline__ void bar_wait(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Entries of compute warp w: 64 e + w and 64 e + 32 + w hold the (e + 1)-th
-// best point of its chunks A and B, e < kChunkEntries (resident kernel; the
-// global kernel fills w only).
+// Entries of compute warp w: 32 e + w holds the (e + 1)-th best point of its
+// chunk, e < kChunkEntries (resident kernel; the global kernel fills w only).
 constexpr int kChunkEntries = 3;
-constexpr int kEntries = 2 * kChunkEntries * kWarps;
+constexpr int kEntries = kChunkEntries * kWarps;
 
 struct FpsShared {
     float4 pxyz[kMaxPicks];     // this round's picks: coordinates (w unused)
     uint64_t cand[kEntries];
     float cx[kEntries], cy[kEntries], cz[kEntries];
-    float sec[2 * kWarps];      // bound on every other point of chunk A (w) or B (32 + w); -1: none
+    float sec[kWarps];          // bound on every other point of warp w's chunk(s); -1: none
     uint64_t pick[kMaxPicks];   // this round's picks (candidate words with the minimum at the pick)
     int n_pick;                 // picks of the round; -1 = stop (timeout)
-    uint64_t qc[kPollers][kTop];  // best entries of each quarter of the blocks
-    float qx[kPollers][kTop], qy[kPollers][kTop], qz[kPollers][kTop];
+    uint64_t qc[kPollers][kKeep];  // best entries of each quarter of the blocks
+    float qx[kPollers][kKeep], qy[kPollers][kKeep], qz[kPollers][kKeep];
     float qbound[kPollers];     // each quarter's bound on everything else
     int qstop[kPollers];
-    int top[kTop];              // entry indices of the block's best entries (block_top)
-    uint32_t hits[kWarps];      // resident kernel: each compute warp's pick masks (A | B << 16)
+    int top[kKeep];             // entry indices of the block's best entries (block_top)
 };
 
 __device__ __forceinline__ void shared_init(FpsShared& s) {
@@ -256,7 +255,7 @@ __device__ __forceinline__ void shared_init(FpsShared& s) {
         s.cand[threadIdx.x] = 0ull;
         s.cx[threadIdx.x] = s.cy[threadIdx.x] = s.cz[threadIdx.x] = 0.0f;
     }
-    if (threadIdx.x < 2 * kWarps) s.sec[threadIdx.x] = -1.0f;
+    if (threadIdx.x < kWarps) s.sec[threadIdx.x] = -1.0f;
 }
 
 __device__ __forceinline__ void order2(uint64_t& a, int& ia, uint64_t& b, int& ib) {
@@ -270,31 +269,20 @@ __device__ __forceinline__ void order2(uint64_t& a, int& ia, uint64_t& b, int& i
     }
 }
 
-// Block reduction (X0): lane l holds entries l + 32 i (i < 6), sorted; the
+// Block reduction (X0): lane l holds entries l + 32 i (i < 3), sorted; the
 // lane holding the k-th best entry records its index in s.top[k], and lane
-// k < kTop receives it. Returns the bound on every other point.
-__device__ __forceinline__ float block_top(FpsShared& s, int lane, uint64_t& me, float& mx, float& my,
+// k < ntop receives it. Returns the bound on every other point.
+__device__ __forceinline__ float block_top(FpsShared& s, int lane, int ntop, uint64_t& me, float& mx, float& my,
                                            float& mz) {
-    static_assert(kEntries == 6 * kWarps, "six entries per lane");
-    uint64_t e0 = s.cand[lane], e1 = s.cand[kWarps + lane], e2 = s.cand[2 * kWarps + lane],
-             e3 = s.cand[3 * kWarps + lane], e4 = s.cand[4 * kWarps + lane], e5 = s.cand[5 * kWarps + lane];
-    int i0 = lane, i1 = kWarps + lane, i2 = 2 * kWarps + lane, i3 = 3 * kWarps + lane, i4 = 4 * kWarps + lane,
-        i5 = 5 * kWarps + lane;
-    // sorting network for six (descending)
-    order2(e0, i0, e5, i5);
-    order2(e1, i1, e3, i3);
-    order2(e2, i2, e4, i4);
-    order2(e1, i1, e2, i2);
-    order2(e3, i3, e4, i4);
-    order2(e0, i0, e3, i3);
-    order2(e2, i2, e5, i5);
+    static_assert(kEntries == 3 * kWarps, "three entries per lane");
+    uint64_t e0 = s.cand[lane], e1 = s.cand[kWarps + lane], e2 = s.cand[2 * kWarps + lane];
+    int i0 = lane, i1 = kWarps + lane, i2 = 2 * kWarps + lane;
     order2(e0, i0, e1, i1);
-    order2(e2, i2, e3, i3);
-    order2(e4, i4, e5, i5);
     order2(e1, i1, e2, i2);
-    order2(e3, i3, e4, i4);
+    order2(e0, i0, e1, i1);
 #pragma unroll
-    for (int k = 0; k < kTop; ++k) {
+    for (int k = 0; k < kKeep; ++k) {
+        if (k == ntop) break;
         const uint64_t m = warp_max_u64(e0);
         if (e0 == m) {  // one lane, unless m == 0 (no entry left: any of them may record it)
             s.top[k] = m != 0ull ? i0 : -1;
@@ -302,21 +290,15 @@ __device__ __forceinline__ float block_top(FpsShared& s, int lane, uint64_t& me,
             i0 = i1;
             e1 = e2;
             i1 = i2;
-            e2 = e3;
-            i2 = i3;
-            e3 = e4;
-            i3 = i4;
-            e4 = e5;
-            i4 = i5;
-            e5 = 0ull;
+            e2 = 0ull;
         }
     }
     const float next = cand_key(warp_max_u64(e0));
-    const float sec = warp_max_f(fmaxf(s.sec[lane], s.sec[kWarps + lane]));
+    const float sec = warp_max_f(s.sec[lane]);
     __syncwarp();
     me = 0ull;
     mx = my = mz = 0.0f;
-    if (lane < kTop) {
+    if (lane < ntop) {
         const int i = s.top[lane];
         if (i >= 0) {
             me = s.cand[i];
@@ -334,23 +316,23 @@ __device__ __forceinline__ float block_top(FpsShared& s, int lane, uint64_t& me,
 __device__ __forceinline__ uint32_t bound_up30(float u) { return ((__float_as_uint(u) + 3u) & ~3u) >> 2; }
 __device__ __forceinline__ float bound_from30(uint32_t v) { return __uint_as_float(v << 2); }
 
-// Slot of block b for round r (parity r & 1): 256 bytes holding kTop
+// Slot of block b for round r (parity r & 1): 128 bytes holding kTop
 // entries of four words, each word tagged with r & 3 in its top bits:
 //   w0 = tag | candidate
 //   w1 = tag | U30 << 32 (first entry only) | bits of x;  w2 = tag | y;  w3 = tag | z.
 // A reader accepts a block once all its words carry round r, so every word is
 // read atomically and no order between them is needed; a block cannot publish
 // round r + 2 (same parity) before every block has finished reading r + 1.
-// Exchange warp h polls blocks [20 h, 20 h + 20): in load l, lane 8 i + q
-// reads entry q of block 20 h + 4 l + i (one 32-byte access per lane).
+// Exchange warp h polls blocks [40 h, 40 h + 40): in load l, lane 4 i + q
+// reads entry q of block 40 h + 8 l + i (one 32-byte access per lane).
 constexpr int kBlocksPerLoad = 32 / kTop;
 constexpr int kPollLoads = 5;
 constexpr int kQuarterBlocks = kBlocksPerLoad * kPollLoads;
 static_assert(kPollers * kQuarterBlocks == kMaxBlocks, "the exchange warps cover every block");
-static_assert(kPollers * kTop == 32, "X0 merges one kept entry per lane");
+static_assert(kPollers * kKeep == 32, "X0 merges one kept entry per lane");
 static_assert(2 * kMaxPicks <= 32, "one box-test lane per pick and chunk");
 
-// Poll quarter h of the blocks until all carry round r; its best kTop entries
+// Poll quarter h of the blocks until all carry round r; its best kKeep entries
 // go to s.qc[h] etc. (each written by the lane holding it) and its bound on
 // every other point to s.qbound[h].
 __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int r, int h, int lane) {
@@ -392,7 +374,7 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
     }
     u30 = __reduce_max_sync(0xffffffffu, u30);
 #pragma unroll
-    for (int k = 0; k <= kTop; ++k) {
+    for (int k = 0; k <= kKeep; ++k) {
         uint64_t v = 0ull;
         int vl = 0;
 #pragma unroll
@@ -402,7 +384,7 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
                 vl = l;
             }
         const uint64_t m = warp_max_u64(v);
-        if (k == kTop) {  // the best entry left out
+        if (k == kKeep) {  // the best entry left out
             if (lane == 0) {
                 s.qbound[h] = fmaxf(bound_from30(u30), cand_key(m));
                 s.qstop[h] = stop;
@@ -432,7 +414,7 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
 __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, int r, int picks_left, int lane) {
     uint64_t me;
     float mx, my, mz;
-    float bound = block_top(s, lane, me, mx, my, mz);
+    float bound = block_top(s, lane, gridDim.x > 1 ? kTop : kKeep, me, mx, my, mz);
     bool stop = false;
     if (gridDim.x > 1) {
         const uint64_t tag = static_cast<uint64_t>(r & 3) << 62;
@@ -447,7 +429,7 @@ __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, in
         bar_wait(kBarQuarters, kPollCount);
         __syncwarp();
         // lane 8 h + k holds entry k of quarter h
-        const int hh = lane / kTop, kk = lane % kTop;
+        const int hh = lane / kKeep, kk = lane % kKeep;
         me = s.qc[hh][kk];
         mx = s.qx[hh][kk];
         my = s.qy[hh][kk];
@@ -565,16 +547,6 @@ __device__ __forceinline__ uint32_t box_hits(const FpsShared& s, int np, float l
     return hit;
 }
 
-// Even bits of v (bit 2 t moves to bit t).
-__device__ __forceinline__ uint32_t even_bits(uint32_t v) {
-    v &= 0x55555555u;
-    v = (v | (v >> 1)) & 0x33333333u;
-    v = (v | (v >> 2)) & 0x0f0f0f0fu;
-    v = (v | (v >> 4)) & 0x00ff00ffu;
-    v = (v | (v >> 8)) & 0x0000ffffu;
-    return v;
-}
-
 // Running top four of a lane's minima (t[0] >= ... >= t[3], as a multiset).
 __device__ __forceinline__ void top4_insert(float v, float t[4]) {
     t[3] = fmaxf(t[3], fminf(t[2], v));
@@ -584,7 +556,7 @@ __device__ __forceinline__ void top4_insert(float v, float t[4]) {
 }
 
 // Entries of a chunk after its update: its kChunkEntries best points in
-// (minimum desc, original row asc) order go to entries slot0 + 64 e, each
+// (minimum desc, original row asc) order go to entries slot0 + 32 e, each
 // written by the lane holding it (0 if the chunk has fewer real points).
 // Each lane's best point not yet given is its (o + 1)-th minimum t[o], o the
 // entries it gave; rows already given are excluded from tie searches (rows
@@ -619,7 +591,7 @@ __device__ __forceinline__ float chunk_entries(FpsShared& s, const float t[4], i
             }
         }
         const uint32_t r = __reduce_min_sync(0xffffffffu, cid);
-        const int slot = slot0 + 2 * kWarps * e;
+        const int slot = slot0 + kWarps * e;
         if (r != 0xffffffffu && cid == r) {
             s.cand[slot] = pack_cand(we, r);
             s.cx[slot] = cx;
@@ -638,24 +610,19 @@ __device__ __forceinline__ float chunk_entries(FpsShared& s, const float t[4], i
 // Chunks are dealt to blocks round-robin (chunk g to block g mod nb), so the
 // few chunks one pick changes, which are neighbours in space and in the point
 // order, fall into different blocks and update in parallel. Compute warp w of
-// block b holds chunk A = 2 w nb + b in registers (points 256 A + lane + 32 k,
-// k < 8) and chunk B = A + nb in shared memory; boxes and chunk B's largest
-// minimum in shared memory, chunk A's in a register.
+// block b holds chunk w nb + b in registers (points 256 (w nb + b) + lane +
+// 32 k, k < 8): with one block on each SM, 148 SMs hold 1,060,864 points.
 // Dynamic shared memory:
-//   ids  int32  [2][28][256]  original rows of chunks A and B
-//   pts  float  [4][28][256]  chunk B: x, y, z, running minimum
-//   box  float4 [32][2][2]    per warp and chunk (A, B): (lo x/y/z, largest
-//                             minimum: chunk B only), (hi x/y/z, unused)
+//   ids  int32  [28][256]  original rows of each warp's chunk
+//   box  float4 [32][2]    per warp: (lo x/y/z, unused), (hi x/y/z, unused)
 constexpr int kResIds = 0;
-constexpr int kResPts = kResIds + 2 * kComputeWarps * kChunk * 4;
-constexpr int kResMeta = kResPts + 4 * kComputeWarps * kChunk * 4;
-constexpr int kResidentSmem = kResMeta + kWarps * 2 * 2 * 16;
+constexpr int kResMeta = kResIds + kComputeWarps * kChunk * 4;
+constexpr int kResidentSmem = kResMeta + kWarps * 2 * 16;
 
 __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
     __shared__ FpsShared s;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     int32_t* s_ids = reinterpret_cast<int32_t*>(s_dyn + kResIds);
-    float* s_pts = reinterpret_cast<float*>(s_dyn + kResPts);
     float4* s_box = reinterpret_cast<float4*>(s_dyn + kResMeta);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     shared_init(s);
@@ -665,46 +632,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
         exchange_loop(a, s, warp, lane);
         return;
     }
-    const int64_t base = (static_cast<int64_t>(2 * warp) * gridDim.x + blockIdx.x) * kChunk;  // chunk A
-    const int64_t base_b = base + static_cast<int64_t>(gridDim.x) * kChunk;                  // chunk B
-    // shared-memory rows of this warp: index field * kPlane + wo + lane + 32 k
-    constexpr int kPlane = kComputeWarps * kChunk;
+    const int64_t base = (static_cast<int64_t>(warp) * gridDim.x + blockIdx.x) * kChunk;
     const int wo = warp * kChunk;
-    // chunk B into shared memory, then chunk A into registers; their boxes
     const float inf = __int_as_float(0x7f800000);
-    {
-        float blox = inf, bloy = inf, bloz = inf, bhix = -inf, bhiy = -inf, bhiz = -inf;
-#pragma unroll
-        for (int k = 0; k < kLanePts; ++k) {
-            const int o = lane + 32 * k;
-            const int64_t ib = base_b + o;
-            const bool okb = ib < a.n;
-            const float qx = okb ? a.x[ib] : 0.0f, qy = okb ? a.y[ib] : 0.0f, qz = okb ? a.z[ib] : 0.0f;
-            s_pts[wo + o] = qx;
-            s_pts[kPlane + wo + o] = qy;
-            s_pts[2 * kPlane + wo + o] = qz;
-            s_pts[3 * kPlane + wo + o] = okb ? inf : -1.0f;
-            s_ids[kPlane + wo + o] = okb ? a.ids[ib] : 0;
-            if (okb) {
-                blox = fminf(blox, qx);
-                bloy = fminf(bloy, qy);
-                bloz = fminf(bloz, qz);
-                bhix = fmaxf(bhix, qx);
-                bhiy = fmaxf(bhiy, qy);
-                bhiz = fmaxf(bhiz, qz);
-            }
-        }
-        blox = warp_min_f(blox);
-        bloy = warp_min_f(bloy);
-        bloz = warp_min_f(bloz);
-        bhix = warp_max_f(bhix);
-        bhiy = warp_max_f(bhiy);
-        bhiz = warp_max_f(bhiz);
-        if (lane == 0) {
-            s_box[(2 * warp + 1) * 2 + 0] = make_float4(blox, bloy, bloz, base_b < a.n ? inf : -1.0f);
-            s_box[(2 * warp + 1) * 2 + 1] = make_float4(bhix, bhiy, bhiz, 0.0f);
-        }
-    }
     float px[kLanePts], py[kLanePts], pz[kLanePts], pd[kLanePts];
     {
         float lox = inf, loy = inf, loz = inf, hix = -inf, hiy = -inf, hiz = -inf;
@@ -734,52 +664,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
         hiy = warp_max_f(hiy);
         hiz = warp_max_f(hiz);
         if (lane == 0) {
-            s_box[(2 * warp + 0) * 2 + 0] = make_float4(lox, loy, loz, 0.0f);
-            s_box[(2 * warp + 0) * 2 + 1] = make_float4(hix, hiy, hiz, 0.0f);
+            s_box[2 * warp] = make_float4(lox, loy, loz, 0.0f);
+            s_box[2 * warp + 1] = make_float4(hix, hiy, hiz, 0.0f);
         }
     }
-    // Largest running minimum of chunk A (lane-replicated); -1 = no points.
+    // Largest running minimum of the chunk (lane-replicated); -1 = no points.
     float maxd = base < a.n ? inf : -1.0f;
     __syncthreads();
     for (int j = 1; j < a.n_landmarks;) {
-        // lanes 2 t + c test pick t against chunk c (0 = A, 1 = B)
+        // lane t tests pick t against the chunk's box
         const int np = s.n_pick;
         bool hit = false;
-        if ((lane >> 1) < np) {
-            const int t = lane >> 1, c = lane & 1;
-            const float4 lo = s_box[(2 * warp + c) * 2], hi = s_box[(2 * warp + c) * 2 + 1], q = s.pxyz[t];
-            hit = !(box_gap2(q.x, q.y, q.z, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z) >= (c ? lo.w : maxd));
+        if (lane < np) {
+            const float4 lo = s_box[2 * warp], hi = s_box[2 * warp + 1], q = s.pxyz[lane];
+            hit = !(box_gap2(q.x, q.y, q.z, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z) >= maxd);
         }
-        const uint32_t hb = __ballot_sync(0xffffffffu, hit);
-        const uint32_t hit_a = even_bits(hb), hit_b = even_bits(hb >> 1);
-        // A warp whose two chunks both changed hands chunk B (shared memory,
-        // foldable by any warp) to a warp with nothing to fold: the i-th such
-        // warp to the i-th idle warp.
-        if (lane == 0) s.hits[warp] = hit_a | (hit_b << 16);
-        bar_wait(kBarHits, kComputeWarps * 32);
-        int bw = -1;  // owner of the chunk B this warp folds
-        uint32_t bmask = 0u;
-        {
-            const uint32_t hw = lane < kComputeWarps ? s.hits[lane] : 0u;
-            const uint32_t both = __ballot_sync(0xffffffffu, (hw & 0xffffu) && (hw >> 16));
-            const uint32_t idle = __ballot_sync(0xffffffffu, lane < kComputeWarps && hw == 0u);
-            const uint32_t below = (1u << warp) - 1u;
-            const int n_move = min(__popc(both), __popc(idle));
-            if (hit_b && !(hit_a && __popc(both & below) < n_move)) {
-                bw = warp;
-                bmask = hit_b;
-            } else if (!hit_a && !hit_b && __popc(idle & below) < n_move) {
-                uint32_t m = both;  // the (rank + 1)-th warp of `both`
-                for (int i = __popc(idle & below); i > 0; --i) m &= m - 1;
-                bw = __ffs(m) - 1;
-                bmask = s.hits[bw] >> 16;
-            }
-        }
-        if (hit_a) {
+        const uint32_t hits = __ballot_sync(0xffffffffu, hit);
+        if (hits) {
 #pragma unroll 1
-            for (uint32_t mt = hit_a; mt; mt &= mt - 1) {
-                const int t = __ffs(mt) - 1;
-                const float4 q = s.pxyz[t];
+            for (uint32_t mt = hits; mt; mt &= mt - 1) {
+                const float4 q = s.pxyz[__ffs(mt) - 1];
 #pragma unroll
                 for (int k = 0; k < kLanePts; ++k) pd[k] = fminf(pd[k], fps_key(px[k], py[k], pz[k], q.x, q.y, q.z));
             }
@@ -797,50 +701,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
                 });
             if (lane == 0) s.sec[warp] = sec;
             maxd = wm;
-        }
-        if (bw >= 0) {
-            const int wb = bw * kChunk;
-            float t[4] = {-1.0f, -1.0f, -1.0f, -1.0f};
-            // two halves of four points per lane, picks in the outer loop so
-            // that the four keys of a pick are independent
-#pragma unroll 1
-            for (int h = 0; h < kLanePts; h += kLanePts / 2) {
-                float bx[kLanePts / 2], by[kLanePts / 2], bz[kLanePts / 2], bd[kLanePts / 2];
-#pragma unroll
-                for (int k = 0; k < kLanePts / 2; ++k) {
-                    const int o = wb + lane + 32 * (h + k);
-                    bx[k] = s_pts[o];
-                    by[k] = s_pts[kPlane + o];
-                    bz[k] = s_pts[2 * kPlane + o];
-                    bd[k] = s_pts[3 * kPlane + o];
-                }
-#pragma unroll 1
-                for (uint32_t mt = bmask; mt; mt &= mt - 1) {
-                    const float4 q = s.pxyz[__ffs(mt) - 1];
-#pragma unroll
-                    for (int k = 0; k < kLanePts / 2; ++k)
-                        bd[k] = fminf(bd[k], fps_key(bx[k], by[k], bz[k], q.x, q.y, q.z));
-                }
-#pragma unroll
-                for (int k = 0; k < kLanePts / 2; ++k) {
-                    s_pts[3 * kPlane + wb + lane + 32 * (h + k)] = bd[k];
-                    top4_insert(bd[k], t);
-                }
-            }
-            float wm;
-            const float sec = chunk_entries(
-                s, t, kWarps + bw, lane, wm, [&](int k) { return s_pts[3 * kPlane + wb + lane + 32 * k]; },
-                [&](int k) { return static_cast<uint32_t>(s_ids[kPlane + wb + lane + 32 * k]); },
-                [&](int k, float& x, float& y, float& z) {
-                    const int o = wb + lane + 32 * k;
-                    x = s_pts[o];
-                    y = s_pts[kPlane + o];
-                    z = s_pts[2 * kPlane + o];
-                });
-            if (lane == 0) {
-                s.sec[kWarps + bw] = sec;
-                reinterpret_cast<float*>(s_box + (2 * bw + 1) * 2)[3] = wm;
-            }
         }
         bar_arrive(kBarCands, kCandsCount);
         bar_wait(kBarPicks, kThreads);
@@ -1051,7 +911,7 @@ struct FpsPlan {
 int max_fps_blocks() { return std::min(device_sm_count(), kMaxBlocks); }
 
 // Launch shape: n_blocks = 0 picks the fewest blocks whose registers and
-// shared memory hold every point (14,336 per block), else 80 blocks (or the SM
+// shared memory hold every point (7,168 per block), else 160 blocks (or the SM
 // count, if smaller) with chunks streamed from global memory; n_blocks = k
 // uses k blocks, resident when they hold every point.
 int plan_fps(int64_t n, int n_blocks, FpsPlan* p) {

@@ -74,12 +74,12 @@ def test_fps_ties_and_duplicates():
 
 
 # Every launch shape of the persistent FPS kernel gives the same picks: one
-# block holding its points on chip (n <= 14,336), several such blocks, one
+# block holding its points on chip (n <= 7,168), several such blocks, one
 # block streaming chunks from memory, several streaming blocks; and runs to
 # the last point, where rounds make many picks at small, close keys.
 @pytest.mark.parametrize("n,n_l,blocks,seed", [
     (5_000, 200, 0, 11), (5_000, 200, 3, 12),
-    (30_000, 300, 0, 13), (30_000, 300, 4, 14), (30_000, 300, 1, 15),
+    (30_000, 300, 0, 13), (30_000, 300, 4, 14), (30_000, 300, 1, 15), (30_000, 300, 5, 24),
     (100_000, 500, 0, 16), (100_000, 500, 1, 17), (100_000, 500, 5, 18),
     (3_000, 3_000, 0, 21), (3_000, 3_000, 2, 22), (20_000, 4_000, 2, 23)])
 def test_fps_launch_shapes_bit_exact(n, n_l, blocks, seed):
