@@ -208,7 +208,7 @@ struct FpsArgs {
 //   1M-point torus with 2,000 picks a round makes about four picks.
 constexpr int kTop = 4;        // entries a block publishes
 constexpr int kKeep = 8;       // entries each exchange warp keeps of its quarter of the blocks
-constexpr int kMaxPicks = 16;  // picks per round
+constexpr int kMaxPicks = 32;  // picks per round
 
 // Exchange warps X0..X3 (warps kComputeWarps..kWarps - 1): X0 reduces the
 // block's entries, publishes them and polls the first quarter of the blocks;
@@ -330,7 +330,7 @@ constexpr int kPollLoads = 5;
 constexpr int kQuarterBlocks = kBlocksPerLoad * kPollLoads;
 static_assert(kPollers * kQuarterBlocks == kMaxBlocks, "the exchange warps cover every block");
 static_assert(kPollers * kKeep == 32, "X0 merges one kept entry per lane");
-static_assert(2 * kMaxPicks <= 32, "one box-test lane per pick and chunk");
+static_assert(kMaxPicks <= 32, "one box-test lane per pick");
 
 // Poll quarter h of the blocks until all carry round r; its best kKeep entries
 // go to s.qc[h] etc. (each written by the lane holding it) and its bound on
