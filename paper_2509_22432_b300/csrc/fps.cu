@@ -85,33 +85,26 @@ __global__ void __launch_bounds__(256) k_morton_count(const float* X, int64_t n,
     atomicAdd(&count[c], 1);
 }
 
-// Counting-sort scatter into structure-of-arrays order; `fill` holds the
-// histogram and is counted down (order within a code is arbitrary, which
-// changes no result: ties are decided by the original row).
+// Counting-sort scatter into point order, one float4 (x, y, z, original row
+// as int bits) per point; `fill` holds the histogram and is counted down
+// (order within a code is arbitrary, which changes no result: ties are
+// decided by the original row).
 __global__ void __launch_bounds__(256) k_morton_scatter(const float* X, int64_t n, const int32_t* code,
-                                                       const int32_t* start, int32_t* fill, float* x, float* y,
-                                                       float* z, int32_t* ids) {
+                                                       const int32_t* start, int32_t* fill, float4* pts) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     const int32_t c = code[i];
     const int32_t pos = start[c] + atomicSub(&fill[c], 1) - 1;
-    x[pos] = X[3 * i + 0];
-    y[pos] = X[3 * i + 1];
-    z[pos] = X[3 * i + 2];
-    ids[pos] = static_cast<int32_t>(i);
+    pts[pos] = make_float4(X[3 * i + 0], X[3 * i + 1], X[3 * i + 2], __int_as_float(static_cast<int32_t>(i)));
 }
 
-// Input order (small clouds): plain structure-of-arrays copy.
-__global__ void __launch_bounds__(256) k_soa_ids(const float* X, int64_t n, float* x, float* y, float* z,
-                                                int32_t* ids, uint32_t* flags) {
+// Input order (small clouds): plain copy into the same packed layout.
+__global__ void __launch_bounds__(256) k_pack_rows(const float* X, int64_t n, float4* pts, uint32_t* flags) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     const float a = X[3 * i + 0], b = X[3 * i + 1], c = X[3 * i + 2];
     if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(flags, FLAG_NONFINITE);
-    x[i] = a;
-    y[i] = b;
-    z[i] = c;
-    ids[i] = static_cast<int32_t>(i);
+    pts[i] = make_float4(a, b, c, __int_as_float(static_cast<int32_t>(i)));
 }
 
 // ---------------------------------------------------------------- keys
@@ -167,10 +160,7 @@ __device__ __forceinline__ float warp_max_f(float v) {
 
 struct FpsArgs {
     const float* X;    // (n, 3) input rows (start point)
-    const float* x;    // points in processing order, structure of arrays
-    const float* y;
-    const float* z;
-    const int32_t* ids;  // original row of each point
+    const float4* pts;  // points in processing order: x, y, z, original row (int bits)
     float* d;          // running minima (global kernel)
     int64_t n;
     int32_t n_landmarks;
@@ -643,11 +633,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_resident(FpsArgs a) {
             const int o = lane + 32 * k;
             const int64_t i = base + o;
             const bool ok = i < a.n;
-            px[k] = ok ? a.x[i] : 0.0f;
-            py[k] = ok ? a.y[i] : 0.0f;
-            pz[k] = ok ? a.z[i] : 0.0f;
+            const float4 v = ok ? a.pts[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            px[k] = v.x;
+            py[k] = v.y;
+            pz[k] = v.z;
             pd[k] = ok ? inf : -1.0f;  // padding never wins
-            s_ids[wo + o] = ok ? a.ids[i] : 0;
+            s_ids[wo + o] = __float_as_int(v.w);
             if (ok) {
                 lox = fminf(lox, px[k]);
                 loy = fminf(loy, py[k]);
@@ -740,10 +731,11 @@ __device__ __forceinline__ void update_chunk(const FpsArgs& a, const FpsShared& 
         for (int k = 0; k < kGlobalBatch; ++k) {
             const int64_t i = base + lane + 32 * (q + k);
             if (i < a.n) {
-                x[k] = __ldg(a.x + i);
-                y[k] = __ldg(a.y + i);
-                z[k] = __ldg(a.z + i);
-                id[k] = __ldg(a.ids + i);
+                const float4 v = __ldg(a.pts + i);
+                x[k] = v.x;
+                y[k] = v.y;
+                z[k] = v.z;
+                id[k] = __float_as_int(v.w);
                 d[k] = a.d[i];
             }
         }
@@ -810,7 +802,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fps_global(FpsArgs a) {
         for (int q = 0; q < a.lane_pts; ++q) {
             const int64_t i = base + lane + 32 * q;
             if (i < a.n) {
-                const float x = a.x[i], y = a.y[i], z = a.z[i];
+                const float4 v = a.pts[i];
+                const float x = v.x, y = v.y, z = v.z;
                 lox = fminf(lox, x);
                 loy = fminf(loy, y);
                 loz = fminf(loz, z);
@@ -986,10 +979,10 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
     if (rc) return rc;
     uint32_t* ctl;  // [0] flags, [1..6] ordered box
     uint64_t* slots;
-    float *x, *y, *z, *d = nullptr;
-    int32_t* ids;
+    float4* pts;
+    float* d = nullptr;
     if ((rc = al.alloc(&ctl, 8)) || (rc = al.alloc(&slots, 2 * kMaxBlocks * kSlotStride)) ||
-        (rc = al.alloc(&x, n)) || (rc = al.alloc(&y, n)) || (rc = al.alloc(&z, n)) || (rc = al.alloc(&ids, n)))
+        (rc = al.alloc(&pts, n)))
         return rc;
     if (!plan.resident && (rc = al.alloc(&d, n))) return rc;
     *flags_out = ctl;
@@ -999,7 +992,7 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
     note_launch();
     const unsigned grid = static_cast<unsigned>(ceil_div(n, 256));
     if (n <= kSortMin) {
-        k_soa_ids<<<grid, 256, 0, s>>>(X, n, x, y, z, ids, ctl);
+        k_pack_rows<<<grid, 256, 0, s>>>(X, n, pts, ctl);
         note_launch();
     } else {
         const int bits = morton_bits(n);
@@ -1013,11 +1006,11 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
         note_launch(2);
         FLOOD_CUDA(cudaGetLastError());
         if ((rc = exclusive_scan(count, cstart, codes, s, al))) return rc;
-        k_morton_scatter<<<grid, 256, 0, s>>>(X, n, code, cstart, count, x, y, z, ids);
+        k_morton_scatter<<<grid, 256, 0, s>>>(X, n, code, cstart, count, pts);
         note_launch();
     }
     FLOOD_CUDA(cudaGetLastError());
-    FpsArgs a{X, x, y, z, ids, d, n, n_landmarks, start, out_idx, out_key, slots, ctl, 0, 0, 0};
+    FpsArgs a{X, pts, d, n, n_landmarks, start, out_idx, out_key, slots, ctl, 0, 0, 0};
     return launch_fps_kernel(plan, a, s);
 }
 
