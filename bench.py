@@ -36,8 +36,8 @@ FLOPS_PER_PAIR = 6               # one pair = 3 FMAs: |x'|^2 - 2 p'.x'
 # DRAM bytes (read + write) of one k_fps_resident launch on torus-1M, from one
 # ncu capture (profiles/k_fps_resident_torus-1M.md), valid only while the FPS
 # source is the one captured: reported as null once fps.cu changes.
-FPS_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 16_086_016 + 12_544,
-                    "fps_cu_sha256": "9c1552ec4032ba53a550e0ed6d87c19e5dae93972b8b6232f9cbd55f26da203b"}
+FPS_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 16_084_736 + 10_752,
+                    "fps_cu_sha256": "f7d7282ff41ccb5c33e4f7c3cae06bcc10b9f14969de5dd912944eeb780dcb36"}
 
 
 def _fps_traffic(workload: str):
