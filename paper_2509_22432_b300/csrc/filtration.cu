@@ -784,17 +784,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
 constexpr int kHeavyTile = 4096;
 constexpr int kHeavyShells = 8;  // class threshold: groups with >= this many shells are heavy
 
-// Evaluate the NSL used sample slots of one tile (NSL <= kHeavyNS).
+// Evaluate the NSL used sample slots of one tile (NSL <= kHeavyNS); slots are
+// paired for packed FMAs (the same three rounded FMAs per pair, in order).
 template <int NSL>
-__device__ __forceinline__ void heavy_tile(const float4* buf, int n, int gs, int G, const float* ax, const float* ay,
-                                           const float* az, float* mn) {
+__device__ __forceinline__ void heavy_tile(const float4* buf, int n, int gs, int G, const float2* ax,
+                                           const float2* ay, const float2* az, float* mn) {
 #pragma unroll 2
     for (int j = gs; j < n; j += G) {
         const float4 x = buf[j];
+        if (NSL == 1) {
+            const float t = __fmaf_rn(ax[0].x, x.x, __fmaf_rn(ay[0].x, x.y, __fmaf_rn(az[0].x, x.z, x.w)));
+            mn[0] = fminf(mn[0], t);
+        } else {
+            const float2 xx = make_float2(x.x, x.x), xy = make_float2(x.y, x.y), xz = make_float2(x.z, x.z),
+                         xw = make_float2(x.w, x.w);
 #pragma unroll
-        for (int q = 0; q < NSL; ++q) {
-            const float t = __fmaf_rn(ax[q], x.x, __fmaf_rn(ay[q], x.y, __fmaf_rn(az[q], x.z, x.w)));
-            mn[q] = fminf(mn[q], t);
+            for (int q = 0; q < NSL / 2; ++q) {
+                const float2 t = __ffma2_rn(ax[q], xx, __ffma2_rn(ay[q], xy, __ffma2_rn(az[q], xz, xw)));
+                mn[2 * q] = fminf(mn[2 * q], t.x);
+                mn[2 * q + 1] = fminf(mn[2 * q + 1], t.y);
+            }
         }
     }
 }
@@ -842,7 +851,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         const int G = kThreads / W;
         const int gs = tid / W, lw = tid % W;
         const int nsl = (n_valid + W - 1) / W;  // sample slots in use per thread
-        float ax[kHeavyNS], ay[kHeavyNS], az[kHeavyNS], pp[kHeavyNS], mn[kHeavyNS];
+        static_assert(kHeavyNS % 2 == 0, "slots are evaluated in pairs");
+        float2 ax[kHeavyNS / 2], ay[kHeavyNS / 2], az[kHeavyNS / 2];  // -2 p' per slot, paired
+        float pp[kHeavyNS], mn[kHeavyNS];
         bool val[kHeavyNS];
         // the group's records, once, into shared memory
         if (tid < kGroup) {
@@ -886,14 +897,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         for (int q = 0; q < kHeavyNS; ++q) {
             const int32_t i = s_begin + q * W + lw;
             val[q] = i < s_end;
-            ax[q] = ay[q] = az[q] = pp[q] = 0.0f;
+            float* const qx = (q & 1) ? &ax[q >> 1].y : &ax[q >> 1].x;
+            float* const qy = (q & 1) ? &ay[q >> 1].y : &ay[q >> 1].x;
+            float* const qz = (q & 1) ? &az[q >> 1].y : &az[q >> 1].x;
+            *qx = *qy = *qz = pp[q] = 0.0f;
             mn[q] = INFINITY;
             if (val[q]) {
                 const int li = i - s_begin;
                 const float px = __fsub_rn(s_x[li], ox), py = __fsub_rn(s_y[li], oy), pz = __fsub_rn(s_z[li], oz);
-                ax[q] = -2.0f * px;
-                ay[q] = -2.0f * py;
-                az[q] = -2.0f * pz;
+                *qx = -2.0f * px;
+                *qy = -2.0f * py;
+                *qz = -2.0f * pz;
                 pp[q] = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
             }
         }
