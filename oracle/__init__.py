@@ -6,6 +6,8 @@ obviously correct numpy/scipy code that follows the paper's definitions:
   fps.py          farthest point sampling (§3.2, greedy k-centre), FP32 keys
   samples.py      barycentric grid P_sigma of Lemma 1 (§4.1)
   flood.py        f_P(sigma) = max_{p in P_sigma} min_{x in X} |p - x| (§4.1)
+  random_flood.py the same for given point sets P_sigma (random draws, Lemma 4):
+                  maximum over every face's set, faces enumerated explicitly
   grad.py         analytic subgradient of sum_sigma gamma_sigma f(sigma), central FD
   persistence.py  Z/2 boundary-matrix reduction, diagrams, bottleneck distance (§2)
 
@@ -21,10 +23,12 @@ from .fps import fps, fps_key
 from .samples import compositions, interior_compositions, full_grid_count, interior_count, sample_points
 from .flood import flood_values, nearest_distance, FloodResult
 from .grad import analytic_gradient, finite_difference
+from .random_flood import flood_values_random, analytic_gradient_random, total_random, RandomFloodResult
 from .persistence import diagrams, bottleneck
 
 __all__ = [
     "fps", "fps_key", "compositions", "interior_compositions", "full_grid_count",
     "interior_count", "sample_points", "flood_values", "nearest_distance", "FloodResult",
     "analytic_gradient", "finite_difference", "diagrams", "bottleneck",
+    "flood_values_random", "analytic_gradient_random", "total_random", "RandomFloodResult",
 ]

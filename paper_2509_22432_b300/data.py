@@ -15,6 +15,7 @@ Workloads:
   shape_mix_cloud   union of 8 random surfaces in [-4,4]^3 (5M)
   swisscheese_cloud uniform in [0,5]^3 minus disjoint balls (§5.3 synthetic data)
   serving_sizes     log-uniform cloud sizes for the batched serving workload
+  random_barycentric  uniform random barycentric coordinates (random P_sigma)
 """
 from __future__ import annotations
 
@@ -29,6 +30,7 @@ __all__ = [
     "poisson_arrivals",
     "jitter",
     "upstream_gradients",
+    "random_barycentric",
 ]
 
 
@@ -203,3 +205,12 @@ def upstream_gradients(sizes, seed: int = 5) -> list:
     """gamma ~ N(0,1) float32 per simplex, one array per dimension."""
     rng = _rng(seed + 17)
     return [_f32(rng.standard_normal(int(s))) for s in sizes]
+
+
+def random_barycentric(n_simplices: int, n_samples: int, k: int, seed: int = 7) -> np.ndarray:
+    """(n_simplices, n_samples, k+1) float32 barycentric coordinates, uniform on
+    the k-simplex and independent per simplex (the random P_sigma of §4.1 and
+    Lemma 4): normalised unit exponentials, i.e. a flat Dirichlet draw."""
+    rng = _rng(seed + 1009 * (k + 1))
+    e = rng.exponential(1.0, (int(n_simplices), int(n_samples), k + 1))
+    return _f32(e / e.sum(axis=2, keepdims=True))
