@@ -53,6 +53,7 @@ typedef enum flood_status {
 
 #define FLOOD_MAX_DIM 3      /* simplices of dimension 0..3 (ambient dimension 3) */
 #define FLOOD_MAX_M 64       /* largest supported grid resolution m */
+#define FLOOD_MAX_GIVEN_SAMPLES 65536 /* largest per-simplex set of flood_filtration_given */
 
 /* ------------------------------------------------------------------------
  * flood_fps — farthest point sampling (§3.2: greedy k-centre, a factor-2
@@ -226,6 +227,46 @@ typedef struct flood_filtration_job {
 } flood_filtration_job;
 
 int flood_filtration_batch(const flood_filtration_job* jobs, int32_t n_jobs, void* stream);
+/* ------------------------------------------------------------------------
+ * flood_filtration_given — flood values for caller-given point sets P_sigma.
+ *
+ * §4.1 allows any finite P_sigma ⊂ conv(sigma) (Theorem 2 bounds the
+ * diagram error by the sets' Hausdorff distance to the simplices); one named
+ * choice is a uniform random draw per simplex, whose Hausdorff distance
+ * Lemma 4 bounds. The discretised complex Flood_r(X, L, P) takes sigma once
+ * P_tau ⊂ X_r for every face tau of sigma, so
+ *
+ *     f(sigma) = max( max_{p in P_sigma} d(p, X),  max_{facets tau} f(tau) ),
+ *
+ * with f(v) = d(v, X) = 0 for a vertex (P_v = {v}, L ⊂ X required). The same
+ * kernels as flood_filtration compute it, with the same exact pruning.
+ *
+ *   grid, L, simplices, facets, n_simplices, values, src
+ *                as flood_filtration (src[k][i] = (dim << 28 | row, s): the
+ *                attaining point is sample s of that simplex's set)
+ *   weights[k]   device float32 (n_simplices[k], n_samples[k], k+1), k >= 1:
+ *                barycentric coordinates (lambda_0..lambda_k) of each point
+ *                of each simplex's own set, relative to its ascending vertex
+ *                ids. The point is p = v_0 + sum_{j>=1} lambda_j (v_j - v_0);
+ *                lambda_0 is not read (it is 1 - sum_{j>=1} lambda_j). Points
+ *                should lie in conv(sigma) (lambda_j >= 0, sum <= 1) for the
+ *                paper's guarantees; the values are computed as defined
+ *                either way. weights[0] is ignored.
+ *   n_samples[k] points per simplex of dimension k, 0..FLOOD_MAX_GIVEN_SAMPLES,
+ *                with n_simplices[k] * n_samples[k] < 2^31; 0 leaves only the
+ *                faces' maximum. n_samples[0] is ignored.
+ * With lambda_j = fl32(c_j / m) for the interior compositions c of m in
+ * lexicographic order, the results (values and src) are bit for bit those of
+ * flood_filtration with that m.
+ * Errors: as flood_filtration; FLOOD_EINVAL also for a NULL weights[k] that
+ * is needed, n_samples out of range, or a non-finite lambda_j (j >= 1).
+ * Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------ */
+int flood_filtration_given(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                           const int32_t* const simplices[4], const int32_t* const facets[4],
+                           const int64_t n_simplices[4], const float* const weights[4],
+                           const int32_t n_samples[4], float* const values[4], int32_t* const src[4],
+                           void* stream);
 
 /* Work counters of the calling thread's last successful flood_filtration(_batch). */
 typedef struct flood_filtration_stats {
@@ -265,6 +306,23 @@ int flood_filtration_backward(const flood_grid* grid, const float* L, int32_t n_
                               int32_t m, const int32_t* const src[4],
                               const float* const grad_values[4],
                               float* grad_X, float* grad_L, void* stream);
+/* ------------------------------------------------------------------------
+ * flood_filtration_given_backward — flood_filtration_backward for the values
+ * of flood_filtration_given.
+ *
+ * The attaining point p* = v_0 + sum_{j>=1} lambda_j (v_j - v_0) comes from
+ * the set named by src; its derivative moves v_j (j >= 1) with weight
+ * lambda_j and v_0 with weight 1 - sum_{j>=1} lambda_j:
+ *     grad_X[x*] += g (x* - p*) / f,   grad_L[v_j] += g lambda_j (p* - x*) / f.
+ *   weights, n_samples   as passed to flood_filtration_given
+ *   other arguments      as flood_filtration_backward (no m)
+ * Errors: FLOOD_EINVAL, FLOOD_ENOMEM, FLOOD_ECUDA. Synchronises `stream`.
+ * ------------------------------------------------------------------------ */
+int flood_filtration_given_backward(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                                    const int32_t* const simplices[4], const int64_t n_simplices[4],
+                                    const float* const weights[4], const int32_t n_samples[4],
+                                    const int32_t* const src[4], const float* const grad_values[4],
+                                    float* grad_X, float* grad_L, void* stream);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of many point clouds on one GPU.

@@ -44,6 +44,7 @@ class FiltrationStats(C.Structure):
 
 P4 = C.c_void_p * 4
 I64x4 = C.c_int64 * 4
+I32x4 = C.c_int32 * 4
 
 
 class FiltrationJob(C.Structure):
@@ -104,6 +105,10 @@ _SIGNATURES = {
     "flood_grid_destroy": (None, [C.c_void_p]),
     "flood_filtration": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, P4, I64x4, C.c_int32, P4, P4,
                                    C.c_void_p]),
+    "flood_filtration_given": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, P4, I64x4, P4, I32x4, P4, P4,
+                                         C.c_void_p]),
+    "flood_filtration_given_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, P4, I32x4, P4,
+                                                  P4, C.c_void_p, C.c_void_p, C.c_void_p]),
     "flood_last_filtration_stats": (C.c_int, [C.POINTER(FiltrationStats)]),
     "flood_filtration_batch": (C.c_int, [C.POINTER(FiltrationJob), C.c_int32, C.c_void_p]),
     "flood_filtration_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, C.c_int32, P4, P4,

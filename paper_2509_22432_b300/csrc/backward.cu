@@ -1,8 +1,9 @@
 // flood_filtration_backward: gradient of F = sum_sigma g_sigma f(sigma).
 //
 // Our derivation from the value definition of §4.1: f(sigma) = |p* - x*| with
-// p* = sum_j lambda_j v_j the attaining grid sample of the attaining simplex
-// tau (recorded by flood_filtration as src) and x* its nearest point of X.
+// p* = sum_j lambda_j v_j the attaining sample of the attaining simplex tau
+// (recorded by the forward call as src; a grid sample of Lemma 1, or a point
+// of a given set for flood_filtration_given) and x* its nearest point of X.
 // One warp per simplex recomputes p* with the forward arithmetic, finds x*
 // among the points of the cells within u_{p*} = min_j |p* - v_j| of p* (a
 // bound on d(p*, X) because v_j ∈ X), ties to the lowest row of X, and
@@ -23,7 +24,8 @@ struct BwdArgs {
     const int32_t* src;      // (n, 2)
     const int32_t* simp[4];  // simplices of every dimension (vertex rows)
     int64_t n_simp[4];
-    const uint8_t* comp[4];  // interior composition tables
+    const uint8_t* comp[4];  // interior composition tables (grid samples)
+    const float* w[4];       // given sets: barycentric coordinates (n_k, I[k], k+1)
     int I[4];
     float m;
     const float* L;
@@ -56,9 +58,16 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
         }
     Simplex S;
     load_simplex(a.L, ids, dim, S);
-    const uint8_t* comp = a.comp[dim] + sample * (dim + 1);
+    const uint8_t* comp = nullptr;
+    const float* lam_w = nullptr;
     float px, py, pz;
-    sample_offset(S, comp, dim, a.m, px, py, pz);
+    if (a.w[dim]) {
+        lam_w = a.w[dim] + (tau * a.I[dim] + sample) * (dim + 1);
+        sample_offset_lambda(S, lam_w, dim, px, py, pz);
+    } else {
+        comp = a.comp[dim] + sample * (dim + 1);
+        sample_offset(S, comp, dim, a.m, px, py, pz);
+    }
     const float u = __fsqrt_ru(vertex_bound_sq(S, dim, px, py, pz));
     const float off[3] = {px, py, pz};
     const CellBox b = cull_box(a.g, S.v0, off, off, u);
@@ -110,7 +119,17 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
         atomicAdd(&a.grad_X[3 * int64_t(xi) + 2], scale * bz);
     }
     if (lane <= dim) {
-        const float lam = __fdiv_rn(static_cast<float>(comp[lane]), a.m);
+        float lam;
+        if (lam_w) {  // d p / d v_0 = 1 - sum_{j>=1} lambda_j, d p / d v_j = lambda_j
+            lam = lam_w[lane];
+            if (lane == 0) {
+                float t = 0.0f;
+                for (int j = 1; j <= dim; ++j) t += lam_w[j];
+                lam = 1.0f - t;
+            }
+        } else {
+            lam = __fdiv_rn(static_cast<float>(comp[lane]), a.m);
+        }
         const int32_t v = ids[lane];
         atomicAdd(&a.grad_L[3 * v + 0], -scale * lam * bx);
         atomicAdd(&a.grad_L[3 * v + 1], -scale * lam * by);
@@ -124,12 +143,15 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
 
 using namespace flood;
 
-extern "C" int flood_filtration_backward(const flood_grid* grid, const float* L, int32_t n_landmarks,
-                                         const int32_t* const simplices[4], const int64_t n_simplices[4], int32_t m,
-                                         const int32_t* const src[4], const float* const grad_values[4],
-                                         float* grad_X, float* grad_L, void* stream_) {
+namespace {
+
+// Grid samples (weights == nullptr, resolution m) or given sets.
+int backward_impl(const flood_grid* grid, const float* L, int32_t n_landmarks, const int32_t* const simplices[4],
+                  const int64_t n_simplices[4], int32_t m, const float* const weights[4],
+                  const int32_t n_samples[4], const int32_t* const src[4], const float* const grad_values[4],
+                  float* grad_X, float* grad_L, void* stream_) {
     if (!grid || !L || n_landmarks < 1 || !simplices || !n_simplices || !src || !grad_values || !grad_X ||
-        !grad_L || m < 1 || m > FLOOD_MAX_M) {
+        !grad_L || m < 1 || m > FLOOD_MAX_M || (weights && !n_samples)) {
         set_error("flood_filtration_backward: NULL argument or m out of range");
         return FLOOD_EINVAL;
     }
@@ -156,6 +178,15 @@ extern "C" int flood_filtration_backward(const flood_grid* grid, const float* L,
             set_error("flood_filtration_backward: simplices[%d] is NULL", k);
             return FLOOD_EINVAL;
         }
+        if (weights) {
+            a.I[k] = n_samples[k];
+            a.w[k] = weights[k];
+            if (a.I[k] < 0 || a.I[k] > FLOOD_MAX_GIVEN_SAMPLES || (a.I[k] > 0 && !a.w[k])) {
+                set_error("flood_filtration_given_backward: weights[%d] / n_samples[%d] invalid", k, k);
+                return FLOOD_EINVAL;
+            }
+            continue;
+        }
         tables[k] = interior_table(m, k);
         a.I[k] = static_cast<int>(tables[k].size() / (k + 1));
         if (a.I[k] > 0 && (rc = device_interior_table(m, k, tables[k], &a.comp[k]))) return rc;
@@ -174,4 +205,27 @@ extern "C" int flood_filtration_backward(const flood_grid* grid, const float* L,
         FLOOD_CUDA(cudaGetLastError());
     }
     return finish(s, flags, "flood_filtration_backward");
+}
+
+}  // namespace
+
+extern "C" int flood_filtration_backward(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                                         const int32_t* const simplices[4], const int64_t n_simplices[4], int32_t m,
+                                         const int32_t* const src[4], const float* const grad_values[4],
+                                         float* grad_X, float* grad_L, void* stream) {
+    return backward_impl(grid, L, n_landmarks, simplices, n_simplices, m, nullptr, nullptr, src, grad_values,
+                         grad_X, grad_L, stream);
+}
+
+extern "C" int flood_filtration_given_backward(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                                               const int32_t* const simplices[4], const int64_t n_simplices[4],
+                                               const float* const weights[4], const int32_t n_samples[4],
+                                               const int32_t* const src[4], const float* const grad_values[4],
+                                               float* grad_X, float* grad_L, void* stream) {
+    if (!weights || !n_samples) {
+        set_error("flood_filtration_given_backward: weights and n_samples must be given");
+        return FLOOD_EINVAL;
+    }
+    return backward_impl(grid, L, n_landmarks, simplices, n_simplices, 1, weights, n_samples, src, grad_values,
+                         grad_X, grad_L, stream);
 }

@@ -27,7 +27,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 int status_from_flags(uint32_t flags, const char* where) {
     if (flags == 0) return FLOOD_OK;
     if (flags & FLAG_NONFINITE) {
-        set_error("%s: input coordinates contain NaN or Inf", where);
+        set_error("%s: input coordinates or sample weights contain NaN or Inf", where);
         return FLOOD_EINVAL;
     }
     if (flags & FLAG_RANGE) {

@@ -97,7 +97,8 @@ struct DimArgs {
     const int32_t* facets;   // k >= 2
     const float* val_lower;  // final values of dimension k-1
     int64_t n_lower;
-    const uint8_t* comp;
+    const uint8_t* comp;     // grid samples: interior compositions (I, k+1), or
+    const float* w;          // given samples: barycentric coordinates (n, I, k+1)
     const float* L;
     int32_t n_L;
     GridView g;
@@ -202,7 +203,18 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
     int n_active = 0;
     for (int s = lane; s < a.I; s += 32) {
         float px, py, pz;
-        sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
+        if (a.w) {
+            const float* lam = a.w + (w * a.I + s) * (k + 1);
+            bool fin = true;
+            for (int j = 1; j <= k; ++j) fin &= isfinite(lam[j]);
+            if (!fin) {
+                if (!SCATTER) atomicOr(&a.ctl->flags, FLAG_NONFINITE);
+                continue;
+            }
+            sample_offset_lambda(S, lam, k, px, py, pz);
+        } else {
+            sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
+        }
         const float u2 = vertex_bound_sq(S, k, px, py, pz);
         if (!(__fsqrt_rn(u2) > lb)) continue;  // cannot exceed the facet maximum
         ++n_active;
@@ -1317,6 +1329,7 @@ struct JobState {
     int64_t n_coarse, n_buckets, max_samples, max_n, max_groups;
     std::vector<uint8_t> tables[4];
     const uint8_t* comp[4];
+    const float* w[4];
     int32_t *bcount, *bstart, *bfill, *goff, *cls;
     int2 *groups, *groups_sorted;
     SampleRec* recs;
@@ -1350,13 +1363,44 @@ int check_job(const flood_filtration_job& j, int idx) {
     return FLOOD_OK;
 }
 
-int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s) {
+// Caller-given sample sets of one job (random P_sigma): per dimension k >= 1,
+// S[k] points per simplex as barycentric coordinates (n_k, S[k], k+1).
+struct GivenSets {
+    const float* w[4];
+    int32_t S[4];
+};
+
+int check_given(const flood_filtration_job& j, const GivenSets& g) {
+    for (int k = 1; k <= 3; ++k) {
+        if (g.S[k] < 0 || g.S[k] > FLOOD_MAX_GIVEN_SAMPLES) {
+            set_error("flood_filtration_given: n_samples[%d] must be in [0, %d]", k, FLOOD_MAX_GIVEN_SAMPLES);
+            return FLOOD_EINVAL;
+        }
+        if (j.n_simplices[k] > 0 && g.S[k] > 0) {
+            if (!g.w[k]) {
+                set_error("flood_filtration_given: weights[%d] is NULL", k);
+                return FLOOD_EINVAL;
+            }
+            if (j.n_simplices[k] * g.S[k] >= (int64_t(1) << 31)) {
+                set_error("flood_filtration_given: n_simplices[%d] * n_samples[%d] must be below 2^31", k, k);
+                return FLOOD_EINVAL;
+            }
+        }
+    }
+    return FLOOD_OK;
+}
+
+int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
+                     const GivenSets* given = nullptr) {
     if (n_jobs < 0 || (n_jobs > 0 && !in)) {
         set_error("flood_filtration_batch: bad job array");
         return FLOOD_EINVAL;
     }
-    for (int i = 0; i < n_jobs; ++i)
+    for (int i = 0; i < n_jobs; ++i) {
         if (int rc = check_job(in[i], i)) return rc;
+        if (given)
+            if (int rc = check_given(in[i], given[i])) return rc;
+    }
     Scratch scr(s);
     Ctl* ctl;
     int rc;
@@ -1385,13 +1429,19 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s)
         for (int k = 1; k <= 3; ++k) {
             J.I[k] = 0;
             J.comp[k] = nullptr;
+            J.w[k] = nullptr;
             if (J.nk[k] == 0) continue;
-            J.tables[k] = interior_table(J.in.m, k);
-            J.I[k] = static_cast<int>(J.tables[k].size() / (k + 1));
+            if (given) {
+                J.I[k] = given[i].S[k];
+                J.w[k] = given[i].w[k];
+            } else {
+                J.tables[k] = interior_table(J.in.m, k);
+                J.I[k] = static_cast<int>(J.tables[k].size() / (k + 1));
+            }
             J.max_samples = std::max(J.max_samples, J.nk[k] * J.I[k]);
             J.max_n = std::max(J.max_n, J.nk[k]);
             total_samples += J.nk[k] * J.I[k];
-            if (J.I[k] > 0 && (rc = device_interior_table(J.in.m, k, J.tables[k], &J.comp[k]))) return rc;
+            if (!given && J.I[k] > 0 && (rc = device_interior_table(J.in.m, k, J.tables[k], &J.comp[k]))) return rc;
         }
         J.lat = make_lattice(grid, total_samples);
         J.n_coarse = int64_t(J.lat.bx) * J.lat.by * J.lat.bz;
@@ -1439,6 +1489,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s)
             a.val_lower = J.val[k - 1];
             a.n_lower = J.nk[k - 1];
             a.comp = J.comp[k];
+            a.w = J.w[k];
             a.L = J.in.L;
             a.n_L = J.in.n_landmarks;
             a.g = view_of(grid);
@@ -1575,4 +1626,31 @@ extern "C" int flood_filtration(const flood_grid* grid, const float* L, int32_t 
         j.src[k] = src ? src[k] : nullptr;
     }
     return filtration_batch(&j, 1, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int flood_filtration_given(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                                      const int32_t* const simplices[4], const int32_t* const facets[4],
+                                      const int64_t n_simplices[4], const float* const weights[4],
+                                      const int32_t n_samples[4], float* const values[4], int32_t* const src[4],
+                                      void* stream) {
+    if (!simplices || !n_simplices || !values || !weights || !n_samples) {
+        set_error("flood_filtration_given: simplices, n_simplices, weights, n_samples and values must be given");
+        return FLOOD_EINVAL;
+    }
+    flood_filtration_job j{};
+    GivenSets g{};
+    j.grid = grid;
+    j.L = L;
+    j.n_landmarks = n_landmarks;
+    j.m = 1;  // unused: the samples are given
+    for (int k = 0; k < 4; ++k) {
+        j.simplices[k] = simplices[k];
+        j.facets[k] = facets ? facets[k] : nullptr;
+        j.n_simplices[k] = n_simplices[k];
+        j.values[k] = values[k];
+        j.src[k] = src ? src[k] : nullptr;
+        g.w[k] = k ? weights[k] : nullptr;
+        g.S[k] = k ? n_samples[k] : 0;
+    }
+    return filtration_batch(&j, 1, static_cast<cudaStream_t>(stream), &g);
 }

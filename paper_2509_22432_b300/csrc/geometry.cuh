@@ -137,6 +137,25 @@ __device__ __forceinline__ void sample_offset(const Simplex& s, const uint8_t* c
     }
 }
 
+// Offset p' = sum_{j>=1} lambda_j e_j of a sample given by its barycentric
+// coordinates (lambda_0 is implied: p = v0 + p'). With lambda_j = fl(c_j/m)
+// this is bit for bit the grid sample of sample_offset.
+__device__ __forceinline__ void sample_offset_lambda(const Simplex& s, const float* lam, int k, float& px,
+                                                     float& py, float& pz) {
+    px = 0.0f;
+    py = 0.0f;
+    pz = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < k) {
+            const float w = lam[j + 1];
+            px = __fmaf_rn(w, s.e[j][0], px);
+            py = __fmaf_rn(w, s.e[j][1], py);
+            pz = __fmaf_rn(w, s.e[j][2], pz);
+        }
+    }
+}
+
 // Squared distance from a sample offset to the nearest vertex of the simplex:
 // u_p^2 = min_j |p - v_j|^2, an upper bound of d(p, X)^2 because v_j ∈ X.
 __device__ __forceinline__ float vertex_bound_sq(const Simplex& s, int k, float px, float py, float pz) {

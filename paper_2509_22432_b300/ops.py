@@ -14,11 +14,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import FloodError, P4, I64x4
+from ._lib import FloodError, P4, I64x4, I32x4
 
 __all__ = ["fps", "fps_noalloc", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
-           "filtration_batch", "filtration_backward",
-           "last_filtration_stats", "FloodFunction", "flood_values"]
+           "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
+           "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given"]
 
 
 def _stream_ptr(device: torch.device) -> C.c_void_p:
@@ -245,4 +245,94 @@ class FloodFunction(torch.autograd.Function):
 def flood_values(X: torch.Tensor, L: torch.Tensor, grid: Grid, cx: DeviceComplex, m: int):
     """Differentiable flood values split per dimension."""
     out = FloodFunction.apply(X, L, grid, cx, m)
+    return list(torch.split(out, cx.counts))
+
+
+def _weights(weights, cx: DeviceComplex, device):
+    """Check given sets: weights[k] float32 CUDA (n_k, S_k, k+1) for k >= 1 (weights[0] unused)."""
+    ws, ptrs, counts = [None], [C.c_void_p(0)], [0]
+    for k in range(1, 4):
+        n_k = cx.counts[k] if k < len(cx.counts) else 0
+        w = weights[k] if k < len(weights) else None
+        if w is None:
+            if n_k:
+                raise ValueError(f"weights[{k}] is required for {n_k} simplices")
+            ws.append(None)
+            ptrs.append(C.c_void_p(0))
+            counts.append(0)
+            continue
+        if not isinstance(w, torch.Tensor) or not w.is_cuda or w.device != device or w.dtype != torch.float32:
+            raise ValueError(f"weights[{k}] must be a float32 CUDA tensor on {device}")
+        if w.dim() != 3 or w.shape[0] != n_k or w.shape[2] != k + 1:
+            raise ValueError(f"weights[{k}] must have shape ({n_k}, S, {k + 1})")
+        w = w.contiguous()
+        ws.append(w)
+        ptrs.append(_ptr(w) if w.numel() else C.c_void_p(0))
+        counts.append(int(w.shape[1]))
+    return ws, P4(*ptrs), I32x4(*counts)
+
+
+def filtration_given(grid: Grid, L: torch.Tensor, cx: DeviceComplex, weights, want_src: bool = True):
+    """Flood values for given point sets P_sigma (§4.1; random draws, Lemma 4).
+
+    weights[k]: float32 CUDA (n_k, S_k, k+1) barycentric coordinates of each
+    simplex's own points (lambda_0 implied). Returns (values[k], src[k] or None).
+    """
+    L = _points(L, "L")
+    ws, wp, ns = _weights(weights, cx, L.device)
+    s, f, n = cx.arrays()
+    vals = [torch.empty(c, dtype=torch.float32, device=L.device) for c in cx.counts]
+    srcs = [torch.empty((c, 2), dtype=torch.int32, device=L.device) for c in cx.counts] if want_src else None
+    vp = P4(*[_ptr(v) if v.numel() else C.c_void_p(0) for v in vals] + [C.c_void_p(0)] * (4 - len(vals)))
+    sp = P4(*([_ptr(t) if t.numel() else C.c_void_p(0) for t in srcs] + [C.c_void_p(0)] * (4 - len(srcs)))
+            if want_src else [C.c_void_p(0)] * 4)
+    with torch.cuda.device(L.device):
+        st = _lib.get().flood_filtration_given(grid.handle, _ptr(L), L.shape[0], s, f, n, wp, ns, vp, sp,
+                                               _stream_ptr(L.device))
+    _lib.check(st, "flood_filtration_given")
+    return vals, srcs
+
+
+def filtration_given_backward(grid: Grid, L: torch.Tensor, cx: DeviceComplex, weights, src, grads,
+                              n_points: int):
+    """(grad_X, grad_L) of sum_sigma grads[k][sigma] * f(sigma) for filtration_given's values."""
+    L = _points(L, "L")
+    ws, wp, ns = _weights(weights, cx, L.device)
+    s, _, n = cx.arrays()
+    gX = torch.zeros((n_points, 3), dtype=torch.float32, device=L.device)
+    gL = torch.zeros_like(L)
+    srcp = P4(*[_ptr(t) if t is not None and t.numel() else C.c_void_p(0) for t in src] +
+              [C.c_void_p(0)] * (4 - len(src)))
+    gs = [None if g is None else g.to(torch.float32).contiguous() for g in grads]
+    gp = P4(*[_ptr(g) if g is not None and g.numel() else C.c_void_p(0) for g in gs] +
+            [C.c_void_p(0)] * (4 - len(gs)))
+    with torch.cuda.device(L.device):
+        st = _lib.get().flood_filtration_given_backward(grid.handle, _ptr(L), L.shape[0], s, n, wp, ns, srcp, gp,
+                                                        _ptr(gX), _ptr(gL), _stream_ptr(L.device))
+    _lib.check(st, "flood_filtration_given_backward")
+    return gX, gL
+
+
+class GivenFloodFunction(torch.autograd.Function):
+    """Differentiable flood values over given point sets: forward(X, L, grid, cx, weights)."""
+
+    @staticmethod
+    def forward(ctx, X, L, grid, cx, weights):
+        vals, srcs = filtration_given(grid, L, cx, weights, want_src=True)
+        ctx.grid, ctx.cx, ctx.weights, ctx.srcs, ctx.n_points = grid, cx, weights, srcs, X.shape[0]
+        ctx.counts = cx.counts
+        ctx.save_for_backward(L)
+        return torch.cat(vals)
+
+    @staticmethod
+    def backward(ctx, g):
+        (L,) = ctx.saved_tensors
+        parts = list(torch.split(g.contiguous(), ctx.counts))
+        gX, gL = filtration_given_backward(ctx.grid, L, ctx.cx, ctx.weights, ctx.srcs, parts, ctx.n_points)
+        return gX, gL, None, None, None
+
+
+def flood_values_given(X: torch.Tensor, L: torch.Tensor, grid: Grid, cx: DeviceComplex, weights):
+    """Differentiable flood values over given point sets, split per dimension."""
+    out = GivenFloodFunction.apply(X, L, grid, cx, weights)
     return list(torch.split(out, cx.counts))
