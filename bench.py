@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -262,7 +263,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2509_22432_b300 import delaunay_complex, ops
+    from paper_2509_22432_b300 import data, delaunay_complex, ops
 
     if args.serving:
         if rank == 0:
@@ -369,6 +370,31 @@ def main():
             e2e_times.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e_times))
 
+    # ---- the same step with uniform random point sets P_sigma (§4.1, Lemma 4)
+    # in place of the grid: as many points per simplex as the grid's interior
+    # samples at this m, drawn independently per simplex.
+    S_rand = [math.comb(m - 1, k) for k in (1, 2, 3)]
+    w_rand = [None] + [torch.from_numpy(data.random_barycentric(cx.counts[k], S_rand[k - 1], k, seed=7)).to(dev)
+                       for k in (1, 2, 3)]
+    rs_times, rs_filt, rs_flood = [], [], []
+    for it in range(args.warmup + min(args.steps, 10)):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        idx, key = ops.fps(Xd, n_l, 0)
+        grid = ops.build_grid(Xd, cell)
+        e[1].record(stream)
+        vals, _ = ops.filtration_given(grid, Xd[idx], dcx, w_rand, want_src=False)
+        e[2].record(stream)
+        e[2].synchronize()
+        grid.close()
+        if it >= args.warmup:
+            rs_times.append(e[0].elapsed_time(e[2]))
+            rs_filt.append(e[1].elapsed_time(e[2]))
+            rs_flood.append(sum(ops.last_filtration_stats()["flood_kernel_ms"]))
+    rs_stats = ops.last_filtration_stats()
+    del w_rand
+
     peaks, peak_kind = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
@@ -432,6 +458,20 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
     }
+    rs_ms, _ = aggregate(float(np.mean(rs_times)), float(n_simp), dev)
+    rs_pairs = sum(rs_stats["pairs"])
+    rs_fk = float(np.mean(rs_flood))
+    rs_tflops = rs_pairs * FLOPS_PER_PAIR / (rs_fk * 1e-3) / 1e12
+    line["random_sets"] = {
+        "metric": "flood simplices/s", "value": world * n_simp / (rs_ms * 1e-3), "unit": "simplices/s",
+        "ms_per_step": rs_ms, "steps": len(rs_times),
+        "points_per_simplex": S_rand, "draw": "uniform on each simplex, independent per simplex (seed 7)",
+        "nn_queries_per_s": world * sum(rs_stats["samples"][1:]) / (rs_ms * 1e-3),
+        "phase_ms": {"fps_and_grid": float(np.mean(rs_times)) - float(np.mean(rs_filt)),
+                     "filtration": float(np.mean(rs_filt)), "flood_kernels": rs_fk},
+        "pairs_per_step": rs_pairs,
+        "roofline_flood": {"bound": "alu", "achieved": rs_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                           "frac": rs_tflops / peak_tflops}}
     if rank == 0 and not args.no_serving:
         clouds = serving_clouds(128)
         b = run_serving(clouds, 500.0, True)
