@@ -283,6 +283,37 @@ typedef struct flood_filtration_stats {
 int flood_last_filtration_stats(flood_filtration_stats* out);
 
 /* ------------------------------------------------------------------------
+ * flood_complex_faces — faces of Del(L) and facet incidence, on the device.
+ *
+ * The discretised complex of §4.1 admits a simplex only after all of its
+ * faces, so the filtration needs every face of the triangulation (§4) and,
+ * per simplex, the rows of its facets. Given the tetrahedra, this writes the
+ * distinct triangles (faces of the tetrahedra) and edges (faces of the
+ * triangles) and the facet columns, in the layout flood_filtration reads:
+ * facets[k][i][j] is the row in the (k-1)-simplices of simplex i without its
+ * vertex j. Row order: a face's row follows the first (parent row, j) that
+ * produces it (j = the dropped vertex), which is deterministic; it is not
+ * lexicographic. Vertex ids ascend within every row.
+ *
+ *   tets             device int32 (n_tets, 4): ascending vertex ids in
+ *                    [0, n_vertices); also simplices[3] of the complex
+ *   n_tets           0..2^24
+ *   n_vertices       1..2^21 - 1 (n_landmarks)
+ *   triangles        device int32 capacity (4 n_tets, 3): rows [0, *n_triangles)
+ *   edges            device int32 capacity (6 n_tets, 2): rows [0, *n_edges)
+ *   tet_facets       device int32 (n_tets, 4): facets[3]
+ *   triangle_facets  device int32 capacity (4 n_tets, 3): facets[2]
+ *   edge_facets      device int32 capacity (6 n_tets, 2) or NULL: facets[1]
+ *                    (the other vertex: (b, a) for edge (a, b))
+ *   n_triangles, n_edges   host outputs: the counts
+ * Every triangle and edge of the input is produced, each exactly once.
+ * Errors: FLOOD_EINVAL (sizes, NULL outputs, a row not ascending or out of
+ * range), FLOOD_ENOMEM, FLOOD_ECUDA. Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------ */
+int flood_complex_faces(const int32_t* tets, int64_t n_tets, int32_t n_vertices, int32_t* triangles,
+                        int32_t* edges, int32_t* tet_facets, int32_t* triangle_facets, int32_t* edge_facets,
+                        int64_t* n_triangles, int64_t* n_edges, void* stream);
+/* ------------------------------------------------------------------------
  * flood_filtration_backward — gradient of F = sum_sigma g_sigma f(sigma).
  *
  * Our derivation from the value definition of §4.1: with p* = sum_j

@@ -10,6 +10,7 @@ obviously correct numpy/scipy code that follows the paper's definitions:
                   maximum over every face's set, faces enumerated explicitly
   grad.py         analytic subgradient of sum_sigma gamma_sigma f(sigma), central FD
   persistence.py  Z/2 boundary-matrix reduction, diagrams, bottleneck distance (§2)
+  faces.py        faces and facet incidence of a set of tetrahedra, by definition
 
 Only tests, the smoke check and the CPU-baseline leg of the benchmark may
 import it. It shares no code with the CUDA path and imports nothing from the
@@ -25,10 +26,12 @@ from .flood import flood_values, nearest_distance, FloodResult
 from .grad import analytic_gradient, finite_difference
 from .random_flood import flood_values_random, analytic_gradient_random, total_random, RandomFloodResult
 from .persistence import diagrams, bottleneck
+from .faces import faces_by_definition, facet_rows
 
 __all__ = [
     "fps", "fps_key", "compositions", "interior_compositions", "full_grid_count",
     "interior_count", "sample_points", "flood_values", "nearest_distance", "FloodResult",
     "analytic_gradient", "finite_difference", "diagrams", "bottleneck",
     "flood_values_random", "analytic_gradient_random", "total_random", "RandomFloodResult",
+    "faces_by_definition", "facet_rows",
 ]

@@ -109,6 +109,9 @@ _SIGNATURES = {
                                          C.c_void_p]),
     "flood_filtration_given_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, P4, I32x4, P4,
                                                   P4, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flood_complex_faces": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.c_void_p]),
     "flood_last_filtration_stats": (C.c_int, [C.POINTER(FiltrationStats)]),
     "flood_filtration_batch": (C.c_int, [C.POINTER(FiltrationJob), C.c_int32, C.c_void_p]),
     "flood_filtration_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, C.c_int32, P4, P4,

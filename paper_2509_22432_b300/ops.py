@@ -18,6 +18,7 @@ from ._lib import FloodError, P4, I64x4, I32x4
 
 __all__ = ["fps", "fps_noalloc", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
            "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
+           "complex_faces",
            "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given"]
 
 
@@ -137,6 +138,32 @@ def to_device(cx, device) -> DeviceComplex:
     sims = [torch.from_numpy(np.ascontiguousarray(s, dtype=np.int32)).to(device) for s in cx.simplices]
     facs = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.int32)).to(device) for f in cx.facets]
     return DeviceComplex(int(cx.n_vertices), sims, facs)
+
+
+def complex_faces(tets: torch.Tensor, n_vertices: int) -> DeviceComplex:
+    """Faces and facet incidence of the tetrahedra on the device (flood_complex_faces).
+
+    tets: int32 CUDA (n, 4) with ascending vertex ids. Rows of the lower
+    dimensions follow their first producing (parent, j), not lexicographic order.
+    """
+    if not isinstance(tets, torch.Tensor) or not tets.is_cuda or tets.dtype != torch.int32 or tets.dim() != 2 \
+            or tets.shape[1] != 4:
+        raise ValueError("tets must be an int32 CUDA tensor of shape (n, 4)")
+    tets = tets.contiguous()
+    dev, n3 = tets.device, tets.shape[0]
+    tri = torch.empty((4 * n3, 3), dtype=torch.int32, device=dev)
+    edg = torch.empty((6 * n3, 2), dtype=torch.int32, device=dev)
+    f3 = torch.empty((n3, 4), dtype=torch.int32, device=dev)
+    f2 = torch.empty((4 * n3, 3), dtype=torch.int32, device=dev)
+    f1 = torch.empty((6 * n3, 2), dtype=torch.int32, device=dev)
+    n2, n1 = C.c_int64(0), C.c_int64(0)
+    with torch.cuda.device(dev):
+        st = _lib.get().flood_complex_faces(_ptr(tets), n3, int(n_vertices), _ptr(tri), _ptr(edg), _ptr(f3),
+                                            _ptr(f2), _ptr(f1), C.byref(n2), C.byref(n1), _stream_ptr(dev))
+    _lib.check(st, "flood_complex_faces")
+    verts = torch.arange(int(n_vertices), dtype=torch.int32, device=dev)[:, None]
+    return DeviceComplex(int(n_vertices), [verts, edg[:n1.value], tri[:n2.value], tets],
+                         [torch.zeros_like(verts), f1[:n1.value], f2[:n2.value], f3])
 
 
 def filtration(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, want_src: bool = True):

@@ -450,3 +450,31 @@ def test_analytic_gradient_matches_central_differences():
     ok = ~kink
     assert ok.sum() >= 40
     assert np.allclose(fd[ok], an[ok], rtol=1e-3, atol=1e-5)
+
+
+# ----------------------------------------------------------------------------- faces
+
+def test_faces_of_one_and_two_tetrahedra():
+    tri, edg = oracle.faces_by_definition([[0, 1, 2, 3]])
+    assert tri.shape == (4, 3) and edg.shape == (6, 2)
+    tri, edg = oracle.faces_by_definition([[0, 1, 2, 3], [1, 2, 3, 4]])   # sharing triangle 123
+    assert tri.shape == (7, 3) and edg.shape == (9, 2)
+    f = oracle.facet_rows(np.array([[0, 1, 2, 3]]), tri)
+    assert [tuple(tri[r]) for r in f[0]] == [(1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)]
+
+
+def test_faces_of_a_delaunay_ball():
+    """Del of generic points is a triangulated 3-ball: Euler characteristic 1, and the
+    triangles used by one tetrahedron are exactly Qhull's convex hull facets."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(7)
+    P = rng.standard_normal((300, 3))
+    d = Delaunay(P)
+    tets = np.sort(d.simplices, axis=1)
+    tri, edg = oracle.faces_by_definition(tets)
+    assert P.shape[0] - edg.shape[0] + tri.shape[0] - tets.shape[0] == 1
+    use = np.bincount(oracle.facet_rows(tets, tri).ravel(), minlength=tri.shape[0])
+    assert set(np.unique(use)) <= {1, 2}
+    hull = {tuple(sorted(r)) for r in d.convex_hull.tolist()}
+    assert {tuple(r) for r in tri[use == 1].tolist()} == hull
+    assert 4 * tets.shape[0] == 2 * np.count_nonzero(use == 2) + len(hull)
