@@ -193,19 +193,20 @@ def serving_clouds(n_clouds: int, seed: int = 4):
     return [data.shape_mix_cloud(int(n), seed=4000 + i) for i, n in enumerate(sizes)]
 
 
-def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4) -> dict:
+def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, device_faces: bool = False) -> dict:
     """Submit the clouds at Poisson arrival times; return clouds/s and latency percentiles.
 
     batched: the continuous-batching server; otherwise the plain path, one
     cloud at a time through the same kernels (one slot, one worker, batch 1).
     Latency = arrival -> values on the host, host Delaunay included.
+    device_faces: the host hands over tetrahedra only; faces are built on the device.
     """
     from paper_2509_22432_b300 import data
     from paper_2509_22432_b300.serve import Server
     arrivals = data.poisson_arrivals(len(clouds), rate, seed=seed)
     kw = (dict(max_inflight=64, max_batch=64, gpu_workers=4, triangulation_workers=8) if batched else
           dict(max_inflight=1, max_batch=1, gpu_workers=1, triangulation_workers=1))
-    with Server(device_budget_bytes=32 << 30, **kw) as srv:
+    with Server(device_budget_bytes=32 << 30, device_faces=device_faces, **kw) as srv:
         t0 = time.perf_counter()
         tickets = []
         for X, t in zip(clouds, arrivals):
@@ -458,6 +459,19 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
     }
+    # ---- faces and facet incidence of the workload's tetrahedra: device vs host builder
+    from paper_2509_22432_b300.complex import complex_from_simplices
+    tets_h = np.ascontiguousarray(cx.simplices[3], dtype=np.int32)
+    tets_d = torch.from_numpy(tets_h).to(dev)
+    fc_dev = []
+    for it in range(args.warmup + min(args.steps, 10)):
+        t0 = time.perf_counter()
+        ops.complex_faces(tets_d, n_l)                 # synchronises its stream
+        if it >= args.warmup:
+            fc_dev.append(1e3 * (time.perf_counter() - t0))
+    t0 = time.perf_counter()
+    complex_from_simplices([tets_h], n_l, top_dim=3)
+    fc_host = 1e3 * (time.perf_counter() - t0)
     rs_ms, _ = aggregate(float(np.mean(rs_times)), float(n_simp), dev)
     rs_pairs = sum(rs_stats["pairs"])
     rs_fk = float(np.mean(rs_flood))
@@ -472,13 +486,18 @@ def main():
         "pairs_per_step": rs_pairs,
         "roofline_flood": {"bound": "alu", "achieved": rs_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                            "frac": rs_tflops / peak_tflops}}
+    line["complex_faces"] = {"tetrahedra": int(cx.counts[3]), "device_ms": float(np.median(fc_dev)),
+                             "host_ms": fc_host, "what": "triangles, edges and facet incidence from the "
+                             "tetrahedra: flood_complex_faces (call to return, synchronised) vs the host "
+                             "numpy builder"}
     if rank == 0 and not args.no_serving:
         clouds = serving_clouds(128)
         b = run_serving(clouds, 500.0, True)
+        bd = run_serving(clouds, 500.0, True, device_faces=True)
         p = run_serving(clouds, 500.0, False)
         line["serving"] = {"workload": "128 clouds, 2k-200k points (log-uniform), shape mix, Poisson 500/s, "
                                        "n_L = 2% of points, m = 8, host Delaunay included",
-                           "batched": b, "per_cloud": p}
+                           "batched": b, "batched_device_faces": bd, "per_cloud": p}
     if rank == 0 and not args.no_cpu_baseline:
         res = cpu_baseline(X, wl)
         step_s = res["t_fps_s"] + res["t_build_s"] + res["per_simplex_s"] * n_simp

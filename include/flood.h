@@ -381,7 +381,11 @@ typedef struct flood_host_complex {
 } flood_host_complex;
 
 /* Triangulate the landmarks (host, (n, 3) float32). Returns 0 on success;
- * any other value fails that request only. Called from library threads. */
+ * any other value fails that request only. Called from library threads.
+ * The callback may fill only the tetrahedra (n_simplices[1] = n_simplices[2]
+ * = 0, facets ignored); the library then builds the triangles, edges and
+ * facet incidence on the device (flood_complex_faces) and reports the rows
+ * it built in flood_result.simplices. */
 typedef int (*flood_triangulate_fn)(void* user, const float* landmarks, int32_t n_landmarks,
                                     flood_host_complex* out);
 typedef void (*flood_release_fn)(void* user, void* owner);
@@ -406,6 +410,8 @@ typedef struct flood_result {
     const float* values[4];         /* host, owned by the server until flood_serve_release */
     const int64_t* landmarks;       /* host, n_landmarks rows of X (FPS order) */
     double latency_ms;              /* submit -> values on the host */
+    const int32_t* simplices[4];    /* host (n_k, k+1), k >= 1: the rows values[k] refer to
+                                       (the callback's, or the device-built faces); [0] NULL */
 } flood_result;
 
 typedef struct flood_serve_stats_t {

@@ -73,7 +73,7 @@ class ServeConfig(C.Structure):
 class ServeResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_landmarks", C.c_int32), ("n_simplices", C.c_int64 * 4),
                 ("values", C.POINTER(C.c_float) * 4), ("landmarks", C.POINTER(C.c_int64)),
-                ("latency_ms", C.c_double)]
+                ("latency_ms", C.c_double), ("simplices", C.POINTER(C.c_int32) * 4)]
 
 
 class ServeStats(C.Structure):

@@ -8,6 +8,9 @@
 //              grid build on its own stream (these overlap across requests).
 //   host       a triangulation worker calls the user's callback on the
 //              landmarks (Del(L) is input to the method, computed on the host).
+//              A callback may return the tetrahedra alone; the worker then
+//              builds the triangles, edges and facet incidence on the device
+//              (flood_complex_faces) on its own stream.
 //   flood      one flood thread takes every request that is ready (up to
 //              max_batch) and runs them through a single batched filtration
 //              (one persistent flood launch per dimension over all of them),
@@ -210,8 +213,38 @@ void gpu_worker(flood_server* s) {
     if (st) cudaStreamDestroy(st);
 }
 
+// Faces of a tetrahedra-only complex on the device; the host copies of the
+// edges and triangles go into the result (their row order is the device's).
+int device_faces(Request* r, cudaStream_t st) {
+    const int64_t n3 = r->nk[3];
+    if (dev_alloc(&r->simp_dev[3], n3 * 4, st) || dev_alloc(&r->simp_dev[2], 4 * n3 * 3, st) ||
+        dev_alloc(&r->simp_dev[1], 6 * n3 * 2, st) || dev_alloc(&r->fac_dev[3], n3 * 4, st) ||
+        dev_alloc(&r->fac_dev[2], 4 * n3 * 3, st))
+        return FLOOD_ENOMEM;
+    if (cudaMemcpyAsync(r->simp_dev[3], r->simp[3].data(), sizeof(int32_t) * n3 * 4, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return FLOOD_ECUDA;
+    int64_t n2 = 0, n1 = 0;
+    int rc = flood_complex_faces(r->simp_dev[3], n3, r->n_L, r->simp_dev[2], r->simp_dev[1], r->fac_dev[3],
+                                 r->fac_dev[2], nullptr, &n2, &n1, st);
+    if (rc) return rc;
+    r->nk[2] = n2;
+    r->nk[1] = n1;
+    r->simp[2].resize(static_cast<size_t>(n2 * 3));
+    r->simp[1].resize(static_cast<size_t>(n1 * 2));
+    if (cudaMemcpyAsync(r->simp[2].data(), r->simp_dev[2], sizeof(int32_t) * n2 * 3, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(r->simp[1].data(), r->simp_dev[1], sizeof(int32_t) * n1 * 2, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return FLOOD_ECUDA;
+    return FLOOD_OK;
+}
+
 void tri_worker(flood_server* s) {
     cudaSetDevice(s->device);
+    cudaStream_t fst = nullptr;  // this worker's stream for device face builds
+    if (cudaStreamCreateWithFlags(&fst, cudaStreamNonBlocking) != cudaSuccess) fst = nullptr;
     for (;;) {
         Request* r;
         {
@@ -224,17 +257,19 @@ void tri_worker(flood_server* s) {
         flood_host_complex hc;
         std::memset(&hc, 0, sizeof(hc));
         int rc = s->cfg.triangulate(s->cfg.user, r->L.data(), r->n_L, &hc);
+        // tetrahedra alone: the faces are built on the device below
+        const bool tets_only = rc == 0 && hc.n_simplices[3] > 0 && hc.n_simplices[1] == 0 && hc.n_simplices[2] == 0;
         if (rc == 0) {
             for (int k = 0; k < 4; ++k) {
                 r->nk[k] = hc.n_simplices[k];
                 if (r->nk[k] < 0 || (k >= 1 && r->nk[k] > 0 && !hc.simplices[k]) ||
-                    (k >= 2 && r->nk[k] > 0 && !hc.facets[k])) {
+                    (k >= 2 && r->nk[k] > 0 && !tets_only && !hc.facets[k])) {
                     rc = FLOOD_EINVAL;
                     break;
                 }
                 if (k >= 1 && r->nk[k] > 0) {
                     r->simp[k].assign(hc.simplices[k], hc.simplices[k] + r->nk[k] * (k + 1));
-                    if (k >= 2) r->fac[k].assign(hc.facets[k], hc.facets[k] + r->nk[k] * (k + 1));
+                    if (k >= 2 && !tets_only) r->fac[k].assign(hc.facets[k], hc.facets[k] + r->nk[k] * (k + 1));
                 }
             }
             if (rc == 0 && r->nk[0] != 0 && r->nk[0] != r->n_L) rc = FLOOD_EINVAL;
@@ -242,6 +277,7 @@ void tri_worker(flood_server* s) {
             rc = FLOOD_EINVAL;
         }
         if (s->cfg.release && hc.owner) s->cfg.release(s->cfg.user, hc.owner);
+        if (rc == 0 && tets_only) rc = fst ? device_faces(r, fst) : FLOOD_ECUDA;
         if (rc) {
             cudaStream_t st = nullptr;
             if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
@@ -253,6 +289,7 @@ void tri_worker(flood_server* s) {
         s->ready.push_back(r);
         s->cv_flood.notify_one();
     }
+    if (fst) cudaStreamDestroy(fst);
 }
 
 // Upload the complexes of a batch, run the batched filtration and copy values back.
@@ -421,6 +458,7 @@ extern "C" int flood_serve_poll(flood_server* s, uint64_t ticket, int32_t timeou
     for (int k = 0; k < 4; ++k) {
         out->n_simplices[k] = k == 0 ? r->n_L : r->nk[k];
         out->values[k] = r->values[k].empty() ? nullptr : r->values[k].data();
+        out->simplices[k] = (k == 0 || r->simp[k].empty()) ? nullptr : r->simp[k].data();
     }
     out->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
     return FLOOD_OK;

@@ -21,6 +21,12 @@ from .complex import delaunay_complex
 __all__ = ["Server"]
 
 
+def _delaunay_tets(L: np.ndarray) -> np.ndarray:
+    """Tetrahedra of Del(L) (scipy/Qhull), ascending vertex ids, int32."""
+    from scipy.spatial import Delaunay
+    return np.ascontiguousarray(np.sort(Delaunay(np.asarray(L, np.float64)).simplices, axis=1), dtype=np.int32)
+
+
 def _lib_serve():
     return _lib.get()
 
@@ -30,13 +36,19 @@ class Server:
 
     triangulate(L) -> SimplexLists (default: scipy Delaunay of the landmarks).
     max_batch = 1 gives the plain one-cloud-at-a-time path.
+    device_faces = True: the callback hands over the tetrahedra of the scipy
+    Delaunay triangulation only, and the library builds the triangles, edges
+    and facet incidence on the device; results then list the rows it built.
     """
 
     def __init__(self, device_budget_bytes: int = 16 << 30, max_inflight: int = 64, max_batch: int = 32,
                  gpu_workers: int = 4, triangulation_workers: int = 4, landmark_fraction: float = 0.02,
-                 cell_factor: float = 0.5, triangulate=None):
+                 cell_factor: float = 0.5, triangulate=None, device_faces: bool = False):
         self._lib = _lib_serve()
+        if device_faces and triangulate is not None:
+            raise ValueError("device_faces uses the built-in tetrahedralisation; pass no triangulate")
         self._fn = triangulate or delaunay_complex
+        self._device_faces = bool(device_faces)
         self._keep = {}
         self._next = 1
         self._lock = threading.Lock()
@@ -53,9 +65,22 @@ class Server:
     def _triangulate(self, user, L_ptr, n, out):
         try:
             L = np.ctypeslib.as_array(L_ptr, shape=(int(n) * 3,)).reshape(int(n), 3).copy()
-            cx = self._fn(L)
             arrays = []
             o = out.contents
+            if self._device_faces:
+                tets = _delaunay_tets(L)
+                arrays.append(tets)
+                for k in range(3):
+                    o.n_simplices[k] = 0
+                o.n_simplices[3] = tets.shape[0]
+                o.simplices[3] = tets.ctypes.data if tets.size else None
+                with self._lock:
+                    key = self._next
+                    self._next += 1
+                    self._keep[key] = arrays
+                o.owner = key
+                return 0
+            cx = self._fn(L)
             for k in range(4):
                 if k < len(cx.simplices):
                     s = np.ascontiguousarray(cx.simplices[k], dtype=np.int32)
@@ -92,13 +117,18 @@ class Server:
         """Wait for a result; returns values per dimension, landmark rows, latency, status."""
         r = ServeResult()
         _lib.check(self._lib.flood_serve_poll(self._h, int(ticket), int(timeout_ms), C.byref(r)), "flood_serve_poll")
-        out = {"status": int(r.status), "latency_ms": float(r.latency_ms), "values": [], "landmarks": None}
+        out = {"status": int(r.status), "latency_ms": float(r.latency_ms), "values": [], "landmarks": None,
+               "simplices": [None]}
         if r.status == 0:
             out["landmarks"] = np.ctypeslib.as_array(r.landmarks, shape=(r.n_landmarks,)).copy()
             for k in range(4):
                 n = int(r.n_simplices[k])
                 out["values"].append(np.ctypeslib.as_array(r.values[k], shape=(n,)).copy() if n else
                                      np.zeros(0, np.float32))
+                if k >= 1:
+                    out["simplices"].append(
+                        np.ctypeslib.as_array(r.simplices[k], shape=(n, k + 1)).copy() if n and r.simplices[k]
+                        else np.zeros((0, k + 1), np.int32))
         return out
 
     def release(self, ticket: int) -> None:

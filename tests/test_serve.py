@@ -54,6 +54,32 @@ def test_batched_server_results_equal_one_cloud_path():
 
 
 @pytest.mark.gpu
+def test_device_faces_server_equals_one_cloud_path_per_simplex():
+    """Tetrahedra-only callbacks: faces built on the device; each simplex's value is
+    bit for bit the one-cloud path's (rows matched by their vertex ids)."""
+    from paper_2509_22432_b300.serve import Server
+    clouds = _clouds(8, seed=9)
+    m = 8
+    with Server(max_inflight=6, max_batch=8, gpu_workers=3, triangulation_workers=3, device_faces=True) as srv:
+        results = [srv.result(t, timeout_ms=120_000) for t in [srv.submit(X, 0, m) for X in clouds]]
+        st = srv.stats()
+    assert st["completed"] == len(clouds) and st["failed"] == 0
+    for X, res in zip(clouds, results):
+        assert res["status"] == 0
+        n_l = max(4, int(round(0.02 * X.shape[0])))
+        idx, vals = _alone(X, n_l, m)
+        assert np.array_equal(res["landmarks"], idx)
+        host = delaunay_complex(X[idx])
+        assert np.array_equal(res["values"][0].view(np.uint32), vals[0].view(np.uint32))
+        for k in (1, 2, 3):
+            rows = res["simplices"][k]
+            assert rows.shape == host.simplices[k].shape, k
+            ref = {tuple(r): v for r, v in zip(host.simplices[k].tolist(), vals[k].view(np.uint32))}
+            got = res["values"][k].view(np.uint32)
+            assert all(ref[tuple(r)] == g for r, g in zip(rows.tolist(), got)), k
+
+
+@pytest.mark.gpu
 def test_failed_triangulation_fails_only_its_request():
     from paper_2509_22432_b300.serve import Server
 
