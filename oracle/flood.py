@@ -13,7 +13,8 @@ P_sigma is the FULL grid, faces included: the discretised complex
 Flood_r(X, L, P) admits sigma only when P_tau is flooded for every face tau of
 sigma (§4.1), and P_tau ⊂ P_sigma, so the full-grid maximum already equals the
 maximum over all faces. For a vertex, P_v = {v} and f(v) = d(v, X) (0 when
-L ⊂ X; §3, after Definition 1).
+L ⊂ X; §3, after Definition 1). L need not be a subset of X (§3): everything
+here is the definition, so it holds for any landmarks.
 
 Nearest distances are taken either by brute force over all of X or with an
 exact FP64 k-d tree (scipy's cKDTree), the paper's own CPU path (App. A.1).

@@ -8,9 +8,10 @@ smooth piece (unique attaining pair, f > 0):
     d f / d x*   = (x* - p*) / f
     d f / d v_j  = lambda_j (p* - x*) / f
 
-and f = 0 contributes a zero subgradient. Vertex values are the constant 0
-(L ⊂ X) and carry no gradient. X and L are independent inputs: moving a
-landmark does not move its copy in X, and vice versa.
+and f = 0 contributes a zero subgradient. A vertex value f(v) = d(v, X) is
+the case p* = v (its grid is the vertex itself): 0 when v is a point of X,
+otherwise |v - x*| with the same two derivatives. X and L are independent
+inputs: moving a landmark does not move its copy in X, and vice versa.
 
 `finite_difference` evaluates (F(theta+h) - F(theta-h)) / 2h for single
 coordinates with the simplex lists held fixed, recomputing only the simplices
@@ -28,9 +29,9 @@ __all__ = ["analytic_gradient", "finite_difference", "total"]
 
 
 def total(result: FloodResult, gamma) -> float:
-    """F = sum over k >= 1 of sum_sigma gamma_sigma f(sigma)."""
+    """F = sum over k >= 0 of sum_sigma gamma_sigma f(sigma) (vertices included)."""
     return float(sum(np.dot(np.asarray(gamma[k], np.float64)[result.simplex_ids[k]], result.values[k])
-                     for k in range(1, len(result.values))))
+                     for k in range(len(result.values))))
 
 
 def analytic_gradient(X, L, simplices, m, gamma, result: FloodResult | None = None,
@@ -42,8 +43,8 @@ def analytic_gradient(X, L, simplices, m, gamma, result: FloodResult | None = No
         result = flood_values(X, L, simplices, m, method=method)
     dX = np.zeros_like(X64)
     dL = np.zeros_like(L64)
-    for k in range(1, len(simplices)):
-        S = np.asarray(simplices[k], dtype=np.int64)[result.simplex_ids[k]]
+    for k in range(len(simplices)):
+        S = np.asarray(simplices[k], dtype=np.int64).reshape(-1, k + 1)[result.simplex_ids[k]]
         if S.shape[0] == 0:
             continue
         g = np.asarray(gamma[k], dtype=np.float64)[result.simplex_ids[k]]
@@ -63,21 +64,22 @@ def analytic_gradient(X, L, simplices, m, gamma, result: FloodResult | None = No
 
 
 class _AllSamples:
-    """Every full-grid sample of every simplex (k >= 1) with its two nearest points of X."""
+    """Every full-grid sample of every simplex (vertices included) with its two nearest points of X."""
 
     def __init__(self, X, L, simplices, m, index: KDIndex):
         self.k_of, self.rows, self.P, self.owner = [], [], [], []
         L64 = np.asarray(L, dtype=np.float64)
+        dv, _ = index.query(L64)                                                     # d(v_j, X)
         self.ranges = {}
         start = 0
         Ps, boxes_lo, boxes_hi, ubs = [], [], [], []
-        for k in range(1, len(simplices)):
-            S = np.asarray(simplices[k], dtype=np.int64)
+        for k in range(len(simplices)):
+            S = np.asarray(simplices[k], dtype=np.int64).reshape(-1, k + 1)
             comps = compositions(m, k)
             V = L64[S]
             P = sample_points(V, comps, m)                                          # (n, F, 3)
-            # u_p = min_j |p - v_j| bounds d(p, X) because every v_j is a point of X.
-            u = np.min(np.linalg.norm(P[:, :, None, :] - V[:, None, :, :], axis=3), axis=2)
+            # u_p = min_j (|p - v_j| + d(v_j, X)) bounds d(p, X) (triangle inequality)
+            u = np.min(np.linalg.norm(P[:, :, None, :] - V[:, None, :, :], axis=3) + dv[S][:, None, :], axis=2)
             self.ranges[k] = (start, S.shape[0], comps.shape[0])
             start += S.shape[0] * comps.shape[0]
             Ps.append(P.reshape(-1, 3))
@@ -116,8 +118,8 @@ def finite_difference(X, L, simplices, m, gamma, probes, h: float = 1e-3,
         plus = minus = 0.0
         changed = False
         if which == "L":
-            for k in range(1, len(simplices)):
-                S = np.asarray(simplices[k], dtype=np.int64)
+            for k in range(len(simplices)):
+                S = np.asarray(simplices[k], dtype=np.int64).reshape(-1, k + 1)
                 sids = np.nonzero((S == row).any(axis=1))[0]
                 if sids.size == 0:
                     continue
@@ -137,8 +139,8 @@ def finite_difference(X, L, simplices, m, gamma, probes, h: float = 1e-3,
                 minus += vals[1]
         else:
             x0 = X64[row]
-            for k in range(1, len(simplices)):
-                lo, hi = A.box_lo[k - 1], A.box_hi[k - 1]
+            for k in range(len(simplices)):
+                lo, hi = A.box_lo[k], A.box_hi[k]
                 near = np.nonzero(np.all((lo - h <= x0) & (x0 <= hi + h), axis=1))[0]
                 if near.size == 0:
                     continue

@@ -138,9 +138,9 @@ def flood_values_random(X, L, simplices, weights, method: str = "brute",
 
 
 def total_random(result: RandomFloodResult, gamma) -> float:
-    """F = sum over k >= 1 of sum_sigma gamma_sigma f_P(sigma)."""
+    """F = sum over k >= 0 of sum_sigma gamma_sigma f_P(sigma) (vertices included)."""
     return float(sum(np.dot(np.asarray(gamma[k], np.float64), result.values[k])
-                     for k in range(1, len(result.values))))
+                     for k in range(len(result.values))))
 
 
 def analytic_gradient_random(X, L, simplices, weights, gamma, result: RandomFloodResult):
@@ -149,21 +149,24 @@ def analytic_gradient_random(X, L, simplices, weights, gamma, result: RandomFloo
     On a smooth piece f_P(sigma) = |p* - x*| with p* = sum_j lambda_j v_j the
     attaining point of the attaining face tau and x* its nearest point of X:
     d f / d x* = (x* - p*) / f and d f / d v_j = lambda_j (p* - x*) / f over
-    tau's vertices (lambda_0 = 1 - sum_{j>=1} lambda_j); f = 0 gives zero.
+    tau's vertices (lambda_0 = 1 - sum_{j>=1} lambda_j); a vertex tau is the
+    point itself (lambda = 1); f = 0 gives zero.
     """
     X64 = np.asarray(X, dtype=np.float64)
     L64 = np.asarray(L, dtype=np.float64)
     dX = np.zeros_like(X64)
     dL = np.zeros_like(L64)
-    for k in range(1, len(simplices)):
+    for k in range(len(result.values)):
         g = np.asarray(gamma[k], dtype=np.float64)
         for r in range(result.values[k].shape[0]):
             dim, row, s = (int(v) for v in result.src[k][r])
-            if dim == 0:
-                continue                             # a vertex attains: f = 0 when L ⊂ X
-            verts = np.asarray(simplices[dim], dtype=np.int64).reshape(-1, dim + 1)[row]
-            lam = lambdas(np.asarray(weights[dim], dtype=np.float64).reshape(
-                np.asarray(simplices[dim]).reshape(-1, dim + 1).shape[0], -1, dim + 1)[row, s])
+            if dim == 0:                             # a vertex attains: p* = v
+                verts = np.array([row])
+                lam = np.ones(1)
+            else:
+                verts = np.asarray(simplices[dim], dtype=np.int64).reshape(-1, dim + 1)[row]
+                lam = lambdas(np.asarray(weights[dim], dtype=np.float64).reshape(
+                    np.asarray(simplices[dim]).reshape(-1, dim + 1).shape[0], -1, dim + 1)[row, s])
             p = lam @ L64[verts]
             xi = int(result.argmin_point[k][r])
             f = float(np.linalg.norm(p - X64[xi]))

@@ -478,3 +478,60 @@ def test_faces_of_a_delaunay_ball():
     hull = {tuple(sorted(r)) for r in d.convex_hull.tolist()}
     assert {tuple(r) for r in tri[use == 1].tolist()} == hull
     assert 4 * tets.shape[0] == 2 * np.count_nonzero(use == 2) + len(hull)
+
+
+# ----------------------------------------------------------------------------- landmarks off X (§3: L need not be in X)
+
+def test_vertex_off_X_is_its_distance():
+    X = np.array([[0.0, 0.0, 0.0], [10.0, 0.0, 0.0]])
+    L = np.array([[3.0, 4.0, 0.0]])
+    r = oracle.flood_values(X, L, [np.zeros((1, 1), np.int64)], m=4)
+    assert abs(r.values[0][0] - 5.0) <= 1e-12
+
+
+@pytest.mark.parametrize("m", [2, 4, 7])
+def test_edge_off_X_attained_at_a_vertex(m):
+    """X = {origin}, edge from (-1,1,0) to (1,1,0): d(p, X) = sqrt(x^2 + 1) peaks at the ends."""
+    X = np.zeros((1, 3))
+    L = np.array([[-1.0, 1.0, 0.0], [1.0, 1.0, 0.0]])
+    r = oracle.flood_values(X, L, [np.arange(2)[:, None], np.array([[0, 1]])], m=m)
+    assert abs(r.values[1][0] - math.sqrt(2.0)) <= 1e-12
+    assert np.allclose(r.values[0], math.sqrt(2.0), rtol=0, atol=1e-12)
+
+
+def test_values_are_1_lipschitz_in_the_landmarks():
+    """Every sample p = sum lambda_j v_j moves by at most max_j |dv_j|, so f moves by at most that."""
+    X = data.torus_cloud(4000, seed=141)
+    idx, _ = oracle.fps(X, 30)
+    rng = np.random.default_rng(142)
+    L = X[idx].astype(np.float64) + rng.uniform(-0.02, 0.02, (30, 3))
+    cx = delaunay_complex(L)
+    delta = 0.01
+    step = rng.standard_normal(L.shape)
+    step *= delta / np.linalg.norm(step, axis=1, keepdims=True)
+    a = oracle.flood_values(X, L, cx.simplices, 5, method="kdtree")
+    b = oracle.flood_values(X, L + step, cx.simplices, 5, method="kdtree")
+    for k in range(4):
+        assert np.max(np.abs(a.values[k] - b.values[k])) <= delta + 1e-12
+    assert np.all(a.values[0] > 0)
+
+
+def test_analytic_gradient_with_landmarks_off_X():
+    X = data.jitter(data.torus_cloud(600, seed=151), amp=1e-6, seed=152).astype(np.float64)
+    idx, _ = oracle.fps(X, 14)
+    rng = np.random.default_rng(153)
+    L = X[idx] + rng.uniform(-0.05, 0.05, (14, 3))
+    cx = delaunay_complex(L)
+    gamma = data.upstream_gradients(cx.counts, seed=154)
+    m = 4
+    res = oracle.flood_values(X, L, cx.simplices, m, method="brute")
+    assert any(np.any(res.argmax_sample[k] >= 0) for k in range(4))
+    dX, dL = oracle.analytic_gradient(X, L, cx.simplices, m, gamma, result=res)
+    nzX = np.argwhere(np.abs(dX) > 0)
+    probes = [("X", int(a), int(b)) for a, b in nzX[rng.choice(len(nzX), 30, replace=False)]]
+    probes += [("L", int(a), int(rng.integers(3))) for a in range(14)]
+    fd, kink, _ = oracle.finite_difference(X, L, cx.simplices, m, gamma, probes, h=1e-6, method="brute")
+    an = np.array([dX[r, c] if w == "X" else dL[r, c] for (w, r, c) in probes])
+    ok = ~kink
+    assert ok.sum() >= 30
+    assert np.allclose(fd[ok], an[ok], rtol=1e-3, atol=1e-5)

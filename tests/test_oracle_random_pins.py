@@ -188,3 +188,36 @@ def test_random_gradient_matches_central_differences():
         assert abs(fd - an) <= 1e-3 * abs(an) + 1e-5, (which, row, col, fd, an)
         n_ok += 1
     assert n_ok >= 30
+
+
+def test_random_sets_with_landmarks_off_X():
+    """Vertices off X: f(v) = d(v, X) > 0 enters every coface; gradient still matches FD."""
+    X = data.jitter(data.torus_cloud(500, seed=161), amp=1e-6, seed=162).astype(np.float64)
+    idx, _ = oracle.fps(X, 12)
+    rng = np.random.default_rng(163)
+    L = X[idx] + rng.uniform(-0.05, 0.05, (12, 3))
+    cx = delaunay_complex(L)
+    w = [None] + [data.random_barycentric(cx.counts[k], 4, k, seed=164) for k in range(1, 4)]
+    gamma = data.upstream_gradients(cx.counts, seed=165)
+    base = oracle.flood_values_random(X, L, cx.simplices, w)
+    d, _ = KDIndex(X, "brute").query(L)
+    assert np.allclose(base.values[0], d, rtol=0, atol=1e-12) and np.all(d > 0)
+    for k in range(1, 4):
+        verts = np.asarray(cx.simplices[k])
+        assert np.all(base.values[k] >= d[verts].max(axis=1))
+    dX, dL = oracle.analytic_gradient_random(X, L, cx.simplices, w, gamma, base)
+    h, n_ok = 1e-6, 0
+    for row in range(12):
+        for col in range(3):
+            F, same = [], True
+            for sgn in (1.0, -1.0):
+                Lp = L.copy()
+                Lp[row, col] += sgn * h
+                r = oracle.flood_values_random(X, Lp, cx.simplices, w)
+                F.append(oracle.total_random(r, gamma))
+                same &= all(np.array_equal(r.src[k], base.src[k]) and
+                            np.array_equal(r.argmin_point[k], base.argmin_point[k]) for k in range(4))
+            if same:
+                assert abs((F[0] - F[1]) / (2 * h) - dL[row, col]) <= 1e-3 * abs(dL[row, col]) + 1e-5
+                n_ok += 1
+    assert n_ok >= 25
