@@ -166,16 +166,18 @@ void flood_grid_destroy(flood_grid* grid);
  * computed as max( own, f(facets) ) with `own` the maximum over the interior
  * samples (all parts c_i >= 1, lambda_i = c_i/m), since P_tau ⊂ P_sigma
  * (App. A.1). Dimensions run in increasing order; a sample whose bound
- * u_p = min_i |p - v_i| (>= d(p, X) because v_i ∈ X, the step behind
- * Lemma 2) does not exceed the facet maximum cannot change the value and is
- * skipped, and the nearest-point search of every other sample stops as soon
- * as it is exact or falls to the facet maximum. Values and attaining samples
- * equal those of the full max-min. Vertices get d(v, X), which is 0 because
- * L ⊂ X is required.
+ * u_p = min_i (|p - v_i| + d(v_i, X)) (>= d(p, X); for v_i ∈ X this is the
+ * step behind Lemma 2) does not exceed the facet maximum cannot change the
+ * value and is skipped, and the nearest-point search of every other sample
+ * stops as soon as it is exact or falls to the facet maximum. Values and
+ * attaining samples equal those of the full max-min. Vertices get d(v, X):
+ * 0 for landmarks that are points of X (the usual case, L = X[FPS picks]);
+ * L need not be a subset of X (§3), at the cost of one exact nearest-point
+ * search per landmark outside X.
  *
  *   grid         from flood_build_grid on X
- *   L            device, (n_landmarks, 3) float32; every row must equal a
- *                row of X bit for bit (L ⊂ X), else FLOOD_EINVAL
+ *   L            device, (n_landmarks, 3) float32, finite; rows equal (bit
+ *                for bit) to rows of X are recognised as points of X
  *   simplices[k] device int32 (n_simplices[k], k+1): ascending vertex ids
  *                (rows of L). simplices[0] may be NULL (vertices = rows of L;
  *                n_simplices[0] must equal n_landmarks or 0).
@@ -193,7 +195,7 @@ void flood_grid_destroy(flood_grid* grid);
  *                (dim, row, sample). Used by flood_filtration_backward.
  * Empty dimensions (n_simplices[k] == 0) are allowed. Results depend only on
  * (simplex, sample, point) arithmetic, so they are bitwise reproducible.
- * Errors: FLOOD_EINVAL (ids out of range, L ⊄ X, m), FLOOD_ENOMEM,
+ * Errors: FLOOD_EINVAL (ids out of range, non-finite L, m), FLOOD_ENOMEM,
  *         FLOOD_ETIMEOUT (bounded shared-memory copy waits), FLOOD_ECUDA.
  * Synchronises `stream` before returning.
  * ------------------------------------------------------------------------ */
@@ -322,11 +324,13 @@ int flood_complex_faces(const int32_t* tets, int64_t n_tets, int32_t n_vertices,
  * of X), f = |p* - x*| and, if f > 0,
  *     grad_X[x*]  += g (x* - p*) / f,
  *     grad_L[v_j] += g lambda_j (p* - x*) / f;
- * f = 0 (vertices, degenerate cases) contributes nothing.
+ * a vertex (its own value, or attaining a coface's) is p* = v, lambda = 1;
+ * f = 0 (vertices that are points of X, degenerate cases) contributes nothing.
  *
  *   grid, L, simplices, n_simplices, m   as passed to flood_filtration
  *   src[k]          device int32 (n_k, 2) from flood_filtration
- *   grad_values[k]  device float32 (n_k) upstream gradients, or NULL (zero)
+ *   grad_values[k]  device float32 (n_k) upstream gradients, or NULL (zero);
+ *                   k = 0 are the vertex values (n_landmarks)
  *   grad_X          device float32 (n_points, 3), accumulated into
  *   grad_L          device float32 (n_landmarks, 3), accumulated into
  * Accumulation uses atomics, so the summation order (last bits) may vary.

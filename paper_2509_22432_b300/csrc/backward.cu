@@ -2,12 +2,13 @@
 //
 // Our derivation from the value definition of §4.1: f(sigma) = |p* - x*| with
 // p* = sum_j lambda_j v_j the attaining sample of the attaining simplex tau
-// (recorded by the forward call as src; a grid sample of Lemma 1, or a point
-// of a given set for flood_filtration_given) and x* its nearest point of X.
+// (recorded by the forward call as src; a grid sample of Lemma 1, a point of
+// a given set for flood_filtration_given, or a vertex itself) and x* its
+// nearest point of X.
 // One warp per simplex recomputes p* with the forward arithmetic, finds x*
-// among the points of the cells within u_{p*} = min_j |p* - v_j| of p* (a
-// bound on d(p*, X) because v_j ∈ X), ties to the lowest row of X, and
-// scatters
+// among the points of the cells within u_{p*} = min_j (|p* - v_j| + d(v_j, X))
+// of p* (a bound on d(p*, X); d(v_j, X) = 0 for landmarks that are points of
+// X), ties to the lowest row of X, and scatters
 //     grad_X[x*]  += g (x* - p*) / f,    grad_L[v_j] += g lambda_j (p* - x*) / f.
 #include <vector>
 
@@ -29,6 +30,7 @@ struct BwdArgs {
     int I[4];
     float m;
     const float* L;
+    const float* vbound;     // per landmark: d(v, X) rounded up, 0 for a point of X
     int32_t n_L;
     GridView g;
     float* grad_X;
@@ -45,30 +47,38 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
     const int32_t s0 = a.src[2 * w], sample = a.src[2 * w + 1];
     const int dim = s0 >> 28;
     const int64_t tau = s0 & ((1 << 28) - 1);
-    if (dim == 0) return;  // a vertex attains: f = 0, zero subgradient
-    if (dim > 3 || tau >= a.n_simp[dim] || sample < 0 || sample >= a.I[dim]) {
+    if (dim > 3 || tau >= a.n_simp[dim] || (dim > 0 && (sample < 0 || sample >= a.I[dim]))) {
         if (lane == 0) atomicOr(a.flags, FLAG_RANGE);
         return;
     }
-    const int32_t* ids = a.simp[dim] + tau * (dim + 1);
-    for (int j = 0; j <= dim; ++j)
+    const int32_t vtx = static_cast<int32_t>(tau);
+    const int32_t* ids = dim == 0 ? &vtx : a.simp[dim] + tau * (dim + 1);
+    float vb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    bool members = true;
+    for (int j = 0; j <= dim; ++j) {
         if (ids[j] < 0 || ids[j] >= a.n_L) {
             if (lane == 0) atomicOr(a.flags, FLAG_RANGE);
             return;
         }
+        vb[j] = a.vbound[ids[j]];
+        members &= vb[j] == 0.0f;
+    }
+    if (dim == 0 && members) return;  // a vertex that is a point of X: f = 0, zero subgradient
     Simplex S;
     load_simplex(a.L, ids, dim, S);
     const uint8_t* comp = nullptr;
     const float* lam_w = nullptr;
-    float px, py, pz;
-    if (a.w[dim]) {
+    float px = 0.0f, py = 0.0f, pz = 0.0f;  // a vertex: p* = v
+    if (dim == 0) {
+    } else if (a.w[dim]) {
         lam_w = a.w[dim] + (tau * a.I[dim] + sample) * (dim + 1);
         sample_offset_lambda(S, lam_w, dim, px, py, pz);
     } else {
         comp = a.comp[dim] + sample * (dim + 1);
         sample_offset(S, comp, dim, a.m, px, py, pz);
     }
-    const float u = __fsqrt_ru(vertex_bound_sq(S, dim, px, py, pz));
+    const float u = members ? __fsqrt_ru(vertex_bound_sq(S, dim, px, py, pz))
+                            : vertex_bound_general(S, dim, px, py, pz, vb);
     const float off[3] = {px, py, pz};
     const CellBox b = cull_box(a.g, S.v0, off, off, u);
     const int rows = b.n[1] * b.n[2];
@@ -120,7 +130,9 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
     }
     if (lane <= dim) {
         float lam;
-        if (lam_w) {  // d p / d v_0 = 1 - sum_{j>=1} lambda_j, d p / d v_j = lambda_j
+        if (dim == 0) {
+            lam = 1.0f;
+        } else if (lam_w) {  // d p / d v_0 = 1 - sum_{j>=1} lambda_j, d p / d v_j = lambda_j
             lam = lam_w[lane];
             if (lane == 0) {
                 float t = 0.0f;
@@ -165,6 +177,15 @@ int backward_impl(const flood_grid* grid, const float* L, int32_t n_landmarks, c
     a.m = static_cast<float>(m);
     a.L = L;
     a.n_L = n_landmarks;
+    // vertex values' bounds d(v, X) (0 for points of X), as in the forward pass
+    float *vval, *vbound;
+    int32_t* vsrc;
+    if ((rc = scr.alloc(&vval, n_landmarks)) || (rc = scr.alloc(&vbound, n_landmarks)) ||
+        (rc = scr.alloc(&vsrc, 2 * int64_t(n_landmarks))))
+        return rc;
+    if ((rc = launch_vertices(L, n_landmarks, grid, vval, vsrc, vbound, flags, s))) return rc;
+    a.vbound = vbound;
+    a.n_simp[0] = n_landmarks;
     a.g = view_of(grid);
     a.grad_X = grad_X;
     a.grad_L = grad_L;
@@ -191,14 +212,15 @@ int backward_impl(const flood_grid* grid, const float* L, int32_t n_landmarks, c
         a.I[k] = static_cast<int>(tables[k].size() / (k + 1));
         if (a.I[k] > 0 && (rc = device_interior_table(m, k, tables[k], &a.comp[k]))) return rc;
     }
-    for (int k = 1; k <= 3; ++k) {
-        if (n_simplices[k] <= 0 || !grad_values[k]) continue;
+    for (int k = 0; k <= 3; ++k) {
+        const int64_t nk = k == 0 ? n_landmarks : n_simplices[k];
+        if (nk <= 0 || !grad_values[k]) continue;
         if (!src[k]) {
             set_error("flood_filtration_backward: src[%d] is NULL", k);
             return FLOOD_EINVAL;
         }
         a.k = k;
-        a.n = n_simplices[k];
+        a.n = nk;
         a.grad = grad_values[k];
         a.src = src[k];
         k_backward<<<static_cast<unsigned>(ceil_div(a.n * 32, 256)), 256, 0, s>>>(a); note_launch();

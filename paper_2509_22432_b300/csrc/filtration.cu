@@ -100,6 +100,7 @@ struct DimArgs {
     const uint8_t* comp;     // grid samples: interior compositions (I, k+1), or
     const float* w;          // given samples: barycentric coordinates (n, I, k+1)
     const float* L;
+    const float* vbound;     // per landmark: d(v, X) rounded up, 0 for a point of X
     int32_t n_L;
     GridView g;
     Lattice lat;
@@ -119,10 +120,13 @@ struct DimArgs {
 };
 
 // ---------------------------------------------------------------- vertices
-// f(v) = d(v, X) = 0 for a landmark that is a point of X; anything else is an
-// input error (the vertex bound relies on L ⊂ X).
-// One warp per landmark: its lanes scan the landmark's cell together.
-__global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, int32_t* src, uint32_t* flags) {
+// f(v) = d(v, X) (P_v = {v}): 0 for a landmark that is a point of X, found in
+// its own cell; otherwise the exact nearest point by doubling cull boxes (§3
+// allows L ⊄ X). vbound[v] = d(v, X) rounded up with a margin (exactly 0 for a
+// point of X) bounds the samples of every coface from above.
+// One warp per landmark: its lanes scan the cells together.
+__global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, int32_t* src, float* vbound,
+                           uint32_t* flags) {
     const int v = static_cast<int>((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (v >= n_L) return;
@@ -147,9 +151,23 @@ __global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, 
             }
         }
     }
+    const bool finite = isfinite(x) && isfinite(y) && isfinite(z);
+    float f = 0.0f, bound = 0.0f;
+    if (finite && !found) {
+        const unsigned long long nn = warp_nearest(g, x, y, z, g.cell, lane);
+        if (nn == ~0ull) {
+            if (lane == 0) atomicOr(flags, FLAG_INTERNAL);
+            f = bound = __int_as_float(0x7fc00000);
+        } else {
+            const float d2 = __uint_as_float(static_cast<uint32_t>(nn >> 32));
+            f = __fsqrt_rn(d2);
+            bound = __fmul_ru(__fsqrt_ru(d2), 1.0f + 1.0f / 65536.0f);
+        }
+    }
     if (lane == 0) {
-        if (!found) atomicOr(flags, FLAG_NOT_SUBSET);
-        val[v] = found ? 0.0f : __int_as_float(0x7fc00000);
+        if (!finite) atomicOr(flags, FLAG_NONFINITE);
+        val[v] = finite ? f : __int_as_float(0x7fc00000);
+        vbound[v] = finite ? bound : __int_as_float(0x7fc00000);
         src[2 * v] = v;
         src[2 * v + 1] = 0;
     }
@@ -186,13 +204,15 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
     const int32_t* ids = a.simplices + w * (k + 1);
     bool ok = true;
     for (int j = 0; j <= k; ++j) ok &= (ids[j] >= 0 && ids[j] < a.n_L);
-    float lb = 0.0f;  // facet maximum (vertices of an edge have value 0)
+    float lb = 0.0f;  // facet maximum (an edge's facets are its vertices)
     if (k >= 2) {
         for (int j = 0; j <= k; ++j) {
             const int32_t t = a.facets[w * (k + 1) + j];
             if (t < 0 || t >= a.n_lower) ok = false;
             else lb = fmaxf(lb, a.val_lower[t]);
         }
+    } else if (ok) {
+        lb = fmaxf(a.val_lower[ids[0]], a.val_lower[ids[1]]);
     }
     if (!ok) {
         if (!SCATTER && lane == 0) atomicOr(&a.ctl->flags, FLAG_RANGE);
@@ -200,6 +220,13 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
     }
     Simplex S;
     load_simplex(a.L, ids, k, S);
+    // vertices that are points of X keep the plain vertex bound min_j |p - v_j|
+    float vb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    bool members = true;
+    for (int j = 0; j <= k; ++j) {
+        vb[j] = a.vbound[ids[j]];
+        members &= vb[j] == 0.0f;
+    }
     int n_active = 0;
     for (int s = lane; s < a.I; s += 32) {
         float px, py, pz;
@@ -215,8 +242,15 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
         } else {
             sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
         }
-        const float u2 = vertex_bound_sq(S, k, px, py, pz);
-        if (!(__fsqrt_rn(u2) > lb)) continue;  // cannot exceed the facet maximum
+        float u;
+        if (members) {
+            const float u2 = vertex_bound_sq(S, k, px, py, pz);
+            if (!(__fsqrt_rn(u2) > lb)) continue;  // cannot exceed the facet maximum
+            u = __fsqrt_ru(u2);
+        } else {
+            u = vertex_bound_general(S, k, px, py, pz, vb);
+            if (!(u > lb)) continue;
+        }
         ++n_active;
         const float x = __fadd_rn(S.v0[0], px), y = __fadd_rn(S.v0[1], py), z = __fadd_rn(S.v0[2], pz);
         const int64_t b = sample_key(a.lat, x, y, z);
@@ -231,7 +265,7 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
             r.lb = lb;
             r.sigma = static_cast<int32_t>(w);
             r.s = s;
-            r.u = __fsqrt_ru(u2);
+            r.u = u;
             r.pad = 0;
             a.recs[pos] = r;
         }
@@ -923,13 +957,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
                 pp[q] = __fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)));
             }
         }
-        // Every landmark is a point of X, so the distance to the nearest one is
-        // also an upper bound of d(p, X), usually far tighter than the simplex's
-        // own vertices for samples in empty space; it narrows the search radius.
+        // A landmark that is a point of X gives, by its distance, another
+        // upper bound of d(p, X), usually far tighter than the simplex's own
+        // vertices for samples in empty space; it narrows the search radius.
         // (landmarks farther than R from the samples' box cannot tighten any
         // bound and are skipped; skipping a landmark only loosens a bound)
         const float R2 = R * R;
         for (int l = tid; l < a.n_L; l += kThreads) {
+            if (a.vbound[l] != 0.0f) continue;  // not a point of X: no bound from it
             const float lx = a.L[3 * l], ly = a.L[3 * l + 1], lz = a.L[3 * l + 2];
             const float gx = fmaxf(fmaxf(wlo[0] - lx, lx - whi[0]), 0.0f);
             const float gy = fmaxf(fmaxf(wlo[1] - ly, ly - whi[1]), 0.0f);
@@ -1251,6 +1286,16 @@ struct EventPairs {
 
 }  // namespace
 
+// Vertex values d(v, X) and bounds (k_vertices), for the backward pass.
+int launch_vertices(const float* L, int32_t n_L, const flood_grid* grid, float* val, int32_t* src, float* vbound,
+                    uint32_t* flags, cudaStream_t s) {
+    const unsigned blocks = static_cast<unsigned>(ceil_div(int64_t(n_L) * 32, 256));  // a warp per landmark
+    k_vertices<<<blocks, 256, 0, s>>>(L, n_L, view_of(grid), val, src, vbound, flags);
+    note_launch();
+    FLOOD_CUDA(cudaGetLastError());
+    return FLOOD_OK;
+}
+
 std::vector<uint8_t> interior_table(int m, int k) {
     // compositions of m into k+1 parts >= 1, lexicographic in (c_0, ..., c_k)
     std::vector<uint8_t> out;
@@ -1330,6 +1375,7 @@ struct JobState {
     std::vector<uint8_t> tables[4];
     const uint8_t* comp[4];
     const float* w[4];
+    float* vbound;
     int32_t *bcount, *bstart, *bfill, *goff, *cls;
     int2 *groups, *groups_sorted;
     SampleRec* recs;
@@ -1419,8 +1465,10 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             if (!J.val[k] && (rc = scr.alloc(&J.val[k], J.nk[k]))) return rc;
             if (!J.src[k] && (rc = scr.alloc(&J.src[k], 2 * J.nk[k]))) return rc;
         }
+        if ((rc = scr.alloc(&J.vbound, J.nk[0]))) return rc;
         const unsigned vblocks = static_cast<unsigned>(ceil_div(J.nk[0] * int64_t(32), 256));  // a warp per landmark
-        k_vertices<<<vblocks, 256, 0, s>>>(J.in.L, J.in.n_landmarks, view_of(grid), J.val[0], J.src[0], &ctl->flags);
+        k_vertices<<<vblocks, 256, 0, s>>>(J.in.L, J.in.n_landmarks, view_of(grid), J.val[0], J.src[0], J.vbound,
+                                           &ctl->flags);
         note_launch();
         FLOOD_CUDA(cudaGetLastError());
         J.max_samples = 1;
@@ -1491,6 +1539,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             a.comp = J.comp[k];
             a.w = J.w[k];
             a.L = J.in.L;
+            a.vbound = J.vbound;
             a.n_L = J.in.n_landmarks;
             a.g = view_of(grid);
             a.lat = J.lat;

@@ -36,6 +36,11 @@ std::vector<uint8_t> interior_table(int m, int k);
 // Device copy of interior_table(m, k) (host: that table), cached per device.
 int device_interior_table(int m, int k, const std::vector<uint8_t>& host, const uint8_t** out);
 
+// d(v, X) and its rounded-up bound (0 for a point of X) for every landmark;
+// src gets (v, 0). Defined with the filtration kernels.
+int launch_vertices(const float* L, int32_t n_L, const flood_grid* grid, float* val, int32_t* src, float* vbound,
+                    uint32_t* flags, cudaStream_t s);
+
 struct GridView {
     const float4* pts;
     const int32_t* cell_start;
@@ -209,6 +214,63 @@ __device__ __forceinline__ void box_row(const GridView& g, const CellBox& b, int
     const int64_t base = (static_cast<int64_t>(cz) * g.dy + cy) * g.dx + b.c0[0];
     begin = g.cell_start[base];
     end = g.cell_start[base + b.n[0]];
+}
+
+// Exact nearest point of X to q, warp-collective: cull boxes of radius R,
+// 2R, 4R, ... around q until the best squared distance found is within the
+// box's radius (every point outside the box is farther) or the box covers the
+// whole grid. Returns min over X of (d^2 bits << 32 | original row) with
+// d = x - q per coordinate as in the flood kernels (ties to the lowest row),
+// or ~0 if X were empty. At most 64 rounds (R doubles each round).
+__device__ __forceinline__ unsigned long long warp_nearest(const GridView& g, float qx, float qy, float qz, float R,
+                                                           int lane) {
+    const float q[3] = {qx, qy, qz}, zero[3] = {0.0f, 0.0f, 0.0f};
+    unsigned long long best = ~0ull;
+    for (int it = 0; it < 64; ++it) {
+        const CellBox b = cull_box(g, q, zero, zero, R);
+        const int rows = b.n[1] * b.n[2];
+        for (int r = 0; r < rows; ++r) {
+            int32_t rb, re;
+            box_row(g, b, r, rb, re);
+            for (int32_t i = rb + lane; i < re; i += 32) {
+                const float4 x = g.pts[i];
+                const float dx = __fsub_rn(x.x, qx), dy = __fsub_rn(x.y, qy), dz = __fsub_rn(x.z, qz);
+                const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+                const unsigned long long key = (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
+                                               static_cast<uint32_t>(__float_as_int(x.w));
+                best = key < best ? key : best;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+            best = y < best ? y : best;
+        }
+        const bool whole = b.c0[0] == 0 && b.c0[1] == 0 && b.c0[2] == 0 && b.n[0] == g.dx && b.n[1] == g.dy &&
+                           b.n[2] == g.dz;
+        if (best != ~0ull && (whole || __uint_as_float(static_cast<uint32_t>(best >> 32)) <= __fmul_rn(R, R)))
+            break;
+        R = __fmul_rn(R, 2.0f);
+    }
+    return best;
+}
+
+// Upper bound of d(p, X) from the simplex's vertices when they need not be
+// points of X: min_j (|p - v_j| + d(v_j, X)) (triangle inequality), rounded
+// up; vb[j] is d(v_j, X) rounded up (0 for a vertex that is a point of X).
+__device__ __forceinline__ float vertex_bound_general(const Simplex& s, int k, float px, float py, float pz,
+                                                      const float vb[4]) {
+    float u = __fadd_ru(__fsqrt_ru(__fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz)))), vb[0]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j < k) {
+            const float dx = __fsub_rn(px, s.e[j][0]);
+            const float dy = __fsub_rn(py, s.e[j][1]);
+            const float dz = __fsub_rn(pz, s.e[j][2]);
+            u = fminf(u, __fadd_ru(__fsqrt_ru(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)))), vb[j + 1]));
+        }
+    }
+    return __fmul_ru(u, 1.0f + 1.0f / 65536.0f);  // margin over the rounding of the distances
 }
 
 }  // namespace flood

@@ -314,9 +314,10 @@ def test_invalid_inputs_raise():
     Xd = torch.from_numpy(X).to(_dev())
     grid = ops.build_grid(Xd)
     dcx = ops.to_device(cx, _dev())
-    Lbad = torch.from_numpy(L + np.float32(1e-3)).to(_dev())
+    Lnan = L.copy()
+    Lnan[2, 1] = np.nan
     with pytest.raises(FloodError) as e:
-        ops.filtration(grid, Lbad, dcx, 6)
+        ops.filtration(grid, torch.from_numpy(Lnan).to(_dev()), dcx, 6)
     assert e.value.name == "FLOOD_EINVAL"
     bad = ops.to_device(cx, _dev())
     bad.simplices[2][0, 1] = 10_000
