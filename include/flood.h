@@ -285,6 +285,27 @@ typedef struct flood_filtration_stats {
 int flood_last_filtration_stats(flood_filtration_stats* out);
 
 /* ------------------------------------------------------------------------
+ * flood_filtration_masked — the paper's own evaluation, as a comparator.
+ *
+ * §4.2 / App. A.1: every sample of the FULL grid P_sigma of Lemma 1 (faces
+ * included) against every point of X inside the masking ball of Lemma 2
+ * (centre: midpoint of the longest edge; radius sqrt(2) max_i |c - v_i|, or
+ * that maximum for an edge), f(sigma) = max over samples of the minimum over
+ * the masked points. No pruning and no reuse of facet values. The values
+ * equal flood_filtration's up to FP32 rounding (the arithmetic differs: the
+ * direct form |x - p|^2 here); it exists to time the paper's design on the
+ * same GPU.
+ *   grid, L, simplices, n_simplices, m   as flood_filtration; every landmark
+ *                must be a point of X (Lemma 2 assumes L ⊂ X), else
+ *                FLOOD_EINVAL; C(m+3, 3) <= 1024 full-grid samples (m <= 15)
+ *   values[k]    device float32 (n_k) output, k = 0..3 (values[0] may be NULL)
+ *   pairs_out    host int64 or NULL: (sample, masked point) pairs evaluated
+ * Errors: FLOOD_EINVAL, FLOOD_ENOMEM, FLOOD_ECUDA. Synchronises `stream`.
+ * ------------------------------------------------------------------------ */
+int flood_filtration_masked(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                            const int32_t* const simplices[4], const int64_t n_simplices[4], int32_t m,
+                            float* const values[4], int64_t* pairs_out, void* stream);
+/* ------------------------------------------------------------------------
  * flood_complex_faces — faces of Del(L) and facet incidence, on the device.
  *
  * The discretised complex of §4.1 admits a simplex only after all of its

@@ -109,6 +109,8 @@ _SIGNATURES = {
                                          C.c_void_p]),
     "flood_filtration_given_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, P4, I32x4, P4,
                                                   P4, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flood_filtration_masked": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, C.c_int32, P4,
+                                          C.POINTER(C.c_int64), C.c_void_p]),
     "flood_complex_faces": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                       C.c_void_p]),

@@ -18,7 +18,7 @@ from ._lib import FloodError, P4, I64x4, I32x4
 
 __all__ = ["fps", "fps_noalloc", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
            "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
-           "complex_faces",
+           "complex_faces", "filtration_masked",
            "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given"]
 
 
@@ -138,6 +138,24 @@ def to_device(cx, device) -> DeviceComplex:
     sims = [torch.from_numpy(np.ascontiguousarray(s, dtype=np.int32)).to(device) for s in cx.simplices]
     facs = [torch.from_numpy(np.ascontiguousarray(f, dtype=np.int32)).to(device) for f in cx.facets]
     return DeviceComplex(int(cx.n_vertices), sims, facs)
+
+
+def filtration_masked(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int):
+    """The paper's masked full-grid evaluation (§4.2, App. A.1), for comparison.
+
+    Returns (values[k] float32, pairs evaluated). Values equal filtration()'s
+    up to FP32 rounding.
+    """
+    L = _points(L, "L")
+    s, _, n = cx.arrays()
+    vals = [torch.empty(c, dtype=torch.float32, device=L.device) for c in cx.counts]
+    vp = P4(*[_ptr(v) if v.numel() else C.c_void_p(0) for v in vals] + [C.c_void_p(0)] * (4 - len(vals)))
+    pairs = C.c_int64(0)
+    with torch.cuda.device(L.device):
+        st = _lib.get().flood_filtration_masked(grid.handle, _ptr(L), L.shape[0], s, n, int(m), vp, C.byref(pairs),
+                                                _stream_ptr(L.device))
+    _lib.check(st, "flood_filtration_masked")
+    return vals, int(pairs.value)
 
 
 def complex_faces(tets: torch.Tensor, n_vertices: int) -> DeviceComplex:
