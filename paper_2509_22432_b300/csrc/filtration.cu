@@ -1274,6 +1274,36 @@ Lattice make_lattice(const flood_grid* grid, int64_t n_samples) {
 thread_local flood_filtration_stats g_stats;
 
 // CUDA events around the flood kernel of each dimension, destroyed on scope exit.
+// A second stream per host thread and device, with a pair of fork/join
+// events, for the light-group kernel: launched beside the heavy-group kernel,
+// its CTAs take SM slots as the heavy CTAs run out of groups.
+struct SideStream {
+    int dev = -1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+int side_stream(SideStream** out) {
+    thread_local SideStream side[8];
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    SideStream& x = side[dev & 7];
+    if (x.dev != dev) {
+        if (x.s) {
+            cudaStreamDestroy(x.s);
+            cudaEventDestroy(x.fork);
+            cudaEventDestroy(x.join);
+        }
+        x = SideStream{};
+        FLOOD_CUDA(cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking));
+        FLOOD_CUDA(cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
+        FLOOD_CUDA(cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming));
+        x.dev = dev;
+    }
+    *out = &x;
+    return FLOOD_OK;
+}
+
 struct EventPairs {
     cudaEvent_t e[4][2] = {};
     cudaEvent_t* operator[](int k) { return e[k]; }
@@ -1605,8 +1635,14 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             note_launch();
             if (cudaEventCreate(&ev[k][0]) == cudaSuccess && cudaEventCreate(&ev[k][1]) == cudaSuccess)
                 cudaEventRecord(ev[k][0], s);
+            SideStream* side;
+            if ((rc = side_stream(&side))) return rc;
+            FLOOD_CUDA(cudaEventRecord(side->fork, s));
+            FLOOD_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0));
             if ((rc = launch_flood_heavy(dj, nj, heavy_off, ctl, k, s))) return rc;
-            if ((rc = launch_flood(dj, nj, light_off, ctl, k, s))) return rc;
+            if ((rc = launch_flood(dj, nj, light_off, ctl, k, side->s))) return rc;
+            FLOOD_CUDA(cudaEventRecord(side->join, side->s));
+            FLOOD_CUDA(cudaStreamWaitEvent(s, side->join, 0));
             if (ev[k][1]) cudaEventRecord(ev[k][1], s);
         }
         for (int i = 0; i < n_jobs; ++i) {
