@@ -1406,10 +1406,12 @@ struct JobState {
     const uint8_t* comp[4];
     const float* w[4];
     float* vbound;
-    int32_t *bcount, *bstart, *bfill, *goff, *cls;
+    // per dimension, carved from one region zeroed by a single memset
+    int32_t *bcount[4], *bfill[4], *cls[4];
+    unsigned long long* best[4];
+    int32_t *bstart, *goff;
     int2 *groups, *groups_sorted;
     SampleRec* recs;
-    unsigned long long* best;
     float shell_slack;
 };
 
@@ -1525,12 +1527,29 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
         J.n_coarse = int64_t(J.lat.bx) * J.lat.by * J.lat.bz;
         J.n_buckets = J.n_coarse * kFine;
         J.max_groups = J.max_samples / kGroup + J.n_coarse + 1;
-        if ((rc = scr.alloc(&J.bcount, J.n_buckets)) || (rc = scr.alloc(&J.bstart, J.n_buckets + 1)) ||
-            (rc = scr.alloc(&J.bfill, J.n_buckets)) || (rc = scr.alloc(&J.goff, J.n_coarse + 1)) ||
+        if ((rc = scr.alloc(&J.bstart, J.n_buckets + 1)) || (rc = scr.alloc(&J.goff, J.n_coarse + 1)) ||
             (rc = scr.alloc(&J.groups, J.max_groups)) || (rc = scr.alloc(&J.groups_sorted, J.max_groups)) ||
-            (rc = scr.alloc(&J.cls, 3 * kClasses + 1)) || (rc = scr.alloc(&J.recs, J.max_samples)) ||
-            (rc = scr.alloc(&J.best, J.max_n)))
+            (rc = scr.alloc(&J.recs, J.max_samples)))
             return rc;
+        // bucket counts and fills, class table and per-simplex maxima of every
+        // dimension in 8-byte words of one region, cleared by one memset
+        const int64_t w_buckets = (J.n_buckets * 4 + 7) / 8, w_cls = ((3 * kClasses + 1) * 4 + 7) / 8;
+        int64_t words = 0;
+        for (int k = 1; k <= 3; ++k)
+            if (J.nk[k] > 0) words += 2 * w_buckets + w_cls + J.nk[k];
+        unsigned long long* zr;
+        if ((rc = scr.alloc(&zr, std::max<int64_t>(words, 1)))) return rc;
+        FLOOD_CUDA(cudaMemsetAsync(zr, 0, sizeof(unsigned long long) * std::max<int64_t>(words, 1), s));
+        for (int k = 1; k <= 3; ++k) {
+            J.bcount[k] = J.bfill[k] = J.cls[k] = nullptr;
+            J.best[k] = nullptr;
+            if (J.nk[k] == 0) continue;
+            J.bcount[k] = reinterpret_cast<int32_t*>(zr);
+            J.bfill[k] = reinterpret_cast<int32_t*>(zr + w_buckets);
+            J.cls[k] = reinterpret_cast<int32_t*>(zr + 2 * w_buckets);
+            J.best[k] = zr + 2 * w_buckets + w_cls;
+            zr += 2 * w_buckets + w_cls + J.nk[k];
+        }
         const float emax = std::max(grid->bbox_hi[0] - grid->bbox_lo[0],
                                     std::max(grid->bbox_hi[1] - grid->bbox_lo[1], grid->bbox_hi[2] - grid->bbox_lo[2]));
         const float amax =
@@ -1554,7 +1573,6 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             JobState& J = js[i];
             const int64_t n = J.nk[k];
             if (n == 0) continue;
-            FLOOD_CUDA(cudaMemsetAsync(J.best, 0, sizeof(unsigned long long) * n, s));
             if (J.I[k] == 0) continue;
             const flood_grid* grid = J.in.grid;
             DimArgs a{};
@@ -1575,22 +1593,20 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             a.lat = J.lat;
             a.n_buckets = J.n_buckets;
             a.n_coarse = J.n_coarse;
-            a.bucket_count = J.bcount;
+            a.bucket_count = J.bcount[k];
             a.bucket_start = J.bstart;
-            a.bucket_fill = J.bfill;
+            a.bucket_fill = J.bfill[k];
             a.group_off = J.goff;
             a.groups = J.groups;
             a.recs = J.recs;
-            a.best = J.best;
+            a.best = J.best[k];
             a.shell_h = grid->cell_size * (1.0f - 1.0f / 1024.0f);
             a.shell_slack = J.shell_slack;
             a.ctl = ctl;
-            FLOOD_CUDA(cudaMemsetAsync(J.bcount, 0, sizeof(int32_t) * J.n_buckets, s));
-            FLOOD_CUDA(cudaMemsetAsync(J.bfill, 0, sizeof(int32_t) * J.n_buckets, s));
             const unsigned wb = static_cast<unsigned>(ceil_div(n * 32, 256));
             k_samples<false><<<wb, 256, 0, s>>>(a);
             note_launch();
-            if ((rc = exclusive_scan(J.bcount, J.bstart, J.n_buckets, s, scr))) return rc;
+            if ((rc = exclusive_scan(J.bcount[k], J.bstart, J.n_buckets, s, scr))) return rc;
             k_samples<true><<<wb, 256, 0, s>>>(a);
             note_launch();
             if (J.n_coarse <= kGroupOffMaxCubes) {
@@ -1598,26 +1614,26 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
                 note_launch();
             } else {
                 const unsigned bb = static_cast<unsigned>(ceil_div(J.n_coarse, 256));
-                k_group_counts<<<bb, 256, 0, s>>>(J.bstart, J.n_coarse, J.bcount);
+                k_group_counts<<<bb, 256, 0, s>>>(J.bstart, J.n_coarse, J.bcount[k]);
                 note_launch();
-                if ((rc = exclusive_scan(J.bcount, J.goff, J.n_coarse, s, scr))) return rc;
+                if ((rc = exclusive_scan(J.bcount[k], J.goff, J.n_coarse, s, scr))) return rc;
                 k_group_fill<<<bb, 256, 0, s>>>(J.goff, J.n_coarse, J.groups);
                 note_launch();
             }
             // longest-first order of this cloud's groups; the count stays on the device
             const int32_t* n_groups = J.goff + J.n_coarse;
             // cls: counts [0, kClasses), fill [kClasses, 2 kClasses), starts [2 kClasses, 3 kClasses + 1)
-            FLOOD_CUDA(cudaMemsetAsync(J.cls, 0, sizeof(int32_t) * 2 * kClasses, s));
             const unsigned gbk = static_cast<unsigned>(ceil_div(J.max_groups, 256));
-            k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, J.cls);
+            int32_t* cls = J.cls[k];
+            k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, cls);
             note_launch();
-            k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, J.cls, J.cls + 2 * kClasses, J.cls + kClasses,
+            k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, cls, cls + 2 * kClasses, cls + kClasses,
                                                       J.groups_sorted);
             note_launch();
             FLOOD_CUDA(cudaGetLastError());
             a.groups = J.groups_sorted;
             // heavy groups: shell bound >= kHeavyShells, i.e. classes [0, kClasses - kHeavyShells)
-            a.n_heavy = J.cls + 2 * kClasses + (kClasses - kHeavyShells);
+            a.n_heavy = cls + 2 * kClasses + (kClasses - kHeavyShells);
             FLOOD_CUDA(cudaMemcpyAsync(d_counts + i * 4 + k, n_groups, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
             h_jobs.push_back(a);
         }
@@ -1650,7 +1666,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             const int64_t n = J.nk[k];
             if (n == 0) continue;
             k_facemax<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, s>>>(
-                k, n, J.in.simplices[k], J.in.facets[k], J.nk[k - 1], J.best, J.val[k - 1], J.src[k - 1],
+                k, n, J.in.simplices[k], J.in.facets[k], J.nk[k - 1], J.best[k], J.val[k - 1], J.src[k - 1],
                 J.val[k], J.src[k], &ctl->flags);
             note_launch();
             FLOOD_CUDA(cudaGetLastError());
