@@ -67,17 +67,19 @@ struct Ctl {
 };
 
 // Sample lattice: coarse cubes of edge B (a power of two) anchored at the grid
-// origin, each split into 4 x 4 x 4 fine buckets numbered in Morton order. A
-// sample's key is coarse id * 64 + fine Morton index, so sorting by key keeps
-// the samples of one coarse cube together and spatially ordered inside it.
+// origin, each split into 2 x 2 x 2 fine buckets (octants). A sample's key is
+// coarse id * 8 + octant, so sorting by key keeps the samples of one coarse
+// cube together and roughly spatially ordered inside it. (4 x 4 x 4 fine
+// buckets, about one sample each, made the per-dimension bucket scan and
+// clearing 8x larger for no gain in the flood kernels.)
 struct Lattice {
     float ox, oy, oz;
     float B, invB;     // coarse edge
-    float invF;        // 4 / B
+    float invF;        // 2 / B
     int bx, by, bz;    // coarse cubes per axis
 };
 
-constexpr int kFine = 64;  // fine buckets per coarse cube
+constexpr int kFine = 8;  // fine buckets per coarse cube
 
 struct SampleRec {
     float x, y, z;  // sample coordinates
@@ -180,16 +182,12 @@ __device__ __forceinline__ int lattice_coord(float v, float o, float invB, int d
     return static_cast<int>(t);
 }
 
-__device__ __forceinline__ uint32_t spread2(uint32_t v) {  // 2-bit Morton spread
-    return (v & 1u) | ((v & 2u) << 2);
-}
-
 __device__ __forceinline__ int64_t sample_key(const Lattice& L, float x, float y, float z) {
-    const int fx = lattice_coord(x, L.ox, L.invF, 4 * L.bx);
-    const int fy = lattice_coord(y, L.oy, L.invF, 4 * L.by);
-    const int fz = lattice_coord(z, L.oz, L.invF, 4 * L.bz);
-    const int64_t coarse = (static_cast<int64_t>(fz >> 2) * L.by + (fy >> 2)) * L.bx + (fx >> 2);
-    const uint32_t fine = spread2(fx & 3) | (spread2(fy & 3) << 1) | (spread2(fz & 3) << 2);
+    const int fx = lattice_coord(x, L.ox, L.invF, 2 * L.bx);
+    const int fy = lattice_coord(y, L.oy, L.invF, 2 * L.by);
+    const int fz = lattice_coord(z, L.oz, L.invF, 2 * L.bz);
+    const int64_t coarse = (static_cast<int64_t>(fz >> 1) * L.by + (fy >> 1)) * L.bx + (fx >> 1);
+    const uint32_t fine = (fx & 1) | ((fy & 1) << 1) | ((fz & 1) << 2);
     return coarse * kFine + fine;
 }
 
@@ -1267,7 +1265,7 @@ Lattice make_lattice(const flood_grid* grid, int64_t n_samples) {
     }
     L.B = B;
     L.invB = 1.0f / B;
-    L.invF = 4.0f / B;
+    L.invF = 2.0f / B;
     return L;
 }
 
