@@ -72,3 +72,27 @@ def test_generators_are_seeded_float32_and_shaped():
     assert np.allclose((rho - 1.0) ** 2 + t[:, 2].astype(np.float64) ** 2, 0.09, atol=1e-5)
     s = data.serving_sizes()
     assert s.min() >= 2000 and s.max() <= 200000 and len(s) == 512
+
+
+def test_new_entry_points_reject_bad_arguments_before_any_device_call():
+    """Host-side validation of the given-sets, masked, faces and backward entry points."""
+    import ctypes as C
+    lib = _lib.get()
+    P4, I64x4, I32x4 = _lib.P4, _lib.I64x4, _lib.I32x4
+    null4, n4 = P4(), I64x4(0, 3, 3, 1)
+    einval = -1
+    # faces: negative count, NULL count outputs
+    n2, n1 = C.c_int64(0), C.c_int64(0)
+    assert lib.flood_complex_faces(None, -1, 4, None, None, None, None, None, C.byref(n2), C.byref(n1), None) == einval
+    assert lib.flood_complex_faces(None, 1, 4, None, None, None, None, None, None, None, None) == einval
+    assert lib.flood_complex_faces(None, 1, 1 << 21, None, None, None, None, None, C.byref(n2), C.byref(n1),
+                                   None) == einval
+    # empty input succeeds without touching the device
+    assert lib.flood_complex_faces(None, 0, 4, None, None, None, None, None, C.byref(n2), C.byref(n1), None) == 0
+    assert n2.value == 0 and n1.value == 0
+    # given sets, masked comparator, given backward: a NULL grid is rejected on the host
+    assert lib.flood_filtration_given(None, None, 4, null4, null4, n4, P4(), I32x4(), null4, null4, None) == einval
+    assert lib.flood_filtration_masked(None, None, 4, null4, n4, 6, null4, None, None) == einval
+    assert lib.flood_filtration_given_backward(None, None, 4, null4, n4, P4(), I32x4(), null4, null4, None, None,
+                                               None) == einval
+    assert lib.flood_last_error().decode() != ""
