@@ -271,8 +271,9 @@ def main():
             clouds = serving_clouds(512)
             for rate in (50, 100, 200, 500, 1000, 2000):
                 for batched in (True, False):
-                    r = run_serving(clouds, rate, batched)
-                    print(json.dumps({"serving": "batched" if batched else "per-cloud", **r}), flush=True)
+                    r = run_serving(clouds, rate, batched, device_faces=True)
+                    print(json.dumps({"serving": "batched" if batched else "per-cloud", "faces": "device", **r}),
+                          flush=True)
         return
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -520,12 +521,15 @@ def main():
                              "numpy builder"}
     if rank == 0 and not args.no_serving:
         clouds = serving_clouds(128)
-        b = run_serving(clouds, 500.0, True)
+        b = run_serving(clouds, 500.0, True, device_faces=False)
         bd = run_serving(clouds, 500.0, True, device_faces=True)
-        p = run_serving(clouds, 500.0, False)
+        p = run_serving(clouds, 500.0, False, device_faces=False)
         line["serving"] = {"workload": "128 clouds, 2k-200k points (log-uniform), shape mix, Poisson 500/s, "
                                        "n_L = 2% of points, m = 8, host Delaunay included",
-                           "batched": b, "batched_device_faces": bd, "per_cloud": p}
+                           "batched": b, "batched_device_faces": bd, "per_cloud": p,
+                           "modes": "batched and per_cloud: whole complex built on the host; "
+                                    "batched_device_faces (the server's default): tetrahedra from the host, "
+                                    "faces built on the device"}
     if rank == 0 and not args.no_cpu_baseline:
         res = cpu_baseline(X, wl)
         step_s = res["t_fps_s"] + res["t_build_s"] + res["per_simplex_s"] * n_simp

@@ -410,7 +410,8 @@ typedef struct flood_host_complex {
  * The callback may fill only the tetrahedra (n_simplices[1] = n_simplices[2]
  * = 0, facets ignored); the library then builds the triangles, edges and
  * facet incidence on the device (flood_complex_faces) and reports the rows
- * it built in flood_result.simplices. */
+ * it built in flood_result.simplices. This is the faster mode: the host then
+ * only triangulates (the Python Server uses it by default). */
 typedef int (*flood_triangulate_fn)(void* user, const float* landmarks, int32_t n_landmarks,
                                     flood_host_complex* out);
 typedef void (*flood_release_fn)(void* user, void* owner);

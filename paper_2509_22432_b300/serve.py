@@ -36,15 +36,20 @@ class Server:
 
     triangulate(L) -> SimplexLists (default: scipy Delaunay of the landmarks).
     max_batch = 1 gives the plain one-cloud-at-a-time path.
-    device_faces = True: the callback hands over the tetrahedra of the scipy
-    Delaunay triangulation only, and the library builds the triangles, edges
-    and facet incidence on the device; results then list the rows it built.
+    device_faces (default when no triangulate is given): the callback hands
+    over the tetrahedra of the scipy Delaunay triangulation only, and the
+    library builds the triangles, edges and facet incidence on the device;
+    results list the rows of every dimension ("simplices"), whose order is then
+    the device's, not lexicographic. device_faces=False builds the whole
+    complex on the host (rows in lexicographic order).
     """
 
     def __init__(self, device_budget_bytes: int = 16 << 30, max_inflight: int = 64, max_batch: int = 32,
                  gpu_workers: int = 4, triangulation_workers: int = 4, landmark_fraction: float = 0.02,
-                 cell_factor: float = 0.5, triangulate=None, device_faces: bool = False):
+                 cell_factor: float = 0.5, triangulate=None, device_faces: bool | None = None):
         self._lib = _lib_serve()
+        if device_faces is None:
+            device_faces = triangulate is None
         if device_faces and triangulate is not None:
             raise ValueError("device_faces uses the built-in tetrahedralisation; pass no triangulate")
         self._fn = triangulate or delaunay_complex

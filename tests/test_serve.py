@@ -38,7 +38,7 @@ def test_batched_server_results_equal_one_cloud_path():
     from paper_2509_22432_b300.serve import Server
     clouds = _clouds()
     m = 8
-    with Server(max_inflight=6, max_batch=8, gpu_workers=3, triangulation_workers=3) as srv:
+    with Server(max_inflight=6, max_batch=8, gpu_workers=3, triangulation_workers=3, device_faces=False) as srv:
         tickets = [srv.submit(X, 0, m) for X in clouds]
         results = [srv.result(t, timeout_ms=120_000) for t in tickets]
         st = srv.stats()
