@@ -111,13 +111,30 @@ def complex_from_simplices(maximal, n_vertices: int, top_dim: int | None = None)
     return SimplexLists(int(n_vertices), simplices, facets)
 
 
-def delaunay_complex(L: np.ndarray) -> SimplexLists:
-    """Delaunay triangulation of 3D landmarks (scipy/Qhull, FP64 predicates)."""
+def delaunay_complex(L: np.ndarray, dim: int | None = None) -> SimplexLists:
+    """Delaunay triangulation of the landmarks (scipy/Qhull, FP64 predicates).
+
+    dim = 3 (default for (n, 3) input): tetrahedra and all their faces.
+    dim = 2: the planar triangulation of (n, 2) landmarks, or of (n, 3)
+    landmarks whose z coordinates are all 0 (a planar cloud embedded at z = 0,
+    which the CUDA path evaluates exactly like a native planar one).
+    """
     from scipy.spatial import Delaunay
 
     L = np.asarray(L, dtype=np.float64)
-    if L.ndim != 2 or L.shape[1] != 3:
-        raise ValueError("landmarks must be (n, 3)")
+    if L.ndim != 2 or L.shape[1] not in (2, 3):
+        raise ValueError("landmarks must be (n, 2) or (n, 3)")
+    if dim is None:
+        dim = L.shape[1]
+    if dim == 2:
+        if L.shape[1] == 3:
+            if np.any(L[:, 2] != 0.0):
+                raise ValueError("dim = 2 needs z = 0 for every landmark")
+            L = L[:, :2]
+        tris = np.sort(Delaunay(L).simplices.astype(np.int64), axis=1)
+        return complex_from_simplices([tris], L.shape[0], top_dim=2)
+    if dim != 3 or L.shape[1] != 3:
+        raise ValueError("dim must be 2, or 3 with (n, 3) landmarks")
     tri = Delaunay(L)
     tets = np.sort(tri.simplices.astype(np.int64), axis=1)
     return complex_from_simplices([tets], L.shape[0], top_dim=3)

@@ -16,6 +16,7 @@ Workloads:
   swisscheese_cloud uniform in [0,5]^3 minus disjoint balls (§5.3 synthetic data)
   serving_sizes     log-uniform cloud sizes for the batched serving workload
   random_barycentric  uniform random barycentric coordinates (random P_sigma)
+  annulus_cloud     planar annulus (ambient dimension 2), embedded at z = 0
 """
 from __future__ import annotations
 
@@ -31,6 +32,8 @@ __all__ = [
     "jitter",
     "upstream_gradients",
     "random_barycentric",
+    "annulus_cloud",
+    "embed_planar",
 ]
 
 
@@ -214,3 +217,17 @@ def random_barycentric(n_simplices: int, n_samples: int, k: int, seed: int = 7) 
     rng = _rng(seed + 1009 * (k + 1))
     e = rng.exponential(1.0, (int(n_simplices), int(n_samples), k + 1))
     return _f32(e / e.sum(axis=2, keepdims=True))
+
+
+def embed_planar(xy: np.ndarray) -> np.ndarray:
+    """(n, 2) planar points as (n, 3) float32 with z = 0 (ambient dimension 2)."""
+    xy = np.asarray(xy, dtype=np.float64)
+    return _f32(np.concatenate([xy, np.zeros((xy.shape[0], 1))], axis=1))
+
+
+def annulus_cloud(n: int = 20_000, r_in: float = 0.6, r_out: float = 1.0, seed: int = 8) -> np.ndarray:
+    """Points uniform (by area) in a planar annulus, embedded at z = 0, float32 (n, 3)."""
+    rng = _rng(seed)
+    r = np.sqrt(rng.uniform(r_in * r_in, r_out * r_out, n))
+    t = rng.uniform(0.0, 2.0 * np.pi, n)
+    return embed_planar(np.stack([r * np.cos(t), r * np.sin(t)], axis=1))

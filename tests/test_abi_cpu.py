@@ -5,6 +5,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 from paper_2509_22432_b300 import complex_from_simplices, data, delaunay_complex
 from paper_2509_22432_b300 import _lib
@@ -96,3 +97,16 @@ def test_new_entry_points_reject_bad_arguments_before_any_device_call():
     assert lib.flood_filtration_given_backward(None, None, 4, null4, n4, P4(), I32x4(), null4, null4, None, None,
                                                None) == einval
     assert lib.flood_last_error().decode() != ""
+
+
+def test_planar_delaunay_complex():
+    """Ambient dimension 2: a triangulated disk (Euler characteristic 1), z = 0 required."""
+    X = data.annulus_cloud(3000, seed=3)
+    cx = delaunay_complex(X[:200], dim=2)
+    assert len(cx.counts) == 3
+    assert cx.counts[0] - cx.counts[1] + cx.counts[2] == 1
+    assert np.all(np.diff(cx.simplices[2], axis=1) > 0)
+    Y = X[:50].copy()
+    Y[0, 2] = 1e-3
+    with pytest.raises(ValueError):
+        delaunay_complex(Y, dim=2)
