@@ -1281,8 +1281,22 @@ struct SideStream {
     cudaEvent_t fork = nullptr, join = nullptr;
 };
 
+// The streams and events of one host thread, released when the thread ends.
+struct SideStreams {
+    SideStream x[8];
+    ~SideStreams() {
+        for (SideStream& y : x)
+            if (y.s) {
+                cudaStreamDestroy(y.s);
+                cudaEventDestroy(y.fork);
+                cudaEventDestroy(y.join);
+            }
+    }
+};
+
 int side_stream(SideStream** out) {
-    thread_local SideStream side[8];
+    thread_local SideStreams holder;
+    SideStream* side = holder.x;
     int dev = 0;
     FLOOD_CUDA(cudaGetDevice(&dev));
     SideStream& x = side[dev & 7];
