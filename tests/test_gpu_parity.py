@@ -180,6 +180,24 @@ def test_flood_resolutions(m):
     assert_close(vals, ref.values, X, f"m={m}")
 
 
+def test_sample_counts_match_the_grid_printed_in_the_paper():
+    """§5.3 prints 210 points per triangle and 1540 per tetrahedron at 20 points per edge
+    (m = 19); the CUDA path evaluates the interior samples of every face once, so on one
+    tetrahedron its per-dimension sample counts plus the vertices add up to those totals."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "grid_counts_sec5_3.txt")
+    per_edge, per_tri, per_tet = [tuple(int(v) for v in l.split()) for l in open(path)
+                                  if l.strip() and not l.startswith("#")][0]
+    m = per_edge - 1
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float32)
+    cx = complex_from_simplices([np.array([[0, 1, 2, 3]])], 4)
+    _, _, stats = gpu_flood(V, V, cx, m)
+    s = stats["samples"]
+    assert s[1] == 6 * (per_edge - 2)
+    assert 3 + 3 * s[1] // 6 + s[2] // 4 == per_tri
+    assert 4 + s[1] + s[2] + s[3] == per_tet
+
+
 @pytest.mark.parametrize("m", [24, 30])
 def test_flood_many_samples_per_simplex(m):
     """Many samples per simplex (hundreds to thousands) through the bucketed sample groups."""

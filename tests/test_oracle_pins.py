@@ -535,3 +535,22 @@ def test_analytic_gradient_with_landmarks_off_X():
     ok = ~kink
     assert ok.sum() >= 30
     assert np.allclose(fd[ok], an[ok], rtol=1e-3, atol=1e-5)
+
+
+def _golden_counts():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "grid_counts_sec5_3.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return [tuple(int(v) for v in r) for r in rows]
+
+
+def test_grid_counts_printed_in_the_paper():
+    """§5.3: 20 points per edge -> 210 per triangle, 1540 per tetrahedron (golden fixture)."""
+    for per_edge, per_tri, per_tet in _golden_counts():
+        m = per_edge - 1
+        assert oracle.compositions(m, 1).shape[0] == per_edge
+        assert oracle.compositions(m, 2).shape[0] == per_tri
+        assert oracle.compositions(m, 3).shape[0] == per_tet
+        # the full grid is the interior grids of all faces: vertices, edges, triangles, itself
+        assert 4 + 6 * oracle.interior_count(m, 1) + 4 * oracle.interior_count(m, 2) + \
+            oracle.interior_count(m, 3) == per_tet
