@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
 // warp kernel's (W sample lanes x 256/W point streams) stretched over the CTA,
 // and per-sample minima are combined in shared memory.
 constexpr int kHeavyTile = 4096;
-constexpr int kHeavyShells = 8;  // class threshold: groups with >= this many shells are heavy
+constexpr int kHeavyShells = 9;  // class threshold: groups with >= this many shells are heavy
 
 // Evaluate the NSL used sample slots of one tile (NSL <= kHeavyNS); slots are
 // paired for packed FMAs (the same three rounded FMAs per pair, in order).
