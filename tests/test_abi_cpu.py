@@ -110,3 +110,21 @@ def test_planar_delaunay_complex():
     Y[0, 2] = 1e-3
     with pytest.raises(ValueError):
         delaunay_complex(Y, dim=2)
+
+
+def test_header_is_plain_c():
+    """include/flood.h compiles as C99 (pedantic) and as C++: the boundary carries no torch or
+    C++ types."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "use.c")
+        with open(src, "w") as f:
+            f.write('#include "flood.h"\nint main(void) { return flood_version() ? 0 : 1; }\n')
+        r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                            "-I", os.path.join(ROOT, "include"), src], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
