@@ -3,8 +3,9 @@
 * 5,000,000-point union of 8 surfaces, 10,000 FPS landmarks, m = 12: FPS
   checked by properties that hold at any size (every key equals the exact
   binary32 minimum over earlier landmarks, keys never increase, and no
-  sampled point beats a pick or ties it with a lower index), flood values of
-  sampled simplices against the FP64 k-d tree oracle.
+  sampled point beats a pick or ties it with a lower index); flood values of
+  sampled simplices, over 10,000 seeded random landmarks, against the FP64
+  k-d tree oracle.
 * 1,000,000-point jittered torus, 2,000 landmarks, m = 10, upstream
   gradients ~ N(0,1): backward against the oracle's analytic subgradient and
   central differences (h = 1e-5) on 1,000 coordinates.
@@ -67,9 +68,12 @@ def test_fps_5m_properties(shapes5m):
 
 
 def test_flood_5m_sampled_simplices(shapes5m):
-    X, Xd, idx, key = shapes5m
+    """Landmarks: 10,000 seeded random rows of X (oracle inputs never come from the CUDA path;
+    the CUDA FPS picks are checked by properties above)."""
+    X, Xd, _, key = shapes5m
     ops = _ops()
     m = 12
+    idx = np.sort(np.random.default_rng(12).choice(X.shape[0], 10_000, replace=False))
     L = X[idx]
     cx = delaunay_complex(L)
     grid = ops.build_grid(Xd, 0.5 * float(np.sqrt(key[-1])))
@@ -94,15 +98,14 @@ def torus_grad():
     X = data.jitter(data.torus_cloud(), amp=1e-6, seed=5)
     ops = _ops()
     Xd = torch.from_numpy(X).cuda()
-    idx, key = ops.fps(Xd, 2000, 0)
-    idx = idx.cpu().numpy()
+    idx, key = oracle.fps(X, 2000, 0)          # the oracle's picks: its inputs never come from CUDA
     L = X[idx].copy()
     cx = delaunay_complex(L)
     gamma = data.upstream_gradients(cx.counts, seed=5)
     m = 10
     Xg = Xd.clone().requires_grad_(True)
     Lg = torch.from_numpy(L).cuda().requires_grad_(True)
-    grid = ops.build_grid(Xd, 0.5 * float(np.sqrt(key[-1].item())))
+    grid = ops.build_grid(Xd, 0.5 * float(np.sqrt(key[-1])))
     vals = ops.flood_values(Xg, Lg, grid, ops.to_device(cx, Xd.device), m)
     loss = sum((v * torch.from_numpy(g).cuda()).sum() for v, g in zip(vals, gamma))
     loss.backward()
