@@ -9,7 +9,7 @@ obviously correct numpy/scipy code that follows the paper's definitions:
   random_flood.py the same for given point sets P_sigma (random draws, Lemma 4):
                   maximum over every face's set, faces enumerated explicitly
   grad.py         analytic subgradient of sum_sigma gamma_sigma f(sigma), central FD
-  persistence.py  Z/2 boundary-matrix reduction, diagrams, bottleneck distance (§2)
+  persistence.py  Z/2 boundary-matrix reduction (pairing), diagrams, bottleneck distance (§2)
   faces.py        faces and facet incidence of a set of tetrahedra, by definition
 
 Only tests, the smoke check and the CPU-baseline leg of the benchmark may
@@ -25,13 +25,14 @@ from .samples import compositions, interior_compositions, full_grid_count, inter
 from .flood import flood_values, nearest_distance, FloodResult
 from .grad import analytic_gradient, finite_difference
 from .random_flood import flood_values_random, analytic_gradient_random, total_random, RandomFloodResult
-from .persistence import diagrams, bottleneck
+from .persistence import diagrams, bottleneck, bottleneck_within, persistence_pairs
 from .faces import faces_by_definition, facet_rows
 
 __all__ = [
     "fps", "fps_key", "compositions", "interior_compositions", "full_grid_count",
     "interior_count", "sample_points", "flood_values", "nearest_distance", "FloodResult",
-    "analytic_gradient", "finite_difference", "diagrams", "bottleneck",
+    "analytic_gradient", "finite_difference", "diagrams", "bottleneck", "bottleneck_within",
+    "persistence_pairs",
     "flood_values_random", "analytic_gradient_random", "total_random", "RandomFloodResult",
     "faces_by_definition", "facet_rows",
 ]

@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["filtration_order", "diagrams", "bottleneck"]
+__all__ = ["filtration_order", "persistence_pairs", "diagrams", "bottleneck", "bottleneck_within"]
 
 
 def filtration_order(simplices, values):
@@ -33,11 +33,16 @@ def filtration_order(simplices, values):
     return [(k, r) for (_, k, _, r) in entries], [e[0] for e in entries]
 
 
-def diagrams(simplices, facets, values, max_dim: int | None = None):
-    """dgm_0 .. dgm_{max_dim} as float64 arrays (n, 2); death = inf for essential classes."""
+def persistence_pairs(simplices, facets, values):
+    """Persistence pairing of the filtration by the Z/2 column reduction.
+
+    Returns (pairs, essential): pairs is a list of ((k, row), (k + 1, row')) with
+    the simplex that creates a k-dimensional class and the one that kills it
+    (zero-persistence pairs included); essential lists the (k, row) of the
+    simplices whose classes never die. Simplices are ordered by (value,
+    dimension, lexicographic vertex ids).
+    """
     K = len(simplices)
-    if max_dim is None:
-        max_dim = K - 1
     order, vals = filtration_order(simplices, values)
     pos = {kr: i for i, kr in enumerate(order)}
     for i, (k, r) in enumerate(order):
@@ -67,52 +72,73 @@ def diagrams(simplices, facets, values, max_dim: int | None = None):
                 pivot_of[p] = i
                 reduced[i] = col
                 cleared.add(p)
+    pairs = sorted((order[p], order[i]) for p, i in pivot_of.items())
+    paired = set(pivot_of) | set(pivot_of.values())
+    # a non-zero reduced column is a death, never a birth
+    essential = [order[i] for i in range(n) if i not in paired and i not in reduced]
+    return pairs, essential
+
+
+def diagrams(simplices, facets, values, max_dim: int | None = None):
+    """dgm_0 .. dgm_{max_dim} as float64 arrays (n, 2); death = inf for essential classes."""
+    K = len(simplices)
+    if max_dim is None:
+        max_dim = K - 1
+    pairs, essential = persistence_pairs(simplices, facets, values)
+    val = lambda kr: float(np.asarray(values[kr[0]], dtype=np.float64)[kr[1]])  # noqa: E731
     dgms = [[] for _ in range(max_dim + 1)]
-    paired = set()
-    for p, i in pivot_of.items():
-        paired.add(p)
-        paired.add(i)
-        k = dims[p]
-        if k <= max_dim and vals[i] > vals[p]:
-            dgms[k].append((vals[p], vals[i]))
-    for i in range(n):
-        if i in paired:
-            continue
-        if i in reduced:       # a non-zero reduced column is a death, never a birth
-            continue
-        k = dims[i]
-        if k <= max_dim:
-            dgms[k].append((vals[i], np.inf))
+    for b, d in pairs:
+        if b[0] <= max_dim and val(d) > val(b):
+            dgms[b[0]].append((val(b), val(d)))
+    for b in essential:
+        if b[0] <= max_dim:
+            dgms[b[0]].append((val(b), np.inf))
     return [np.array(sorted(d), dtype=np.float64).reshape(-1, 2) for d in dgms]
 
 
 def _matching_exists(A, B, eps):
-    from scipy.sparse import csr_matrix
+    """Perfect matching of A + diag(B) against B + diag(A) using only pairs within eps (L-inf)."""
+    from scipy.sparse import coo_matrix
     from scipy.sparse.csgraph import maximum_bipartite_matching
 
     na, nb = A.shape[0], B.shape[0]
     n = na + nb
-    rows, cols = [], []
-    for i in range(na):
-        for j in range(nb):
-            if max(abs(A[i, 0] - B[j, 0]), abs(A[i, 1] - B[j, 1])) <= eps:
-                rows.append(i)
-                cols.append(j)
-        if (A[i, 1] - A[i, 0]) / 2.0 <= eps:
-            rows.append(i)
-            cols.append(nb + i)               # A_i to its diagonal projection
-    for j in range(nb):
-        if (B[j, 1] - B[j, 0]) / 2.0 <= eps:
-            rows.append(na + j)
-            cols.append(j)                    # diagonal copy of B_j to B_j
-        for i in range(na):
-            rows.append(na + j)
-            cols.append(nb + i)               # diagonal to diagonal is free
     if n == 0:
         return True
-    M = csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    rows, cols = [], []
+    if na and nb:
+        cost = np.maximum(np.abs(A[:, None, 0] - B[None, :, 0]), np.abs(A[:, None, 1] - B[None, :, 1]))
+        i, j = np.nonzero(cost <= eps)
+        rows.append(i)
+        cols.append(j)                            # A_i to B_j
+    ia = np.nonzero((A[:, 1] - A[:, 0]) / 2.0 <= eps)[0]
+    rows.append(ia)
+    cols.append(nb + ia)                          # A_i to its diagonal projection
+    jb = np.nonzero((B[:, 1] - B[:, 0]) / 2.0 <= eps)[0]
+    rows.append(na + jb)
+    cols.append(jb)                               # diagonal copy of B_j to B_j
+    if na and nb:
+        rr, cc = np.meshgrid(np.arange(nb), np.arange(na), indexing="ij")
+        rows.append(na + rr.ravel())
+        cols.append(nb + cc.ravel())              # diagonal to diagonal is free
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    M = coo_matrix((np.ones(r.shape[0]), (r, c)), shape=(n, n)).tocsr()
     match = maximum_bipartite_matching(M, perm_type="column")
     return bool(np.all(match >= 0))
+
+
+def bottleneck_within(D1, D2, eps: float) -> bool:
+    """True iff the bottleneck distance between two diagrams is at most eps (one matching test)."""
+    D1 = np.asarray(D1, dtype=np.float64).reshape(-1, 2)
+    D2 = np.asarray(D2, dtype=np.float64).reshape(-1, 2)
+    inf1, inf2 = np.sort(D1[np.isinf(D1[:, 1]), 0]), np.sort(D2[np.isinf(D2[:, 1]), 0])
+    if inf1.shape[0] != inf2.shape[0]:
+        return False
+    # essential points lie on a line: the sorted matching is a bottleneck-optimal one
+    if inf1.shape[0] and np.max(np.abs(inf1 - inf2)) > eps:
+        return False
+    return _matching_exists(D1[np.isfinite(D1[:, 1])], D2[np.isfinite(D2[:, 1])], eps)
 
 
 def bottleneck(D1, D2) -> float:

@@ -429,6 +429,67 @@ def test_bottleneck_known_cases():
     assert oracle.bottleneck(D[0], D[1]) == pytest.approx(oracle.bottleneck(D[1], D[0]))
 
 
+def _bottleneck_brute(A, B):
+    """Bottleneck distance by trying every bijection of A + diag(B) onto B + diag(A) (tiny diagrams)."""
+    import itertools
+    A = [tuple(p) for p in np.asarray(A, np.float64).reshape(-1, 2)]
+    B = [tuple(p) for p in np.asarray(B, np.float64).reshape(-1, 2)]
+    left = [("pt", p) for p in A] + [("diag", q) for q in B]
+    right = [("pt", q) for q in B] + [("diag", p) for p in A]
+
+    def cost(a, b):
+        if a[0] == "pt" and b[0] == "pt":
+            p, q = a[1], b[1]
+            if np.isinf(p[1]) != np.isinf(q[1]):
+                return np.inf
+            return max(abs(p[0] - q[0]), 0.0 if np.isinf(p[1]) else abs(p[1] - q[1]))
+        if a[0] == "pt":                       # a point to the diagonal
+            return np.inf if np.isinf(a[1][1]) else (a[1][1] - a[1][0]) / 2
+        if b[0] == "pt":
+            return np.inf if np.isinf(b[1][1]) else (b[1][1] - b[1][0]) / 2
+        return 0.0
+    return min(max([cost(a, b) for a, b in zip(left, perm)], default=0.0)
+               for perm in itertools.permutations(right))
+
+
+def test_bottleneck_and_its_threshold_test_match_brute_force():
+    """bottleneck = the min over bijections of the largest L-inf move (§2), diagonal allowed;
+    bottleneck_within(eps) is true exactly from that value on."""
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        na, nb = rng.integers(0, 4), rng.integers(0, 4)
+        A = np.sort(rng.uniform(0, 1, (na, 2)), axis=1)
+        B = np.sort(rng.uniform(0, 1, (nb, 2)), axis=1)
+        if trial % 3 == 0:                              # one essential class on each side
+            A = np.vstack([A, [[rng.uniform(0, 1), np.inf]]])
+            B = np.vstack([B, [[rng.uniform(0, 1), np.inf]]])
+        want = _bottleneck_brute(A, B)
+        got = oracle.bottleneck(A, B)
+        assert got == pytest.approx(want, abs=1e-12), (trial, got, want)
+        assert oracle.bottleneck_within(A, B, want + 1e-12)
+        if want > 1e-9:
+            assert not oracle.bottleneck_within(A, B, want - 1e-9)
+
+
+def test_persistence_pairs_partition_the_simplices():
+    """Every simplex is created-and-killed in exactly one pair or is essential; a pair joins a
+    k-simplex to a (k+1)-simplex later in the filtration order; the essential classes of a
+    triangulated 3-ball are one component (beta = 1, 0, 0, 0)."""
+    X = data.sphere_cloud(800, seed=72)
+    idx, _ = oracle.fps(X, 40)
+    L = X[idx]
+    cx = delaunay_complex(L)
+    vals = oracle.flood_values(X, L, cx.simplices, 4).values
+    pairs, essential = oracle.persistence_pairs(cx.simplices, cx.facets, vals)
+    order, _ = oracle.persistence.filtration_order(cx.simplices, vals)
+    pos = {kr: i for i, kr in enumerate(order)}
+    seen = [b for b, _ in pairs] + [d for _, d in pairs] + list(essential)
+    assert len(seen) == len(set(seen)) == sum(cx.counts)
+    for b, d in pairs:
+        assert d[0] == b[0] + 1 and pos[b] < pos[d]
+    assert [sum(1 for e in essential if e[0] == k) for k in range(4)] == [1, 0, 0, 0]
+
+
 # ----------------------------------------------------------------------------- gradient
 
 def test_analytic_gradient_matches_central_differences():
