@@ -98,6 +98,49 @@ int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t sta
 int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,
                      int32_t n_blocks, int64_t* out_idx, float* out_key, void* stream);
 
+/* Counters of the calling thread's last successful flood_fps (or
+ * flood_fps_blocks / flood_fps_noalloc) call. Picks are made in rounds: one
+ * grid-wide exchange per round selects one or more picks (all exact). */
+typedef struct flood_fps_stats {
+    int64_t picks;     /* landmarks (including the start point) */
+    int64_t rounds;    /* grid-wide exchange rounds */
+    int32_t blocks;    /* persistent blocks launched (one per SM) */
+    int32_t resident;  /* 1: every point stayed in registers; 0: points streamed from memory */
+} flood_fps_stats;
+
+int flood_last_fps_stats(flood_fps_stats* out);
+
+/* ------------------------------------------------------------------------
+ * flood_fps_scratch_bytes — device scratch that flood_fps_blocks takes for
+ * n_points points and launch width n_blocks (0 = automatic, as flood_fps).
+ *
+ * Host arithmetic (the launch width is clamped to the current device's SM
+ * count; without a device one SM is assumed). The sum of the library's
+ * 256-byte-aligned scratch pieces: control words, exchange
+ * slots, the Morton-ordered point copy (16 B per point), the running minima
+ * when the points do not all fit in registers (4 B per point), and the
+ * Morton sort's codes, histogram, offsets and prefix-sum scratch.
+ *   out_bytes  host int64 output
+ * Errors: FLOOD_EINVAL (n_points out of range, n_blocks < 0, NULL output).
+ * ------------------------------------------------------------------------ */
+int flood_fps_scratch_bytes(int64_t n_points, int32_t n_blocks, int64_t* out_bytes);
+
+/* ------------------------------------------------------------------------
+ * flood_fps_wait_test — exercises the bounded wait of the FPS exchange.
+ *
+ * Test support, not part of the method: runs flood_fps_blocks on n_blocks
+ * (>= 2) blocks with a grid exchange that also waits for `extra_blocks`
+ * (>= 1, n_blocks + extra_blocks <= 160) blocks that are never launched, so
+ * that every wait of the first round runs out after `poll_limit` polls
+ * (each poll is one round of L2 loads, about a microsecond). The kernel then
+ * raises its timeout flag and every block returns; nothing traps or hangs.
+ *   X, n_points, n_landmarks, out_idx   as flood_fps (start = 0)
+ * Returns FLOOD_ETIMEOUT when the wait ran out (the expected outcome); the
+ * device context stays usable. Synchronises `stream`.
+ * ------------------------------------------------------------------------ */
+int flood_fps_wait_test(const float* X, int64_t n_points, int32_t n_landmarks, int32_t n_blocks,
+                        int32_t extra_blocks, uint32_t poll_limit, int64_t* out_idx, void* stream);
+
 /* ------------------------------------------------------------------------
  * flood_fps_noalloc — flood_fps without any device allocation.
  *
@@ -113,7 +156,9 @@ int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_landmarks, int6
  *
  *   Arguments, outputs and errors as flood_fps, plus:
  *   n_points   at most 1,048,576 (2^20); larger inputs are rejected with
- *              FLOOD_ECAPACITY and nothing is launched.
+ *              FLOOD_ECAPACITY and nothing is launched. The fixed array holds
+ *              flood_fps_scratch_bytes(2^20, 1) bytes, the largest need of
+ *              any launch width at that size (points streamed from memory).
  * The first call on a device looks up the array's device address with
  * cudaGetSymbolAddress (with that device current); make that first call
  * before any stream capture. All calls share the one array: calls whose work
@@ -306,6 +351,40 @@ int flood_filtration_masked(const flood_grid* grid, const float* L, int32_t n_la
                             const int32_t* const simplices[4], const int64_t n_simplices[4], int32_t m,
                             float* const values[4], int64_t* pairs_out, void* stream);
 /* ------------------------------------------------------------------------
+ * flood_masking_ball_counts — size of the paper's masked candidate sets.
+ *
+ * §4.2: Lemma 2 restricts the nearest-point search of a simplex to the
+ * points of X in the ball B(c, sqrt(2) r) (c the midpoint of the longest
+ * edge, r = max_i |c - v_i|; radius r for an edge). This counts them:
+ *   counts_out[k] = sum over k-simplices of |X ∩ B|   (host int64[4];
+ *                   counts_out[0] = 0)
+ * so that sum_k C(m-1, k) counts_out[k] is the method's own work in
+ * (interior sample, candidate point) pairs, and sum_k C(m+k, k) counts_out[k]
+ * that of the paper's full-grid evaluation. The ball test runs in FP32
+ * (points within rounding of the sphere may count either way).
+ *   grid, L, simplices, n_simplices   as flood_filtration
+ * Errors: FLOOD_EINVAL, FLOOD_ENOMEM, FLOOD_ECUDA. Synchronises `stream`.
+ * ------------------------------------------------------------------------ */
+int flood_masking_ball_counts(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                              const int32_t* const simplices[4], const int64_t n_simplices[4],
+                              int64_t counts_out[4], void* stream);
+
+/* ------------------------------------------------------------------------
+ * flood_fp32_peak_probe — measured FP32 FMA throughput (roofline helper).
+ *
+ * Not part of the method: the flood kernels are bound by the FP32 pipe when
+ * they are dense, and this launches a kernel that does nothing but
+ * independent FP32 fused multiply-adds (16 chains per thread, 8 blocks of
+ * 256 threads per SM) so that the caller can time it with CUDA events on
+ * `stream`. packed = 0 issues scalar FMAs, 1 packed pairs (two lanes' worth
+ * per instruction, the form the flood kernels use).
+ *   iterations  loop trips per thread, 1..2^30
+ *   flops_out   host: floating-point operations the launch performs (2 per FMA)
+ * Errors: FLOOD_EINVAL, FLOOD_ENOMEM, FLOOD_ECUDA. Does not synchronise.
+ * ------------------------------------------------------------------------ */
+int flood_fp32_peak_probe(int32_t packed, int64_t iterations, double* flops_out, void* stream);
+
+/* ------------------------------------------------------------------------
  * flood_complex_faces — faces of Del(L) and facet incidence, on the device.
  *
  * The discretised complex of §4.1 admits a simplex only after all of its
@@ -423,7 +502,8 @@ typedef struct flood_serve_config {
     int32_t gpu_workers;            /* host threads driving FPS + grid (>= 1) */
     int32_t triangulation_workers;  /* host threads calling triangulate (>= 1) */
     float landmark_fraction;        /* n_landmarks when a request passes 0: round(fraction * N), >= 4 */
-    float cell_factor;              /* grid cell = cell_factor * FPS covering radius (> 0) */
+    float cell_factor;              /* grid cell = cell_factor * FPS covering radius (> 0), or 0: the
+                                       tuning table's factor for each request's bucket */
     flood_triangulate_fn triangulate;
     flood_release_fn release;       /* may be NULL */
     void* user;
@@ -465,6 +545,54 @@ int flood_serve_release(flood_server* server, uint64_t ticket);
 int flood_serve_stats(flood_server* server, flood_serve_stats_t* out);
 /* Stop the threads (waiting for in-flight work) and free everything. */
 void flood_serve_destroy(flood_server* server);
+
+/* ------------------------------------------------------------------------
+ * Tuning table: launch parameters of the filtration per workload bucket.
+ *
+ * Not in the paper. Two parameters change the speed of a filtration but not
+ * its results (values and sources are bitwise the same for every choice):
+ *   cell_factor   grid cell edge as a multiple of the FPS covering radius
+ *                 (sqrt of the last FPS key); used by the serving loop and by
+ *                 callers that size flood_build_grid's cells from FPS;
+ *   heavy_shells  sample groups whose bound allows at least this many shells
+ *                 of cells are run one per CTA instead of one per warp
+ *                 (flood_filtration and its variants look it up per call).
+ * Entries are keyed by (SM count, round(log2 points), round(log2 landmarks),
+ * m); a lookup returns the entry of the nearest bucket (distance |d log2
+ * points| + |d log2 landmarks| + |d m| / 4) among entries for the current
+ * device's SM count, else the defaults (0.5, 9). The paper_2509_22432_b300.tune
+ * module measures entries and writes them to a file; FLOOD_TUNE_CACHE names
+ * a file loaded at the first use of the table. The table is process-wide and
+ * thread-safe.
+ * File format: one entry per line, "sm_count log2_points log2_landmarks m
+ * cell_factor heavy_shells"; '#' starts a comment line.
+ * ------------------------------------------------------------------------ */
+typedef struct flood_tuning {
+    float cell_factor;
+    int32_t heavy_shells;
+    int32_t tuned;           /* 1: from a table entry; 0: defaults */
+} flood_tuning;
+
+typedef struct flood_tuning_entry {
+    int32_t sm_count;        /* >= 1 */
+    int32_t log2_points;     /* 0..40 */
+    int32_t log2_landmarks;  /* 0..40 */
+    int32_t m;               /* 1..FLOOD_MAX_M */
+    float cell_factor;       /* (0, 64] */
+    int32_t heavy_shells;    /* 1..63 */
+} flood_tuning_entry;
+
+/* Parameters for a workload (host output). Errors: FLOOD_EINVAL. */
+int flood_tuning_lookup(int64_t n_points, int32_t n_landmarks, int32_t m, flood_tuning* out);
+/* Add or replace the entry of e's bucket. Errors: FLOOD_EINVAL (out of range). */
+int flood_tuning_set(const flood_tuning_entry* e);
+/* Add or replace entries from a file; *n_loaded (nullable) receives how many.
+ * Errors: FLOOD_EINVAL (unreadable file or bad line; entries before it stay). */
+int flood_tuning_load(const char* path, int32_t* n_loaded);
+/* Copy up to `capacity` entries to out (host); *n_entries receives the total. */
+int flood_tuning_entries(flood_tuning_entry* out, int32_t capacity, int32_t* n_entries);
+/* Remove every entry (lookups return the defaults until entries are added). */
+int flood_tuning_clear(void);
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* flood_last_error(void);

@@ -42,6 +42,19 @@ class FiltrationStats(C.Structure):
     ]
 
 
+class FpsStats(C.Structure):
+    _fields_ = [("picks", C.c_int64), ("rounds", C.c_int64), ("blocks", C.c_int32), ("resident", C.c_int32)]
+
+
+class TuningEntry(C.Structure):
+    _fields_ = [("sm_count", C.c_int32), ("log2_points", C.c_int32), ("log2_landmarks", C.c_int32),
+                ("m", C.c_int32), ("cell_factor", C.c_float), ("heavy_shells", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("cell_factor", C.c_float), ("heavy_shells", C.c_int32), ("tuned", C.c_int32)]
+
+
 P4 = C.c_void_p * 4
 I64x4 = C.c_int64 * 4
 I32x4 = C.c_int32 * 4
@@ -100,6 +113,13 @@ _SIGNATURES = {
                                    C.c_void_p]),
     "flood_fps_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "flood_last_fps_stats": (C.c_int, [C.POINTER(FpsStats)]),
+    "flood_fps_scratch_bytes": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(C.c_int64)]),
+    "flood_fps_wait_test": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint32,
+                                      C.c_void_p, C.c_void_p]),
+    "flood_masking_ball_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, C.POINTER(C.c_int64),
+                                            C.c_void_p]),
+    "flood_fp32_peak_probe": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_double), C.c_void_p]),
     "flood_build_grid": (C.c_int, [C.c_void_p, C.c_int64, C.c_float, C.POINTER(C.c_void_p), C.c_void_p]),
     "flood_grid_get_info": (C.c_int, [C.c_void_p, C.POINTER(GridInfo)]),
     "flood_grid_destroy": (None, [C.c_void_p]),
@@ -118,6 +138,11 @@ _SIGNATURES = {
     "flood_filtration_batch": (C.c_int, [C.POINTER(FiltrationJob), C.c_int32, C.c_void_p]),
     "flood_filtration_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P4, I64x4, C.c_int32, P4, P4,
                                             C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flood_tuning_lookup": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.POINTER(Tuning)]),
+    "flood_tuning_set": (C.c_int, [C.POINTER(TuningEntry)]),
+    "flood_tuning_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_int32)]),
+    "flood_tuning_entries": (C.c_int, [C.POINTER(TuningEntry), C.c_int32, C.POINTER(C.c_int32)]),
+    "flood_tuning_clear": (C.c_int, []),
     "flood_last_error": (C.c_char_p, []),
     "flood_version": (C.c_char_p, []),
     "flood_kernel_launches": (C.c_int64, []),

@@ -168,10 +168,12 @@ struct FpsArgs {
     int64_t* out_idx;
     float* out_key;
     uint64_t* slots;   // 2 (parity) x kMaxBlocks lines of kSlotStride words
-    uint32_t* flags;
+    uint32_t* flags;   // [0] status flags, [1..6] ordered box, [7] exchange rounds
     int32_t lane_pts;  // global kernel: points per lane of a chunk (multiple of 8)
     int32_t chunks_per_block;
     int64_t n_chunks;
+    int32_t poll_blocks;  // blocks whose slots the exchange waits for (gridDim.x)
+    uint32_t poll_limit;  // polls before a wait gives up (kWaitPolls)
 };
 
 // ---------------------------------------------------------------- rounds
@@ -328,7 +330,7 @@ static_assert(kMaxPicks <= 32, "one box-test lane per pick");
 __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int r, int h, int lane) {
     const uint64_t tag = static_cast<uint64_t>(r & 3) << 62;
     const uint64_t* buf = a.slots + static_cast<size_t>(r & 1) * kMaxBlocks * kSlotStride;
-    const int nb = gridDim.x, q = lane % kTop, bi = lane / kTop;
+    const int nb = a.poll_blocks, q = lane % kTop, bi = lane / kTop;
     uint64_t w0[kPollLoads], w1[kPollLoads], w2[kPollLoads], w3[kPollLoads];
     bool stop = false;
     for (uint32_t polls = 0;;) {
@@ -345,7 +347,7 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
 #pragma unroll
         for (int l = 0; l < kPollLoads; ++l) stale |= (w0[l] ^ tag) | (w1[l] ^ tag) | (w2[l] ^ tag) | (w3[l] ^ tag);
         if (__all_sync(0xffffffffu, (stale >> 62) == 0ull)) break;
-        if (++polls > kWaitPolls) {
+        if (++polls > a.poll_limit) {
             stop = true;
             if (lane == 0) atomicOr(a.flags, FLAG_TIMEOUT);
             break;
@@ -520,6 +522,8 @@ __device__ __forceinline__ void exchange_loop(const FpsArgs& a, FpsShared& s, in
             bar_wait(kBarPicks, kThreads);
         }
         const int n = take_picks(a, s, j);
+        // block 0's X1 counts the rounds (off the critical path, like the picks it records)
+        if (blockIdx.x == 0 && warp == kX0 + 1 && lane == 0) a.flags[7] = static_cast<uint32_t>(r);
         if (n == 0) break;
         j += n;
     }
@@ -971,13 +975,42 @@ int morton_bits(int64_t n) {
 
 // The whole FPS on `s`; scratch from `al` (stream-ordered allocations, or a
 // fixed buffer). *flags_out receives the device status word.
+// Scratch bytes of run_fps for n points and launch shape p, as its allocator
+// carves them (every piece rounded up to 256 bytes): the control words, the
+// exchange slots, the point order, the running minima when the points do not
+// stay on chip, and the Morton sort's codes, histogram, offsets and scan.
+size_t fps_scratch_bytes(int64_t n, const FpsPlan& p) {
+    auto piece = [](size_t bytes) { return (std::max<size_t>(bytes, 1) + 255) & ~size_t(255); };
+    size_t b = piece(8 * 4) + piece(2 * kMaxBlocks * kSlotStride * 8) + piece(16 * size_t(n));
+    if (!p.resident) b += piece(4 * size_t(n));
+    if (n > kSortMin) {
+        const int64_t codes = int64_t(1) << (3 * morton_bits(n));
+        b += piece(4 * size_t(n)) + piece(4 * size_t(codes)) + piece(4 * size_t(codes + 1)) +
+             exclusive_scan_scratch_bytes(codes);
+    }
+    return b;
+}
+
+// Test support: the exchange waits for `extra_blocks` blocks that are never
+// launched and gives up after `poll_limit` polls (0: the normal bound).
+struct FpsWaitTest {
+    int extra_blocks = 0;
+    uint32_t poll_limit = 0;
+};
+
 template <class Alloc>
 int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n_blocks, int64_t* out_idx,
-            float* out_key, cudaStream_t s, Alloc& al, uint32_t** flags_out) {
+            float* out_key, cudaStream_t s, Alloc& al, uint32_t** flags_out, FpsPlan* plan_out = nullptr,
+            const FpsWaitTest& wt = FpsWaitTest()) {
     FpsPlan plan;
     int rc = plan_fps(n, n_blocks, &plan);
     if (rc) return rc;
-    uint32_t* ctl;  // [0] flags, [1..6] ordered box
+    if (plan_out) *plan_out = plan;
+    if (wt.extra_blocks < 0 || plan.blocks + wt.extra_blocks > kMaxBlocks || (wt.extra_blocks > 0 && plan.blocks < 2)) {
+        set_error("flood_fps: a wait test needs at least 2 launched blocks and at most %d in all", kMaxBlocks);
+        return FLOOD_EINVAL;
+    }
+    uint32_t* ctl;  // [0] flags, [1..6] ordered box, [7] exchange rounds
     uint64_t* slots;
     float4* pts;
     float* d = nullptr;
@@ -988,6 +1021,7 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
     *flags_out = ctl;
     // Slot tags must start from zero (stale tags could match iterations 1 or 2).
     FLOOD_CUDA(cudaMemsetAsync(slots, 0, sizeof(uint64_t) * 2 * kMaxBlocks * kSlotStride, s));
+    FLOOD_CUDA(cudaMemsetAsync(ctl, 0, sizeof(uint32_t) * 8, s));
     k_box_init<<<1, 1, 0, s>>>(ctl + 1, ctl);
     note_launch();
     const unsigned grid = static_cast<unsigned>(ceil_div(n, 256));
@@ -1010,8 +1044,30 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
         note_launch();
     }
     FLOOD_CUDA(cudaGetLastError());
-    FpsArgs a{X, pts, d, n, n_landmarks, start, out_idx, out_key, slots, ctl, 0, 0, 0};
+    FpsArgs a{X,     pts,   d, n, n_landmarks, start, out_idx, out_key, slots, ctl, 0, 0, 0,
+              plan.blocks + wt.extra_blocks, wt.poll_limit ? wt.poll_limit : kWaitPolls};
     return launch_fps_kernel(plan, a, s);
+}
+
+thread_local flood_fps_stats g_fps_stats;
+
+// Wait for `s`, read the status and the round count, and turn the status
+// into a flood_status; the statistics of a successful call are kept for
+// flood_last_fps_stats.
+int fps_finish(cudaStream_t s, const uint32_t* ctl, const FpsPlan& plan, int32_t n_landmarks, const char* where) {
+    uint32_t h[8] = {};
+    FLOOD_CUDA(cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FLOOD_CUDA(cudaStreamSynchronize(s));
+    const int rc = status_from_flags(h[0], where);
+    if (rc == FLOOD_OK) {
+        flood_fps_stats st{};
+        st.picks = n_landmarks;
+        st.rounds = h[7];
+        st.blocks = plan.blocks;
+        st.resident = plan.resident ? 1 : 0;
+        g_fps_stats = st;
+    }
+    return rc;
 }
 
 bool fps_args_ok(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start, const int64_t* out_idx) {
@@ -1035,12 +1091,55 @@ extern "C" int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_land
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
     Scratch scr(s);
     uint32_t* flags = nullptr;
-    int rc = run_fps(X, n_points, n_landmarks, start, n_blocks, out_idx, out_key, s, scr, &flags);
+    FpsPlan plan{};
+    int rc = run_fps(X, n_points, n_landmarks, start, n_blocks, out_idx, out_key, s, scr, &flags, &plan);
     if (rc) {
         if (flags) cudaStreamSynchronize(s);
         return rc;
     }
-    return finish(s, flags, "flood_fps");
+    return fps_finish(s, flags, plan, n_landmarks, "flood_fps");
+}
+
+extern "C" int flood_last_fps_stats(flood_fps_stats* out) {
+    if (!out) {
+        set_error("flood_last_fps_stats: out is NULL");
+        return FLOOD_EINVAL;
+    }
+    *out = g_fps_stats;
+    return FLOOD_OK;
+}
+
+extern "C" int flood_fps_scratch_bytes(int64_t n_points, int32_t n_blocks, int64_t* out_bytes) {
+    if (!out_bytes || n_points < 1 || n_points >= (int64_t(1) << 31) - 1) {
+        set_error("flood_fps_scratch_bytes: need out_bytes != NULL and 1 <= n_points < 2^31 - 1");
+        return FLOOD_EINVAL;
+    }
+    FpsPlan plan;
+    int rc = plan_fps(n_points, n_blocks, &plan);
+    if (rc) return rc;
+    *out_bytes = static_cast<int64_t>(fps_scratch_bytes(n_points, plan));
+    return FLOOD_OK;
+}
+
+extern "C" int flood_fps_wait_test(const float* X, int64_t n_points, int32_t n_landmarks, int32_t n_blocks,
+                                   int32_t extra_blocks, uint32_t poll_limit, int64_t* out_idx, void* stream_) {
+    if (!fps_args_ok(X, n_points, n_landmarks, 0, out_idx) || n_blocks < 2 || extra_blocks < 1 || poll_limit < 1) {
+        set_error("flood_fps_wait_test: need valid FPS arguments, n_blocks >= 2, extra_blocks >= 1, poll_limit >= 1");
+        return FLOOD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    Scratch scr(s);
+    uint32_t* flags = nullptr;
+    FpsPlan plan{};
+    FpsWaitTest wt;
+    wt.extra_blocks = extra_blocks;
+    wt.poll_limit = poll_limit;
+    int rc = run_fps(X, n_points, n_landmarks, 0, n_blocks, out_idx, nullptr, s, scr, &flags, &plan, wt);
+    if (rc) {
+        if (flags) cudaStreamSynchronize(s);
+        return rc;
+    }
+    return fps_finish(s, flags, plan, n_landmarks, "flood_fps_wait_test");
 }
 
 extern "C" int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start, int64_t* out_idx,
@@ -1118,10 +1217,18 @@ extern "C" int flood_fps_noalloc(const float* X, int64_t n_points, int32_t n_lan
     if (rc) return rc;
     Bump al{base, kNoAllocBytes};
     uint32_t* flags = nullptr;
-    rc = run_fps(X, n_points, n_landmarks, start, 0, out_idx, out_key, s, al, &flags);
+    FpsPlan plan{};
+    rc = run_fps(X, n_points, n_landmarks, start, 0, out_idx, out_key, s, al, &flags, &plan);
     if (rc) {
         if (flags) cudaStreamSynchronize(s);
         return rc;
     }
-    return finish(s, flags, "flood_fps_noalloc");
+    rc = fps_finish(s, flags, plan, n_landmarks, "flood_fps_noalloc");
+    // the carved pieces must be exactly what flood_fps_scratch_bytes reports
+    if (rc == FLOOD_OK && kNoAllocBytes - al.left != fps_scratch_bytes(n_points, plan)) {
+        set_error("flood_fps_noalloc: scratch used (%zu bytes) differs from the computed size (%zu bytes)",
+                  kNoAllocBytes - al.left, fps_scratch_bytes(n_points, plan));
+        return FLOOD_EINTERNAL;
+    }
+    return rc;
 }

@@ -196,6 +196,64 @@ __global__ void __launch_bounds__(kMThreads) k_masked(MaskedArgs a) {
     if (tid == 0 && my_pairs) atomicAdd(a.pairs, my_pairs);
 }
 
+// |X ∩ B(c, rho)| per simplex, summed per dimension: the masking ball of
+// Lemma 2 as k_masked builds it (c the midpoint of the longest edge, rho =
+// sqrt(2) max_i |c - v_i|, or that maximum for an edge), without k_masked's
+// safety margin. One warp per simplex walks the rows of the ball's cell box.
+__global__ void k_ball_counts(int k, int64_t n, const int32_t* simplices, const float* L, int32_t n_L, GridView g,
+                              unsigned long long* count, uint32_t* flags) {
+    const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const int32_t* ids = simplices + w * (k + 1);
+    float V[4][3];
+    for (int j = 0; j <= k; ++j) {
+        const int32_t v = ids[j];
+        if (v < 0 || v >= n_L) {
+            if (lane == 0) atomicOr(flags, FLAG_RANGE);
+            return;
+        }
+        V[j][0] = L[3 * v];
+        V[j][1] = L[3 * v + 1];
+        V[j][2] = L[3 * v + 2];
+    }
+    int ia = 0, ib = 1;
+    float best = -1.0f;
+    for (int i = 0; i <= k; ++i)
+        for (int j = i + 1; j <= k; ++j) {
+            const float dx = V[i][0] - V[j][0], dy = V[i][1] - V[j][1], dz = V[i][2] - V[j][2];
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 > best) {
+                best = d2;
+                ia = i;
+                ib = j;
+            }
+        }
+    const float c[3] = {0.5f * (V[ia][0] + V[ib][0]), 0.5f * (V[ia][1] + V[ib][1]), 0.5f * (V[ia][2] + V[ib][2])};
+    float r2 = 0.0f;
+    for (int i = 0; i <= k; ++i) {
+        const float dx = V[i][0] - c[0], dy = V[i][1] - c[1], dz = V[i][2] - c[2];
+        r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+    }
+    const float R2 = k == 1 ? r2 : 2.0f * r2;
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    const CellBox b = cull_box(g, c, zero, zero, sqrtf(R2));
+    const int rows = b.n[1] * b.n[2];
+    unsigned long long cnt = 0;
+    for (int r = 0; r < rows; ++r) {
+        int32_t rb, re;
+        box_row(g, b, r, rb, re);
+        for (int32_t i = rb + lane; i < re; i += 32) {
+            const float4 x = g.pts[i];
+            const float dx = x.x - c[0], dy = x.y - c[1], dz = x.z - c[2];
+            cnt += dx * dx + dy * dy + dz * dz <= R2;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(count, cnt);
+}
+
 // Full grid of Lemma 1: compositions of m into k+1 parts >= 0, lexicographic.
 std::vector<uint8_t> full_table(int m, int k) {
     std::vector<uint8_t> out;
@@ -282,5 +340,39 @@ extern "C" int flood_filtration_masked(const flood_grid* grid, const float* L, i
     FLOOD_CUDA(cudaMemcpyAsync(&h_pairs, pairs, sizeof(h_pairs), cudaMemcpyDeviceToHost, s));
     if ((rc = finish(s, flags, "flood_filtration_masked"))) return rc;
     if (pairs_out) *pairs_out = static_cast<int64_t>(h_pairs);
+    return FLOOD_OK;
+}
+
+extern "C" int flood_masking_ball_counts(const flood_grid* grid, const float* L, int32_t n_landmarks,
+                                         const int32_t* const simplices[4], const int64_t n_simplices[4],
+                                         int64_t counts_out[4], void* stream) {
+    if (!grid || !L || n_landmarks < 1 || !simplices || !n_simplices || !counts_out) {
+        set_error("flood_masking_ball_counts: NULL argument or n_landmarks < 1");
+        return FLOOD_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch scr(s);
+    uint32_t* flags;
+    unsigned long long* cnt;
+    int rc;
+    if ((rc = scr.alloc(&flags, 1)) || (rc = scr.alloc(&cnt, 4))) return rc;
+    FLOOD_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), s));
+    FLOOD_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
+    for (int k = 1; k <= 3; ++k) {
+        if (n_simplices[k] <= 0) continue;
+        if (!simplices[k]) {
+            set_error("flood_masking_ball_counts: simplices[%d] is NULL", k);
+            return FLOOD_EINVAL;
+        }
+        const unsigned blocks = static_cast<unsigned>(ceil_div(n_simplices[k] * 32, 256));
+        k_ball_counts<<<blocks, 256, 0, s>>>(k, n_simplices[k], simplices[k], L, n_landmarks, view_of(grid), cnt + k,
+                                             flags);
+        note_launch();
+        FLOOD_CUDA(cudaGetLastError());
+    }
+    unsigned long long h[4] = {0, 0, 0, 0};
+    FLOOD_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    if ((rc = finish(s, flags, "flood_masking_ball_counts"))) return rc;
+    for (int k = 0; k < 4; ++k) counts_out[k] = static_cast<int64_t>(h[k]);
     return FLOOD_OK;
 }

@@ -106,6 +106,13 @@ int scan_total(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Alloc
 
 }  // namespace
 
+size_t exclusive_scan_scratch_bytes(int64_t n) {
+    size_t b = 0;
+    for (int64_t tiles = ceil_div(n, kScanTile); n > 0 && tiles > 1; n = tiles, tiles = ceil_div(n, kScanTile))
+        b += 2 * ((size_t(4) * tiles + 255) & ~size_t(255));  // block sums and their offsets
+    return b;
+}
+
 int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, Scratch& scr) {
     return scan_total(in, out, n, s, scr);
 }

@@ -16,7 +16,8 @@ import torch
 from . import _lib
 from ._lib import FloodError, P4, I64x4, I32x4
 
-__all__ = ["fps", "fps_noalloc", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
+__all__ = ["fps", "fps_noalloc", "fps_stats", "fps_scratch_bytes", "fps_wait_test", "masking_ball_counts",
+           "fp32_peak_probe", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
            "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
            "complex_faces", "filtration_masked",
            "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given"]
@@ -71,6 +72,42 @@ def fps_noalloc(X: torch.Tensor, n_landmarks: int, start: int = 0):
                                           _ptr(key), _stream_ptr(X.device))
     _lib.check(st, "flood_fps_noalloc")
     return idx, key
+
+
+def fps_stats() -> dict:
+    """Counters of this thread's last successful FPS call: picks, exchange rounds, blocks, resident."""
+    st = _lib.FpsStats()
+    _lib.check(_lib.get().flood_last_fps_stats(C.byref(st)), "flood_last_fps_stats")
+    return {"picks": int(st.picks), "rounds": int(st.rounds), "blocks": int(st.blocks),
+            "resident": bool(st.resident)}
+
+
+def fps_scratch_bytes(n_points: int, n_blocks: int = 0) -> int:
+    """Device scratch bytes flood_fps_blocks takes for n_points at launch width n_blocks (host arithmetic)."""
+    out = C.c_int64(0)
+    _lib.check(_lib.get().flood_fps_scratch_bytes(int(n_points), int(n_blocks), C.byref(out)),
+               "flood_fps_scratch_bytes")
+    return int(out.value)
+
+
+def fps_wait_test(X: torch.Tensor, n_landmarks: int, n_blocks: int, extra_blocks: int, poll_limit: int) -> int:
+    """Run FPS with an exchange that waits for never-launched blocks; returns the raw status (test support)."""
+    X = _points(X, "X")
+    idx = torch.full((n_landmarks,), -1, dtype=torch.int64, device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.get().flood_fps_wait_test(_ptr(X), X.shape[0], int(n_landmarks), int(n_blocks), int(extra_blocks),
+                                            int(poll_limit), _ptr(idx), _stream_ptr(X.device))
+    return int(st)
+
+
+def fp32_peak_probe(device: torch.device, packed: bool, iterations: int) -> float:
+    """Enqueue the FP32 FMA throughput kernel on the current stream; returns its flop count."""
+    flops = C.c_double(0.0)
+    with torch.cuda.device(device):
+        st = _lib.get().flood_fp32_peak_probe(int(bool(packed)), int(iterations), C.byref(flops),
+                                              _stream_ptr(device))
+    _lib.check(st, "flood_fp32_peak_probe")
+    return float(flops.value)
 
 
 class Grid:
@@ -156,6 +193,19 @@ def filtration_masked(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int):
                                                 _stream_ptr(L.device))
     _lib.check(st, "flood_filtration_masked")
     return vals, int(pairs.value)
+
+
+def masking_ball_counts(grid: Grid, L: torch.Tensor, cx: DeviceComplex) -> list:
+    """Per dimension, the number of (simplex, point) incidences with the point in the simplex's
+    Lemma 2 masking ball (§4.2): sum over k-simplices of |X ∩ B(c, sqrt(2) r)|."""
+    L = _points(L, "L")
+    s, _, n = cx.arrays()
+    out = I64x4(0, 0, 0, 0)
+    with torch.cuda.device(L.device):
+        st = _lib.get().flood_masking_ball_counts(grid.handle, _ptr(L), L.shape[0], s, n, out,
+                                                  _stream_ptr(L.device))
+    _lib.check(st, "flood_masking_ball_counts")
+    return [int(v) for v in out]
 
 
 def complex_faces(tets: torch.Tensor, n_vertices: int) -> DeviceComplex:

@@ -128,3 +128,15 @@ def test_header_is_plain_c():
         r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                             "-I", os.path.join(ROOT, "include"), src], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_noalloc_fixed_array_holds_fps_scratch_at_its_maximum_size():
+    """flood_fps_noalloc's fixed array (27 MiB) must hold FPS's scratch for 2^20 points at any
+    launch width; the largest need is the streamed kernel (one block), which adds 4 bytes of
+    running minimum per point."""
+    from paper_2509_22432_b300 import ops
+
+    worst = ops.fps_scratch_bytes(1 << 20, 1)
+    assert worst >= (16 + 4 + 4) << 20                    # point copy, running minima, Morton codes
+    assert worst <= 27 << 20, worst
+    assert ops.fps_scratch_bytes(1000, 1) < ops.fps_scratch_bytes(100_000, 1)

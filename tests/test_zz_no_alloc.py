@@ -31,6 +31,26 @@ def test_noalloc_fps_matches_fps_on_two_calls_in_a_row():
         assert np.array_equal(key.cpu().numpy().view(np.uint32), key_ref.cpu().numpy().view(np.uint32))
 
 
+def test_noalloc_fps_at_its_maximum_size_against_fps_and_the_oracle():
+    """Exactly 2^20 points, the documented maximum; the picks are also checked against the
+    oracle (integers: exact equality). The library checks on every call that the pieces it
+    carved from the fixed array add up to flood_fps_scratch_bytes, whose worst case over the
+    launch widths (points streamed from memory) a CPU test compares with the array's size."""
+    from paper_2509_22432_b300 import ops
+    import oracle
+
+    X = data.shape_mix_cloud(1 << 20, seed=21)
+    Xd = torch.from_numpy(X).cuda()
+    for _ in range(2):                                  # two calls in a row share the array
+        idx, key = ops.fps_noalloc(Xd, 200, 0)
+        idx_ref, key_ref = ops.fps(Xd, 200, 0)
+        assert torch.equal(idx, idx_ref)
+        assert np.array_equal(key.cpu().numpy().view(np.uint32), key_ref.cpu().numpy().view(np.uint32))
+    ri, rk = oracle.fps(X, 200, 0)
+    assert np.array_equal(idx.cpu().numpy(), ri)
+    assert np.array_equal(key.cpu().numpy().view(np.uint32), rk.view(np.uint32))
+
+
 def test_noalloc_fps_rejects_more_points_than_its_fixed_maximum():
     from paper_2509_22432_b300 import ops
 
