@@ -113,6 +113,9 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int device_sm_count();
 
+// Tuned launch parameters for a workload bucket (tuning table, or defaults).
+flood_tuning tuning_for(int64_t n_points, int32_t n_landmarks, int32_t m);
+
 // Process-wide count of kernels this library has launched (reported by
 // flood_kernel_launches for launch accounting).
 void note_launch(int n = 1);

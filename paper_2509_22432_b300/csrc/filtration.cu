@@ -359,7 +359,7 @@ __global__ void k_group_class_count(DimArgs a, const int32_t* n_groups, int32_t*
 }
 
 // Every block takes the exclusive scan of the kClasses counts itself (block 0
-// also stores it: entry kClasses - kHeavyShells is the heavy prefix), then
+// also stores it: entry kClasses - heavy_shells is the heavy prefix), then
 // places its groups.
 __global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const int32_t* class_count,
                                       int32_t* class_start, int32_t* class_fill, int2* sorted) {
@@ -826,7 +826,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
 // warp kernel's (W sample lanes x 256/W point streams) stretched over the CTA,
 // and per-sample minima are combined in shared memory.
 constexpr int kHeavyTile = 4096;
-constexpr int kHeavyShells = 9;  // class threshold: groups with >= this many shells are heavy
 
 // Evaluate the NSL used sample slots of one tile (NSL <= kHeavyNS); slots are
 // paired for packed FMAs (the same three rounded FMAs per pair, in order).
@@ -1425,6 +1424,7 @@ struct JobState {
     int2 *groups, *groups_sorted;
     SampleRec* recs;
     float shell_slack;
+    int heavy_shells;  // groups with at least this many shells go to the CTA kernel
 };
 
 int check_job(const flood_filtration_job& j, int idx) {
@@ -1567,6 +1567,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
         const float amax =
             std::max(std::fabs(grid->origin[0]), std::max(std::fabs(grid->origin[1]), std::fabs(grid->origin[2])));
         J.shell_slack = (amax + emax) * (1.0f / 262144.0f);
+        J.heavy_shells = tuning_for(grid->n_points, J.in.n_landmarks, J.in.m).heavy_shells;
     }
     DimArgs* d_jobs;
     int32_t *d_off, *d_counts;
@@ -1644,8 +1645,8 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             note_launch();
             FLOOD_CUDA(cudaGetLastError());
             a.groups = J.groups_sorted;
-            // heavy groups: shell bound >= kHeavyShells, i.e. classes [0, kClasses - kHeavyShells)
-            a.n_heavy = cls + 2 * kClasses + (kClasses - kHeavyShells);
+            // heavy groups: shell bound >= heavy_shells, i.e. classes [0, kClasses - heavy_shells)
+            a.n_heavy = cls + 2 * kClasses + (kClasses - J.heavy_shells);
             FLOOD_CUDA(cudaMemcpyAsync(d_counts + i * 4 + k, n_groups, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
             h_jobs.push_back(a);
         }

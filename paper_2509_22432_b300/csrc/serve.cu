@@ -184,7 +184,8 @@ int gpu_stage(flood_server* s, Request* r, cudaStream_t st) {
         cudaSuccess)
         return cuda_fail(cudaGetLastError(), "serve: copy L");
     const float cover = (r->n_L > 1 && std::isfinite(last_key)) ? std::sqrt(last_key) : 0.0f;
-    const float cell = cover > 0.0f ? s->cfg.cell_factor * cover : 0.0f;
+    const float factor = s->cfg.cell_factor > 0.0f ? s->cfg.cell_factor : tuning_for(r->N, r->n_L, r->m).cell_factor;
+    const float cell = cover > 0.0f ? factor * cover : 0.0f;
     return flood_build_grid(r->X_dev, r->N, cell, &r->grid, st);
 }
 
@@ -378,7 +379,7 @@ using namespace flood;
 
 extern "C" int flood_serve_create(const flood_serve_config* cfg, flood_server** out) {
     if (!cfg || !out || cfg->device_budget_bytes <= 0 || cfg->max_inflight < 1 || cfg->max_batch < 1 ||
-        cfg->gpu_workers < 1 || cfg->triangulation_workers < 1 || !(cfg->cell_factor > 0.0f) ||
+        cfg->gpu_workers < 1 || cfg->triangulation_workers < 1 || !(cfg->cell_factor >= 0.0f) ||
         !(cfg->landmark_fraction > 0.0f) || !cfg->triangulate) {
         set_error("flood_serve_create: invalid configuration");
         return FLOOD_EINVAL;
