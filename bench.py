@@ -37,24 +37,49 @@ WORKLOADS = {
 }
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
 FLOPS_PER_PAIR = 6               # one pair = 3 FMAs: |x'|^2 - 2 p'.x'
-# DRAM bytes (read + write) of one k_fps_resident launch on torus-1M, from one
-# ncu capture (profiles/k_fps_resident_torus-1M.md), valid only while the FPS
-# source is the one captured: reported as null once fps.cu changes.
-FPS_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 16_084_736 + 10_752,
-                    "fps_cu_sha256": "f7d7282ff41ccb5c33e4f7c3cae06bcc10b9f14969de5dd912944eeb780dcb36"}
+# DRAM bytes (read + write) of the flood kernels of one filtration on torus-1M
+# (k_flood_heavy and k_flood, dimensions 1-3: six launches), from one ncu
+# capture; valid only while the filtration source is the one captured, else
+# reported as null.
+FLOOD_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": None, "filtration_cu_sha256": None}
 
 
-def _fps_traffic(workload: str):
+def _source_sha(name: str):
     import hashlib
     try:
-        with open(os.path.join(ROOT, "paper_2509_22432_b300", "csrc", "fps.cu"), "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
+        with open(os.path.join(ROOT, "paper_2509_22432_b300", "csrc", name), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()
     except OSError:
         return None
-    cap = FPS_DRAM_CAPTURE
-    if workload != cap["workload"] or digest != cap["fps_cu_sha256"]:
+
+
+def _flood_traffic(workload: str):
+    cap = FLOOD_DRAM_CAPTURE
+    if cap["bytes"] is None or workload != cap["workload"]:
+        return None
+    if _source_sha("filtration.cu") != cap["filtration_cu_sha256"]:
         return None
     return float(cap["bytes"])
+
+
+def _golden_landmarks(workload: str, X):
+    """The oracle's FPS picks for this workload (tests/golden), if stored and X is the stored cloud."""
+    import hashlib
+    path = os.path.join(ROOT, "tests", "golden", f"fps_{workload}_oracle.txt")
+    if not os.path.exists(path):
+        return None
+    head, rows = {}, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                parts = line[1:].split()
+                if len(parts) == 2:
+                    head[parts[0]] = parts[1]
+            elif line.strip():
+                rows.append(int(line))
+    if hashlib.sha256(np.ascontiguousarray(X, np.float32).tobytes()).hexdigest() != head.get("x_sha256"):
+        return None
+    return np.array(rows, dtype=np.int64)
 
 
 def _peaks():
@@ -149,43 +174,74 @@ def make_inputs(wl: dict, seed_offset: int = 0):
     return gen(wl["n"], seed=wl["seed"] + seed_offset)
 
 
-def cpu_baseline(X, wl, budget_s: float = 20.0):
-    """The oracle as it stands, on a bounded sample of the same workload.
+def oracle_workload(X, wl, workload):
+    """Landmarks and complex of the workload for the oracle: the oracle's own FPS picks.
 
-    Sample: FPS for a fixed number of iterations on all of X, the FP64 k-d
-    tree over X, and flood values (full barycentric grid, FP64) of a random
-    sample of simplices; extrapolated to one full step in simplices/s.
+    For the full-size workloads they are stored under tests/golden (written by a
+    script that runs only the oracle); small clouds run the oracle's FPS here.
+    Returns (L, complex, where the landmarks came from).
     """
     import oracle
     from paper_2509_22432_b300 import delaunay_complex
-
-    t0 = time.perf_counter()
-    j = 24
-    idx, _ = oracle.fps(X, j, 0)
-    t_fps_iter = (time.perf_counter() - t0) / (j - 1)
-    t_fps = t_fps_iter * (wl["n_l"] - 1)
-    idx, _ = oracle.fps(X, min(wl["n_l"], 400), 0)     # landmarks for a representative complex
+    idx = _golden_landmarks(workload, X)
+    where = f"tests/golden/fps_{workload}_oracle.txt"
+    if idx is None:
+        if X.shape[0] * wl["n_l"] > 5e8:
+            return None, None, "no stored oracle picks for this cloud"
+        idx, _ = oracle.fps(X, wl["n_l"], 0)
+        where = "oracle.fps in this run"
     L = X[idx]
-    cx = delaunay_complex(L)
+    return L, delaunay_complex(L), where
+
+
+def oracle_sample_costs(X, L, cx, m, fps_iters, n_simplices, seed, index=None):
+    """Time the oracle on a bounded sample of the workload itself.
+
+    FPS: `fps_iters` iterations of oracle.fps over all of X (each pick costs one
+    pass over X, the same for every pick). Flood values: `n_simplices` simplices
+    drawn uniformly from the workload's own complex (dimensions 1-3, FP64 k-d
+    tree over the full grid). Returns per-pick and per-simplex seconds.
+    """
+    import oracle
+    t0 = time.perf_counter()
+    oracle.fps(X, fps_iters + 1, 0)
+    t_pick = (time.perf_counter() - t0) / fps_iters
+    counts = [cx.simplices[k].shape[0] for k in (1, 2, 3)]
+    rng = np.random.default_rng(seed)
+    draw = rng.choice(sum(counts), min(sum(counts), n_simplices), replace=False)
+    bounds = np.cumsum([0] + counts)
+    subset = [np.zeros(0, np.int64)] + [np.sort(draw[(draw >= bounds[i]) & (draw < bounds[i + 1])] - bounds[i])
+                                        for i in range(3)]
     t1 = time.perf_counter()
+    oracle.flood_values(X, L, cx.simplices, m, index=index, subset=subset)
+    t_simplex = (time.perf_counter() - t1) / max(1, len(draw))
+    return t_pick, t_simplex, len(draw)
+
+
+def cpu_baseline(X, wl, workload):
+    """The oracle as it stands, timed on a bounded sample of the workload's own complex.
+
+    Extrapolated to one step: per-pick FPS cost x (n_L - 1) + k-d tree build +
+    per-simplex cost x the complex's simplices (dimensions 1-3).
+    """
+    import oracle
+    L, cx, where = oracle_workload(X, wl, workload)
+    if cx is None:
+        return None
+    t0 = time.perf_counter()
     index = oracle.flood.KDIndex(X, "kdtree")
-    t_build = time.perf_counter() - t1
-    rng = np.random.default_rng(0)
-    per_dim, sampled = [], 0
-    remaining = max(1.0, budget_s - (time.perf_counter() - t0))
-    sub = [None] * 4
-    for k in (1, 2, 3):
-        n = cx.simplices[k].shape[0]
-        sub[k] = rng.choice(n, min(n, 300), replace=False)
-    t2 = time.perf_counter()
-    res = oracle.flood_values(X, L, cx.simplices, wl["m"], index=index,
-                              subset=[np.zeros(0, np.int64)] + sub[1:])
-    t_sample = time.perf_counter() - t2
-    sampled = sum(len(s) for s in sub[1:])
-    per_simplex = t_sample / sampled
-    return {"per_simplex_s": per_simplex, "t_fps_s": t_fps, "t_build_s": t_build, "sampled": sampled,
-            "note": f"FPS {j} iterations on all {X.shape[0]} points; k-d tree build; "
-                    f"flood values of {sampled} random simplices (dims 1-3) of a {L.shape[0]}-landmark Delaunay"}
+    t_build = time.perf_counter() - t0
+    fps_iters = max(8, int(2e8 // X.shape[0]))                  # a few seconds of FPS passes
+    t_pick, t_simplex, sampled = oracle_sample_costs(X, L, cx, wl["m"], fps_iters, 1500, seed=0, index=index)
+    n_simp = sum(cx.counts[1:])
+    step_s = t_pick * (wl["n_l"] - 1) + t_build + t_simplex * n_simp
+    return {"value": n_simp / step_s, "unit": "simplices/s", "cores": os.cpu_count(), "kind": "oracle",
+            "estimate": True, "step_s_estimated": step_s,
+            "sample": f"sample of the workload itself, extrapolated to one step: {fps_iters} FPS iterations over all "
+                      f"{X.shape[0]} points ({1e3 * t_pick:.1f} ms per pick, x {wl['n_l'] - 1} picks); FP64 k-d tree "
+                      f"build ({t_build:.2f} s); flood values of {sampled} simplices drawn uniformly from the "
+                      f"workload's own complex of {n_simp} ({1e3 * t_simplex:.2f} ms per simplex); landmarks: "
+                      f"{where}"}
 
 
 def serving_clouds(n_clouds: int, seed: int = 4):
@@ -194,6 +250,13 @@ def serving_clouds(n_clouds: int, seed: int = 4):
     from paper_2509_22432_b300 import data
     sizes = data.serving_sizes(n_clouds, seed=seed)
     return [data.shape_mix_cloud(int(n), seed=4000 + i) for i, n in enumerate(sizes)]
+
+
+def warm_serving(clouds, m: int = 8):
+    """Run a few clouds through both server modes first: the first requests of a process pay
+    one-time costs (kernel loading, memory-pool growth, imports) that are not serving latency."""
+    for batched in (True, False):
+        run_serving(clouds[:16], 2000.0, batched, m=m, device_faces=True)
 
 
 def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, device_faces: bool = False) -> dict:
@@ -226,19 +289,49 @@ def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, d
 
 
 def run_reference(args, wl):
-    """--impl reference: the FP64 oracle timed on the host cores."""
+    """--impl reference: the FP64 oracle, timed on the host cores, on this workload's own complex.
+
+    A full oracle step takes minutes (about 20 ms per FPS pick and a millisecond
+    per simplex on one host), so each timed step is a bounded sample of the
+    workload: a few FPS passes over all of X and a few dozen simplices of the
+    workload's complex. `value` extrapolates the measured per-pick and
+    per-simplex costs to one full step (marked as an estimate); ms_per_step is
+    the measured time of one sample step.
+    """
+    import oracle
     X = make_inputs(wl)
-    res = cpu_baseline(X, wl)
-    # simplex count of the full workload's complex, estimated from the landmark count
-    n_simplices = 28.1 * wl["n_l"]
-    step_s = res["t_fps_s"] + res["t_build_s"] + res["per_simplex_s"] * n_simplices
-    v = n_simplices / step_s
+    L, cx, where = oracle_workload(X, wl, args.workload)
+    if cx is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"{where}: the oracle's FPS on this cloud takes too "
+                                                              "long to run here"}))
+        return
+    t0 = time.perf_counter()
+    index = oracle.flood.KDIndex(X, "kdtree")
+    t_build = time.perf_counter() - t0
+    fps_iters, n_sample = 4, 40
+    picks, simps, step_ms = [], [], []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        tp, ts, _ = oracle_sample_costs(X, L, cx, wl["m"], fps_iters, n_sample, seed=100 + it, index=index)
+        if it >= args.warmup:
+            picks.append(tp)
+            simps.append(ts)
+            step_ms.append(1e3 * (time.perf_counter() - t0))
+    n_simp = sum(cx.counts[1:])
+    step_s = float(np.mean(picks)) * (wl["n_l"] - 1) + t_build + float(np.mean(simps)) * n_simp
+    v = n_simp / step_s
+    sample = (f"each step: {fps_iters} oracle FPS iterations over all {X.shape[0]} points and flood values of "
+              f"{n_sample} simplices drawn from the workload's own complex ({n_simp} simplices, landmarks: {where}); "
+              f"value extrapolates the mean per-pick and per-simplex costs to one full step "
+              f"({step_s:.1f} s estimated)")
     line = {"impl": "reference", "metric": "flood simplices/s", "value": v, "unit": "simplices/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
+            "ms_per_step_is": "measured time of one sample step (not a full oracle step)",
+            "full_step_s_estimated": step_s, "estimate": True,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n_points": wl["n"], "n_landmarks": wl["n_l"], "m": wl["m"]},
             "cpu_baseline": {"value": v, "unit": "simplices/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": res["note"]},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "simplices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -272,6 +365,7 @@ def main():
     if args.serving:
         if rank == 0:
             clouds = serving_clouds(512)
+            warm_serving(clouds)
             for rate in (50, 100, 200, 500, 1000, 2000):
                 for batched in (True, False):
                     r = run_serving(clouds, rate, batched, device_faces=True)
@@ -292,9 +386,12 @@ def main():
     L_host = X[idx0.cpu().numpy()]
     cx = delaunay_complex(L_host)
     dcx = ops.to_device(cx, dev)
-    grid0 = ops.build_grid(Xd, 0.0)
-    cell = 0.5 * float(np.sqrt(key0[-1].item()))           # half the FPS covering radius
-    grid0.close()
+    # launch parameters by the project's autotuner (untimed): grid cell factor and
+    # heavy-group threshold, measured on this workload and kept in the tuning table
+    from paper_2509_22432_b300 import tune
+    cover = float(np.sqrt(key0[-1].item()))                # FPS covering radius
+    tuned = tune.tune_workload(Xd, Xd[idx0], dcx, m, cover)
+    cell = tuned["cell_factor"] * cover
     n_simp = sum(cx.counts[1:])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (126 MB)
@@ -403,61 +500,112 @@ def main():
     peaks, peak_kind = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fps_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in phase_events]))
+
+    # ---- FP32 peak of this GPU, measured: a pure-FMA kernel (scalar and packed
+    # forms) timed with CUDA events, clocks sampled while it runs
+    def probe(packed, iters=40_000):
+        ops.fp32_peak_probe(dev, packed, 2000)
+        best = 0.0
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fl = ops.fp32_peak_probe(dev, packed, iters)
+            b.record(stream)
+            b.synchronize()
+            best = max(best, fl / (a.elapsed_time(b) * 1e-3) / 1e12)
+        return best
+
+    pclk = ClockSampler(local).__enter__()
+    time.sleep(0.3)
+    tp0 = time.monotonic()
+    peak_scalar, peak_packed = probe(False), probe(True)
+    pclk.mark(tp0, time.monotonic())
+    pclk.__exit__(None, None, None)
+    peak_tflops = max(peak_scalar, peak_packed)
+
+    # ---- flood kernels on the FP32 pipe: evaluated pairs x 6 flops / their event time
     pairs = sum(stats["pairs"])
     fk = float(np.mean(flood_ms))
     achieved = pairs * FLOPS_PER_PAIR / (fk * 1e-3) / 1e12
     queries = sum(stats["samples"][1:])
-    # FPS: algorithmic bytes of one iteration = 12N (coordinates) + 8N (read and
-    # write the running minimum); the kernel keeps them on chip, so this is an
-    # effective bandwidth against the measured HBM copy bandwidth.
-    fps_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in phase_events]))
-    fps_bytes = 20.0 * wl["n"] * (n_l - 1)
-    fps_gbs = fps_bytes / (fps_ms * 1e-3) / 1e9
-    hbm = float(peaks.get("hbm_gbs", 6400.0))
-    # Per-pick cost of the late picks (few chunks still change; the grid-wide
-    # exchange dominates): difference of two FPS calls, n_l and n_l / 2 picks.
+    # the method's own work (§8(d)): interior samples x points of X in each
+    # simplex's Lemma 2 masking ball, counted on the device
+    gb = ops.build_grid(Xd, cell)
+    ball = ops.masking_ball_counts(gb, Xd[idx0], dcx)
+    gb.close()
+    interior = [0] + [math.comb(m - 1, k) for k in (1, 2, 3)]
+    alg_pairs = sum(interior[k] * ball[k] for k in (1, 2, 3))
+
+    # ---- FPS: latency of the exchange rounds. Floor: the same launch width on
+    # a cloud of one chunk per block (the exchange with almost no chunk work).
+    fst = ops.fps_stats()
+    rounds = max(1, fst["rounds"])
     Xd_fps = torch.from_numpy(X).to(dev)
 
-    def fps_time(k):
+    def fps_time(Xs, k, nb=0):
         best = float("inf")
         for _ in range(3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            ops.fps(Xd_fps, k, 0)
+            ops.fps(Xs, k, 0, n_blocks=nb)
             b.record(stream)
             b.synchronize()
             best = min(best, a.elapsed_time(b))
-        return best
+        return best, ops.fps_stats()
 
-    late_us = 1e3 * (fps_time(n_l) - fps_time(n_l // 2)) / (n_l - n_l // 2)
-    del Xd_fps
+    late_us = 1e3 * (fps_time(Xd_fps, n_l)[0] - fps_time(Xd_fps, n_l // 2)[0]) / (n_l - n_l // 2)
+    small = torch.from_numpy(data.sphere_cloud(fst["blocks"] * 256, seed=77)).to(dev)
+    n_floor = min(n_l, small.shape[0])
+    floor_ms, floor_st = fps_time(small, n_floor, nb=fst["blocks"])
+    floor_round_us = 1e3 * floor_ms / max(1, floor_st["rounds"])
+    floor_pick_us = 1e3 * floor_ms / max(1, n_floor - 1)
+    round_us = 1e3 * fps_ms / rounds
+    pick_us = 1e3 * fps_ms / max(n_l - 1, 1)
+    del Xd_fps, small
     line = {
         "metric": "flood simplices/s", "value": total_simplices / (ms * 1e-3), "unit": "simplices/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "n_points": wl["n"], "n_landmarks": n_l, "m": m,
                    "simplices_per_step": n_simp, "simplex_counts": cx.counts, "cell_size": cell,
+                   "tuning": {"cell_factor": tuned["cell_factor"], "heavy_shells": tuned["heavy_shells"],
+                              "grid_and_filtration_ms": tuned["ms"], "at_defaults_ms": tuned["default_ms"],
+                              "by": "paper_2509_22432_b300.tune: every (cell factor, heavy threshold) candidate "
+                                    "timed with CUDA events on this workload before the timed steps"},
                    "l2": "flushed between steps (256 MB write)", "delaunay": "host, untimed, computed once",
                    "parallelism": f"replicas x{world}"},
         "nn_queries_per_s": world * queries / (ms * 1e-3),
         "pairs_per_step": pairs,
-        "phase_ms": {"fps": float(np.mean([e[0].elapsed_time(e[1]) for e in phase_events])),
+        "phase_ms": {"fps": fps_ms,
                      "grid": float(np.mean([e[1].elapsed_time(e[2]) for e in phase_events])),
                      "filtration": float(np.mean([e[2].elapsed_time(e[3]) for e in phase_events])),
                      "flood_kernels": fk},
-        "roofline": {"bound": "hbm", "achieved": fps_gbs, "peak": hbm, "unit": "GB/s", "frac": fps_gbs / hbm,
-                     "traffic": _fps_traffic(args.workload), "traffic_unit": "bytes per launch",
-                     "kernel": "k_fps_resident (FPS, dominant by time)", "effective": True,
-                     "algorithmic_bytes": "20 N per pick (12N coordinates + 8N running minima) of the streaming "
-                                          "algorithm; effective: points stay on chip and chunks whose minima "
-                                          "provably cannot change are skipped (exact)",
-                     "per_pick_us": 1e3 * fps_ms / max(n_l - 1, 1), "late_per_pick_us": late_us,
-                     "peak_kind": f"{peak_kind} hbm_gbs"},
-        "roofline_flood": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                           "frac": achieved / peak_tflops, "kernel": "k_flood + k_flood_heavy (all dims)",
-                           "flops_per_pair": FLOPS_PER_PAIR,
-                           "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": _flood_traffic(args.workload),
+                     "traffic_unit": "DRAM bytes of the six flood launches of one filtration (ncu)",
+                     "kernel": "k_flood_heavy + k_flood (dimensions 1-3), the largest stage of the step",
+                     "flops_per_pair": FLOPS_PER_PAIR,
+                     "evaluated_pairs": pairs,
+                     "algorithmic_pairs": alg_pairs,
+                     "algorithmic_pairs_are": "sum over simplices of C(m-1,k) interior samples x |X in the Lemma 2 "
+                                              "masking ball| (the method's own work); the kernels evaluate "
+                                              "evaluated_pairs of them after exact pruning",
+                     "algorithmic_over_evaluated": alg_pairs / max(1, pairs),
+                     "peak_kind": "measured in this run: pure-FMA kernel (flood_fp32_peak_probe), best of scalar "
+                                  "and packed forms",
+                     "peak_scalar": peak_scalar, "peak_packed": peak_packed, "peak_clocks": pclk.summary(),
+                     "nominal_peak": sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12},
+        "roofline_fps": {"bound": "latency", "kernel": "k_fps_resident" if fst["resident"] else "k_fps_global",
+                         "rounds": rounds, "picks": n_l, "blocks": fst["blocks"],
+                         "per_round_us": round_us, "per_pick_us": pick_us, "late_per_pick_us": late_us,
+                         "floor_per_round_us": floor_round_us, "floor_per_pick_us": floor_pick_us,
+                         "floor_rounds": floor_st["rounds"],
+                         "floor_is": f"the same kernel and launch width ({fst['blocks']} blocks) on a cloud of one "
+                                    f"256-point chunk per block, {n_floor} picks: the grid exchange and pick "
+                                    "selection with almost no chunk work",
+                         "frac": floor_pick_us / pick_us,
+                         "frac_is": "floor per pick / this workload's per pick"},
         "e2e": {"value": world * n_simp / e2e_s, "unit": "simplices/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -525,21 +673,23 @@ def main():
                              "tetrahedra: flood_complex_faces (call to return, synchronised) vs the host "
                              "numpy builder"}
     if rank == 0 and not args.no_serving:
-        clouds = serving_clouds(128)
-        b = run_serving(clouds, 500.0, True, device_faces=False)
-        bd = run_serving(clouds, 500.0, True, device_faces=True)
-        p = run_serving(clouds, 500.0, False, device_faces=False)
-        line["serving"] = {"workload": "128 clouds, 2k-200k points (log-uniform), shape mix, Poisson 500/s, "
-                                       "n_L = 2% of points, m = 8, host Delaunay included",
-                           "batched": b, "batched_device_faces": bd, "per_cloud": p,
-                           "modes": "batched and per_cloud: whole complex built on the host; "
-                                    "batched_device_faces (the server's default): tetrahedra from the host, "
-                                    "faces built on the device"}
+        clouds = serving_clouds(512)
+        warm_serving(clouds)
+        runs = {}
+        for rate in (50.0, 500.0):
+            runs[f"{rate:g}"] = {"batched": run_serving(clouds, rate, True, device_faces=True),
+                                 "per_cloud": run_serving(clouds, rate, False, device_faces=True)}
+        line["serving"] = {"workload": "512 clouds, 2k-200k points (log-uniform), shape mix, Poisson arrivals, "
+                                       "n_L = 2% of points, m = 8, host Delaunay (Qhull) included, faces built on "
+                                       "the device in both arms",
+                           "by_rate": runs,
+                           "arms": "batched: continuous batching (64 slots, batches of up to 64 clouds); per_cloud: "
+                                   "the same kernels one cloud at a time (one slot, batch 1)",
+                           "warm_up": "16 clouds through each server mode before the timed runs"}
     if rank == 0 and not args.no_cpu_baseline:
-        res = cpu_baseline(X, wl)
-        step_s = res["t_fps_s"] + res["t_build_s"] + res["per_simplex_s"] * n_simp
-        line["cpu_baseline"] = {"value": n_simp / step_s, "unit": "simplices/s", "cores": os.cpu_count(),
-                                "kind": "oracle", "sample": res["note"]}
+        cb = cpu_baseline(X, wl, args.workload)
+        if cb is not None:
+            line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

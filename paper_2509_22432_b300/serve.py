@@ -13,6 +13,9 @@ import ctypes as C
 import threading
 
 import numpy as np
+# imported here, not inside the callback: a first import from the library's
+# triangulation threads would hold up the first requests behind the import lock
+from scipy.spatial import Delaunay
 
 from . import _lib
 from ._lib import RELEASE, ServeConfig, ServeResult, ServeStats, TRIANGULATE
@@ -23,7 +26,6 @@ __all__ = ["Server"]
 
 def _delaunay_tets(L: np.ndarray) -> np.ndarray:
     """Tetrahedra of Del(L) (scipy/Qhull), ascending vertex ids, int32."""
-    from scipy.spatial import Delaunay
     return np.ascontiguousarray(np.sort(Delaunay(np.asarray(L, np.float64)).simplices, axis=1), dtype=np.int32)
 
 
