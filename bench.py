@@ -399,26 +399,29 @@ def main():
     phase_events = []
 
     def step(record=False):
+        # every call is asynchronous (no host wait inside the step); the stream's
+        # status is checked once at the end of the step (ops.check)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
         if record:
             ev[0].record(stream)
-        idx, key = ops.fps(Xd, n_l, 0)
+        idx, key = ops.fps(Xd, n_l, 0, sync=False)
         if record:
             ev[1].record(stream)
-        grid = ops.build_grid(Xd, cell)
+        grid = ops.build_grid(Xd, cell, sync=False)
         if record:
             ev[2].record(stream)
         L = Xd[idx]
-        vals, _ = ops.filtration(grid, L, dcx, m, want_src=False)
+        vals, _ = ops.filtration(grid, L, dcx, m, want_src=False, sync=False)
         if record:
             ev[3].record(stream)
             phase_events.append(ev)
-        grid.close()
-        return idx, vals
+        return idx, vals, grid
 
     clocks = ClockSampler(local).__enter__()  # running before the timed region; samples filtered to it
     for _ in range(args.warmup):
-        idx, vals = step()
+        idx, vals, grid = step()
+        ops.check(dev)
+        grid.close()
     assert torch.equal(idx, idx0), "FPS must be deterministic"
     stats = ops.last_filtration_stats()
 
@@ -435,9 +438,10 @@ def main():
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(record=True)
+            _, _, grid = step(record=True)
             e1.record(stream)
-            e1.synchronize()
+            ops.check(dev)                  # waits for the step; raises if any call of it failed
+            grid.close()
             times.append(e0.elapsed_time(e1))
             flood_ms.append(sum(ops.last_filtration_stats()["flood_kernel_ms"]))
         torch.cuda.synchronize()
@@ -459,13 +463,14 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Xg = Xh.to(dev, non_blocking=True)
-        idx, key = ops.fps(Xg, n_l, 0)
-        idx_h = idx.cpu()
+        idx, key = ops.fps(Xg, n_l, 0, sync=False)
+        idx_h = idx.cpu()                   # the landmarks go to the host (the triangulation's input)
         dc = ops.DeviceComplex(cx.n_vertices, [t.to(dev, non_blocking=True) for t in simp_h],
                                [t.to(dev, non_blocking=True) for t in fac_h])
-        grid = ops.build_grid(Xg, cell)
-        vals, _ = ops.filtration(grid, Xg[idx_h.to(dev)], dc, m, want_src=False)
+        grid = ops.build_grid(Xg, cell, sync=False)
+        vals, _ = ops.filtration(grid, Xg[idx_h.to(dev)], dc, m, want_src=False, sync=False)
         out = [v.cpu() for v in vals]
+        ops.check(dev)
         grid.close()
         torch.cuda.synchronize()
         if it >= args.warmup:

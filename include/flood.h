@@ -22,8 +22,15 @@
  *     by the caller except the opaque flood_grid, which the library owns and
  *     frees in flood_grid_destroy.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
- *     enqueued on it; entry points that must report device-side errors
- *     synchronise that stream before returning (stated per function).
+ *     enqueued on it. The hot-path calls (flood_fps, flood_fps_blocks,
+ *     flood_build_grid, flood_filtration, flood_filtration_batch,
+ *     flood_filtration_given) are asynchronous: they check their arguments on
+ *     the host, enqueue, and return without waiting. Their device-side
+ *     status (non-finite input, ids out of range, a bounded wait that gave
+ *     up, ...) is copied back in stream order and reported by
+ *     flood_check(stream), or by the next library call on the same stream
+ *     once it has arrived. Other entry points synchronise the stream and
+ *     report their own status (stated per function).
  *   - Coordinates are float32, row-major (n, 3). Vertex ids are int32 rows of
  *     L. Values are Euclidean distances (not squared), float32.
  *   - Scratch device memory is taken from the stream-ordered allocator
@@ -39,6 +46,14 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* ------------------------------------------------------------------------
+ * flood_check — wait for `stream` and report the device-side status of the
+ * asynchronous calls enqueued on it since the last check: FLOOD_OK, or the
+ * first error (flood_last_error() names the call). Check before destroying a
+ * stream that asynchronous calls used.
+ * ------------------------------------------------------------------------ */
+int flood_check(void* stream);
 
 typedef enum flood_status {
     FLOOD_OK = 0,
@@ -71,10 +86,11 @@ typedef enum flood_status {
  *   out_key    device, float32[n_landmarks] or NULL: d of each pick when it
  *              was picked (out_key[0] = +inf; out_key[j] is the squared
  *              covering radius of the first j picks)
- * Errors: FLOOD_EINVAL (sizes, start out of range, non-finite X),
- *         FLOOD_EDEGENERATE (fewer than n_landmarks distinct points; out_idx
- *         holds the picks made so far), FLOOD_ETIMEOUT (grid barrier wait).
- * Synchronises `stream` before returning.
+ * Errors: FLOOD_EINVAL (sizes, start out of range) on return; through
+ *         flood_check: FLOOD_EINVAL (non-finite X), FLOOD_EDEGENERATE (fewer
+ *         than n_landmarks distinct points; out_idx holds the picks made so
+ *         far), FLOOD_ETIMEOUT (grid exchange wait).
+ * Asynchronous (see the conventions above).
  * ------------------------------------------------------------------------ */
 int flood_fps(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start,
               int64_t* out_idx, float* out_key, void* stream);
@@ -182,7 +198,13 @@ int flood_fps_noalloc(const float* X, int64_t n_points, int32_t n_landmarks, int
  *              the bounding box and n_points. h is enlarged if the dense
  *              cell table would exceed 2^27 cells.
  *   out        receives a library-owned grid (free with flood_grid_destroy)
- * Errors: FLOOD_EINVAL, FLOOD_ENOMEM, FLOOD_ECUDA. Synchronises `stream`.
+ * The bounding box, the cell size and the table dimensions are computed on
+ * the device (no host readback); the cell table is allocated for
+ * min(2^27, max(2^16, 4 n_points)) cells and the cell edge is enlarged on the
+ * device until the box fits (results of the filtration do not depend on the
+ * cell size). flood_grid_get_info waits for the build and reads them back.
+ * Errors: FLOOD_EINVAL (arguments), FLOOD_ENOMEM, FLOOD_ECUDA on return;
+ * through flood_check: FLOOD_EINVAL (non-finite X). Asynchronous.
  * ------------------------------------------------------------------------ */
 typedef struct flood_grid flood_grid;
 
@@ -199,7 +221,9 @@ typedef struct flood_grid_info {
 
 int flood_build_grid(const float* X, int64_t n_points, float cell_size,
                      flood_grid** out, void* stream);
+/* Waits for the grid's build to finish, then fills *out. */
 int flood_grid_get_info(const flood_grid* grid, flood_grid_info* out);
+/* Waits for all device work, then frees the grid. */
 void flood_grid_destroy(flood_grid* grid);
 
 /* ------------------------------------------------------------------------
@@ -240,9 +264,11 @@ void flood_grid_destroy(flood_grid* grid);
  *                (dim, row, sample). Used by flood_filtration_backward.
  * Empty dimensions (n_simplices[k] == 0) are allowed. Results depend only on
  * (simplex, sample, point) arithmetic, so they are bitwise reproducible.
- * Errors: FLOOD_EINVAL (ids out of range, non-finite L, m), FLOOD_ENOMEM,
- *         FLOOD_ETIMEOUT (bounded shared-memory copy waits), FLOOD_ECUDA.
- * Synchronises `stream` before returning.
+ * Errors: FLOOD_EINVAL (m, sizes, NULL arrays), FLOOD_ENOMEM, FLOOD_ECUDA on
+ *         return; through flood_check: FLOOD_EINVAL (ids out of range,
+ *         non-finite L), FLOOD_ETIMEOUT (bounded shared-memory copy waits).
+ * Asynchronous; the work counters of flood_last_filtration_stats are read
+ * back without waiting.
  * ------------------------------------------------------------------------ */
 int flood_filtration(const flood_grid* grid, const float* L, int32_t n_landmarks,
                      const int32_t* const simplices[4], const int32_t* const facets[4],
@@ -259,7 +285,7 @@ int flood_filtration(const flood_grid* grid, const float* L, int32_t n_landmarks
  *   jobs    host array of n_jobs job descriptions (device pointers inside,
  *           with the meaning and layout of flood_filtration's arguments)
  * Errors as flood_filtration; a bad job fails the whole call before any
- * launch. Synchronises `stream` before returning.
+ * launch. Asynchronous.
  * ------------------------------------------------------------------------ */
 typedef struct flood_filtration_job {
     const flood_grid* grid;
@@ -306,8 +332,8 @@ int flood_filtration_batch(const flood_filtration_job* jobs, int32_t n_jobs, voi
  * lexicographic order, the results (values and src) are bit for bit those of
  * flood_filtration with that m.
  * Errors: as flood_filtration; FLOOD_EINVAL also for a NULL weights[k] that
- * is needed, n_samples out of range, or a non-finite lambda_j (j >= 1).
- * Synchronises `stream` before returning.
+ * is needed, n_samples out of range (on return), or a non-finite lambda_j
+ * (j >= 1, through flood_check). Asynchronous.
  * ------------------------------------------------------------------------ */
 int flood_filtration_given(const flood_grid* grid, const float* L, int32_t n_landmarks,
                            const int32_t* const simplices[4], const int32_t* const facets[4],
@@ -315,7 +341,8 @@ int flood_filtration_given(const flood_grid* grid, const float* L, int32_t n_lan
                            const int32_t n_samples[4], float* const values[4], int32_t* const src[4],
                            void* stream);
 
-/* Work counters of the calling thread's last successful flood_filtration(_batch). */
+/* Work counters of the calling thread's last flood_filtration(_batch/_given)
+ * call; waits for that call's device work (meaningful when it succeeded). */
 typedef struct flood_filtration_stats {
     int64_t simplices[4];        /* simplices per dimension */
     int64_t samples[4];          /* interior samples resolved (NN queries) per dimension */

@@ -143,6 +143,7 @@ _SIGNATURES = {
     "flood_tuning_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_int32)]),
     "flood_tuning_entries": (C.c_int, [C.POINTER(TuningEntry), C.c_int32, C.POINTER(C.c_int32)]),
     "flood_tuning_clear": (C.c_int, []),
+    "flood_check": (C.c_int, [C.c_void_p]),
     "flood_last_error": (C.c_char_p, []),
     "flood_version": (C.c_char_p, []),
     "flood_kernel_launches": (C.c_int64, []),

@@ -32,7 +32,7 @@ struct BwdArgs {
     const float* L;
     const float* vbound;     // per landmark: d(v, X) rounded up, 0 for a point of X
     int32_t n_L;
-    GridView g;
+    const GridView* gp;      // device copy of the grid's view
     float* grad_X;
     float* grad_L;
     uint32_t* flags;
@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
     const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= a.n) return;
+    const GridView g = *a.gp;
     const float gam = a.grad[w];
     if (gam == 0.0f) return;
     const int32_t s0 = a.src[2 * w], sample = a.src[2 * w + 1];
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
     const float u = members ? __fsqrt_ru(vertex_bound_sq(S, dim, px, py, pz))
                             : vertex_bound_general(S, dim, px, py, pz, vb);
     const float off[3] = {px, py, pz};
-    const CellBox b = cull_box(a.g, S.v0, off, off, u);
+    const CellBox b = cull_box(g, S.v0, off, off, u);
     const int rows = b.n[1] * b.n[2];
     // nearest point: minimum of (d^2 bits << 32 | original row), with the
     // offset x* - p* kept by the lane that holds it
@@ -88,9 +89,9 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
     float bx = 0.0f, by = 0.0f, bz = 0.0f;
     for (int r = 0; r < rows; ++r) {
         int32_t rb, re;
-        box_row(a.g, b, r, rb, re);
+        box_row(g, b, r, rb, re);
         for (int32_t i = rb + lane; i < re; i += 32) {
-            const float4 x = a.g.pts[i];
+            const float4 x = g.pts[i];
             const float dx = __fsub_rn(__fsub_rn(x.x, S.v0[0]), px);
             const float dy = __fsub_rn(__fsub_rn(x.y, S.v0[1]), py);
             const float dz = __fsub_rn(__fsub_rn(x.z, S.v0[2]), pz);
@@ -168,6 +169,7 @@ int backward_impl(const flood_grid* grid, const float* L, int32_t n_landmarks, c
         return FLOOD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    if (int rc = pending_error(s)) return rc;
     Scratch scr(s);
     uint32_t* flags;
     int rc;
@@ -186,7 +188,7 @@ int backward_impl(const flood_grid* grid, const float* L, int32_t n_landmarks, c
     if ((rc = launch_vertices(L, n_landmarks, grid, vval, vsrc, vbound, flags, s))) return rc;
     a.vbound = vbound;
     a.n_simp[0] = n_landmarks;
-    a.g = view_of(grid);
+    a.gp = view_of(grid);
     a.grad_X = grad_X;
     a.grad_L = grad_L;
     a.flags = flags;

@@ -3,6 +3,7 @@
 #include <atomic>
 #include <mutex>
 #include <stdio.h>
+#include <vector>
 
 #include "common.cuh"
 
@@ -57,6 +58,133 @@ int finish(cudaStream_t stream, const uint32_t* d_flags, const char* where) {
     return status_from_flags(flags, where);
 }
 
+// ---------------------------------------------------------------- deferred status
+namespace {
+
+constexpr int kStatusSlots = 4096;
+constexpr int kMaxPendingPerStream = 1024;
+
+struct Pending {
+    cudaStream_t stream;
+    int device;
+    int slot;
+    char where[48];
+};
+
+std::mutex g_pend_mu;
+volatile uint32_t* g_slot_words = nullptr;  // pinned host memory, written by stream-ordered copies
+std::vector<int> g_free_slots;
+std::vector<Pending> g_pending;
+
+int slots_ready_locked() {
+    if (g_slot_words) return FLOOD_OK;
+    void* p = nullptr;
+    cudaError_t e = cudaHostAlloc(&p, sizeof(uint32_t) * kStatusSlots, cudaHostAllocPortable);
+    if (e != cudaSuccess) return cuda_fail(e, "status slots (cudaHostAlloc)");
+    g_slot_words = static_cast<volatile uint32_t*>(p);
+    for (int i = kStatusSlots - 1; i >= 0; --i) g_free_slots.push_back(i);
+    return FLOOD_OK;
+}
+
+// Remove the entries of (stream, device) that are final (all of them, or
+// those whose word already arrived non-zero) and return the first error.
+int collect_locked(cudaStream_t s, int dev, bool all) {
+    int rc = FLOOD_OK;
+    size_t keep = 0;
+    for (size_t i = 0; i < g_pending.size(); ++i) {
+        Pending& p = g_pending[i];
+        const bool mine = p.stream == s && p.device == dev;
+        const uint32_t w = mine ? g_slot_words[p.slot] : 0u;
+        if (mine && (all || w != 0u)) {
+            if (rc == FLOOD_OK && w != 0u) rc = status_from_flags(w, p.where);
+            g_free_slots.push_back(p.slot);
+        } else {
+            g_pending[keep++] = p;
+        }
+    }
+    g_pending.resize(keep);
+    return rc;
+}
+
+size_t count_locked(cudaStream_t s, int dev) {
+    size_t n = 0;
+    for (const Pending& p : g_pending) n += p.stream == s && p.device == dev;
+    return n;
+}
+
+}  // namespace
+
+int pending_error(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return FLOOD_OK;
+    }
+    std::lock_guard<std::mutex> lock(g_pend_mu);
+    if (g_pending.empty()) return FLOOD_OK;
+    return collect_locked(s, dev, false);
+}
+
+static int check_stream(cudaStream_t s) {
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    FLOOD_CUDA(cudaStreamSynchronize(s));
+    std::lock_guard<std::mutex> lock(g_pend_mu);
+    if (g_pending.empty()) return FLOOD_OK;
+    return collect_locked(s, dev, true);
+}
+
+int defer_status(cudaStream_t s, const uint32_t* d_flags, const char* where) {
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    int slot = -1;
+    size_t n_mine = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_pend_mu);
+        if (int rc = slots_ready_locked()) return rc;
+        if (!g_free_slots.empty()) {
+            slot = g_free_slots.back();
+            g_free_slots.pop_back();
+            g_slot_words[slot] = 0u;
+            Pending p{s, dev, slot, {0}};
+            snprintf(p.where, sizeof(p.where), "%s", where);
+            g_pending.push_back(p);
+            n_mine = count_locked(s, dev);
+        }
+    }
+    if (slot < 0) return finish(s, d_flags, where);  // table full: wait for this call's status now
+    FLOOD_CUDA(cudaMemcpyAsync(const_cast<uint32_t*>(g_slot_words + slot), d_flags, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+    if (n_mine > static_cast<size_t>(kMaxPendingPerStream)) return check_stream(s);  // bound the table per stream
+    return FLOOD_OK;
+}
+
+HostStats::~HostStats() {
+    if (host) cudaFreeHost(host);
+    if (done) cudaEventDestroy(done);
+}
+
+int HostStats::reserve(size_t n) {
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    if (done && device != dev) {
+        cudaEventDestroy(done);
+        done = nullptr;
+    }
+    if (!done) {
+        FLOOD_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        device = dev;
+    }
+    if (bytes < n) {
+        if (host) cudaFreeHost(host);
+        host = nullptr;
+        bytes = 0;
+        FLOOD_CUDA(cudaHostAlloc(&host, n, cudaHostAllocPortable));
+        bytes = n;
+    }
+    return FLOOD_OK;
+}
+
 static std::atomic<long long> g_launches{0};
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -93,6 +221,8 @@ void keep_pool_warm() {
 }  // namespace flood
 
 extern "C" const char* flood_last_error(void) { return flood::g_error; }
+
+extern "C" int flood_check(void* stream) { return flood::check_stream(static_cast<cudaStream_t>(stream)); }
 
 extern "C" const char* flood_version(void) { return "0.1.0"; }
 

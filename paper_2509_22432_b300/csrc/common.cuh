@@ -109,6 +109,29 @@ struct Bump {
 // Wait for `stream`, then turn the device status word into a flood_status.
 int finish(cudaStream_t stream, const uint32_t* d_flags, const char* where);
 
+// Deferred status of the asynchronous entry points. defer_status enqueues a
+// copy of the call's device status word into a pinned host slot and returns
+// at once; flood_check(stream) synchronises the stream and reports the first
+// error of its calls. pending_error returns, without waiting, an error that
+// an earlier call on `stream` has already delivered (every asynchronous
+// entry point calls it first, so an error is reported by the next call at
+// the latest). A status that arrives while the slot table is full is
+// waited for on the spot.
+int defer_status(cudaStream_t stream, const uint32_t* d_flags, const char* where);
+int pending_error(cudaStream_t stream);
+
+// Pinned host buffer and a completion event of the calling thread, for
+// statistics that calls copy back without waiting (one per purpose and thread).
+struct HostStats {
+    void* host = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+    int device = -1;
+    bool valid = false;
+    ~HostStats();
+    int reserve(size_t n);  // pinned buffer of at least n bytes and an event on the current device
+};
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int device_sm_count();

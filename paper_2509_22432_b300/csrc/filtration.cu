@@ -36,6 +36,7 @@
 // depend on how the work is tiled or batched, nor on the cell size.
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -90,6 +91,16 @@ struct SampleRec {
     int32_t pad;
 };
 
+// Geometry of one job, computed on the device from its grid (no host
+// readback): the grid view, the sample lattice and the shell constants.
+struct JobGeo {
+    GridView g;
+    Lattice lat;
+    float shell_h;      // cell edge times (1 - 2^-10)
+    float shell_slack;  // absolute rounding slack of cell assignment
+    int64_t n_coarse;   // coarse cubes of the lattice
+};
+
 struct DimArgs {
     int k;
     int I;
@@ -104,10 +115,9 @@ struct DimArgs {
     const float* L;
     const float* vbound;     // per landmark: d(v, X) rounded up, 0 for a point of X
     int32_t n_L;
-    GridView g;
-    Lattice lat;
-    int64_t n_buckets;      // n_coarse * kFine sample keys
-    int64_t n_coarse;
+    const JobGeo* geo;       // device: grid view, sample lattice, shell constants
+    int64_t n_buckets;      // capacity: n_coarse * kFine sample keys
+    int64_t n_coarse;       // capacity: coarse cubes of any lattice this job can get
     int32_t* bucket_count;
     int32_t* bucket_start;  // n_buckets + 1
     int32_t* bucket_fill;
@@ -116,8 +126,6 @@ struct DimArgs {
     SampleRec* recs;
     unsigned long long* best;  // per simplex: (d^2 bits << 32) | ~sample
     const int32_t* n_heavy;    // groups [0, *n_heavy) of the sorted queue go to the CTA kernel
-    float shell_h;             // cell edge times (1 - 2^-10)
-    float shell_slack;         // absolute rounding slack of cell assignment
     Ctl* ctl;
 };
 
@@ -127,11 +135,12 @@ struct DimArgs {
 // allows L ⊄ X). vbound[v] = d(v, X) rounded up with a margin (exactly 0 for a
 // point of X) bounds the samples of every coface from above.
 // One warp per landmark: its lanes scan the cells together.
-__global__ void k_vertices(const float* L, int32_t n_L, GridView g, float* val, int32_t* src, float* vbound,
+__global__ void k_vertices(const float* L, int32_t n_L, const GridView* gp, float* val, int32_t* src, float* vbound,
                            uint32_t* flags) {
     const int v = static_cast<int>((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (v >= n_L) return;
+    const GridView g = *gp;
     const float x = L[3 * v], y = L[3 * v + 1], z = L[3 * v + 2];
     bool found = false;
     if (isfinite(x) && isfinite(y) && isfinite(z)) {
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
         }
         ++n_active;
         const float x = __fadd_rn(S.v0[0], px), y = __fadd_rn(S.v0[1], py), z = __fadd_rn(S.v0[2], pz);
-        const int64_t b = sample_key(a.lat, x, y, z);
+        const int64_t b = sample_key(a.geo->lat, x, y, z);
         if (!SCATTER) {
             atomicAdd(&a.bucket_count[b], 1);
         } else {
@@ -348,7 +357,7 @@ __device__ __forceinline__ int group_class(const DimArgs& a, int2 gb) {
     const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
     float R = 0.0f;
     for (int32_t i = s_begin; i < s_end; ++i) R = fmaxf(R, a.recs[i].u);
-    const int c = static_cast<int>(ceilf(R / a.shell_h));
+    const int c = static_cast<int>(ceilf(R / a.geo->shell_h));
     return kClasses - 1 - min(max(c, 0), kClasses - 1);  // heavier -> smaller class
 }
 
@@ -567,6 +576,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
                                               uint64_t* bar, float* s_u, float* s_lb, uint32_t& phases, bool& abort,
                                               WarpCounters& cnt, int lane) {
     static_assert(NS % 2 == 0, "samples are evaluated in pairs");
+    const float shell_h = a.geo->shell_h, shell_slack = a.geo->shell_slack;
     // -2 p' per sample, paired over consecutive samples for packed FMAs
     float2 ax[NS / 2], ay[NS / 2], az[NS / 2];
     float pp[NS], mn[NS];
@@ -629,7 +639,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
     // Beyond shell s every point is at least s*h (less rounding slack) from
     // every sample; at max u_p no nearest point can lie farther out.
     const int dmax = max(g.dx, max(g.dy, g.dz));
-    const int s_max = min(static_cast<int>(ceilf((R + a.shell_slack) / a.shell_h)) + 1, dmax);
+    const int s_max = min(static_cast<int>(ceilf((R + shell_slack) / shell_h)) + 1, dmax);
     Shell sh;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -638,7 +648,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
         sh.wlo[c] = wlo[c];
         sh.whi[c] = whi[c];
     }
-    sh.slack = a.shell_slack + g.cell * (1.0f / 1024.0f);
+    sh.slack = shell_slack + g.cell * (1.0f / 1024.0f);
     // combine the partial minima of the point streams
     auto combine = [&]() {
 #pragma unroll
@@ -729,7 +739,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
             combine();
             dirty = false;
         }
-        const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * a.shell_h, a.shell_slack), 0.0f);
+        const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * shell_h, shell_slack), 0.0f);
         const float sl2 = __fmul_rn(sl, sl);
         bool done = true;
 #pragma unroll
@@ -797,15 +807,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
         if (item >= total || abort) break;
         const int j = job_of(light_off, n_jobs, item);
         const DimArgs& a = jobs[j];
-        const GridView gv = a.g;
+        const GridView gv = a.geo->g;
+        const Lattice lat = a.geo->lat;
         const int2 gb = a.groups[*a.n_heavy + (item - light_off[j])];
         const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
         const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
         // coarse cube corner: the origin of the pair arithmetic for this group
-        const int bxi = gb.x % a.lat.bx, byi = (gb.x / a.lat.bx) % a.lat.by, bzi = gb.x / (a.lat.bx * a.lat.by);
-        const float ox = __fadd_rn(a.lat.ox, static_cast<float>(bxi) * a.lat.B);
-        const float oy = __fadd_rn(a.lat.oy, static_cast<float>(byi) * a.lat.B);
-        const float oz = __fadd_rn(a.lat.oz, static_cast<float>(bzi) * a.lat.B);
+        const int bxi = gb.x % lat.bx, byi = (gb.x / lat.bx) % lat.by, bzi = gb.x / (lat.bx * lat.by);
+        const float ox = __fadd_rn(lat.ox, static_cast<float>(bxi) * lat.B);
+        const float oy = __fadd_rn(lat.oy, static_cast<float>(byi) * lat.B);
+        const float oz = __fadd_rn(lat.oz, static_cast<float>(bzi) * lat.B);
         const int n = s_end - s_begin;
         const int W = n <= kNS ? 1 : n <= 2 * kNS ? 2 : n <= 4 * kNS ? 4 : n <= 8 * kNS ? 8 : 16;
         process_group<kNS>(a, gv, W, s_begin, s_end, ox, oy, oz, tiles, bar, s_ub[warp][0], s_ub[warp][1], phases,
@@ -881,15 +892,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         if (item >= n_heavy || s_abort) break;
         const int jb = job_of(heavy_off, n_jobs, item);
         const DimArgs& a = jobs[jb];
-        const GridView g = a.g;
+        const GridView g = a.geo->g;
+        const Lattice lat = a.geo->lat;
+        const float shell_h = a.geo->shell_h, shell_slack = a.geo->shell_slack;
         const int2 gb = a.groups[item - heavy_off[jb]];
         const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
         const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
         const int n_valid = s_end - s_begin;
-        const int bxi = gb.x % a.lat.bx, byi = (gb.x / a.lat.bx) % a.lat.by, bzi = gb.x / (a.lat.bx * a.lat.by);
-        const float ox = __fadd_rn(a.lat.ox, static_cast<float>(bxi) * a.lat.B);
-        const float oy = __fadd_rn(a.lat.oy, static_cast<float>(byi) * a.lat.B);
-        const float oz = __fadd_rn(a.lat.oz, static_cast<float>(bzi) * a.lat.B);
+        const int bxi = gb.x % lat.bx, byi = (gb.x / lat.bx) % lat.by, bzi = gb.x / (lat.bx * lat.by);
+        const float ox = __fadd_rn(lat.ox, static_cast<float>(bxi) * lat.B);
+        const float oy = __fadd_rn(lat.oy, static_cast<float>(byi) * lat.B);
+        const float oz = __fadd_rn(lat.oz, static_cast<float>(bzi) * lat.B);
         const int W = n_valid <= kHeavyNS ? 1 : n_valid <= 2 * kHeavyNS ? 2 : n_valid <= 4 * kHeavyNS ? 4 : 8;
         const int G = kThreads / W;
         const int gs = tid / W, lw = tid % W;
@@ -981,7 +994,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         if (tid < n_valid) {
             const float u = fminf(s_u[tid], __fsqrt_ru(__uint_as_float(s_ub2[tid])) * (1.0f + 1.0f / 65536.0f));
             s_u[tid] = u;
-            if (__fadd_rn(__fmul_rn(u, 1.0f + 1.0f / 4096.0f), a.shell_slack) <= s_lb[tid]) {
+            if (__fadd_rn(__fmul_rn(u, 1.0f + 1.0f / 4096.0f), shell_slack) <= s_lb[tid]) {
                 s_live[tid] = 0;
                 s_min[tid] = 0u;
             }
@@ -995,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
                 any_live = true;
             }
         const int dmax = max(g.dx, max(g.dy, g.dz));
-        const int s_max = any_live ? min(static_cast<int>(ceilf((R + a.shell_slack) / a.shell_h)) + 1, dmax) : -1;
+        const int s_max = any_live ? min(static_cast<int>(ceilf((R + shell_slack) / shell_h)) + 1, dmax) : -1;
         Shell sh;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -1004,7 +1017,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             sh.wlo[c] = wlo[c];
             sh.whi[c] = whi[c];
         }
-        sh.slack = a.shell_slack + g.cell * (1.0f / 1024.0f);
+        sh.slack = shell_slack + g.cell * (1.0f / 1024.0f);
         // Fold the threads' partial minima into s_min (squared distances >= 0
         // order like their bit patterns) and recompute the search radius.
         auto fold = [&]() {
@@ -1116,7 +1129,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
                 dirty = false;
             }
             // termination: every sample exact (below the next shell) or dominated
-            const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * a.shell_h, a.shell_slack), 0.0f);
+            const float sl = fmaxf(__fsub_rn(static_cast<float>(s) * shell_h, shell_slack), 0.0f);
             const float sl2 = __fmul_rn(sl, sl);
             int live = 0;
             if (tid < n_valid && s_live[tid]) {
@@ -1242,33 +1255,78 @@ int launch_flood(const DimArgs* jobs, int n_jobs, const int32_t* light_off, Ctl*
 // the grid origin, with c = cbrt(samples / 64) clamped to [4, 40] so that a
 // coarse cube holds enough samples for full groups. It depends only on X's
 // bounding box and the size of the complex, never on the cell size or on
-// how clouds are batched.
-Lattice make_lattice(const flood_grid* grid, int64_t n_samples) {
-    Lattice L{};
-    L.ox = grid->origin[0];
-    L.oy = grid->origin[1];
-    L.oz = grid->origin[2];
+// how clouds are batched. Computed on the device from the grid's box (one
+// thread per job); the host sizes the bucket arrays for the largest lattice
+// any box can give: ext / B <= sqrt(2) c per axis, so at most cap_axis =
+// floor(1.5 c) + 2 cubes per axis (B doubles should rounding exceed it).
+float lattice_divisions(int64_t n_samples) {
+    return std::min(40.0f, std::max(4.0f, std::cbrt(static_cast<float>(n_samples) / 64.0f)));
+}
+int lattice_cap_axis(float div) { return static_cast<int>(std::floor(1.5f * div)) + 2; }
+
+__global__ void k_job_geometry(const GridGeom* gg, float div, int cap_axis, JobGeo* out) {
+    JobGeo J;
+    J.g = gg->v;
     float ext[3], emax = 0.0f;
     for (int c = 0; c < 3; ++c) {
-        ext[c] = grid->bbox_hi[c] - grid->bbox_lo[c];
-        emax = std::max(emax, ext[c]);
+        ext[c] = gg->bbox_hi[c] - gg->bbox_lo[c];
+        emax = fmaxf(emax, ext[c]);
     }
-    const float div = std::min(40.0f, std::max(4.0f, std::cbrt(static_cast<float>(n_samples) / 64.0f)));
-    float B = emax > 0.0f ? std::exp2(std::round(std::log2(emax / div))) : 1.0f;
+    Lattice& L = J.lat;
+    L.ox = J.g.ox;
+    L.oy = J.g.oy;
+    L.oz = J.g.oz;
+    float B = emax > 0.0f ? exp2f(rintf(log2f(emax / div))) : 1.0f;
     for (;;) {
-        L.bx = static_cast<int>(std::floor(ext[0] / B)) + 1;
-        L.by = static_cast<int>(std::floor(ext[1] / B)) + 1;
-        L.bz = static_cast<int>(std::floor(ext[2] / B)) + 1;
-        if (int64_t(L.bx) * L.by * L.bz * kFine <= kMaxBuckets) break;
+        L.bx = static_cast<int>(floorf(ext[0] / B)) + 1;
+        L.by = static_cast<int>(floorf(ext[1] / B)) + 1;
+        L.bz = static_cast<int>(floorf(ext[2] / B)) + 1;
+        if (L.bx <= cap_axis && L.by <= cap_axis && L.bz <= cap_axis) break;
         B *= 2.0f;
     }
     L.B = B;
     L.invB = 1.0f / B;
     L.invF = 2.0f / B;
-    return L;
+    J.n_coarse = int64_t(L.bx) * L.by * L.bz;
+    J.shell_h = J.g.cell * (1.0f - 1.0f / 1024.0f);
+    const float amax = fmaxf(fabsf(J.g.ox), fmaxf(fabsf(J.g.oy), fabsf(J.g.oz)));
+    J.shell_slack = (amax + emax) * (1.0f / 262144.0f);
+    *out = J;
 }
 
-thread_local flood_filtration_stats g_stats;
+// The calling thread's last filtration: its counters are copied back without
+// waiting (pinned buffer: Ctl, then int32 work items per job and dimension)
+// and read by flood_last_filtration_stats once the call's stream is done.
+struct LastFiltration {
+    HostStats buf;
+    cudaEvent_t ev[4][2] = {};  // flood kernels of each dimension (timing events, this thread's device)
+    int ev_device = -1;
+    bool timed[4] = {false, false, false, false};
+    int n_jobs = 0;
+    int64_t simplices[4] = {0, 0, 0, 0}, samples[4] = {0, 0, 0, 0};
+    bool valid = false;
+    ~LastFiltration() {
+        for (auto& p : ev)
+            for (auto& e : p)
+                if (e) cudaEventDestroy(e);
+    }
+    int events() {  // timing events on the current device
+        int dev = 0;
+        FLOOD_CUDA(cudaGetDevice(&dev));
+        if (ev_device != dev) {
+            for (auto& p : ev)
+                for (auto& e : p) {
+                    if (e) cudaEventDestroy(e);
+                    e = nullptr;
+                }
+            for (auto& p : ev)
+                for (auto& e : p) FLOOD_CUDA(cudaEventCreate(&e));
+            ev_device = dev;
+        }
+        return FLOOD_OK;
+    }
+};
+thread_local LastFiltration g_last;
 
 // CUDA events around the flood kernel of each dimension, destroyed on scope exit.
 // A second stream per host thread and device, with a pair of fork/join
@@ -1314,16 +1372,6 @@ int side_stream(SideStream** out) {
     *out = &x;
     return FLOOD_OK;
 }
-
-struct EventPairs {
-    cudaEvent_t e[4][2] = {};
-    cudaEvent_t* operator[](int k) { return e[k]; }
-    ~EventPairs() {
-        for (auto& p : e)
-            for (auto& x : p)
-                if (x) cudaEventDestroy(x);
-    }
-};
 
 }  // namespace
 
@@ -1397,7 +1445,25 @@ extern "C" int flood_last_filtration_stats(flood_filtration_stats* out) {
         set_error("flood_last_filtration_stats: out is NULL");
         return FLOOD_EINVAL;
     }
-    *out = g_stats;
+    flood_filtration_stats st{};
+    if (g_last.valid) {
+        FLOOD_CUDA(cudaEventSynchronize(g_last.buf.done));
+        Ctl c;
+        const unsigned char* hb = static_cast<const unsigned char*>(g_last.buf.host);
+        memcpy(&c, hb, sizeof(Ctl));
+        const int32_t* items = reinterpret_cast<const int32_t*>(hb + sizeof(Ctl));
+        for (int k = 0; k <= 3; ++k) {
+            st.simplices[k] = g_last.simplices[k];
+            st.samples[k] = g_last.samples[k];
+            for (int i = 0; i < g_last.n_jobs; ++i) st.work_items[k] += items[i * 4 + k];
+            st.pairs[k] = static_cast<int64_t>(c.pairs[k]);
+            st.active_samples[k] = static_cast<int64_t>(c.active[k]);
+            st.shells[k] = static_cast<int64_t>(c.shells[k]);
+            st.tiles[k] = static_cast<int64_t>(c.tiles[k]);
+            if (g_last.timed[k]) cudaEventElapsedTime(&st.flood_kernel_ms[k], g_last.ev[k][0], g_last.ev[k][1]);
+        }
+    }
+    *out = st;
     return FLOOD_OK;
 }
 
@@ -1411,8 +1477,8 @@ struct JobState {
     int32_t* src[4];
     int64_t nk[4];
     int I[4];
-    Lattice lat;
-    int64_t n_coarse, n_buckets, max_samples, max_n, max_groups;
+    JobGeo* geo;  // device
+    int64_t n_coarse, n_buckets, max_samples, max_n, max_groups;  // capacities
     std::vector<uint8_t> tables[4];
     const uint8_t* comp[4];
     const float* w[4];
@@ -1423,7 +1489,6 @@ struct JobState {
     int32_t *bstart, *goff;
     int2 *groups, *groups_sorted;
     SampleRec* recs;
-    float shell_slack;
     int heavy_shells;  // groups with at least this many shells go to the CTA kernel
 };
 
@@ -1491,6 +1556,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
         if (given)
             if (int rc = check_given(in[i], given[i])) return rc;
     }
+    if (int rc = pending_error(s)) return rc;
     Scratch scr(s);
     Ctl* ctl;
     int rc;
@@ -1535,9 +1601,13 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             total_samples += J.nk[k] * J.I[k];
             if (!given && J.I[k] > 0 && (rc = device_interior_table(J.in.m, k, J.tables[k], &J.comp[k]))) return rc;
         }
-        J.lat = make_lattice(grid, total_samples);
-        J.n_coarse = int64_t(J.lat.bx) * J.lat.by * J.lat.bz;
+        const float div = lattice_divisions(total_samples);
+        const int cap_axis = lattice_cap_axis(div);
+        J.n_coarse = int64_t(cap_axis) * cap_axis * cap_axis;
         J.n_buckets = J.n_coarse * kFine;
+        if ((rc = scr.alloc(&J.geo, 1))) return rc;
+        k_job_geometry<<<1, 1, 0, s>>>(grid->geom, div, cap_axis, J.geo);
+        note_launch();
         J.max_groups = J.max_samples / kGroup + J.n_coarse + 1;
         if ((rc = scr.alloc(&J.bstart, J.n_buckets + 1)) || (rc = scr.alloc(&J.goff, J.n_coarse + 1)) ||
             (rc = scr.alloc(&J.groups, J.max_groups)) || (rc = scr.alloc(&J.groups_sorted, J.max_groups)) ||
@@ -1562,11 +1632,6 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             J.best[k] = zr + 2 * w_buckets + w_cls;
             zr += 2 * w_buckets + w_cls + J.nk[k];
         }
-        const float emax = std::max(grid->bbox_hi[0] - grid->bbox_lo[0],
-                                    std::max(grid->bbox_hi[1] - grid->bbox_lo[1], grid->bbox_hi[2] - grid->bbox_lo[2]));
-        const float amax =
-            std::max(std::fabs(grid->origin[0]), std::max(std::fabs(grid->origin[1]), std::fabs(grid->origin[2])));
-        J.shell_slack = (amax + emax) * (1.0f / 262144.0f);
         J.heavy_shells = tuning_for(grid->n_points, J.in.n_landmarks, J.in.m).heavy_shells;
     }
     DimArgs* d_jobs;
@@ -1577,9 +1642,9 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
     FLOOD_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * 4 * std::max(n_jobs, 1), s));
     std::vector<DimArgs> h_jobs;
     h_jobs.reserve(n_jobs);
-    EventPairs ev;
-    int64_t h_items[4] = {0, 0, 0, 0};
-    std::vector<int32_t> items_per_job(static_cast<size_t>(n_jobs) * 4, 0);
+    g_last.valid = false;
+    if ((rc = g_last.events())) return rc;
+    for (int k = 0; k < 4; ++k) g_last.timed[k] = false;
     for (int k = 1; k <= 3; ++k) {
         h_jobs.clear();
         for (int i = 0; i < n_jobs; ++i) {
@@ -1587,7 +1652,6 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             const int64_t n = J.nk[k];
             if (n == 0) continue;
             if (J.I[k] == 0) continue;
-            const flood_grid* grid = J.in.grid;
             DimArgs a{};
             a.k = k;
             a.I = J.I[k];
@@ -1602,8 +1666,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             a.L = J.in.L;
             a.vbound = J.vbound;
             a.n_L = J.in.n_landmarks;
-            a.g = view_of(grid);
-            a.lat = J.lat;
+            a.geo = J.geo;
             a.n_buckets = J.n_buckets;
             a.n_coarse = J.n_coarse;
             a.bucket_count = J.bcount[k];
@@ -1613,8 +1676,6 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             a.groups = J.groups;
             a.recs = J.recs;
             a.best = J.best[k];
-            a.shell_h = grid->cell_size * (1.0f - 1.0f / 1024.0f);
-            a.shell_slack = J.shell_slack;
             a.ctl = ctl;
             const unsigned wb = static_cast<unsigned>(ceil_div(n * 32, 256));
             k_samples<false><<<wb, 256, 0, s>>>(a);
@@ -1662,8 +1723,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             if (k > 1) light_off = heavy_off + (nj + 1);
             k_queue_offsets<<<1, 32, 0, s>>>(dj, nj, heavy_off, light_off);
             note_launch();
-            if (cudaEventCreate(&ev[k][0]) == cudaSuccess && cudaEventCreate(&ev[k][1]) == cudaSuccess)
-                cudaEventRecord(ev[k][0], s);
+            FLOOD_CUDA(cudaEventRecord(g_last.ev[k][0], s));
             SideStream* side;
             if ((rc = side_stream(&side))) return rc;
             FLOOD_CUDA(cudaEventRecord(side->fork, s));
@@ -1672,7 +1732,8 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             if ((rc = launch_flood(dj, nj, light_off, ctl, k, side->s))) return rc;
             FLOOD_CUDA(cudaEventRecord(side->join, side->s));
             FLOOD_CUDA(cudaStreamWaitEvent(s, side->join, 0));
-            if (ev[k][1]) cudaEventRecord(ev[k][1], s);
+            FLOOD_CUDA(cudaEventRecord(g_last.ev[k][1], s));
+            g_last.timed[k] = true;
         }
         for (int i = 0; i < n_jobs; ++i) {
             JobState& J = js[i];
@@ -1685,31 +1746,24 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             FLOOD_CUDA(cudaGetLastError());
         }
     }
-    Ctl h_ctl{};
-    FLOOD_CUDA(cudaMemcpyAsync(&h_ctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    // counters back without waiting; the status word is reported by flood_check
+    const size_t stat_bytes = sizeof(Ctl) + sizeof(int32_t) * 4 * std::max(n_jobs, 1);
+    if ((rc = g_last.buf.reserve(stat_bytes))) return rc;
+    unsigned char* hb = static_cast<unsigned char*>(g_last.buf.host);
+    FLOOD_CUDA(cudaMemcpyAsync(hb, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     if (n_jobs > 0)
-        FLOOD_CUDA(cudaMemcpyAsync(items_per_job.data(), d_counts, sizeof(int32_t) * 4 * n_jobs,
-                                   cudaMemcpyDeviceToHost, s));
-    FLOOD_CUDA(cudaStreamSynchronize(s));
-    rc = status_from_flags(h_ctl.flags, "flood_filtration");
-    if (rc) return rc;
-    flood_filtration_stats st{};
+        FLOOD_CUDA(cudaMemcpyAsync(hb + sizeof(Ctl), d_counts, sizeof(int32_t) * 4 * n_jobs, cudaMemcpyDeviceToHost, s));
+    FLOOD_CUDA(cudaEventRecord(g_last.buf.done, s));
+    g_last.n_jobs = n_jobs;
     for (int k = 0; k <= 3; ++k) {
+        g_last.simplices[k] = g_last.samples[k] = 0;
         for (int i = 0; i < n_jobs; ++i) {
-            st.simplices[k] += js[i].nk[k];
-            st.samples[k] += k == 0 ? 0 : js[i].nk[k] * js[i].I[k];
-            h_items[k] += items_per_job[i * 4 + k];
+            g_last.simplices[k] += js[i].nk[k];
+            g_last.samples[k] += k == 0 ? 0 : js[i].nk[k] * js[i].I[k];
         }
-        st.pairs[k] = static_cast<int64_t>(h_ctl.pairs[k]);
-        st.work_items[k] = h_items[k];
-        st.active_samples[k] = static_cast<int64_t>(h_ctl.active[k]);
-        st.shells[k] = static_cast<int64_t>(h_ctl.shells[k]);
-        st.tiles[k] = static_cast<int64_t>(h_ctl.tiles[k]);
-        st.flood_kernel_ms[k] = 0.0f;
-        if (ev[k][0] && ev[k][1]) cudaEventElapsedTime(&st.flood_kernel_ms[k], ev[k][0], ev[k][1]);
     }
-    g_stats = st;
-    return FLOOD_OK;
+    g_last.valid = true;
+    return defer_status(s, &ctl->flags, "flood_filtration");
 }
 
 }  // namespace

@@ -1049,25 +1049,42 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
     return launch_fps_kernel(plan, a, s);
 }
 
-thread_local flood_fps_stats g_fps_stats;
+// The calling thread's last FPS call: its control words (status, box, round
+// count) are copied back into a pinned buffer without waiting and read by
+// flood_last_fps_stats once the call's stream is done.
+struct LastFps {
+    HostStats buf;       // asynchronous calls: pinned copy, read after its event
+    uint32_t words[8];   // synchronous calls: the copy itself (no pinned memory needed)
+    bool in_words = false;
+    FpsPlan plan{};
+    int32_t n_landmarks = 0;
+    bool valid = false;
+};
+thread_local LastFps g_last_fps;
 
-// Wait for `s`, read the status and the round count, and turn the status
-// into a flood_status; the statistics of a successful call are kept for
-// flood_last_fps_stats.
+int fps_copy_back(cudaStream_t s, const uint32_t* ctl, const FpsPlan& plan, int32_t n_landmarks) {
+    g_last_fps.valid = false;
+    if (int rc = g_last_fps.buf.reserve(8 * sizeof(uint32_t))) return rc;
+    FLOOD_CUDA(cudaMemcpyAsync(g_last_fps.buf.host, ctl, 8 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FLOOD_CUDA(cudaEventRecord(g_last_fps.buf.done, s));
+    g_last_fps.in_words = false;
+    g_last_fps.plan = plan;
+    g_last_fps.n_landmarks = n_landmarks;
+    g_last_fps.valid = true;
+    return FLOOD_OK;
+}
+
+// Synchronous completion (flood_fps_noalloc, flood_fps_wait_test): wait for
+// `s` and turn the status word into a flood_status. Allocates nothing.
 int fps_finish(cudaStream_t s, const uint32_t* ctl, const FpsPlan& plan, int32_t n_landmarks, const char* where) {
-    uint32_t h[8] = {};
-    FLOOD_CUDA(cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    g_last_fps.valid = false;
+    FLOOD_CUDA(cudaMemcpyAsync(g_last_fps.words, ctl, sizeof(g_last_fps.words), cudaMemcpyDeviceToHost, s));
     FLOOD_CUDA(cudaStreamSynchronize(s));
-    const int rc = status_from_flags(h[0], where);
-    if (rc == FLOOD_OK) {
-        flood_fps_stats st{};
-        st.picks = n_landmarks;
-        st.rounds = h[7];
-        st.blocks = plan.blocks;
-        st.resident = plan.resident ? 1 : 0;
-        g_fps_stats = st;
-    }
-    return rc;
+    g_last_fps.in_words = true;
+    g_last_fps.plan = plan;
+    g_last_fps.n_landmarks = n_landmarks;
+    g_last_fps.valid = true;
+    return status_from_flags(g_last_fps.words[0], where);
 }
 
 bool fps_args_ok(const float* X, int64_t n_points, int32_t n_landmarks, int64_t start, const int64_t* out_idx) {
@@ -1089,6 +1106,7 @@ extern "C" int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_land
         return FLOOD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    if (int rc = pending_error(s)) return rc;
     Scratch scr(s);
     uint32_t* flags = nullptr;
     FpsPlan plan{};
@@ -1097,7 +1115,8 @@ extern "C" int flood_fps_blocks(const float* X, int64_t n_points, int32_t n_land
         if (flags) cudaStreamSynchronize(s);
         return rc;
     }
-    return fps_finish(s, flags, plan, n_landmarks, "flood_fps");
+    if ((rc = fps_copy_back(s, flags, plan, n_landmarks))) return rc;
+    return defer_status(s, flags, "flood_fps");
 }
 
 extern "C" int flood_last_fps_stats(flood_fps_stats* out) {
@@ -1105,7 +1124,18 @@ extern "C" int flood_last_fps_stats(flood_fps_stats* out) {
         set_error("flood_last_fps_stats: out is NULL");
         return FLOOD_EINVAL;
     }
-    *out = g_fps_stats;
+    flood_fps_stats st{};
+    if (g_last_fps.valid) {
+        if (!g_last_fps.in_words) FLOOD_CUDA(cudaEventSynchronize(g_last_fps.buf.done));
+        const uint32_t* h = g_last_fps.in_words ? g_last_fps.words : static_cast<const uint32_t*>(g_last_fps.buf.host);
+        if (h[0] == 0u) {
+            st.picks = g_last_fps.n_landmarks;
+            st.rounds = h[7];
+            st.blocks = g_last_fps.plan.blocks;
+            st.resident = g_last_fps.plan.resident ? 1 : 0;
+        }
+    }
+    *out = st;
     return FLOOD_OK;
 }
 

@@ -11,20 +11,42 @@
 
 #include "common.cuh"
 
+namespace flood {
+
+struct GridView {
+    const float4* pts;
+    const int32_t* cell_start;
+    const uint32_t* occupied;
+    const uint8_t* bdist;
+    int dx, dy, dz;
+    int bx, by, bz;
+    float ox, oy, oz;
+    float inv_cell;
+    float cell;
+};
+
+// Device-resident geometry of a grid. The host fills the pointers of v at
+// allocation; k_grid_geometry fills everything else from X's bounding box,
+// so no host readback is needed to build or use a grid.
+struct GridGeom {
+    GridView v;
+    float bbox_lo[3], bbox_hi[3];
+    int64_t n_cells;
+    int64_t n_blocks;
+};
+
+}  // namespace flood
+
 struct flood_grid {
     int64_t n_points;
-    int64_t n_cells;
-    int32_t dims[3];
-    float cell_size;
-    float inv_cell;
-    float origin[3];
-    float bbox_lo[3];
-    float bbox_hi[3];
+    int64_t cap_cells;    // capacity of the cell table; the grid uses at most this many cells
+    int64_t cap_blocks;   // capacity of the 4 x 4 x 4 block arrays
     float4* pts;          // points sorted by cell: (x, y, z, original row as int bits)
-    int32_t* cell_start;  // n_cells + 1 offsets into pts
+    int32_t* cell_start;  // cap_cells + 1 offsets into pts (entries past the used cells equal n_points)
     uint32_t* occupied;   // one bit per block of 4 x 4 x 4 cells that holds any point
     uint8_t* bdist;       // per block: Chebyshev distance in blocks to the nearest occupied one (capped, a lower bound)
-    int32_t bdims[3];     // blocks per axis
+    flood::GridGeom* geom;  // device
+    cudaEvent_t ready;    // recorded after the build's last kernel (flood_grid_get_info waits for it)
     int64_t device_bytes;
 };
 
@@ -41,37 +63,8 @@ int device_interior_table(int m, int k, const std::vector<uint8_t>& host, const 
 int launch_vertices(const float* L, int32_t n_L, const flood_grid* grid, float* val, int32_t* src, float* vbound,
                     uint32_t* flags, cudaStream_t s);
 
-struct GridView {
-    const float4* pts;
-    const int32_t* cell_start;
-    const uint32_t* occupied;
-    const uint8_t* bdist;
-    int dx, dy, dz;
-    int bx, by, bz;
-    float ox, oy, oz;
-    float inv_cell;
-    float cell;
-};
-
-inline GridView view_of(const flood_grid* g) {
-    GridView v;
-    v.pts = g->pts;
-    v.cell_start = g->cell_start;
-    v.occupied = g->occupied;
-    v.bdist = g->bdist;
-    v.bx = g->bdims[0];
-    v.by = g->bdims[1];
-    v.bz = g->bdims[2];
-    v.cell = g->cell_size;
-    v.dx = g->dims[0];
-    v.dy = g->dims[1];
-    v.dz = g->dims[2];
-    v.ox = g->origin[0];
-    v.oy = g->origin[1];
-    v.oz = g->origin[2];
-    v.inv_cell = g->inv_cell;
-    return v;
-}
+// The device copy of a grid's view (kernels load it into registers).
+inline const GridView* view_of(const flood_grid* g) { return &g->geom->v; }
 
 // Cell coordinate of v along one axis; monotone in v and clamped to the grid,
 // so a point inside [lo, hi] always lands between the cells of lo and hi.

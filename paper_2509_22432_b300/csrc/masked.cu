@@ -33,7 +33,7 @@ struct MaskedArgs {
     const uint8_t* comp;  // full-grid compositions (F, k+1), lexicographic
     int F;
     float m;
-    GridView g;
+    const GridView* gp;  // device copy of the grid's view
     float* val;
     uint32_t* flags;
     unsigned long long* pairs;
@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(kMThreads) k_masked(MaskedArgs a) {
     __shared__ uint32_t s_max;
     const int tid = threadIdx.x;
     const int k = a.k, F = a.F;
+    const GridView g = *a.gp;
     // (sample, point) split: nparts threads share each sample's points
     const int nparts = F >= kMThreads ? 1 : kMThreads / F;
     const int part = tid % nparts, s_first = tid / nparts, s_step = kMThreads / nparts;
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kMThreads) k_masked(MaskedArgs a) {
             qz[q] = sq < F ? s_pz[sq] : 0.0f;
         }
         const float zero[3] = {0.0f, 0.0f, 0.0f};
-        const CellBox b = cull_box(a.g, c, zero, zero, R);
+        const CellBox b = cull_box(g, c, zero, zero, R);
         const int rows = b.n[1] * b.n[2];
         if (tid == 0) s_cnt = 0;
         __syncthreads();
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kMThreads) k_masked(MaskedArgs a) {
         // thread (read after a barrier), so every barrier is reached by all.
         int r = 0;
         int32_t cur = 0, re = 0;
-        if (rows > 0) box_row(a.g, b, 0, cur, re);
+        if (rows > 0) box_row(g, b, 0, cur, re);
         bool more = rows > 0;
         int cnt = 0;
         for (;;) {
@@ -141,14 +142,14 @@ __global__ void __launch_bounds__(kMThreads) k_masked(MaskedArgs a) {
                         more = false;
                         break;
                     }
-                    box_row(a.g, b, r, cur, re);
+                    box_row(g, b, r, cur, re);
                     continue;
                 }
                 const int32_t i = cur + tid;
                 bool in = false;
                 float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (i < re) {
-                    x = a.g.pts[i];
+                    x = g.pts[i];
                     const float dx = x.x - c[0], dy = x.y - c[1], dz = x.z - c[2];
                     in = dx * dx + dy * dy + dz * dz <= R2;  // the mask
                 }
@@ -200,11 +201,12 @@ __global__ void __launch_bounds__(kMThreads) k_masked(MaskedArgs a) {
 // Lemma 2 as k_masked builds it (c the midpoint of the longest edge, rho =
 // sqrt(2) max_i |c - v_i|, or that maximum for an edge), without k_masked's
 // safety margin. One warp per simplex walks the rows of the ball's cell box.
-__global__ void k_ball_counts(int k, int64_t n, const int32_t* simplices, const float* L, int32_t n_L, GridView g,
-                              unsigned long long* count, uint32_t* flags) {
+__global__ void k_ball_counts(int k, int64_t n, const int32_t* simplices, const float* L, int32_t n_L,
+                              const GridView* gp, unsigned long long* count, uint32_t* flags) {
     const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n) return;
+    const GridView g = *gp;
     const int32_t* ids = simplices + w * (k + 1);
     float V[4][3];
     for (int j = 0; j <= k; ++j) {
@@ -287,6 +289,7 @@ extern "C" int flood_filtration_masked(const flood_grid* grid, const float* L, i
         return FLOOD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (int rc = pending_error(s)) return rc;
     Scratch scr(s);
     uint32_t* flags;
     unsigned long long* pairs;
@@ -327,7 +330,7 @@ extern "C" int flood_filtration_masked(const flood_grid* grid, const float* L, i
         a.comp = dcomp[k];
         a.F = F;
         a.m = static_cast<float>(m);
-        a.g = view_of(grid);
+        a.gp = view_of(grid);
         a.val = values[k];
         a.flags = flags;
         a.pairs = pairs;
@@ -351,6 +354,7 @@ extern "C" int flood_masking_ball_counts(const flood_grid* grid, const float* L,
         return FLOOD_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (int rc = pending_error(s)) return rc;
     Scratch scr(s);
     uint32_t* flags;
     unsigned long long* cnt;

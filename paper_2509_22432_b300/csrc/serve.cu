@@ -173,9 +173,9 @@ int gpu_stage(flood_server* s, Request* r, cudaStream_t st) {
     if (cudaMemcpyAsync(r->idx.data(), r->idx_dev, sizeof(int64_t) * r->n_L, cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(&last_key, r->key_dev + (r->n_L - 1), sizeof(float), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
+            cudaSuccess)
         return cuda_fail(cudaGetLastError(), "serve: copy landmarks");
+    if ((rc = flood_check(st))) return rc;  // waits for the landmarks; FPS's own status
     // L = X[idx], taken from the host copy: the same floats bit for bit
     r->L.resize(3 * static_cast<size_t>(r->n_L));
     for (int32_t i = 0; i < r->n_L; ++i)
@@ -186,7 +186,8 @@ int gpu_stage(flood_server* s, Request* r, cudaStream_t st) {
     const float cover = (r->n_L > 1 && std::isfinite(last_key)) ? std::sqrt(last_key) : 0.0f;
     const float factor = s->cfg.cell_factor > 0.0f ? s->cfg.cell_factor : tuning_for(r->N, r->n_L, r->m).cell_factor;
     const float cell = cover > 0.0f ? factor * cover : 0.0f;
-    return flood_build_grid(r->X_dev, r->N, cell, &r->grid, st);
+    if ((rc = flood_build_grid(r->X_dev, r->N, cell, &r->grid, st))) return rc;
+    return flood_check(st);  // the grid is complete before another stream uses it
 }
 
 void gpu_worker(flood_server* s) {
@@ -337,8 +338,7 @@ int run_batch(std::vector<Request*>& batch, cudaStream_t st) {
             if (n > 0)
                 cudaMemcpyAsync(r->values[k].data(), r->val_dev[k], sizeof(float) * n, cudaMemcpyDeviceToHost, st);
         }
-    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "serve: copy values");
-    return FLOOD_OK;
+    return flood_check(st);  // waits for the values; the filtration's own status
 }
 
 void flood_worker(flood_server* s) {

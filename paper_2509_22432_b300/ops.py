@@ -16,7 +16,7 @@ import torch
 from . import _lib
 from ._lib import FloodError, P4, I64x4, I32x4
 
-__all__ = ["fps", "fps_noalloc", "fps_stats", "fps_scratch_bytes", "fps_wait_test", "masking_ball_counts",
+__all__ = ["check", "fps", "fps_noalloc", "fps_stats", "fps_scratch_bytes", "fps_wait_test", "masking_ball_counts",
            "fp32_peak_probe", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
            "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
            "complex_faces", "filtration_masked",
@@ -39,11 +39,26 @@ def _points(X: torch.Tensor, name: str) -> torch.Tensor:
     return X.contiguous()
 
 
-def fps(X: torch.Tensor, n_landmarks: int, start: int = 0, n_blocks: int = 0):
+def check(device: torch.device | None = None) -> None:
+    """Wait for the current stream and raise FloodError if an asynchronous call on it failed (flood_check)."""
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(device):
+        st = _lib.get().flood_check(_stream_ptr(device))
+    _lib.check(st, "flood_check")
+
+
+def _finish(st: int, where: str, device: torch.device, sync: bool) -> None:
+    _lib.check(st, where)
+    if sync:
+        check(device)
+
+
+def fps(X: torch.Tensor, n_landmarks: int, start: int = 0, n_blocks: int = 0, sync: bool = True):
     """Farthest point sampling (§3.2). Returns (idx int64[n], key float32[n]).
 
     n_blocks: launch width (0 automatic, 1 one SM, k blocks); the picks are
-    the same for every width.
+    the same for every width. sync=False leaves the call asynchronous: its
+    device-side status is then reported by check() or by the next call.
     """
     X = _points(X, "X")
     idx = torch.empty(n_landmarks, dtype=torch.int64, device=X.device)
@@ -51,7 +66,7 @@ def fps(X: torch.Tensor, n_landmarks: int, start: int = 0, n_blocks: int = 0):
     with torch.cuda.device(X.device):
         st = _lib.get().flood_fps_blocks(_ptr(X), X.shape[0], int(n_landmarks), int(start), int(n_blocks), _ptr(idx),
                                          _ptr(key), _stream_ptr(X.device))
-    _lib.check(st, "flood_fps")
+    _finish(st, "flood_fps", X.device, sync)
     return idx, key
 
 
@@ -142,13 +157,17 @@ class Grid:
             pass
 
 
-def build_grid(X: torch.Tensor, cell_size: float = 0.0) -> Grid:
+def build_grid(X: torch.Tensor, cell_size: float = 0.0, sync: bool = True) -> Grid:
+    """Uniform cell grid over X (flood_build_grid); sync=False: asynchronous, see fps()."""
     X = _points(X, "X")
     h = C.c_void_p(0)
     with torch.cuda.device(X.device):
         st = _lib.get().flood_build_grid(_ptr(X), X.shape[0], float(cell_size), C.byref(h), _stream_ptr(X.device))
     _lib.check(st, "flood_build_grid")
-    return Grid(h, X.device)
+    grid = Grid(h, X.device)
+    if sync:
+        check(X.device)
+    return grid
 
 
 @dataclass
@@ -234,8 +253,10 @@ def complex_faces(tets: torch.Tensor, n_vertices: int) -> DeviceComplex:
                          [torch.zeros_like(verts), f1[:n1.value], f2[:n2.value], f3])
 
 
-def filtration(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, want_src: bool = True):
-    """Flood values of every simplex (§4.1). Returns (values[k] float32, src[k] int32 (n_k,2) or None)."""
+def filtration(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, want_src: bool = True, sync: bool = True):
+    """Flood values of every simplex (§4.1). Returns (values[k] float32, src[k] int32 (n_k,2) or None).
+
+    sync=False: asynchronous, see fps()."""
     L = _points(L, "L")
     s, f, n = cx.arrays()
     vals = [torch.empty(c, dtype=torch.float32, device=L.device) for c in cx.counts]
@@ -246,11 +267,11 @@ def filtration(grid: Grid, L: torch.Tensor, cx: DeviceComplex, m: int, want_src:
     with torch.cuda.device(L.device):
         st = _lib.get().flood_filtration(grid.handle, _ptr(L), L.shape[0], s, f, n, int(m), vp, sp,
                                          _stream_ptr(L.device))
-    _lib.check(st, "flood_filtration")
+    _finish(st, "flood_filtration", L.device, sync)
     return vals, srcs
 
 
-def filtration_batch(jobs, want_src: bool = False):
+def filtration_batch(jobs, want_src: bool = False, sync: bool = True):
     """Flood values of several clouds in one batched call.
 
     jobs: list of (grid, L, DeviceComplex, m). Returns a list of (values, src).
@@ -281,7 +302,7 @@ def filtration_batch(jobs, want_src: bool = False):
         outs.append((vals, srcs))
     with torch.cuda.device(dev):
         st = _lib.get().flood_filtration_batch(arr, len(jobs), _stream_ptr(dev))
-    _lib.check(st, "flood_filtration_batch")
+    _finish(st, "flood_filtration_batch", dev, sync)
     return outs
 
 
@@ -367,7 +388,8 @@ def _weights(weights, cx: DeviceComplex, device):
     return ws, P4(*ptrs), I32x4(*counts)
 
 
-def filtration_given(grid: Grid, L: torch.Tensor, cx: DeviceComplex, weights, want_src: bool = True):
+def filtration_given(grid: Grid, L: torch.Tensor, cx: DeviceComplex, weights, want_src: bool = True,
+                     sync: bool = True):
     """Flood values for given point sets P_sigma (§4.1; random draws, Lemma 4).
 
     weights[k]: float32 CUDA (n_k, S_k, k+1) barycentric coordinates of each
@@ -384,7 +406,7 @@ def filtration_given(grid: Grid, L: torch.Tensor, cx: DeviceComplex, weights, wa
     with torch.cuda.device(L.device):
         st = _lib.get().flood_filtration_given(grid.handle, _ptr(L), L.shape[0], s, f, n, wp, ns, vp, sp,
                                                _stream_ptr(L.device))
-    _lib.check(st, "flood_filtration_given")
+    _finish(st, "flood_filtration_given", L.device, sync)
     return vals, srcs
 
 

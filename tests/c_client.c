@@ -51,6 +51,11 @@ int main(void) {
         printf("filtration: %s\n", flood_last_error());
         return 1;
     }
+    /* the calls above are asynchronous: their device-side status arrives here */
+    if (flood_check(NULL) != FLOOD_OK) {
+        printf("check: %s\n", flood_last_error());
+        return 1;
+    }
     float v[4][6];
     for (int k = 0; k < 4; ++k) cudaMemcpy(v[k], dvals[k], n[k] * sizeof(float), cudaMemcpyDeviceToHost);
     flood_grid_destroy(grid);

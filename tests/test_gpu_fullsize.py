@@ -1,15 +1,20 @@
 """Parity at the full workload sizes (B300; slow).
 
-* 5,000,000-point union of 8 surfaces, 10,000 FPS landmarks, m = 12: FPS
-  checked by properties that hold at any size (every key equals the exact
-  binary32 minimum over earlier landmarks, keys never increase, and no
-  sampled point beats a pick or ties it with a lower index); flood values of
-  sampled simplices, over 10,000 seeded random landmarks, against the FP64
+* 5,000,000-point union of 8 surfaces, 10,000 FPS landmarks, m = 12: the CUDA
+  picks equal the oracle's picks (stored by tests/golden/make_fps_golden.py,
+  which runs only the oracle), index for index, and the keys bit for bit;
+  flood values of the complex of those landmarks (the workload's own
+  complex) on thousands of sampled simplices per dimension against the FP64
   k-d tree oracle.
+* 1,000,000-point noisy torus, 2,000 landmarks: the same check of the picks.
 * 1,000,000-point jittered torus, 2,000 landmarks, m = 10, upstream
   gradients ~ N(0,1): backward against the oracle's analytic subgradient and
   central differences (h = 1e-5) on 1,000 coordinates.
 """
+import hashlib
+import importlib.util
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -20,6 +25,7 @@ from paper_2509_22432_b300 import data, delaunay_complex
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL = 1e-5
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def _ops():
@@ -32,57 +38,57 @@ def _diam(X):
     return float(np.linalg.norm(X.max(0) - X.min(0)))
 
 
-def check_fps_properties(X, idx, key, n_sample=2000, seed=0):
-    """Sampled verification of FPS picks (binary32 keys, lowest-index ties)."""
-    n_l = idx.shape[0]
-    assert len(set(idx.tolist())) == n_l
-    L = X[idx]
-    # key[j] = min_{l < j} kappa(x_{idx[j]}, l), exactly
-    for j in range(1, n_l):
-        k = oracle.fps_key(L[:j], L[j]).min()
-        assert k == key[j], j
-    assert np.all(np.diff(key[1:]) <= 0)
-    # sampled points never beat (or tie with a lower index) the pick of any iteration
-    rng = np.random.default_rng(seed)
-    sample = rng.choice(X.shape[0], n_sample, replace=False)
-    d = np.full(n_sample, np.inf, np.float32)
-    for j in range(1, n_l):
-        d = np.minimum(d, oracle.fps_key(X[sample], L[j - 1]))
-        assert np.all(d <= key[j]), j
-        tie = d == key[j]
-        assert np.all(sample[tie] >= idx[j]), j
+def _golden(workload, X):
+    """The oracle's stored picks for this workload; the cloud must be the one they were computed on."""
+    spec = importlib.util.spec_from_file_location("make_fps_golden", os.path.join(HERE, "golden",
+                                                                                 "make_fps_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    g = mod.read(workload)
+    assert mod.cloud_sha256(X) == g["x_sha256"], "the seeded generator drew a different cloud on this host"
+    return g
+
+
+def _check_picks(X, n_l, workload):
+    g = _golden(workload, X)
+    idx, key = _ops().fps(torch.from_numpy(X).cuda(), n_l, 0)
+    idx, key = idx.cpu().numpy(), key.cpu().numpy()
+    assert np.array_equal(idx, g["idx"]), int(np.argmax(idx != g["idx"]))
+    assert hashlib.sha256(np.ascontiguousarray(key, np.float32).tobytes()).hexdigest() == g["key_sha256"]
+    return g
 
 
 @pytest.fixture(scope="module")
 def shapes5m():
     X = data.shape_mix_cloud()
-    Xd = torch.from_numpy(X).cuda()
-    idx, key = _ops().fps(Xd, 10_000, 0)
-    return X, Xd, idx.cpu().numpy(), key.cpu().numpy()
+    g = _check_picks(X, 10_000, "shapes-5M")
+    return X, g["idx"], np.uint32(int(g["last_key_hex"], 16)).view(np.float32)
 
 
-def test_fps_5m_properties(shapes5m):
-    X, _, idx, key = shapes5m
-    assert idx[0] == 0
-    check_fps_properties(X, idx, key)
+def test_fps_5m_equals_the_oracle_picks(shapes5m):
+    X, idx, _ = shapes5m
+    assert idx[0] == 0 and len(set(idx.tolist())) == 10_000
 
 
-def test_flood_5m_sampled_simplices(shapes5m):
-    """Landmarks: 10,000 seeded random rows of X (oracle inputs never come from the CUDA path;
-    the CUDA FPS picks are checked by properties above)."""
-    X, Xd, _, key = shapes5m
+def test_fps_1m_torus_equals_the_oracle_picks():
+    _check_picks(data.torus_cloud(1_000_000, seed=2), 2000, "torus-1M")
+
+
+def test_flood_5m_on_the_fps_complex(shapes5m):
+    """The workload's own complex: Delaunay of the 10,000 oracle (= CUDA) FPS landmarks, m = 12."""
+    X, idx, last_key = shapes5m
     ops = _ops()
     m = 12
-    idx = np.sort(np.random.default_rng(12).choice(X.shape[0], 10_000, replace=False))
     L = X[idx]
     cx = delaunay_complex(L)
-    grid = ops.build_grid(Xd, 0.5 * float(np.sqrt(key[-1])))
+    Xd = torch.from_numpy(X).cuda()
+    grid = ops.build_grid(Xd, 0.5 * float(np.sqrt(last_key)))
     vals, src = ops.filtration(grid, torch.from_numpy(L).cuda(), ops.to_device(cx, Xd.device), m)
     vals = [v.cpu().numpy() for v in vals]
     grid.close()
     rng = np.random.default_rng(1)
-    subset = [None] + [rng.choice(cx.counts[k], min(cx.counts[k], 1500), replace=False) for k in (1, 2, 3)]
-    subset[0] = np.arange(L.shape[0])
+    subset = [np.arange(L.shape[0])] + [rng.choice(cx.counts[k], min(cx.counts[k], 4000), replace=False)
+                                        for k in (1, 2, 3)]
     ref = oracle.flood_values(X, L, cx.simplices, m, method="kdtree", subset=subset)
     tol = TOL * _diam(X)
     for k in range(4):
@@ -90,7 +96,8 @@ def test_flood_5m_sampled_simplices(shapes5m):
         assert err <= tol, (k, err, tol)
     # monotone filtration over the whole complex
     for k in range(1, 4):
-        assert np.all(vals[k - 1][cx.facets[k]].max(axis=1) <= vals[k])
+        lower = vals[0][cx.simplices[1]] if k == 1 else vals[k - 1][cx.facets[k]]
+        assert np.all(lower.max(axis=1) <= vals[k])
 
 
 @pytest.fixture(scope="module")
