@@ -673,6 +673,22 @@ def main():
         # 3 FSUB + 2 FFMA + 1 FMUL + 1 FMNMX = 7 instructions per pair and lane)
         "alu_floor_ms": 1e3 * mk_pairs * 7 / (sms * FP32_LANES_PER_SM * sm_max * 1e6),
         "pair_ratio": mk_pairs / max(pairs, 1)}
+    # ---- persistence pairs of the step's filtration on the device (§2; the PH share of Table 1)
+    gph = ops.build_grid(Xd, cell)
+    ph_vals, _ = ops.filtration(gph, Xd[idx0], dcx, m, want_src=False)
+    gph.close()
+    ph_ms = []
+    for it in range(args.warmup + min(args.steps, 10)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ph = ops.persistence(dcx, ph_vals)            # synchronises its stream
+        if it >= args.warmup:
+            ph_ms.append(1e3 * (time.perf_counter() - t0))
+    line["persistence"] = {"device_ms": float(np.median(ph_ms)), "pairs": [int(p.shape[0]) for p in ph["pairs"]],
+                           "essential": [int(e.numel()) for e in ph["essential"]], "rounds": ph["rounds"],
+                           "what": "flood_persistence on the step's values: per-dimension bitonic order, parallel "
+                                   "Z/2 column reduction with clearing (call to return, synchronised)"}
+    ph_values = [v.cpu().numpy().astype(np.float64) for v in ph_vals]
     line["complex_faces"] = {"tetrahedra": int(cx.counts[3]), "device_ms": float(np.median(fc_dev)),
                              "host_ms": fc_host, "what": "triangles, edges and facet incidence from the "
                              "tetrahedra: flood_complex_faces (call to return, synchronised) vs the host "
@@ -695,6 +711,11 @@ def main():
         cb = cpu_baseline(X, wl, args.workload)
         if cb is not None:
             line["cpu_baseline"] = cb
+        # the oracle's host reduction of the same filtration, beside the device's
+        import oracle
+        t0 = time.perf_counter()
+        oracle.persistence_pairs(cx.simplices, cx.facets, ph_values)
+        line["persistence"]["host_oracle_ms"] = 1e3 * (time.perf_counter() - t0)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

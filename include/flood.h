@@ -397,6 +397,40 @@ int flood_masking_ball_counts(const flood_grid* grid, const float* L, int32_t n_
                               int64_t counts_out[4], void* stream);
 
 /* ------------------------------------------------------------------------
+ * flood_persistence — persistence pairs of the flood filtration (§2), on
+ * the device.
+ *
+ * The values make the complex a filtration (every face's value <= its
+ * cofaces'); §2's persistence diagrams pair the simplex that creates each
+ * homology class with the one that kills it. Simplices are ordered by
+ * (value, dimension, lexicographic vertex ids), faces before cofaces on ties,
+ * and the Z/2 boundary matrix is reduced with clearing (twist), higher
+ * dimensions first. The reduction runs in parallel rounds of left-to-right
+ * column additions; any reduced form reached that way has the pivots of the
+ * sequential reduction, so the pairs are those of the standard algorithm.
+ *   simplices, facets, n_simplices   as flood_filtration (device; vertex ids
+ *                    < 2^21; simplices[0] is ignored: vertex i is row i)
+ *   values[k]        device float32 (n_k): the flood values (finite, >= 0)
+ *   pairs[k]         device int32 capacity (n_{k+1}, 2), k = 0..2: (birth row
+ *                    of dimension k, death row of dimension k+1) per finite
+ *                    pair (zero-persistence pairs included), in the deaths'
+ *                    filtration order; n_pairs[k] (host) receives the count
+ *   essential[k]     device int32 capacity n_k, k = 0..3: rows of dimension
+ *                    k whose class never dies, in filtration order;
+ *                    n_essential[k] (host) receives the count
+ *   rounds           host int64[4] or NULL: parallel rounds per dimension
+ * The diagram dgm_k is {(values[k][b], values[k+1][d])} over pairs[k] with
+ * d's value above b's, plus (values[k][e], inf) per essential row.
+ * Errors: FLOOD_EINVAL (sizes, NULL arrays, ids out of range, a value that is
+ * negative or not finite), FLOOD_ENOMEM, FLOOD_ECAPACITY (columns beyond
+ * 2^31 entries), FLOOD_ECUDA. Synchronises `stream`.
+ * ------------------------------------------------------------------------ */
+int flood_persistence(const int32_t* const simplices[4], const int32_t* const facets[4],
+                      const int64_t n_simplices[4], const float* const values[4], int32_t* const pairs[3],
+                      int64_t n_pairs[3], int32_t* const essential[4], int64_t n_essential[4], int64_t rounds[4],
+                      void* stream);
+
+/* ------------------------------------------------------------------------
  * flood_fp32_peak_probe — measured FP32 FMA throughput (roofline helper).
  *
  * Not part of the method: the flood kernels are bound by the FP32 pipe when

@@ -144,6 +144,8 @@ _SIGNATURES = {
     "flood_tuning_entries": (C.c_int, [C.POINTER(TuningEntry), C.c_int32, C.POINTER(C.c_int32)]),
     "flood_tuning_clear": (C.c_int, []),
     "flood_check": (C.c_int, [C.c_void_p]),
+    "flood_persistence": (C.c_int, [P4, P4, I64x4, P4, C.c_void_p * 3, C.c_int64 * 3, P4, I64x4,
+                                    C.POINTER(C.c_int64), C.c_void_p]),
     "flood_last_error": (C.c_char_p, []),
     "flood_version": (C.c_char_p, []),
     "flood_kernel_launches": (C.c_int64, []),

@@ -19,7 +19,7 @@ from ._lib import FloodError, P4, I64x4, I32x4
 __all__ = ["check", "fps", "fps_noalloc", "fps_stats", "fps_scratch_bytes", "fps_wait_test", "masking_ball_counts",
            "fp32_peak_probe", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
            "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
-           "complex_faces", "filtration_masked",
+           "complex_faces", "filtration_masked", "persistence", "diagrams_from_pairs",
            "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given"]
 
 
@@ -311,6 +311,45 @@ def last_filtration_stats() -> dict:
     _lib.check(_lib.get().flood_last_filtration_stats(C.byref(st)), "flood_last_filtration_stats")
     return {k: list(getattr(st, k)) for k in ("simplices", "samples", "pairs", "work_items", "active_samples",
                                                "shells", "tiles", "flood_kernel_ms")}
+
+
+def persistence(cx: DeviceComplex, values) -> dict:
+    """Persistence pairs of the flood filtration on the device (flood_persistence, §2).
+
+    values: float32 CUDA tensors per dimension (the flood values of cx).
+    Returns {"pairs": [k -> int32 (n, 2) CUDA tensor of (birth row of dim k,
+    death row of dim k+1)] for k = 0..2, "essential": [k -> int32 rows] for
+    k = 0..3, "rounds": [parallel reduction rounds per dimension]}.
+    """
+    dev = values[0].device
+    counts = cx.counts + [0] * (4 - len(cx.counts))
+    s, f, n = cx.arrays()
+    vals = [v.to(torch.float32).contiguous() for v in values] + [None] * (4 - len(values))
+    vp = P4(*[_ptr(v) if v is not None and v.numel() else C.c_void_p(0) for v in vals])
+    pairs = [torch.empty((max(counts[k + 1], 1), 2), dtype=torch.int32, device=dev) for k in range(3)]
+    ess = [torch.empty(max(counts[k], 1), dtype=torch.int32, device=dev) for k in range(4)]
+    pp = (C.c_void_p * 3)(*[_ptr(t) for t in pairs])
+    ep = P4(*[_ptr(t) for t in ess])
+    n_pairs, n_ess, rounds = (C.c_int64 * 3)(), I64x4(), I64x4()
+    with torch.cuda.device(dev):
+        st = _lib.get().flood_persistence(s, f, n, vp, pp, n_pairs, ep, n_ess, rounds, _stream_ptr(dev))
+    _lib.check(st, "flood_persistence")
+    return {"pairs": [pairs[k][:n_pairs[k]] for k in range(3)], "essential": [ess[k][:n_ess[k]] for k in range(4)],
+            "rounds": [int(r) for r in rounds]}
+
+
+def diagrams_from_pairs(ph: dict, values, max_dim: int = 2) -> list:
+    """dgm_0..dgm_max_dim (host float64 (n, 2), death inf for essential classes) from persistence()."""
+    v = [np.asarray(x.cpu().numpy() if isinstance(x, torch.Tensor) else x, dtype=np.float64) for x in values]
+    out = []
+    for k in range(max_dim + 1):
+        pr = ph["pairs"][k].cpu().numpy()
+        b, d = v[k][pr[:, 0]], v[k + 1][pr[:, 1]]
+        keep = d > b
+        e = v[k][ph["essential"][k].cpu().numpy()]
+        pts = np.concatenate([np.stack([b[keep], d[keep]], 1), np.stack([e, np.full(e.shape, np.inf)], 1)])
+        out.append(pts[np.lexsort((pts[:, 1], pts[:, 0]))].reshape(-1, 2))
+    return out
 
 
 def kernel_launches() -> int:
