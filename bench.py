@@ -41,7 +41,8 @@ FLOPS_PER_PAIR = 6               # one pair = 3 FMAs: |x'|^2 - 2 p'.x'
 # (k_flood_heavy and k_flood, dimensions 1-3: six launches), from one ncu
 # capture; valid only while the filtration source is the one captured, else
 # reported as null.
-FLOOD_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": None, "filtration_cu_sha256": None}
+FLOOD_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 153_871_616 + 261_632,
+                      "filtration_cu_sha256": "ebe5e47a0e3e46047f6e898146d69d1dc146134f58698e6774e1e9c5f8db9deb"}
 
 
 def _source_sha(name: str):
@@ -345,6 +346,8 @@ def main():
     ap.add_argument("--workload", default="torus-1M", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="take the tuning table's parameters instead of sweeping them first (profiling runs)")
     ap.add_argument("--serving", action="store_true",
                     help="sweep the batched-serving workload (512 clouds, Poisson rates 50..2000/s)")
     args = ap.parse_args()
@@ -390,7 +393,11 @@ def main():
     # heavy-group threshold, measured on this workload and kept in the tuning table
     from paper_2509_22432_b300 import tune
     cover = float(np.sqrt(key0[-1].item()))                # FPS covering radius
-    tuned = tune.tune_workload(Xd, Xd[idx0], dcx, m, cover)
+    if args.no_tune:
+        t = tune.lookup(wl["n"], n_l, m)
+        tuned = {"cell_factor": t["cell_factor"], "heavy_shells": t["heavy_shells"], "ms": None, "default_ms": None}
+    else:
+        tuned = tune.tune_workload(Xd, Xd[idx0], dcx, m, cover)
     cell = tuned["cell_factor"] * cover
     n_simp = sum(cx.counts[1:])
     stream = torch.cuda.current_stream(dev)
