@@ -284,67 +284,141 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
     }
 }
 
-// Groups never span coarse cubes (their samples share the cube corner as the
-// origin of the pair arithmetic).
-__global__ void k_group_counts(const int32_t* bucket_start, int64_t n_coarse, int32_t* n_groups) {
-    const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (c >= n_coarse) return;
-    const int32_t cnt = bucket_start[(c + 1) * kFine] - bucket_start[c * kFine];
-    n_groups[c] = (cnt + kGroup - 1) / kGroup;
-}
+// Bucket offsets and the group list, from the bucket counts, in two
+// launches. Groups never span coarse cubes (their samples share the cube
+// corner as the origin of the pair arithmetic): cube c holds
+// ceil(samples(c) / kGroup) groups. Both prefix sums (samples over buckets,
+// groups over cubes) run over tiles of kCubeTile cubes: the first kernel
+// sums each tile, the second adds the sums of the tiles before its own (a
+// block reduction over at most a few hundred values) to its block scan.
+constexpr int kCubeTile = 1024;  // cubes per block (one per thread)
 
-__global__ void k_group_fill(const int32_t* group_off, int64_t n_coarse, int2* groups) {
-    const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (c >= n_coarse) return;
-    const int32_t o = group_off[c], e = group_off[c + 1];
-    for (int32_t j = o; j < e; ++j) groups[j] = make_int2(static_cast<int>(c), j - o);
-}
-
-// The three steps above in one block, for lattices of up to 16 x 1024 coarse
-// cubes: thread t takes a run of consecutive cubes, a block scan of the runs'
-// group counts places them.
-constexpr int kGroupOffThreads = 1024;
-constexpr int64_t kGroupOffMaxCubes = int64_t(16) * kGroupOffThreads;
-
-__global__ void __launch_bounds__(kGroupOffThreads) k_group_offsets_one_block(const int32_t* bucket_start,
-                                                                             int64_t n_coarse, int32_t* group_off,
-                                                                             int2* groups) {
-    __shared__ int32_t s_warp[kGroupOffThreads / 32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t per = (n_coarse + kGroupOffThreads - 1) / kGroupOffThreads;
-    const int64_t c0 = min(n_coarse, t * per), c1 = min(n_coarse, c0 + per);
-    auto groups_of = [&](int64_t c) {
-        const int32_t cnt = bucket_start[(c + 1) * kFine] - bucket_start[c * kFine];
-        return (cnt + kGroup - 1) / kGroup;
-    };
-    int32_t mine = 0;
-    for (int64_t c = c0; c < c1; ++c) mine += groups_of(c);
-    int32_t incl = mine;
+__device__ __forceinline__ int32_t cube_samples(const int32_t* count, int64_t c, int64_t n_coarse) {
+    if (c >= n_coarse) return 0;
+    int32_t t = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+    for (int f = 0; f < kFine; ++f) t += count[c * kFine + f];
+    return t;
+}
+
+__global__ void __launch_bounds__(kCubeTile) k_cube_sums(const int32_t* count, int64_t n_coarse,
+                                                        int32_t* tile_samples, int32_t* tile_groups) {
+    const int64_t c = blockIdx.x * int64_t(kCubeTile) + threadIdx.x;
+    const int32_t ns = cube_samples(count, c, n_coarse);
+    __shared__ int32_t s_red[2][kCubeTile / 32];
+    int32_t a = ns, g = (ns + kGroup - 1) / kGroup;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        g += __shfl_xor_sync(0xffffffffu, g, o);
     }
-    if (lane == 31) s_warp[warp] = incl;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_red[0][warp] = a;
+        s_red[1][warp] = g;
+    }
     __syncthreads();
     if (warp == 0) {
-        int32_t w = s_warp[lane];
+        a = s_red[0][lane];
+        g = s_red[1][lane];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
         }
-        s_warp[lane] = w;  // inclusive over warps
+        if (lane == 0) {
+            tile_samples[blockIdx.x] = a;
+            tile_groups[blockIdx.x] = g;
+        }
+    }
+}
+
+// bucket_start[0..n_coarse * kFine] and group_off[0..n_coarse] (the last
+// entries are the totals) and groups[] = (cube, index within the cube).
+__global__ void __launch_bounds__(kCubeTile) k_cube_scan(const int32_t* count, int64_t n_coarse,
+                                                        const int32_t* tile_samples, const int32_t* tile_groups,
+                                                        int32_t* bucket_start, int32_t* group_off, int2* groups) {
+    __shared__ int32_t s_red[2][kCubeTile / 32];
+    __shared__ int32_t s_base[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // sums of the tiles before this one
+    int32_t ps = 0, pg = 0;
+    for (int t = threadIdx.x; t < static_cast<int>(blockIdx.x); t += kCubeTile) {
+        ps += tile_samples[t];
+        pg += tile_groups[t];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ps += __shfl_xor_sync(0xffffffffu, ps, o);
+        pg += __shfl_xor_sync(0xffffffffu, pg, o);
+    }
+    if (lane == 0) {
+        s_red[0][warp] = ps;
+        s_red[1][warp] = pg;
     }
     __syncthreads();
-    int32_t off = (warp > 0 ? s_warp[warp - 1] : 0) + incl - mine;
-    for (int64_t c = c0; c < c1; ++c) {
-        const int32_t ng = groups_of(c);
-        group_off[c] = off;
-        for (int32_t j = 0; j < ng; ++j) groups[off + j] = make_int2(static_cast<int>(c), j);
-        off += ng;
+    if (warp == 0) {
+        ps = s_red[0][lane];
+        pg = s_red[1][lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ps += __shfl_xor_sync(0xffffffffu, ps, o);
+            pg += __shfl_xor_sync(0xffffffffu, pg, o);
+        }
+        if (lane == 0) {
+            s_base[0] = ps;
+            s_base[1] = pg;
+        }
     }
-    if (t == kGroupOffThreads - 1) group_off[n_coarse] = s_warp[31];
+    __syncthreads();
+    // block scan of this tile's (samples, groups) per cube
+    const int64_t c = blockIdx.x * int64_t(kCubeTile) + threadIdx.x;
+    const int32_t ns = cube_samples(count, c, n_coarse), ng = (ns + kGroup - 1) / kGroup;
+    int32_t is = ns, ig = ng;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t ys = __shfl_up_sync(0xffffffffu, is, o), yg = __shfl_up_sync(0xffffffffu, ig, o);
+        if (lane >= o) {
+            is += ys;
+            ig += yg;
+        }
+    }
+    __syncthreads();  // s_red is reused
+    if (lane == 31) {
+        s_red[0][warp] = is;
+        s_red[1][warp] = ig;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int32_t ws = s_red[0][lane], wg = s_red[1][lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t ys = __shfl_up_sync(0xffffffffu, ws, o), yg = __shfl_up_sync(0xffffffffu, wg, o);
+            if (lane >= o) {
+                ws += ys;
+                wg += yg;
+            }
+        }
+        s_red[0][lane] = ws;  // inclusive over warps
+        s_red[1][lane] = wg;
+    }
+    __syncthreads();
+    const int32_t off_s = s_base[0] + (warp > 0 ? s_red[0][warp - 1] : 0) + is - ns;
+    const int32_t off_g = s_base[1] + (warp > 0 ? s_red[1][warp - 1] : 0) + ig - ng;
+    if (c < n_coarse) {
+        int32_t run = off_s;
+#pragma unroll
+        for (int f = 0; f < kFine; ++f) {
+            bucket_start[c * kFine + f] = run;
+            run += count[c * kFine + f];
+        }
+        group_off[c] = off_g;
+        for (int32_t j = 0; j < ng; ++j) groups[off_g + j] = make_int2(static_cast<int>(c), j);
+        if (c == n_coarse - 1) {  // totals
+            bucket_start[n_coarse * kFine] = run;
+            group_off[n_coarse] = off_g + ng;
+        }
+    }
 }
 
 // Longest-first queue: groups are counting-sorted by the number of shells
@@ -371,9 +445,11 @@ __global__ void k_group_class_count(DimArgs a, const int32_t* n_groups, int32_t*
 // also stores it: entry kClasses - heavy_shells is the heavy prefix), then
 // places its groups.
 __global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const int32_t* class_count,
-                                      int32_t* class_start, int32_t* class_fill, int2* sorted) {
+                                      int32_t* class_start, int32_t* class_fill, int2* sorted,
+                                      int32_t* groups_out) {
     static_assert(kClasses == 64, "two lanes' worth of classes per lane of one warp");
     __shared__ int32_t s_start[kClasses + 1];
+    if (blockIdx.x == 0 && threadIdx.x == 32) *groups_out = *n_groups;  // work items of this job (statistics)
     if (threadIdx.x < 32) {
         const int l = threadIdx.x;
         const int32_t c0 = class_count[2 * l], c1 = class_count[2 * l + 1];
@@ -781,7 +857,8 @@ __device__ __forceinline__ int job_of(const int32_t* off, int n, int32_t item) {
 }
 
 // Light groups of every cloud of the batch: the queue is the concatenation of
-// each cloud's sorted groups after its heavy prefix (offsets in light_off).
+// each cloud's sorted groups after its heavy prefix (offsets in light_off;
+// NULL for a single cloud).
 __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int n_jobs, const int32_t* light_off,
                                                        Ctl* ctl, int k) {
     extern __shared__ __align__(128) float4 s_tiles[];  // kWarps x 2 x kWTile
@@ -799,17 +876,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
     uint32_t phases = 0u;
     bool abort = false;
     WarpCounters cnt;
-    const int32_t total = light_off[n_jobs];
+    // one cloud: its light groups follow its heavy prefix; a batch: offsets per cloud
+    const int32_t total = light_off ? light_off[n_jobs] : jobs[0].group_off[jobs[0].n_coarse] - *jobs[0].n_heavy;
     for (;;) {
         int item = 0;
         if (lane == 0) item = static_cast<int>(atomicAdd(&ctl->head[k], 1u));
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total || abort) break;
-        const int j = job_of(light_off, n_jobs, item);
+        const int j = light_off ? job_of(light_off, n_jobs, item) : 0;
         const DimArgs& a = jobs[j];
         const GridView gv = a.geo->g;
         const Lattice lat = a.geo->lat;
-        const int2 gb = a.groups[*a.n_heavy + (item - light_off[j])];
+        const int2 gb = a.groups[*a.n_heavy + (item - (light_off ? light_off[j] : 0))];
         const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
         const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
         // coarse cube corner: the origin of the pair arithmetic for this group
@@ -884,18 +962,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
     __syncthreads();
     uint32_t phases = 0u;
     unsigned long long pairs = 0ull, n_shells = 0ull, n_tiles = 0ull;
-    const int32_t n_heavy = heavy_off[n_jobs];
+    const int32_t n_heavy = heavy_off ? heavy_off[n_jobs] : *jobs[0].n_heavy;
     for (;;) {
         if (tid == 0) s_item = static_cast<int>(atomicAdd(&ctl->heavy_head[k], 1u));
         __syncthreads();
         const int item = s_item;
         if (item >= n_heavy || s_abort) break;
-        const int jb = job_of(heavy_off, n_jobs, item);
+        const int jb = heavy_off ? job_of(heavy_off, n_jobs, item) : 0;
         const DimArgs& a = jobs[jb];
         const GridView g = a.geo->g;
         const Lattice lat = a.geo->lat;
         const float shell_h = a.geo->shell_h, shell_slack = a.geo->shell_slack;
-        const int2 gb = a.groups[item - heavy_off[jb]];
+        const int2 gb = a.groups[item - (heavy_off ? heavy_off[jb] : 0)];
         const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
         const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
         const int n_valid = s_end - s_begin;
@@ -1487,6 +1565,7 @@ struct JobState {
     int32_t *bcount[4], *bfill[4], *cls[4];
     unsigned long long* best[4];
     int32_t *bstart, *goff;
+    int32_t* tile_sums;  // per tile of kCubeTile cubes: samples, then groups
     int2 *groups, *groups_sorted;
     SampleRec* recs;
     int heavy_shells;  // groups with at least this many shells go to the CTA kernel
@@ -1610,6 +1689,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
         note_launch();
         J.max_groups = J.max_samples / kGroup + J.n_coarse + 1;
         if ((rc = scr.alloc(&J.bstart, J.n_buckets + 1)) || (rc = scr.alloc(&J.goff, J.n_coarse + 1)) ||
+            (rc = scr.alloc(&J.tile_sums, 2 * ceil_div(J.n_coarse, kCubeTile))) ||
             (rc = scr.alloc(&J.groups, J.max_groups)) || (rc = scr.alloc(&J.groups_sorted, J.max_groups)) ||
             (rc = scr.alloc(&J.recs, J.max_samples)))
             return rc;
@@ -1634,29 +1714,26 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
         }
         J.heavy_shells = tuning_for(grid->n_points, J.in.n_landmarks, J.in.m).heavy_shells;
     }
-    DimArgs* d_jobs;
-    int32_t *d_off, *d_counts;
-    if ((rc = scr.alloc(&d_jobs, std::max(n_jobs, 1))) || (rc = scr.alloc(&d_off, 2 * (n_jobs + 1))) ||
-        (rc = scr.alloc(&d_counts, 4 * std::max(n_jobs, 1))))
-        return rc;
+    int32_t* d_counts;  // work items per (job, dimension), for the statistics
+    if ((rc = scr.alloc(&d_counts, 4 * std::max(n_jobs, 1)))) return rc;
     FLOOD_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * 4 * std::max(n_jobs, 1), s));
-    std::vector<DimArgs> h_jobs;
-    h_jobs.reserve(n_jobs);
     g_last.valid = false;
     if ((rc = g_last.events())) return rc;
     for (int k = 0; k < 4; ++k) g_last.timed[k] = false;
+    // every dimension's job table, built and uploaded at once (all pointers are known now)
+    std::vector<DimArgs> h_jobs;
+    std::vector<int> job_of_entry;
+    int first[5] = {0, 0, 0, 0, 0};
     for (int k = 1; k <= 3; ++k) {
-        h_jobs.clear();
+        first[k] = static_cast<int>(h_jobs.size());
         for (int i = 0; i < n_jobs; ++i) {
             JobState& J = js[i];
-            const int64_t n = J.nk[k];
-            if (n == 0) continue;
-            if (J.I[k] == 0) continue;
+            if (J.nk[k] == 0 || J.I[k] == 0) continue;
             DimArgs a{};
             a.k = k;
             a.I = J.I[k];
             a.m = static_cast<float>(J.in.m);
-            a.n = n;
+            a.n = J.nk[k];
             a.simplices = J.in.simplices[k];
             a.facets = k >= 2 ? J.in.facets[k] : nullptr;
             a.val_lower = J.val[k - 1];
@@ -1673,56 +1750,60 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             a.bucket_start = J.bstart;
             a.bucket_fill = J.bfill[k];
             a.group_off = J.goff;
-            a.groups = J.groups;
+            a.groups = J.groups_sorted;  // the flood kernels read the longest-first order
             a.recs = J.recs;
             a.best = J.best[k];
             a.ctl = ctl;
-            const unsigned wb = static_cast<unsigned>(ceil_div(n * 32, 256));
+            // heavy groups: shell bound >= heavy_shells, i.e. classes [0, kClasses - heavy_shells)
+            a.n_heavy = J.cls[k] + 2 * kClasses + (kClasses - J.heavy_shells);
+            h_jobs.push_back(a);
+            job_of_entry.push_back(i);
+        }
+    }
+    first[4] = static_cast<int>(h_jobs.size());
+    DimArgs* d_jobs = nullptr;
+    int32_t* d_off = nullptr;  // queue offsets (batches of several clouds)
+    if (!h_jobs.empty()) {
+        if ((rc = scr.alloc(&d_jobs, h_jobs.size())) || (rc = scr.alloc(&d_off, 2 * (n_jobs + 1)))) return rc;
+        FLOOD_CUDA(cudaMemcpyAsync(d_jobs, h_jobs.data(), sizeof(DimArgs) * h_jobs.size(), cudaMemcpyHostToDevice, s));
+    }
+    for (int k = 1; k <= 3; ++k) {
+        const int nj = first[k + 1] - first[k];
+        for (int e = first[k]; e < first[k + 1]; ++e) {
+            DimArgs a = h_jobs[e];
+            JobState& J = js[job_of_entry[e]];
+            a.groups = J.groups;  // preparation kernels fill the cube order; the class scatter sorts it
+            const unsigned wb = static_cast<unsigned>(ceil_div(a.n * 32, 256));
             k_samples<false><<<wb, 256, 0, s>>>(a);
-            note_launch();
-            if ((rc = exclusive_scan(J.bcount[k], J.bstart, J.n_buckets, s, scr))) return rc;
+            const unsigned tiles = static_cast<unsigned>(ceil_div(J.n_coarse, kCubeTile));
+            k_cube_sums<<<tiles, kCubeTile, 0, s>>>(J.bcount[k], J.n_coarse, J.tile_sums, J.tile_sums + tiles);
+            k_cube_scan<<<tiles, kCubeTile, 0, s>>>(J.bcount[k], J.n_coarse, J.tile_sums, J.tile_sums + tiles,
+                                                    J.bstart, J.goff, J.groups);
             k_samples<true><<<wb, 256, 0, s>>>(a);
-            note_launch();
-            if (J.n_coarse <= kGroupOffMaxCubes) {
-                k_group_offsets_one_block<<<1, kGroupOffThreads, 0, s>>>(J.bstart, J.n_coarse, J.goff, J.groups);
-                note_launch();
-            } else {
-                const unsigned bb = static_cast<unsigned>(ceil_div(J.n_coarse, 256));
-                k_group_counts<<<bb, 256, 0, s>>>(J.bstart, J.n_coarse, J.bcount[k]);
-                note_launch();
-                if ((rc = exclusive_scan(J.bcount[k], J.goff, J.n_coarse, s, scr))) return rc;
-                k_group_fill<<<bb, 256, 0, s>>>(J.goff, J.n_coarse, J.groups);
-                note_launch();
-            }
             // longest-first order of this cloud's groups; the count stays on the device
             const int32_t* n_groups = J.goff + J.n_coarse;
             // cls: counts [0, kClasses), fill [kClasses, 2 kClasses), starts [2 kClasses, 3 kClasses + 1)
             const unsigned gbk = static_cast<unsigned>(ceil_div(J.max_groups, 256));
             int32_t* cls = J.cls[k];
             k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, cls);
-            note_launch();
             k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, cls, cls + 2 * kClasses, cls + kClasses,
-                                                      J.groups_sorted);
-            note_launch();
+                                                      J.groups_sorted, d_counts + job_of_entry[e] * 4 + k);
+            note_launch(6);
             FLOOD_CUDA(cudaGetLastError());
-            a.groups = J.groups_sorted;
-            // heavy groups: shell bound >= heavy_shells, i.e. classes [0, kClasses - heavy_shells)
-            a.n_heavy = cls + 2 * kClasses + (kClasses - J.heavy_shells);
-            FLOOD_CUDA(cudaMemcpyAsync(d_counts + i * 4 + k, n_groups, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-            h_jobs.push_back(a);
         }
-        const int nj = static_cast<int>(h_jobs.size());
         if (nj > 0) {
-            DimArgs* dj = d_jobs;
-            // the per-dimension job table lives in its own buffer (earlier launches may still read the old one)
-            if (k > 1 && (rc = scr.alloc(&dj, nj))) return rc;
-            FLOOD_CUDA(cudaMemcpyAsync(dj, h_jobs.data(), sizeof(DimArgs) * nj, cudaMemcpyHostToDevice, s));
-            int32_t* heavy_off = d_off;
-            int32_t* light_off = d_off + (n_jobs + 1);
-            if (k > 1 && (rc = scr.alloc(&heavy_off, 2 * (nj + 1)))) return rc;
-            if (k > 1) light_off = heavy_off + (nj + 1);
-            k_queue_offsets<<<1, 32, 0, s>>>(dj, nj, heavy_off, light_off);
-            note_launch();
+            const DimArgs* dj = d_jobs + first[k];
+            // a batch needs the queue offsets of its clouds; one cloud's queues start at 0
+            int32_t* heavy_off = nullptr;
+            int32_t* light_off = nullptr;
+            if (nj > 1) {
+                heavy_off = d_off;
+                light_off = d_off + (nj + 1);
+                if (k > 1 && (rc = scr.alloc(&heavy_off, 2 * (nj + 1)))) return rc;  // earlier launches may read d_off
+                if (k > 1) light_off = heavy_off + (nj + 1);
+                k_queue_offsets<<<1, 32, 0, s>>>(dj, nj, heavy_off, light_off);
+                note_launch();
+            }
             FLOOD_CUDA(cudaEventRecord(g_last.ev[k][0], s));
             SideStream* side;
             if ((rc = side_stream(&side))) return rc;

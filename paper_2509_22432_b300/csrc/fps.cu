@@ -431,29 +431,26 @@ __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, in
     }
     // Picks: the best live entry while its minimum stays positive and above
     // the bound (the first one unconditionally); each pick lowers the others.
-    // The best is found with two 32-bit reductions: the largest minimum, then
-    // among the lanes holding it the lowest row, through the rank of each
-    // lane's row among the entries (rows are distinct) packed with the lane.
+    // The best is the largest candidate word (minimum, then lowest row: rows
+    // are distinct), found with one 64-bit warp maximum; its lane by a ballot.
     const int cap = min(picks_left, kMaxPicks);
     const uint32_t row = cand_row(me);
     float cur = cand_key(me);
     bool live = me != 0ull;
-    uint32_t rank = 0u;
-#pragma unroll 8
-    for (int i = 0; i < 32; ++i) rank += __shfl_sync(0xffffffffu, row, i) < row;
-    const uint32_t tag = (rank << 5) | static_cast<uint32_t>(lane);
     int np = 0;
     while (np < cap) {
-        const uint32_t kb = live ? __float_as_uint(cur) : 0u;  // minima are >= +0: bits order like values
-        const uint32_t mh = __reduce_max_sync(0xffffffffu, kb);
-        if (np > 0 && !(__uint_as_float(mh) > 0.0f && __uint_as_float(mh) > bound)) break;
-        const uint32_t sel = __reduce_min_sync(0xffffffffu, live && kb == mh ? tag : 0xffffffffu);
-        if (sel == 0xffffffffu) {  // no entry at all: an empty pick (reported as degenerate)
-            if (lane == 0) s.pick[np] = 0ull;
-            ++np;
+        const uint64_t w = live ? pack_cand(cur, row) : 0ull;  // non-zero for every live entry
+        const uint64_t mw = warp_max_u64(w);
+        if (mw == 0ull) {  // no entry left: the round ends (with none at all, an empty pick: degenerate)
+            if (np == 0) {
+                if (lane == 0) s.pick[0] = 0ull;
+                np = 1;
+            }
             break;
         }
-        const int o = static_cast<int>(sel & 31u);
+        const float mk = cand_key(mw);
+        if (np > 0 && !(mk > 0.0f && mk > bound)) break;
+        const int o = __ffs(__ballot_sync(0xffffffffu, live && w == mw)) - 1;
         const float qx = __shfl_sync(0xffffffffu, mx, o), qy = __shfl_sync(0xffffffffu, my, o),
                     qz = __shfl_sync(0xffffffffu, mz, o);
         if (lane == o) {
