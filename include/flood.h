@@ -405,9 +405,11 @@ int flood_masking_ball_counts(const flood_grid* grid, const float* L, int32_t n_
  * homology class with the one that kills it. Simplices are ordered by
  * (value, dimension, lexicographic vertex ids), faces before cofaces on ties,
  * and the Z/2 boundary matrix is reduced with clearing (twist), higher
- * dimensions first. The reduction runs in parallel rounds of left-to-right
- * column additions; any reduced form reached that way has the pivots of the
- * sequential reduction, so the pairs are those of the standard algorithm.
+ * dimensions first; the tetrahedra's pairs come from the anti-transposed
+ * (coboundary) matrix, which has the same pairs. The reduction runs in
+ * parallel rounds of left-to-right column additions; any reduced form
+ * reached that way has the pivots of the sequential reduction, so the pairs
+ * are those of the standard algorithm.
  *   simplices, facets, n_simplices   as flood_filtration (device; vertex ids
  *                    < 2^21; simplices[0] is ignored: vertex i is row i)
  *   values[k]        device float32 (n_k): the flood values (finite, >= 0)

@@ -21,6 +21,13 @@
 //   3. clear   a simplex that is the pivot of a reduced column of dimension
 //              k+1 creates a class, so its own column would reduce to zero:
 //              it is skipped in dimension k.
+// The tetrahedra are reduced on the anti-transposed matrix instead (columns:
+// the triangles in reverse order, entries: the tetrahedra that contain them,
+// in reverse order), whose pairs are the same (the pairing of a filtration
+// and of its coboundary matrix agree). Its columns have at most two entries
+// in a triangulated region of space and reduce like a graph's edges, in few
+// rounds; the boundary columns of the tetrahedra of a void would need a
+// round per step of a chain as long as the void's tetrahedra.
 // Columns live in one pool of int32 rows; a sum is written to fresh space
 // (an atomic bump of the pool head), and a full pool is compacted into a
 // larger one between rounds.
@@ -119,6 +126,53 @@ __global__ void k_init_columns(int k, int64_t n, const int32_t* order_k, const i
     off[c] = static_cast<int32_t>(c * (k + 1));
     for (int j = 0; j <= k; ++j) pool[c * (k + 1) + j] = e[j];
     len[c] = cleared && cleared[c] ? 0 : k + 1;
+}
+
+// Coboundary columns of the triangles (the anti-transposed boundary matrix of
+// the tetrahedra): per triangle position, the reversed positions n3-1-p of
+// the tetrahedra that contain it.
+__global__ void k_count_cofaces(int64_t n3, const int32_t* facets3, const int32_t* pos2, int64_t n2, int32_t* cnt,
+                                uint32_t* flags) {
+    const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (t >= n3) return;
+    for (int j = 0; j < 4; ++j) {
+        const int32_t f = facets3[t * 4 + j];
+        if (f < 0 || f >= n2) {
+            atomicOr(flags, FLAG_RANGE);
+            continue;
+        }
+        atomicAdd(&cnt[pos2[f]], 1);
+    }
+}
+
+__global__ void k_fill_cofaces(int64_t n3, const int32_t* facets3, const int32_t* pos2, int64_t n2,
+                               const int32_t* pos3, const int32_t* ptr, int32_t* fill, int32_t* entries) {
+    const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (t >= n3) return;
+    const int32_t rev = static_cast<int32_t>(n3 - 1 - pos3[t]);
+    for (int j = 0; j < 4; ++j) {
+        const int32_t f = facets3[t * 4 + j];
+        if (f < 0 || f >= n2) continue;
+        const int32_t p = pos2[f];
+        entries[ptr[p] + atomicAdd(&fill[p], 1)] = rev;
+    }
+}
+
+// Column c of the coboundary matrix is triangle position n2-1-c: its entries
+// sorted in place (a triangle has few cofaces); cleared columns are empty.
+__global__ void k_init_coface_columns(int64_t n2, const int32_t* ptr, int32_t* pool, int32_t* off, int32_t* len) {
+    const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (c >= n2) return;
+    const int64_t p = n2 - 1 - c;
+    const int32_t b = ptr[p], e = ptr[p + 1];
+    for (int32_t a = b + 1; a < e; ++a)
+        for (int32_t q = a; q > b && pool[q - 1] > pool[q]; --q) {
+            const int32_t t = pool[q];
+            pool[q] = pool[q - 1];
+            pool[q - 1] = t;
+        }
+    off[c] = b;
+    len[c] = e - b;
 }
 
 // Round r, first half: the earliest column holding each pivot. owner[row] =
@@ -251,36 +305,77 @@ int order_dimension(int k, int64_t n, const int32_t* simplices, const float* val
     return FLOOD_OK;
 }
 
-// Reduce the columns of dimension k (rows: positions of dimension k-1).
-// low[c] receives each column's final pivot; cleared_lower[p] = 1 for every
-// position of dimension k-1 that is a pivot. Synchronises `s` between rounds.
-int reduce_dimension(int k, int64_t n, int64_t n_lower, const int32_t* order_k, const int32_t* simplices,
-                     const int32_t* facets, const int32_t* pos_lower, const uint8_t* cleared, int32_t* low,
-                     uint8_t* cleared_lower, int32_t* is_pair, uint32_t* flags, int64_t* rounds_out, cudaStream_t s,
-                     Scratch& scr) {
+// Columns in one pool: column c is pool[off[c], off[c] + len[c]), ascending.
+struct Columns {
+    int32_t *pool = nullptr, *off = nullptr, *len = nullptr;
+    int64_t n = 0, cap = 0, used = 0;
+};
+
+// Boundary columns of dimension k (rows: positions of dimension k-1), with
+// the columns of `cleared` positions empty.
+int facet_columns(int k, int64_t n, int64_t n_lower, const int32_t* order_k, const int32_t* simplices,
+                  const int32_t* facets, const int32_t* pos_lower, const uint8_t* cleared, uint32_t* flags,
+                  cudaStream_t s, Scratch& scr, Columns* C) {
+    C->n = n;
+    C->used = n * (k + 1);
+    C->cap = C->used * 8 + (int64_t(1) << 20);
+    int rc;
+    if ((rc = scr.alloc(&C->pool, C->cap)) || (rc = scr.alloc(&C->off, n)) || (rc = scr.alloc(&C->len, n))) return rc;
+    k_init_columns<<<blocks_for(n), kThreads, 0, s>>>(k, n, order_k, simplices, facets, pos_lower, n_lower, cleared,
+                                                      C->pool, C->off, C->len, flags);
+    note_launch();
+    FLOOD_CUDA(cudaGetLastError());
+    return FLOOD_OK;
+}
+
+// Coboundary columns of the triangles (rows: reversed tetrahedron positions).
+int coface_columns(int64_t n2, int64_t n3, const int32_t* facets3, const int32_t* pos2, const int32_t* pos3,
+                   uint32_t* flags, cudaStream_t s, Scratch& scr, Columns* C) {
+    int32_t *cnt, *ptr;
+    int rc;
+    if ((rc = scr.alloc(&cnt, n2)) || (rc = scr.alloc(&ptr, n2 + 1))) return rc;
+    FLOOD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n2, s));
+    k_count_cofaces<<<blocks_for(n3), kThreads, 0, s>>>(n3, facets3, pos2, n2, cnt, flags);
+    note_launch();
+    if ((rc = exclusive_scan(cnt, ptr, n2, s, scr))) return rc;
+    C->n = n2;
+    C->used = 4 * n3;  // every tetrahedron lists each of its 4 facets once
+    C->cap = C->used * 8 + (int64_t(1) << 20);
+    if ((rc = scr.alloc(&C->pool, C->cap)) || (rc = scr.alloc(&C->off, n2)) || (rc = scr.alloc(&C->len, n2)))
+        return rc;
+    FLOOD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n2, s));
+    k_fill_cofaces<<<blocks_for(n3), kThreads, 0, s>>>(n3, facets3, pos2, n2, pos3, ptr, cnt, C->pool);
+    k_init_coface_columns<<<blocks_for(n2), kThreads, 0, s>>>(n2, ptr, C->pool, C->off, C->len);
+    note_launch(2);
+    FLOOD_CUDA(cudaGetLastError());
+    return FLOOD_OK;
+}
+
+// Reduce the columns (rows 0..n_rows-1) by parallel rounds; low[c] receives
+// each column's final pivot (-1: zero column) and marked[row] = 1 for every
+// pivot row. Synchronises `s` every few rounds.
+int reduce_columns(Columns& C, int64_t n_rows, int32_t* low, uint8_t* marked, int32_t* is_pair,
+                   int64_t* rounds_out, cudaStream_t s, Scratch& scr) {
+    const int64_t n = C.n;
     *rounds_out = 0;
     if (n == 0) return FLOOD_OK;
-    int64_t cap = n * (k + 1) * 8 + (int64_t(1) << 20);
-    int32_t *pool, *off, *len;
     unsigned long long *owner, *head;
     uint32_t* rflags;  // [0] changed in the last round, [1] pool full
     int rc;
-    if ((rc = scr.alloc(&pool, cap)) || (rc = scr.alloc(&off, n)) || (rc = scr.alloc(&len, n)) ||
-        (rc = scr.alloc(&owner, n_lower)) || (rc = scr.alloc(&head, 1)) || (rc = scr.alloc(&rflags, 2)))
+    if ((rc = scr.alloc(&owner, std::max<int64_t>(n_rows, 1))) || (rc = scr.alloc(&head, 1)) ||
+        (rc = scr.alloc(&rflags, 2)))
         return rc;
-    FLOOD_CUDA(cudaMemsetAsync(owner, 0, sizeof(unsigned long long) * n_lower, s));
-    k_init_columns<<<blocks_for(n), kThreads, 0, s>>>(k, n, order_k, simplices, facets, pos_lower, n_lower, cleared,
-                                                      pool, off, len, flags);
-    note_launch();
-    const unsigned long long used = static_cast<unsigned long long>(n) * (k + 1);
+    FLOOD_CUDA(cudaMemsetAsync(owner, 0, sizeof(unsigned long long) * std::max<int64_t>(n_rows, 1), s));
+    FLOOD_CUDA(cudaMemsetAsync(rflags, 0, 2 * sizeof(uint32_t), s));
+    const unsigned long long used = static_cast<unsigned long long>(C.used);
     FLOOD_CUDA(cudaMemcpyAsync(head, &used, sizeof(used), cudaMemcpyHostToDevice, s));
     uint32_t r = 0;
     for (;;) {
         for (int i = 0; i < kRoundsPerCheck; ++i) {
             ++r;
             FLOOD_CUDA(cudaMemsetAsync(rflags, 0, sizeof(uint32_t), s));
-            k_round_owner<<<blocks_for(n), kThreads, 0, s>>>(n, pool, off, len, owner, r);
-            k_round_add<<<blocks_for(n), kThreads, 0, s>>>(n, pool, cap, head, off, len, owner, rflags);
+            k_round_owner<<<blocks_for(n), kThreads, 0, s>>>(n, C.pool, C.off, C.len, owner, r);
+            k_round_add<<<blocks_for(n), kThreads, 0, s>>>(n, C.pool, C.cap, head, C.off, C.len, owner, rflags);
             note_launch(2);
         }
         FLOOD_CUDA(cudaGetLastError());
@@ -289,27 +384,26 @@ int reduce_dimension(int k, int64_t n, int64_t n_lower, const int32_t* order_k, 
         FLOOD_CUDA(cudaStreamSynchronize(s));
         if (h[1]) {  // pool full: compact the live columns into a pool twice as large
             int32_t *new_off, *new_pool;
-            int64_t live = 0;
             if ((rc = scr.alloc(&new_off, n + 1))) return rc;
-            if ((rc = exclusive_scan(len, new_off, n, s, scr))) return rc;
+            if ((rc = exclusive_scan(C.len, new_off, n, s, scr))) return rc;
             int32_t h_live = 0;
             FLOOD_CUDA(cudaMemcpyAsync(&h_live, new_off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             FLOOD_CUDA(cudaStreamSynchronize(s));
-            live = h_live;
-            const int64_t new_cap = std::max<int64_t>(2 * cap, 4 * live + (int64_t(1) << 20));
+            const int64_t live = h_live;
+            const int64_t new_cap = std::max<int64_t>(2 * C.cap, 4 * live + (int64_t(1) << 20));
             if (new_cap >= (int64_t(1) << 31)) {
                 set_error("flood_persistence: reduced columns exceed 2^31 entries");
                 return FLOOD_ECAPACITY;
             }
             if ((rc = scr.alloc(&new_pool, new_cap))) return rc;
-            k_compact<<<blocks_for(n), kThreads, 0, s>>>(n, pool, off, len, new_off, new_pool);
+            k_compact<<<blocks_for(n), kThreads, 0, s>>>(n, C.pool, C.off, C.len, new_off, new_pool);
             note_launch();
-            FLOOD_CUDA(cudaMemcpyAsync(off, new_off, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            FLOOD_CUDA(cudaMemcpyAsync(C.off, new_off, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
             const unsigned long long nh = static_cast<unsigned long long>(live);
             FLOOD_CUDA(cudaMemcpyAsync(head, &nh, sizeof(nh), cudaMemcpyHostToDevice, s));
             FLOOD_CUDA(cudaMemsetAsync(rflags, 0, 2 * sizeof(uint32_t), s));
-            pool = new_pool;
-            cap = new_cap;
+            C.pool = new_pool;
+            C.cap = new_cap;
             FLOOD_CUDA(cudaStreamSynchronize(s));  // the host values above are copied before they go out of scope
             continue;
         }
@@ -319,11 +413,28 @@ int reduce_dimension(int k, int64_t n, int64_t n_lower, const int32_t* order_k, 
             return FLOOD_EINTERNAL;
         }
     }
-    k_pivots<<<blocks_for(n), kThreads, 0, s>>>(n, pool, off, len, low, cleared_lower, is_pair);
+    k_pivots<<<blocks_for(n), kThreads, 0, s>>>(n, C.pool, C.off, C.len, low, marked, is_pair);
     note_launch();
     FLOOD_CUDA(cudaGetLastError());
     *rounds_out = r;
     return FLOOD_OK;
+}
+
+// Pairs of the coboundary reduction, per tetrahedron position: the
+// triangle it kills (its column's partner), or nothing.
+__global__ void k_coface_pairs(int64_t n2, int64_t n3, const int32_t* low, int32_t* tri_of_tet, uint8_t* cleared2) {
+    const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (c >= n2 || low[c] < 0) return;
+    const int64_t p2 = n2 - 1 - c, p3 = n3 - 1 - low[c];
+    tri_of_tet[p3] = static_cast<int32_t>(p2);
+    cleared2[p2] = 1;  // a triangle whose class a tetrahedron kills is a birth: its own column is zero
+}
+
+__global__ void k_tet_pair_flags(int64_t n3, const int32_t* tri_of_tet, int32_t* low3, int32_t* is_pair) {
+    const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (p >= n3) return;
+    low3[p] = tri_of_tet[p];
+    is_pair[p] = tri_of_tet[p] >= 0;
 }
 
 }  // namespace
@@ -382,11 +493,33 @@ extern "C" int flood_persistence(const int32_t* const simplices[4], const int32_
     FLOOD_CUDA(cudaStreamSynchronize(s));
     if (h_flags) return status_from_flags(h_flags, "flood_persistence");
     int64_t r[4] = {0, 0, 0, 0};
-    for (int k = 3; k >= 1; --k) {  // twist: higher dimensions first, their pivots cleared below
+    // Tetrahedra: the pairs of the anti-transposed (coboundary) matrix equal
+    // those of the boundary matrix, and its columns (the cofaces of each
+    // triangle, at most two in a triangulation of a region of space) reduce
+    // in few rounds, where the tetrahedra's boundary columns would need a
+    // round per step of every long chain of additions.
+    if (n[3] > 0) {
+        Columns C;
+        int32_t *clow, *cpair, *tri_of_tet;
+        uint8_t* cmark;
+        if ((rc = scr.alloc(&clow, n[2])) || (rc = scr.alloc(&cpair, n[2])) || (rc = scr.alloc(&tri_of_tet, n[3])) ||
+            (rc = scr.alloc(&cmark, n[3])))
+            return rc;
+        FLOOD_CUDA(cudaMemsetAsync(tri_of_tet, 0xff, sizeof(int32_t) * n[3], s));
+        if ((rc = coface_columns(n[2], n[3], facets[3], pos[2], pos[3], flags, s, scr, &C)) ||
+            (rc = reduce_columns(C, n[3], clow, cmark, cpair, &r[3], s, scr)))
+            return rc;
+        k_coface_pairs<<<blocks_for(n[2]), kThreads, 0, s>>>(n[2], n[3], clow, tri_of_tet, cleared[2]);
+        k_tet_pair_flags<<<blocks_for(n[3]), kThreads, 0, s>>>(n[3], tri_of_tet, low[3], is_pair[3]);
+        note_launch(2);
+        FLOOD_CUDA(cudaGetLastError());
+    }
+    for (int k = 2; k >= 1; --k) {  // twist: higher dimensions first, their pivots cleared below
         if (n[k] == 0) continue;
-        if ((rc = reduce_dimension(k, n[k], n[k - 1], order[k], simplices[k], facets[k], pos[k - 1],
-                                   k < 3 ? cleared[k] : nullptr, low[k], cleared[k - 1], is_pair[k], flags, &r[k], s,
-                                   scr)))
+        Columns C;
+        if ((rc = facet_columns(k, n[k], n[k - 1], order[k], simplices[k], facets[k], pos[k - 1], cleared[k], flags, s,
+                                scr, &C)) ||
+            (rc = reduce_columns(C, n[k - 1], low[k], cleared[k - 1], is_pair[k], &r[k], s, scr)))
             return rc;
     }
     // pairs (birth row of dimension k-1, death row of dimension k), in the deaths' filtration order
