@@ -842,8 +842,8 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
     }
 }
 
-constexpr int kNS = 8;       // samples per lane (light groups)
-constexpr int kHeavyNS = 8;  // samples per thread slot (heavy groups)
+constexpr int kNS = 4;       // samples per lane (light groups)
+constexpr int kHeavyNS = 4;  // samples per thread slot (heavy groups)
 
 // Largest j with off[j] <= item (off has n + 1 non-decreasing entries).
 __device__ __forceinline__ int job_of(const int32_t* off, int n, int32_t item) {
@@ -896,7 +896,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood(const DimArgs* jobs, int 
         const float oy = __fadd_rn(lat.oy, static_cast<float>(byi) * lat.B);
         const float oz = __fadd_rn(lat.oz, static_cast<float>(bzi) * lat.B);
         const int n = s_end - s_begin;
-        const int W = n <= kNS ? 1 : n <= 2 * kNS ? 2 : n <= 4 * kNS ? 4 : n <= 8 * kNS ? 8 : 16;
+        int W = 1;  // sample lanes: the fewest whose slots hold the group
+        while (W * kNS < n) W <<= 1;
         process_group<kNS>(a, gv, W, s_begin, s_end, ox, oy, oz, tiles, bar, s_ub[warp][0], s_ub[warp][1], phases,
                            abort, cnt, lane);
     }
@@ -981,7 +982,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         const float ox = __fadd_rn(lat.ox, static_cast<float>(bxi) * lat.B);
         const float oy = __fadd_rn(lat.oy, static_cast<float>(byi) * lat.B);
         const float oz = __fadd_rn(lat.oz, static_cast<float>(bzi) * lat.B);
-        const int W = n_valid <= kHeavyNS ? 1 : n_valid <= 2 * kHeavyNS ? 2 : n_valid <= 4 * kHeavyNS ? 4 : 8;
+        int W = 1;  // sample threads: the fewest whose slots hold the group
+        while (W * kHeavyNS < n_valid) W <<= 1;
         const int G = kThreads / W;
         const int gs = tid / W, lw = tid % W;
         const int nsl = (n_valid + W - 1) / W;  // sample slots in use per thread
