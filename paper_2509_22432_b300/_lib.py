@@ -10,7 +10,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libflood.so")
+# FLOOD_LIBRARY=checked loads the bounds-checked build (libflood_checked.so).
+CHECKED = os.environ.get("FLOOD_LIBRARY", "") == "checked"
+LIB_PATH = os.path.join(HERE, "libflood_checked.so" if CHECKED else "libflood.so")
 
 STATUS = {
     0: "FLOOD_OK", -1: "FLOOD_EINVAL", -2: "FLOOD_ENOMEM", -3: "FLOOD_ECUDA", -4: "FLOOD_ETIMEOUT",
@@ -168,8 +170,8 @@ def get() -> C.CDLL:
     with _lock:
         if _lib is None:
             from . import build as _build
-            if _build.needs_build():
-                _build.build()
+            if _build.needs_build(CHECKED):
+                _build.build(checked=CHECKED)
             if not os.path.exists(LIB_PATH):
                 raise ImportError(f"libflood.so not found at {LIB_PATH}; run paper_2509_22432_b300/build.py")
             lib = C.CDLL(LIB_PATH)

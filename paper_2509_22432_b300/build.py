@@ -15,6 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libflood.so")
+# The bounds-checked build (-DFLOOD_BOUNDS_CHECK): every data-dependent index of
+# the kernels is tested before use and reported as a status instead of read or
+# written out of range. Loaded instead of LIB when FLOOD_LIBRARY=checked.
+LIB_CHECKED = os.path.join(HERE, "libflood_checked.so")
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
@@ -33,10 +37,11 @@ def _inputs() -> list:
     return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "flood.h")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _inputs())
 
 
@@ -47,20 +52,22 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libflood.so if needed; returns its path. Raises on failure."""
-    if not force and not needs_build():
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *sources(), "-lcudart"]
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile libflood.so (or, checked=True, libflood_checked.so) if needed; returns its path. Raises on failure."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not needs_build(checked):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
+    extra = ["-DFLOOD_BOUNDS_CHECK"] if checked else []
+    cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I", INCLUDE, "-o", tmp, *sources(), "-lcudart"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

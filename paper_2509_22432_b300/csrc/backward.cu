@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_backward(BwdArgs a) {
     if (!(f > 0.0f)) return;
     const float scale = gam / f;
     const int32_t xi = static_cast<int32_t>(all & 0xffffffffu);
-    if (lane == 0) {
+    if (lane == 0 && !FLOOD_OOB(xi, g.n_pts, a.flags)) {
         atomicAdd(&a.grad_X[3 * int64_t(xi) + 0], scale * bx);
         atomicAdd(&a.grad_X[3 * int64_t(xi) + 1], scale * by);
         atomicAdd(&a.grad_X[3 * int64_t(xi) + 2], scale * bz);

@@ -47,6 +47,10 @@ int status_from_flags(uint32_t flags, const char* where) {
         set_error("%s: fewer distinct points than requested landmarks", where);
         return FLOOD_EDEGENERATE;
     }
+    if (flags & FLAG_BOUNDS) {
+        set_error("%s: an index was out of range (bounds-checked build; the access was skipped)", where);
+        return FLOOD_EINTERNAL;
+    }
     set_error("%s: internal consistency check failed (flags 0x%x)", where, flags);
     return FLOOD_EINTERNAL;
 }

@@ -23,7 +23,19 @@ enum : uint32_t {
     FLAG_TIMEOUT = 1u << 3,     // a bounded wait gave up
     FLAG_DEGENERATE = 1u << 4,  // FPS ran out of distinct points
     FLAG_INTERNAL = 1u << 5,    // internal capacity / consistency check
+    FLAG_BOUNDS = 1u << 6,      // bounds-checked build: an index was out of range (the access was skipped)
 };
+
+// Bounds-checked builds (compiled with -DFLOOD_BOUNDS_CHECK, the library
+// libflood_checked.so): every data-dependent index of the kernels is tested
+// before use; an index outside [0, n) skips the access and raises FLAG_BOUNDS
+// in the call's status word (reported as FLOOD_EINTERNAL) instead of reading
+// or writing out of range. In the normal build the test compiles away.
+#ifdef FLOOD_BOUNDS_CHECK
+#define FLOOD_OOB(i, n, flags) (::flood::index_out_of_range(static_cast<long long>(i), static_cast<long long>(n), (flags)))
+#else
+#define FLOOD_OOB(i, n, flags) false
+#endif
 
 // Bound on polls of a device-side wait (mbarrier phase, grid barrier). Each
 // poll is at least a round trip to L2 or a try_wait time slice, so the bound
@@ -218,6 +230,14 @@ __device__ __forceinline__ void st_relaxed_v4_u64(uint64_t* p, uint64_t a, uint6
     asm volatile("st.relaxed.gpu.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
                  : "memory");
 }
+
+#ifdef FLOOD_BOUNDS_CHECK
+__device__ __forceinline__ bool index_out_of_range(long long i, long long n, uint32_t* flags) {
+    if (i >= 0 && i < n) return false;
+    if (flags) atomicOr(flags, FLAG_BOUNDS);
+    return true;
+}
+#endif
 
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int mask) {
     uint32_t lo = static_cast<uint32_t>(v), hi = static_cast<uint32_t>(v >> 32);

@@ -124,6 +124,8 @@ struct DimArgs {
     int32_t* group_off;     // n_coarse + 1
     int2* groups;           // (bucket, index within bucket)
     SampleRec* recs;
+    int64_t rec_cap;           // records the sample arrays hold
+    int64_t groups_cap;        // groups the group arrays hold
     unsigned long long* best;  // per simplex: (d^2 bits << 32) | ~sample
     const int32_t* n_heavy;    // groups [0, *n_heavy) of the sorted queue go to the CTA kernel
     Ctl* ctl;
@@ -148,10 +150,11 @@ __global__ void k_vertices(const float* L, int32_t n_L, const GridView* gp, floa
         const int cy = cell_coord(y, g.oy, g.inv_cell, g.dy);
         const int cz = cell_coord(z, g.oz, g.inv_cell, g.dz);
         const int64_t c = (static_cast<int64_t>(cz) * g.dy + cy) * g.dx + cx;
-        const int32_t b = g.cell_start[c], e = g.cell_start[c + 1];
+        const bool bad = FLOOD_OOB(c, g.n_cells, flags);
+        const int32_t b = bad ? 0 : g.cell_start[c], e = bad ? 0 : g.cell_start[c + 1];
         for (int32_t i0 = b; i0 < e; i0 += 32) {
             bool hit = false;
-            if (i0 + lane < e) {
+            if (i0 + lane < e && !FLOOD_OOB(i0 + lane, g.n_pts, flags)) {
                 const float4 p = g.pts[i0 + lane];
                 hit = __float_as_uint(p.x) == __float_as_uint(x) && __float_as_uint(p.y) == __float_as_uint(y) &&
                       __float_as_uint(p.z) == __float_as_uint(z);
@@ -261,10 +264,12 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
         ++n_active;
         const float x = __fadd_rn(S.v0[0], px), y = __fadd_rn(S.v0[1], py), z = __fadd_rn(S.v0[2], pz);
         const int64_t b = sample_key(a.geo->lat, x, y, z);
+        if (FLOOD_OOB(b, a.n_buckets, &a.ctl->flags)) continue;
         if (!SCATTER) {
             atomicAdd(&a.bucket_count[b], 1);
         } else {
             const int32_t pos = a.bucket_start[b] + atomicAdd(&a.bucket_fill[b], 1);
+            if (FLOOD_OOB(pos, a.rec_cap, &a.ctl->flags)) continue;
             SampleRec r;
             r.x = x;
             r.y = y;
@@ -337,7 +342,8 @@ __global__ void __launch_bounds__(kCubeTile) k_cube_sums(const int32_t* count, i
 // entries are the totals) and groups[] = (cube, index within the cube).
 __global__ void __launch_bounds__(kCubeTile) k_cube_scan(const int32_t* count, int64_t n_coarse,
                                                         const int32_t* tile_samples, const int32_t* tile_groups,
-                                                        int32_t* bucket_start, int32_t* group_off, int2* groups) {
+                                                        int32_t* bucket_start, int32_t* group_off, int2* groups,
+                                                        int64_t groups_cap, uint32_t* flags) {
     __shared__ int32_t s_red[2][kCubeTile / 32];
     __shared__ int32_t s_base[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -413,7 +419,8 @@ __global__ void __launch_bounds__(kCubeTile) k_cube_scan(const int32_t* count, i
             run += count[c * kFine + f];
         }
         group_off[c] = off_g;
-        for (int32_t j = 0; j < ng; ++j) groups[off_g + j] = make_int2(static_cast<int>(c), j);
+        for (int32_t j = 0; j < ng; ++j)
+            if (!FLOOD_OOB(off_g + j, groups_cap, flags)) groups[off_g + j] = make_int2(static_cast<int>(c), j);
         if (c == n_coarse - 1) {  // totals
             bucket_start[n_coarse * kFine] = run;
             group_off[n_coarse] = off_g + ng;
@@ -430,7 +437,8 @@ __device__ __forceinline__ int group_class(const DimArgs& a, int2 gb) {
     const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
     const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
     float R = 0.0f;
-    for (int32_t i = s_begin; i < s_end; ++i) R = fmaxf(R, a.recs[i].u);
+    for (int32_t i = s_begin; i < s_end; ++i)
+        if (!FLOOD_OOB(i, a.rec_cap, &a.ctl->flags)) R = fmaxf(R, a.recs[i].u);
     const int c = static_cast<int>(ceilf(R / a.geo->shell_h));
     return kClasses - 1 - min(max(c, 0), kClasses - 1);  // heavier -> smaller class
 }
@@ -474,7 +482,8 @@ __global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const 
     if (j >= *n_groups) return;
     const int2 gb = a.groups[j];
     const int c = group_class(a, gb);
-    sorted[s_start[c] + atomicAdd(&class_fill[c], 1)] = gb;
+    const int32_t at = s_start[c] + atomicAdd(&class_fill[c], 1);
+    if (!FLOOD_OOB(at, a.groups_cap, &a.ctl->flags)) sorted[at] = gb;
 }
 
 // ---------------------------------------------------------------- shell streaming
@@ -521,7 +530,7 @@ __device__ __forceinline__ float slab_gap(float o, float h, int c, float lo, flo
 // x) whose cells lie farther than sqrt(T2) from every sample of the group
 // contributes nothing; it cannot change any live sample's nearest distance.
 __device__ __forceinline__ void shell_row(const GridView& g, const Shell& sh, int r, int32_t& b1, int32_t& l1,
-                                          int32_t& b2, int32_t& l2) {
+                                          int32_t& b2, int32_t& l2, uint32_t* flags) {
     const int s = sh.s;
     const int cy = sh.y0 + r % sh.ny;
     const int cz = sh.z0 + r / sh.ny;
@@ -541,17 +550,17 @@ __device__ __forceinline__ void shell_row(const GridView& g, const Shell& sh, in
     // in one round of independent loads
     if (face) {
         const int x0 = max(max(sh.lo[0] - s, 0), xa), x1 = min(min(sh.hi[0] + s, g.dx - 1), xb);
-        if (x0 <= x1) {
+        if (x0 <= x1 && !FLOOD_OOB(base + x1 + 1, g.n_cells + 1, flags)) {
             b1 = g.cell_start[base + x0];
             l1 = g.cell_start[base + x1 + 1] - b1;
         }
     } else {
         const int xl = sh.lo[0] - s, xr = sh.hi[0] + s;
-        if (xl >= 0 && xl >= xa && xl <= xb) {
+        if (xl >= 0 && xl >= xa && xl <= xb && !FLOOD_OOB(base + xl + 1, g.n_cells + 1, flags)) {
             b1 = g.cell_start[base + xl];
             l1 = g.cell_start[base + xl + 1] - b1;
         }
-        if (xr < g.dx && xr >= xa && xr <= xb) {
+        if (xr < g.dx && xr >= xa && xr <= xb && !FLOOD_OOB(base + xr + 1, g.n_cells + 1, flags)) {
             b2 = g.cell_start[base + xr];
             l2 = g.cell_start[base + xr + 1] - b2;
         }
@@ -568,12 +577,12 @@ struct Cursor {
 // copies that complete on `bar` (warp-collective; lane 0 arrives once).
 // Returns the number of points copied (warp-uniform).
 __device__ __noinline__ int produce_shell_tile(const GridView& g, const Shell& sh, Cursor& c, int want, float4* buf,
-                                  uint64_t* bar, int lane, int* n_out = nullptr) {
+                                  uint64_t* bar, int lane, uint32_t* flags) {
     int filled = 0;
     while (filled < want && c.row < sh.rows) {
         const int r = c.row + lane;
         int32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-        if (r < sh.rows) shell_row(g, sh, r, b1, l1, b2, l2);
+        if (r < sh.rows) shell_row(g, sh, r, b1, l1, b2, l2, flags);
         const int32_t len = l1 + l2;
         int32_t incl = len;
 #pragma unroll
@@ -593,10 +602,13 @@ __device__ __noinline__ int produce_shell_tile(const GridView& g, const Shell& s
         if (total > 0) {
             if (lane == 0) mbar_expect_tx(bar, static_cast<uint32_t>(total) * 16u);
             __syncwarp();
-            if (n1 > 0)
+            // (checked builds: a copy out of range is skipped; its bytes never arrive and the wait gives up)
+            if (n1 > 0 && !FLOOD_OOB(b1 + (o1lo - seg) + n1 - 1, g.n_pts, flags) &&
+                !FLOOD_OOB(filled + (o1lo - win_lo) + n1 - 1, want, flags))
                 bulk_copy_g2s(buf + filled + (o1lo - win_lo), g.pts + b1 + (o1lo - seg),
                               static_cast<uint32_t>(n1) * 16u, bar);
-            if (n2 > 0)
+            if (n2 > 0 && !FLOOD_OOB(b2 + (o2lo - seg - l1) + n2 - 1, g.n_pts, flags) &&
+                !FLOOD_OOB(filled + (o2lo - win_lo) + n2 - 1, want, flags))
                 bulk_copy_g2s(buf + filled + (o2lo - win_lo), g.pts + b2 + (o2lo - seg - l1),
                               static_cast<uint32_t>(n2) * 16u, bar);
         }
@@ -611,10 +623,7 @@ __device__ __noinline__ int produce_shell_tile(const GridView& g, const Shell& s
         if (total == 0 && nfull == 0) break;  // nothing left (defensive)
     }
     __syncwarp();
-    if (lane == 0) {
-        if (n_out) *n_out = filled;  // visible to waiters: the arrive releases it
-        mbar_arrive(bar);
-    }
+    if (lane == 0) mbar_arrive(bar);
     return filled;
 }
 
@@ -761,7 +770,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
         if (sh.rows > 0) {
             Cursor cur{0, 0, 0};
             int nbuf[2];
-            nbuf[0] = produce_shell_tile(g, sh, cur, kWTile, tiles, &bar[0], lane);
+            nbuf[0] = produce_shell_tile(g, sh, cur, kWTile, tiles, &bar[0], lane, &a.ctl->flags);
             int b = 0;
             for (;;) {
                 const int n = nbuf[b];
@@ -770,7 +779,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
                 if (n == 0 || abort) break;
                 const bool more = cur.row < sh.rows;
                 if (more)
-                    nbuf[b ^ 1] = produce_shell_tile(g, sh, cur, kWTile, tiles + (b ^ 1) * kWTile, &bar[b ^ 1], lane);
+                    nbuf[b ^ 1] = produce_shell_tile(g, sh, cur, kWTile, tiles + (b ^ 1) * kWTile, &bar[b ^ 1], lane, &a.ctl->flags);
                 float4* buf = tiles + b * kWTile;
                 for (int e = lane; e < n; e += 32) {
                     float4 p = buf[e];
@@ -835,7 +844,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
         if (i < s_end && gs == 0) {
             const SampleRec r = a.recs[i];
             const float d2 = fmaxf(__fadd_rn(mn[q], pp[q]), 0.0f);
-            if (__fsqrt_rn(d2) > r.lb)
+            if (__fsqrt_rn(d2) > r.lb && !FLOOD_OOB(r.sigma, a.n, &a.ctl->flags))
                 atomicMax(&a.best[r.sigma], (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
                                                 (0xffffffffu - static_cast<uint32_t>(r.s)));
         }
@@ -1144,7 +1153,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
             // and the owners bulk-copy them into the tile window by window.
             for (int row0 = 0; row0 < sh.rows && !s_abort; row0 += kThreads) {
                 int32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-                if (row0 + tid < sh.rows) shell_row(g, sh, row0 + tid, b1, l1, b2, l2);
+                if (row0 + tid < sh.rows) shell_row(g, sh, row0 + tid, b1, l1, b2, l2, &a.ctl->flags);
                 const int32_t len = l1 + l2;
                 int32_t incl = len;
 #pragma unroll
@@ -1168,10 +1177,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
                     __syncthreads();
                     const int32_t o1lo = max(off, w0), o1hi = min(off + l1, w0 + cnt);
                     const int32_t o2lo = max(off + l1, w0), o2hi = min(off + len, w0 + cnt);
-                    if (o1hi > o1lo)
+                    if (o1hi > o1lo && !FLOOD_OOB(b1 + (o1hi - off) - 1, g.n_pts, &a.ctl->flags) &&
+                        !FLOOD_OOB(o1hi - w0 - 1, kHeavyTile, &a.ctl->flags))
                         bulk_copy_g2s(s_tiles + (o1lo - w0), g.pts + b1 + (o1lo - off),
                                       static_cast<uint32_t>(o1hi - o1lo) * 16u, &s_bar[0]);
-                    if (o2hi > o2lo)
+                    if (o2hi > o2lo && !FLOOD_OOB(b2 + (o2hi - off - l1) - 1, g.n_pts, &a.ctl->flags) &&
+                        !FLOOD_OOB(o2hi - w0 - 1, kHeavyTile, &a.ctl->flags))
                         bulk_copy_g2s(s_tiles + (o2lo - w0), g.pts + b2 + (o2lo - off - l1),
                                       static_cast<uint32_t>(o2hi - o2lo) * 16u, &s_bar[0]);
                     if (!mbar_wait(&s_bar[0], phases & 1u, &a.ctl->flags)) s_abort = 1;
@@ -1224,7 +1235,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_flood_heavy(const DimArgs* jobs
         if (tid < n_valid) {
             const SampleRec r = a.recs[s_begin + tid];
             const float d2 = __uint_as_float(s_min[tid]);
-            if (s_min[tid] != 0xffffffffu && __fsqrt_rn(d2) > r.lb)
+            if (s_min[tid] != 0xffffffffu && __fsqrt_rn(d2) > r.lb && !FLOOD_OOB(r.sigma, a.n, &a.ctl->flags))
                 atomicMax(&a.best[r.sigma], (static_cast<unsigned long long>(s_min[tid]) << 32) |
                                                 (0xffffffffu - static_cast<uint32_t>(r.s)));
         }
@@ -1754,6 +1765,8 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             a.group_off = J.goff;
             a.groups = J.groups_sorted;  // the flood kernels read the longest-first order
             a.recs = J.recs;
+            a.rec_cap = J.max_samples;
+            a.groups_cap = J.max_groups;
             a.best = J.best[k];
             a.ctl = ctl;
             // heavy groups: shell bound >= heavy_shells, i.e. classes [0, kClasses - heavy_shells)
@@ -1780,7 +1793,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             const unsigned tiles = static_cast<unsigned>(ceil_div(J.n_coarse, kCubeTile));
             k_cube_sums<<<tiles, kCubeTile, 0, s>>>(J.bcount[k], J.n_coarse, J.tile_sums, J.tile_sums + tiles);
             k_cube_scan<<<tiles, kCubeTile, 0, s>>>(J.bcount[k], J.n_coarse, J.tile_sums, J.tile_sums + tiles,
-                                                    J.bstart, J.goff, J.groups);
+                                                    J.bstart, J.goff, J.groups, J.max_groups, &ctl->flags);
             k_samples<true><<<wb, 256, 0, s>>>(a);
             // longest-first order of this cloud's groups; the count stays on the device
             const int32_t* n_groups = J.goff + J.n_coarse;

@@ -90,11 +90,13 @@ __global__ void __launch_bounds__(256) k_morton_count(const float* X, int64_t n,
 // (order within a code is arbitrary, which changes no result: ties are
 // decided by the original row).
 __global__ void __launch_bounds__(256) k_morton_scatter(const float* X, int64_t n, const int32_t* code,
-                                                       const int32_t* start, int32_t* fill, float4* pts) {
+                                                       const int32_t* start, int32_t* fill, float4* pts,
+                                                       uint32_t* flags) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     const int32_t c = code[i];
     const int32_t pos = start[c] + atomicSub(&fill[c], 1) - 1;
+    if (FLOOD_OOB(pos, n, flags)) return;
     pts[pos] = make_float4(X[3 * i + 0], X[3 * i + 1], X[3 * i + 2], __int_as_float(static_cast<int32_t>(i)));
 }
 
@@ -479,7 +481,7 @@ __device__ __forceinline__ int take_picks(const FpsArgs& a, const FpsShared& s, 
         return 0;
     }
     const int t = static_cast<int>(threadIdx.x) - (kX0 + 1) * 32;  // lane of X1
-    if (blockIdx.x == 0 && t >= 0 && t < n) {
+    if (blockIdx.x == 0 && t >= 0 && t < n && !FLOOD_OOB(j + t, a.n_landmarks, a.flags)) {
         a.out_idx[j + t] = cand_row(s.pick[t]);
         if (a.out_key) a.out_key[j + t] = cand_key(s.pick[t]);
     }
@@ -1037,7 +1039,7 @@ int run_fps(const float* X, int64_t n, int32_t n_landmarks, int64_t start, int n
         note_launch(2);
         FLOOD_CUDA(cudaGetLastError());
         if ((rc = exclusive_scan(count, cstart, codes, s, al))) return rc;
-        k_morton_scatter<<<grid, 256, 0, s>>>(X, n, code, cstart, count, pts);
+        k_morton_scatter<<<grid, 256, 0, s>>>(X, n, code, cstart, count, pts, ctl);
         note_launch();
     }
     FLOOD_CUDA(cudaGetLastError());

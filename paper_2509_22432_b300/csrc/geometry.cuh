@@ -23,6 +23,8 @@ struct GridView {
     float ox, oy, oz;
     float inv_cell;
     float cell;
+    int64_t n_cells;  // cells in use (cell_start has n_cells + 1 entries that matter)
+    int32_t n_pts;    // points of the grid
 };
 
 // Device-resident geometry of a grid. The host fills the pointers of v at

@@ -96,10 +96,12 @@ __global__ void k_grid_geometry(const uint32_t* box, const uint32_t* flags, int6
     G.v.inv_cell = 1.0f / h;
     G.n_cells = int64_t(dims[0]) * dims[1] * dims[2];
     G.n_blocks = int64_t(G.v.bx) * G.v.by * G.v.bz;
+    G.v.n_cells = G.n_cells;
+    G.v.n_pts = static_cast<int32_t>(n);
 }
 
 __global__ void __launch_bounds__(kThreads) k_cell_ids(const float* X, int64_t n, const GridView* gp, int32_t* cell,
-                                                      int32_t* count) {
+                                                      int32_t* count, uint32_t* flags) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     const GridView g = *gp;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_cell_ids(const float* X, int64_t n
     const int cz = cell_coord(X[3 * i + 2], g.oz, g.inv_cell, g.dz);
     const int32_t c = static_cast<int32_t>((static_cast<int64_t>(cz) * g.dy + cy) * g.dx + cx);
     cell[i] = c;
+    if (FLOOD_OOB(c, g.n_cells, flags)) return;
     atomicAdd(&count[c], 1);
 }
 
@@ -115,11 +118,14 @@ __global__ void __launch_bounds__(kThreads) k_cell_ids(const float* X, int64_t n
 // order of points within a cell is arbitrary and changes no result: minima
 // do not depend on it and nearest-point ties go to the lowest original row).
 __global__ void __launch_bounds__(kThreads) k_scatter(const float* X, int64_t n, const int32_t* cell,
-                                                     const int32_t* cell_start, int32_t* fill, float4* pts) {
+                                                     const int32_t* cell_start, int32_t* fill, float4* pts,
+                                                     int64_t cap_cells, uint32_t* flags) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     const int32_t c = cell[i];
+    if (FLOOD_OOB(c, cap_cells, flags)) return;
     const int32_t pos = cell_start[c] + atomicSub(&fill[c], 1) - 1;
+    if (FLOOD_OOB(pos, n, flags)) return;
     pts[pos] = make_float4(X[3 * i + 0], X[3 * i + 1], X[3 * i + 2], __int_as_float(static_cast<int>(i)));
 }
 
@@ -258,12 +264,13 @@ extern "C" int flood_build_grid(const float* X, int64_t n_points, float cell_siz
         k_box_init<<<1, 1, 0, s>>>(d_box, d_box + 6);
         k_bbox<<<bbox_blocks(n_points, device_sm_count()), kBoxThreads, 0, s>>>(X, n_points, d_box, d_box + 6);
         k_grid_geometry<<<1, 1, 0, s>>>(d_box, d_box + 6, n_points, cell_size, g->cap_cells, ptrs, g->geom);
-        k_cell_ids<<<nb, kThreads, 0, s>>>(X, n_points, view_of(g), d_cell, d_count);
+        k_cell_ids<<<nb, kThreads, 0, s>>>(X, n_points, view_of(g), d_cell, d_count, d_box + 6);
         note_launch(4);
         // cells past the used ones count 0, so their offsets all equal n_points
         rc = exclusive_scan(d_count, g->cell_start, g->cap_cells, s, scr);
         if (rc == FLOOD_OK) {
-            k_scatter<<<nb, kThreads, 0, s>>>(X, n_points, d_cell, g->cell_start, d_count, g->pts);
+            k_scatter<<<nb, kThreads, 0, s>>>(X, n_points, d_cell, g->cell_start, d_count, g->pts, g->cap_cells,
+                                              d_box + 6);
             k_block_bits<<<nbb, kThreads, 0, s>>>(g->geom, g->occupied);
             k_bdist_x<<<nbb, kThreads, 0, s>>>(g->geom, g->bdist);
             k_bdist_pass<<<nbb, kThreads, 0, s>>>(g->geom, g->bdist, d_bd, 1);

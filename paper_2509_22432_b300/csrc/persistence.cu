@@ -179,10 +179,11 @@ __global__ void k_init_coface_columns(int64_t n2, const int32_t* ptr, int32_t* p
 // (r << 32) | (0xffffffff - column), so the latest round wins and, within a
 // round, the smallest column.
 __global__ void k_round_owner(int64_t n, const int32_t* pool, const int32_t* off, const int32_t* len,
-                              unsigned long long* owner, uint32_t r) {
+                              unsigned long long* owner, uint32_t r, int64_t n_rows, uint32_t* flags) {
     const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (c >= n || len[c] == 0) return;
     const int32_t low = pool[off[c] + len[c] - 1];
+    if (FLOOD_OOB(low, n_rows, flags)) return;
     atomicMax(&owner[low], (static_cast<unsigned long long>(r) << 32) | (0xffffffffu - static_cast<uint32_t>(c)));
 }
 
@@ -355,7 +356,7 @@ int coface_columns(int64_t n2, int64_t n3, const int32_t* facets3, const int32_t
 // each column's final pivot (-1: zero column) and marked[row] = 1 for every
 // pivot row. Synchronises `s` every few rounds.
 int reduce_columns(Columns& C, int64_t n_rows, int32_t* low, uint8_t* marked, int32_t* is_pair,
-                   int64_t* rounds_out, cudaStream_t s, Scratch& scr) {
+                   int64_t* rounds_out, uint32_t* flags, cudaStream_t s, Scratch& scr) {
     const int64_t n = C.n;
     *rounds_out = 0;
     if (n == 0) return FLOOD_OK;
@@ -374,7 +375,7 @@ int reduce_columns(Columns& C, int64_t n_rows, int32_t* low, uint8_t* marked, in
         for (int i = 0; i < kRoundsPerCheck; ++i) {
             ++r;
             FLOOD_CUDA(cudaMemsetAsync(rflags, 0, sizeof(uint32_t), s));
-            k_round_owner<<<blocks_for(n), kThreads, 0, s>>>(n, C.pool, C.off, C.len, owner, r);
+            k_round_owner<<<blocks_for(n), kThreads, 0, s>>>(n, C.pool, C.off, C.len, owner, r, n_rows, flags);
             k_round_add<<<blocks_for(n), kThreads, 0, s>>>(n, C.pool, C.cap, head, C.off, C.len, owner, rflags);
             note_launch(2);
         }
@@ -507,7 +508,7 @@ extern "C" int flood_persistence(const int32_t* const simplices[4], const int32_
             return rc;
         FLOOD_CUDA(cudaMemsetAsync(tri_of_tet, 0xff, sizeof(int32_t) * n[3], s));
         if ((rc = coface_columns(n[2], n[3], facets[3], pos[2], pos[3], flags, s, scr, &C)) ||
-            (rc = reduce_columns(C, n[3], clow, cmark, cpair, &r[3], s, scr)))
+            (rc = reduce_columns(C, n[3], clow, cmark, cpair, &r[3], flags, s, scr)))
             return rc;
         k_coface_pairs<<<blocks_for(n[2]), kThreads, 0, s>>>(n[2], n[3], clow, tri_of_tet, cleared[2]);
         k_tet_pair_flags<<<blocks_for(n[3]), kThreads, 0, s>>>(n[3], tri_of_tet, low[3], is_pair[3]);
@@ -519,7 +520,7 @@ extern "C" int flood_persistence(const int32_t* const simplices[4], const int32_
         Columns C;
         if ((rc = facet_columns(k, n[k], n[k - 1], order[k], simplices[k], facets[k], pos[k - 1], cleared[k], flags, s,
                                 scr, &C)) ||
-            (rc = reduce_columns(C, n[k - 1], low[k], cleared[k - 1], is_pair[k], &r[k], s, scr)))
+            (rc = reduce_columns(C, n[k - 1], low[k], cleared[k - 1], is_pair[k], &r[k], flags, s, scr)))
             return rc;
     }
     // pairs (birth row of dimension k-1, death row of dimension k), in the deaths' filtration order
