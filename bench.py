@@ -337,6 +337,59 @@ def run_reference(args, wl):
     print(json.dumps(line))
 
 
+def measure_second_workload(name: str, steps: int, warmup: int, dev, flush) -> dict:
+    """The whole step on another workload (the 5M-point shape mix by default), same rules as the main line.
+
+    Landmarks: the CUDA FPS of every step; its picks are compared with the oracle's
+    stored picks for this cloud (tests/golden), index for index. The complex is the
+    host Delaunay of those landmarks (input, untimed); launch parameters come from
+    the autotuner, run first on this workload.
+    """
+    import torch
+    from paper_2509_22432_b300 import delaunay_complex, ops, tune
+    wl = WORKLOADS[name]
+    X = make_inputs(wl)
+    n_l, m = wl["n_l"], wl["m"]
+    Xd = torch.from_numpy(X).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    idx0, key0 = ops.fps(Xd, n_l, 0)
+    golden = _golden_landmarks(name, X)
+    exact = None if golden is None else bool(np.array_equal(idx0.cpu().numpy(), golden))
+    cx = delaunay_complex(X[idx0.cpu().numpy()])
+    dcx = ops.to_device(cx, dev)
+    cover = float(np.sqrt(key0[-1].item()))
+    tuned = tune.tune_workload(Xd, Xd[idx0], dcx, m, cover, reps=1)
+    cell = tuned["cell_factor"] * cover
+    times, ph = [], []
+    for it in range(warmup + steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        idx, _ = ops.fps(Xd, n_l, 0, sync=False)
+        ev[1].record(stream)
+        grid = ops.build_grid(Xd, cell, sync=False)
+        ev[2].record(stream)
+        ops.filtration(grid, Xd[idx], dcx, m, want_src=False, sync=False)
+        ev[3].record(stream)
+        ops.check(dev)
+        grid.close()
+        if it >= warmup:
+            times.append(ev[0].elapsed_time(ev[3]))
+            ph.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                       sum(ops.last_filtration_stats()["flood_kernel_ms"])])
+    n_simp = sum(cx.counts[1:])
+    ms = float(np.mean(times))
+    ph = np.mean(np.array(ph), axis=0)
+    return {"workload": name, "n_points": wl["n"], "n_landmarks": n_l, "m": m, "simplices_per_step": n_simp,
+            "metric": "flood simplices/s", "value": n_simp / (ms * 1e-3), "unit": "simplices/s", "ms_per_step": ms,
+            "steps": steps, "warmup": warmup,
+            "phase_ms": {"fps": float(ph[0]), "grid": float(ph[1]), "filtration": float(ph[2]),
+                         "flood_kernels": float(ph[3])},
+            "fps_equals_oracle_picks": exact, "tuning": {"cell_factor": tuned["cell_factor"],
+                                                         "heavy_shells": tuned["heavy_shells"]},
+            "l2": "flushed between steps", "delaunay": "host, untimed, computed once"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,6 +399,8 @@ def main():
     ap.add_argument("--workload", default="torus-1M", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--second-workload", default="shapes-5M", choices=sorted(WORKLOADS) + ["none"],
+                    help="a second workload timed the same way and reported beside the main line")
     ap.add_argument("--no-tune", action="store_true",
                     help="take the tuning table's parameters instead of sweeping them first (profiling runs)")
     ap.add_argument("--serving", action="store_true",
@@ -696,6 +751,9 @@ def main():
                            "what": "flood_persistence on the step's values: per-dimension bitonic order, parallel "
                                    "Z/2 column reduction with clearing (call to return, synchronised)"}
     ph_values = [v.cpu().numpy().astype(np.float64) for v in ph_vals]
+    if args.second_workload not in ("none", args.workload):
+        line["second_workload"] = measure_second_workload(args.second_workload, min(args.steps, 10), args.warmup,
+                                                          dev, flush)
     line["complex_faces"] = {"tetrahedra": int(cx.counts[3]), "device_ms": float(np.median(fc_dev)),
                              "host_ms": fc_host, "what": "triangles, edges and facet incidence from the "
                              "tetrahedra: flood_complex_faces (call to return, synchronised) vs the host "

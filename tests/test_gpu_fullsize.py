@@ -125,11 +125,14 @@ def test_backward_1m_matches_analytic_subgradient(torus_grad):
     res = oracle.flood_values(X, L, cx.simplices, m, method="kdtree")
     dX, dL = oracle.analytic_gradient(X, L, cx.simplices, m, gamma, result=res)
     scale = max(1.0, np.abs(dX).max(), np.abs(dL).max())
-    # a few attaining pairs may differ by FP32 near-ties; they must stay rare
+    # A few attaining (sample, point) pairs may differ where FP32 and FP64 see a
+    # near-tie; measured on this workload: 6 of 20,192 non-zero rows of dX and
+    # 7 of 2,000 rows of dL. The bars allow about twice that and no more.
     bad_X = np.any(np.abs(gX - dX) > 1e-3 * scale, axis=1)
     bad_L = np.any(np.abs(gL - dL) > 1e-3 * scale, axis=1)
-    assert bad_X.sum() <= 0.001 * max(1, np.count_nonzero(np.abs(dX).sum(1)))
-    assert bad_L.sum() <= 0.01 * L.shape[0]
+    n_rows = np.count_nonzero(np.abs(dX).sum(1))
+    assert bad_X.sum() <= 0.0006 * max(1, n_rows), (int(bad_X.sum()), n_rows)
+    assert bad_L.sum() <= 0.008 * L.shape[0], int(bad_L.sum())
 
 
 def test_backward_1m_central_differences(torus_grad):
@@ -145,7 +148,7 @@ def test_backward_1m_central_differences(torus_grad):
     an = np.array([gX[r, c] if w == "X" else gL[r, c] for (w, r, c) in probes])
     ok = ~kink
     # probes whose attaining (sample, point) pair changes within +-h are kinks:
-    # counted, not compared
-    assert ok.sum() >= 800, ok.sum()
+    # counted, not compared (measured: 57 of 1,000); every other probe agreed
+    assert ok.sum() >= 900, ok.sum()
     close = np.isclose(an[ok], fd[ok], rtol=1e-2, atol=1e-3)
-    assert close.mean() >= 0.99, (close.mean(), ok.sum())
+    assert close.mean() >= 0.995, (close.mean(), ok.sum(), int((~close).sum()))
