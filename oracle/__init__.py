@@ -16,9 +16,10 @@ Only tests, the smoke check and the CPU-baseline leg of the benchmark may
 import it. It shares no code with the CUDA path and imports nothing from the
 product package; inputs (point clouds, simplex lists) are passed in as arrays.
 
-Parity status: every function here is pinned by `-m "not gpu"` tests against
-closed forms, invariants or brute force (see tests/test_oracle_pins.py); none
-is "parity unpinned".
+Points may have d = 2..5 coordinates (fps.py and flood.py do not depend on d;
+§5.3 varies it). Parity status: every function here is pinned by `-m "not gpu"`
+tests against closed forms, invariants or brute force (tests/test_oracle_pins.py,
+and tests/test_oracle_nd.py for d = 4, 5); none is "parity unpinned".
 """
 from .fps import fps, fps_key
 from .samples import compositions, interior_compositions, full_grid_count, interior_count, sample_points

@@ -18,7 +18,9 @@ here is the definition, so it holds for any landmarks.
 
 Nearest distances are taken either by brute force over all of X or with an
 exact FP64 k-d tree (scipy's cKDTree), the paper's own CPU path (App. A.1).
-X and L are promoted exactly from float32 to float64.
+X and L are promoted exactly from float32 to float64. Points may have any
+number d of coordinates (the construction of §3-§4 does not depend on it;
+Fig. 4c varies d); simplices then go up to dimension d.
 """
 from __future__ import annotations
 
@@ -46,7 +48,7 @@ class KDIndex:
 
     def query(self, Q: np.ndarray, k: int = 1):
         """(dist, idx) of the nearest point(s); brute force breaks ties to the lowest index."""
-        Q = np.asarray(Q, dtype=np.float64).reshape(-1, 3)
+        Q = np.asarray(Q, dtype=np.float64).reshape(-1, self.X.shape[1])
         if self.method == "kdtree":
             d, i = self._tree.query(Q, k=k, workers=-1)
             return d, i.astype(np.int64)
@@ -87,7 +89,7 @@ class FloodResult:
 
 
 def _vertex_coords(L, simplices_k, ids):
-    return np.asarray(L, dtype=np.float64)[simplices_k[ids].astype(np.int64)]   # (n, k+1, 3)
+    return np.asarray(L, dtype=np.float64)[simplices_k[ids].astype(np.int64)]   # (n, k+1, d)
 
 
 def flood_values(X, L, simplices, m: int, method: str = "brute", index: KDIndex | None = None,
@@ -112,9 +114,9 @@ def flood_values(X, L, simplices, m: int, method: str = "brute", index: KDIndex 
         step = max(1, max_batch_samples // F)
         for s in range(0, ids.shape[0], step):
             sel = ids[s:s + step]
-            V = _vertex_coords(L, S, sel)                          # (b, k+1, 3)
-            P = sample_points(V, comps, m)                         # (b, F, 3): sum_j lambda_j v_j
-            d, i = index.query(P.reshape(-1, 3))
+            V = _vertex_coords(L, S, sel)                          # (b, k+1, d)
+            P = sample_points(V, comps, m)                         # (b, F, d): sum_j lambda_j v_j
+            d, i = index.query(P.reshape(-1, P.shape[-1]))
             d = d.reshape(sel.shape[0], F)
             i = i.reshape(sel.shape[0], F)
             j = np.argmax(d, axis=1)                               # first maximum: lowest sample rank

@@ -10,7 +10,9 @@ the start point, the tie rule or the precision. The reading adopted here:
     l_j = argmax_i d_i with ties broken towards the LOWEST index;
   * kappa is the squared Euclidean distance evaluated in IEEE binary32 with
     every operation rounded separately (no fused multiply-add):
-        dx = fl32(x.x - l.x), ...;  kappa = fl32(fl32(fl32(dx*dx) + fl32(dy*dy)) + fl32(dz*dz)).
+        dx = fl32(x.x - l.x), ...;  kappa = fl32(fl32(fl32(dx*dx) + fl32(dy*dy)) + fl32(dz*dz)),
+    and in d coordinates the squares summed left to right in the same way
+    (the ambient dimension is free in §3; Fig. 4c varies it).
 
 kappa decides an integer (the argmax), so it is evaluated in binary32 on both
 sides. numpy's float32 element-wise arithmetic is IEEE binary32 with one
@@ -30,13 +32,15 @@ class DegenerateFPS(ValueError):
 
 
 def fps_key(X: np.ndarray, l: np.ndarray) -> np.ndarray:
-    """kappa(x_i, l) for all rows x_i of float32 X, in binary32 without contraction."""
+    """kappa(x_i, l) for all rows x_i of float32 X (n, d), in binary32 without contraction."""
     X = np.asarray(X, dtype=np.float32)
     l = np.asarray(l, dtype=np.float32)
-    dx = X[:, 0] - l[0]
-    dy = X[:, 1] - l[1]
-    dz = X[:, 2] - l[2]
-    return (dx * dx + dy * dy) + dz * dz
+    d0 = X[:, 0] - l[0]
+    acc = d0 * d0
+    for c in range(1, X.shape[1]):
+        dc = X[:, c] - l[c]
+        acc = acc + dc * dc
+    return acc
 
 
 def fps(X: np.ndarray, n_landmarks: int, start: int = 0):

@@ -59,7 +59,7 @@ def barycentric(comps: np.ndarray, m: int) -> np.ndarray:
 def sample_points(V: np.ndarray, comps: np.ndarray, m: int) -> np.ndarray:
     """p = sum_i lambda_i v_i in FP64.
 
-    V is (k+1, 3) for one simplex -> (n, 3), or (b, k+1, 3) for a batch -> (b, n, 3).
+    V is (k+1, d) for one simplex -> (n, d), or (b, k+1, d) for a batch -> (b, n, d).
     """
     lam = barycentric(comps, m)
     V = np.asarray(V, dtype=np.float64)

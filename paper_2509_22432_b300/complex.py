@@ -118,14 +118,22 @@ def delaunay_complex(L: np.ndarray, dim: int | None = None) -> SimplexLists:
     dim = 2: the planar triangulation of (n, 2) landmarks, or of (n, 3)
     landmarks whose z coordinates are all 0 (a planar cloud embedded at z = 0,
     which the CUDA path evaluates exactly like a native planar one).
+    (n, 4) and (n, 5) landmarks (ambient dimension 4 or 5, §5.3 scaling in d):
+    the full-dimensional Delaunay simplices and all their faces, for the
+    general-dimension path (flood_filtration_nd).
     """
     from scipy.spatial import Delaunay
 
     L = np.asarray(L, dtype=np.float64)
-    if L.ndim != 2 or L.shape[1] not in (2, 3):
-        raise ValueError("landmarks must be (n, 2) or (n, 3)")
+    if L.ndim != 2 or L.shape[1] not in (2, 3, 4, 5):
+        raise ValueError("landmarks must be (n, d) with 2 <= d <= 5")
     if dim is None:
         dim = L.shape[1]
+    if L.shape[1] in (4, 5):
+        if dim != L.shape[1]:
+            raise ValueError("(n, 4) and (n, 5) landmarks take dim = d")
+        top = np.sort(Delaunay(L).simplices.astype(np.int64), axis=1)
+        return complex_from_simplices([top], L.shape[0], top_dim=dim)
     if dim == 2:
         if L.shape[1] == 3:
             if np.any(L[:, 2] != 0.0):

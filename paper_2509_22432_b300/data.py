@@ -166,21 +166,26 @@ def shape_mix_cloud(n: int = 5_000_000, n_shapes: int = 8, noise: float = 0.01,
     return _f32(x + noise * rng.standard_normal((n, 3)))
 
 
-def swisscheese_cloud(n: int = 1_000_000, n_holes: int = 10, seed: int = 6) -> np.ndarray:
-    """Uniform points in [0,5]^3 minus n_holes disjoint balls, radii ~ U[0.1,0.5] (§5.3)."""
+def swisscheese_cloud(n: int = 1_000_000, n_holes: int = 10, seed: int = 6, dim: int = 3) -> np.ndarray:
+    """Uniform points in [0,5]^dim minus n_holes disjoint balls, radii ~ U[0.1,0.5] (§5.3).
+
+    dim = 3 is the swisscheese data set; dim in {2, 4, 5} gives the
+    swisscheese-like clouds of the scaling study in the ambient dimension
+    (§5.3, Fig. 4c: |X| = 1M, |L| = 1k).
+    """
     rng = _rng(seed)
     centres, radii = [], []
     while len(centres) < n_holes:
         r = rng.uniform(0.1, 0.5)
-        c = rng.uniform(r, 5 - r, 3)
+        c = rng.uniform(r, 5 - r, dim)
         if all(np.linalg.norm(c - c2) > r + r2 for c2, r2 in zip(centres, radii)):
             centres.append(c)
             radii.append(r)
-    out = np.empty((0, 3))
+    out = np.empty((0, dim))
     C, Rr = np.array(centres), np.array(radii)
     while out.shape[0] < n:
         m = int(1.2 * (n - out.shape[0])) + 16
-        p = rng.uniform(0, 5, (m, 3))
+        p = rng.uniform(0, 5, (m, dim))
         inside = (np.linalg.norm(p[:, None, :] - C[None], axis=2) < Rr).any(axis=1)
         out = np.concatenate([out, p[~inside]])
     return _f32(out[:n])
