@@ -69,6 +69,7 @@ typedef enum flood_status {
 #define FLOOD_MAX_DIM 3      /* simplices of dimension 0..3 (ambient dimension 3) */
 #define FLOOD_MAX_M 64       /* largest supported grid resolution m */
 #define FLOOD_MAX_GIVEN_SAMPLES 65536 /* largest per-simplex set of flood_filtration_given */
+#define FLOOD_ND_MAX_DIM 5   /* ambient dimensions 2..5 of the general-dimension path */
 
 /* ------------------------------------------------------------------------
  * flood_fps — farthest point sampling (§3.2: greedy k-centre, a factor-2
@@ -656,6 +657,128 @@ int flood_tuning_load(const char* path, int32_t* n_loaded);
 int flood_tuning_entries(flood_tuning_entry* out, int32_t capacity, int32_t* n_entries);
 /* Remove every entry (lookups return the defaults until entries are added). */
 int flood_tuning_clear(void);
+
+/* ========================================================================
+ * General ambient dimension d = 2..5 (§3 leaves d free; §5.3 scales it:
+ * Fig. 4c, swisscheese-like clouds with |X| = 1M, |L| = 1k, d = 2..5).
+ * Points are rows of a row-major (n, d) float32 array; simplices go up to
+ * dimension d. Same conventions as the three-dimensional entry points:
+ * caller-owned device buffers, asynchronous on `stream`, device-side errors
+ * through flood_check (or the next call on the stream).
+ * ======================================================================== */
+
+/* ------------------------------------------------------------------------
+ * flood_fps_nd — farthest point sampling in R^d (§3.2, greedy k-centre).
+ *
+ * The same rule as flood_fps: l_0 = X[start]; each later pick maximises the
+ * distance to the picks so far, ties to the lowest index. The key is the
+ * binary32 squared distance with the d squares summed left to right and
+ * every subtraction, product and sum rounded on its own (no fused
+ * multiply-add), so picks are bit-exact against any implementation of that
+ * arithmetic.
+ *   X          device, (n_points, dim) float32 row-major, finite
+ *   dim        2..FLOOD_ND_MAX_DIM
+ *   out_idx    device int64[n_landmarks]: the picks, out_idx[0] = start
+ *   out_key    device float32[n_landmarks] or NULL: squared distance of each
+ *              pick when picked (out_key[0] = +inf)
+ * Errors: FLOOD_EINVAL (sizes, dim, start), FLOOD_ENOMEM, FLOOD_ECUDA on
+ * return; through flood_check: FLOOD_EINVAL (non-finite X),
+ * FLOOD_EDEGENERATE (fewer than n_landmarks distinct points),
+ * FLOOD_ETIMEOUT (a bounded wait of the pick exchange gave up).
+ * ------------------------------------------------------------------------ */
+int flood_fps_nd(const float* X, int64_t n_points, int32_t dim, int32_t n_landmarks, int64_t start,
+                 int64_t* out_idx, float* out_key, void* stream);
+
+/* ------------------------------------------------------------------------
+ * flood_build_grid_nd — uniform cell grid of X in R^d (the masking
+ * structure of §4.2 for any d).
+ *
+ * A dense row-major table of cubic cells of edge h over X's bounding box,
+ * with X's points copied in cell order (library-owned; X may be freed
+ * afterwards). cell_size <= 0 picks h for about one point per cell over the
+ * axes X spans; the table holds at most min(2^25, max(2^12, 2 n_points))
+ * cells and h is enlarged on the device until it fits. Results of
+ * flood_filtration_nd do not depend on h.
+ * Errors: FLOOD_EINVAL (arguments), FLOOD_ENOMEM, FLOOD_ECUDA on return;
+ * through flood_check: FLOOD_EINVAL (non-finite X). Asynchronous.
+ * ------------------------------------------------------------------------ */
+typedef struct flood_grid_nd flood_grid_nd;
+
+typedef struct flood_grid_nd_info {
+    int64_t n_points;
+    int64_t n_cells;
+    int32_t dim;
+    int32_t dims[FLOOD_ND_MAX_DIM];      /* cells per axis (axes >= dim: 0) */
+    float cell_size;
+    float bbox_lo[FLOOD_ND_MAX_DIM];     /* also the lower corner of cell 0 */
+    float bbox_hi[FLOOD_ND_MAX_DIM];
+    int64_t device_bytes;
+} flood_grid_nd_info;
+
+int flood_build_grid_nd(const float* X, int64_t n_points, int32_t dim, float cell_size,
+                        flood_grid_nd** out, void* stream);
+/* Waits for the build, then fills *out. */
+int flood_grid_nd_get_info(const flood_grid_nd* grid, flood_grid_nd_info* out);
+/* Waits for all device work, then frees the grid. */
+void flood_grid_nd_destroy(flood_grid_nd* grid);
+
+/* ------------------------------------------------------------------------
+ * flood_filtration_nd — flood values of every simplex of Del(L) in R^d (§4.1).
+ *
+ * f(sigma) = max over Lemma 1's grid P_sigma (faces included) of the
+ * distance to the nearest point of X, computed as in flood_filtration:
+ * max(own, f(facets)) over dimensions 0..d in increasing order, `own` the
+ * maximum over the interior samples (lambda_i = c_i/m, all c_i >= 1).
+ * A sample's nearest-point search stops as soon as its distance is exact or
+ * can no longer exceed max(f(facets), the simplex's running maximum); every
+ * such decision uses bounds rounded toward the safe side, so the value is
+ * that of the full search: max(f(facets), sqrt(max over interior samples of
+ * min over X of the binary32 squared distance)), whatever the cell size.
+ * Vertices get d(v, X) (0 for rows of L that are points of X).
+ *
+ *   grid         from flood_build_grid_nd on X (its dim is the dimension d)
+ *   L            device, (n_landmarks, d) float32, finite
+ *   simplices[k] device int32 (n_simplices[k], k+1) vertex ids (rows of L),
+ *                k = 1..d; simplices[0] is ignored (vertices are L's rows;
+ *                n_simplices[0] must be n_landmarks or 0)
+ *   facets[k]    device int32 (n_simplices[k], k+1), k >= 2: column j is the
+ *                row in simplices[k-1] of the facet without vertex j
+ *   m            1..FLOOD_MAX_M
+ *   values[k]    device float32 (n_simplices[k]) output, k = 0..d (values[0]:
+ *                n_landmarks entries); NULL skips the output (the dimension
+ *                is still computed for the ones above it)
+ * Entries above d must have n_simplices[k] == 0.
+ * Errors: FLOOD_EINVAL (arguments), FLOOD_ENOMEM, FLOOD_ECUDA on return;
+ * through flood_check: FLOOD_EINVAL (ids out of range, non-finite L),
+ * FLOOD_EINTERNAL (a consistency check). Asynchronous; the work counters of
+ * flood_last_filtration_nd_stats are read back without waiting.
+ * ------------------------------------------------------------------------ */
+int flood_filtration_nd(const flood_grid_nd* grid, const float* L, int32_t n_landmarks,
+                        const int32_t* const simplices[FLOOD_ND_MAX_DIM + 1],
+                        const int32_t* const facets[FLOOD_ND_MAX_DIM + 1],
+                        const int64_t n_simplices[FLOOD_ND_MAX_DIM + 1], int32_t m,
+                        float* const values[FLOOD_ND_MAX_DIM + 1], void* stream);
+
+/* Work counters of the calling thread's last flood_filtration_nd, per
+ * dimension (waits for that call's stream). items: (simplex, interior
+ * sample) pairs (vertices: one each); pruned: settled by the vertices'
+ * nearest points alone; resolved: settled within the 3^d cells around the
+ * sample; exact: nearest distance exact within those cells; fallback: handed
+ * to the shell search; pairs / pairs_fallback: (sample, point) distances
+ * evaluated in each pass; cells: cells whose points were read. */
+typedef struct flood_nd_stats {
+    int32_t dim;
+    int64_t items[FLOOD_ND_MAX_DIM + 1];
+    int64_t pruned[FLOOD_ND_MAX_DIM + 1];
+    int64_t resolved[FLOOD_ND_MAX_DIM + 1];
+    int64_t exact[FLOOD_ND_MAX_DIM + 1];
+    int64_t fallback[FLOOD_ND_MAX_DIM + 1];
+    int64_t pairs[FLOOD_ND_MAX_DIM + 1];
+    int64_t pairs_fallback[FLOOD_ND_MAX_DIM + 1];
+    int64_t cells[FLOOD_ND_MAX_DIM + 1];
+} flood_nd_stats;
+
+int flood_last_filtration_nd_stats(flood_nd_stats* out);
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* flood_last_error(void);

@@ -60,6 +60,23 @@ class Tuning(C.Structure):
 P4 = C.c_void_p * 4
 I64x4 = C.c_int64 * 4
 I32x4 = C.c_int32 * 4
+ND_MAX_DIM = 5
+P6 = C.c_void_p * (ND_MAX_DIM + 1)
+I64x6 = C.c_int64 * (ND_MAX_DIM + 1)
+
+
+class GridNdInfo(C.Structure):
+    _fields_ = [
+        ("n_points", C.c_int64), ("n_cells", C.c_int64), ("dim", C.c_int32), ("dims", C.c_int32 * ND_MAX_DIM),
+        ("cell_size", C.c_float), ("bbox_lo", C.c_float * ND_MAX_DIM), ("bbox_hi", C.c_float * ND_MAX_DIM),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+class NdStats(C.Structure):
+    _fields_ = [("dim", C.c_int32)] + [
+        (name, C.c_int64 * (ND_MAX_DIM + 1))
+        for name in ("items", "pruned", "resolved", "exact", "fallback", "pairs", "pairs_fallback", "cells")]
 
 
 class FiltrationJob(C.Structure):
@@ -148,6 +165,15 @@ _SIGNATURES = {
     "flood_check": (C.c_int, [C.c_void_p]),
     "flood_persistence": (C.c_int, [P4, P4, I64x4, P4, C.c_void_p * 3, C.c_int64 * 3, P4, I64x4,
                                     C.POINTER(C.c_int64), C.c_void_p]),
+    "flood_fps_nd": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                               C.c_void_p]),
+    "flood_build_grid_nd": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.POINTER(C.c_void_p),
+                                      C.c_void_p]),
+    "flood_grid_nd_get_info": (C.c_int, [C.c_void_p, C.POINTER(GridNdInfo)]),
+    "flood_grid_nd_destroy": (None, [C.c_void_p]),
+    "flood_filtration_nd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, P6, P6, I64x6, C.c_int32, P6,
+                                      C.c_void_p]),
+    "flood_last_filtration_nd_stats": (C.c_int, [C.POINTER(NdStats)]),
     "flood_last_error": (C.c_char_p, []),
     "flood_version": (C.c_char_p, []),
     "flood_kernel_launches": (C.c_int64, []),

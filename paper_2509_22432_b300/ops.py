@@ -20,7 +20,8 @@ __all__ = ["check", "fps", "fps_noalloc", "fps_stats", "fps_scratch_bytes", "fps
            "fp32_peak_probe", "Grid", "build_grid", "DeviceComplex", "to_device", "filtration",
            "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
            "complex_faces", "filtration_masked", "persistence", "diagrams_from_pairs",
-           "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given"]
+           "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given",
+           "fps_nd", "GridNd", "build_grid_nd", "filtration_nd", "last_filtration_nd_stats"]
 
 
 def _stream_ptr(device: torch.device) -> C.c_void_p:
@@ -492,3 +493,104 @@ def flood_values_given(X: torch.Tensor, L: torch.Tensor, grid: Grid, cx: DeviceC
     """Differentiable flood values over given point sets, split per dimension."""
     out = GivenFloodFunction.apply(X, L, grid, cx, weights)
     return list(torch.split(out, cx.counts))
+
+
+# ---------------------------------------------------------------- ambient dimension d = 2..5
+def _points_nd(X: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(X, torch.Tensor) or not X.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if X.dtype != torch.float32 or X.dim() != 2 or not 2 <= X.shape[1] <= _lib.ND_MAX_DIM:
+        raise ValueError(f"{name} must be float32 of shape (n, d), 2 <= d <= {_lib.ND_MAX_DIM}")
+    return X.contiguous()
+
+
+def fps_nd(X: torch.Tensor, n_landmarks: int, start: int = 0, sync: bool = True):
+    """Farthest point sampling in R^d (flood_fps_nd). Returns (idx int64[n], key float32[n])."""
+    X = _points_nd(X, "X")
+    idx = torch.empty(n_landmarks, dtype=torch.int64, device=X.device)
+    key = torch.empty(n_landmarks, dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.get().flood_fps_nd(_ptr(X), X.shape[0], X.shape[1], int(n_landmarks), int(start), _ptr(idx),
+                                     _ptr(key), _stream_ptr(X.device))
+    _finish(st, "flood_fps_nd", X.device, sync)
+    return idx, key
+
+
+class GridNd:
+    """Library-owned cell grid over X in R^d (flood_build_grid_nd)."""
+
+    def __init__(self, handle: C.c_void_p, device: torch.device, dim: int):
+        self._h = handle
+        self.device = device
+        self.dim = dim
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if not self._h:
+            raise ValueError("grid already destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = _lib.GridNdInfo()
+        _lib.check(_lib.get().flood_grid_nd_get_info(self.handle, C.byref(inf)), "flood_grid_nd_get_info")
+        d = inf.dim
+        return {"n_points": inf.n_points, "n_cells": inf.n_cells, "dim": d, "dims": tuple(inf.dims[:d]),
+                "cell_size": inf.cell_size, "bbox_lo": tuple(inf.bbox_lo[:d]), "bbox_hi": tuple(inf.bbox_hi[:d]),
+                "device_bytes": inf.device_bytes}
+
+    def close(self) -> None:
+        if self._h:
+            _lib.get().flood_grid_nd_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_grid_nd(X: torch.Tensor, cell_size: float = 0.0, sync: bool = True) -> GridNd:
+    """Cell grid over X in R^d (flood_build_grid_nd)."""
+    X = _points_nd(X, "X")
+    h = C.c_void_p(0)
+    with torch.cuda.device(X.device):
+        st = _lib.get().flood_build_grid_nd(_ptr(X), X.shape[0], X.shape[1], float(cell_size), C.byref(h),
+                                            _stream_ptr(X.device))
+    _lib.check(st, "flood_build_grid_nd")
+    grid = GridNd(h, X.device, X.shape[1])
+    if sync:
+        check(X.device)
+    return grid
+
+
+def filtration_nd(grid: GridNd, L: torch.Tensor, cx: DeviceComplex, m: int, sync: bool = True) -> list:
+    """Flood values of every simplex of Del(L) in R^d (flood_filtration_nd): values[k] float32, k = 0..d."""
+    L = _points_nd(L, "L")
+    if L.shape[1] != grid.dim:
+        raise ValueError(f"L has {L.shape[1]} coordinates, the grid {grid.dim}")
+    K = _lib.ND_MAX_DIM + 1
+    counts = cx.counts + [0] * (K - len(cx.counts))
+    counts[0] = L.shape[0]
+    s = _lib.P6(*[C.c_void_p(t.data_ptr() if t.numel() else 0) for t in cx.simplices[:K]] +
+                [C.c_void_p(0)] * (K - len(cx.simplices)))
+    f = _lib.P6(*[C.c_void_p(t.data_ptr() if t.numel() else 0) for t in cx.facets[:K]] +
+                [C.c_void_p(0)] * (K - len(cx.facets)))
+    n = _lib.I64x6(*counts)
+    vals = [torch.empty(counts[k], dtype=torch.float32, device=L.device) for k in range(len(cx.simplices))]
+    vp = _lib.P6(*[_ptr(v) if v.numel() else C.c_void_p(0) for v in vals] + [C.c_void_p(0)] * (K - len(vals)))
+    with torch.cuda.device(L.device):
+        st = _lib.get().flood_filtration_nd(grid.handle, _ptr(L), L.shape[0], s, f, n, int(m), vp,
+                                            _stream_ptr(L.device))
+    _finish(st, "flood_filtration_nd", L.device, sync)
+    return vals
+
+
+def last_filtration_nd_stats() -> dict:
+    st = _lib.NdStats()
+    _lib.check(_lib.get().flood_last_filtration_nd_stats(C.byref(st)), "flood_last_filtration_nd_stats")
+    d = st.dim
+    out = {"dim": d}
+    for k in ("items", "pruned", "resolved", "exact", "fallback", "pairs", "pairs_fallback", "cells"):
+        out[k] = list(getattr(st, k))[:d + 1]
+    return out
