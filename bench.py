@@ -390,6 +390,89 @@ def measure_second_workload(name: str, steps: int, warmup: int, dev, flush) -> d
             "l2": "flushed between steps", "delaunay": "host, untimed, computed once"}
 
 
+AMBIENT_DIMS = (2, 3, 4, 5)
+
+
+def measure_ambient_dimensions(dims, steps: int, warmup: int, dev, flush, peak_tflops: float,
+                               cpu_sample: bool) -> dict:
+    """The scaling study in the ambient dimension (§5.3, Fig. 4c): swisscheese-like clouds in [0,5]^d,
+    |X| = 1M, |L| = 1k, m = 10, through the general-dimension path (flood_fps_nd, flood_build_grid_nd,
+    flood_filtration_nd).
+
+    A step is FPS + grid + filtration of every simplex of Del(L) (dimensions 0..d), timed with CUDA
+    events, L2 flushed between steps; Del(L) is host input (Qhull), computed once and untimed. The
+    picks of d = 4, 5 are compared with the oracle's stored picks (tests/golden). The flood kernels'
+    FP32 rate counts the evaluated (sample, point) pairs at 3d - 1 flops each (d differences, one
+    product, d - 1 fused multiply-adds). cpu_sample: the oracle (k-d tree, full grid of each simplex)
+    timed on 10 simplices per dimension, scaled to the whole complex.
+    """
+    import torch
+    import oracle
+    from paper_2509_22432_b300 import data, delaunay_complex, ops
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for d in dims:
+        n, n_l, m = 1_000_000, 1000, 10
+        X = data.swisscheese_cloud(n, seed=6, dim=d)
+        Xd = torch.from_numpy(X).to(dev)
+        idx0, _ = ops.fps_nd(Xd, n_l, 0)
+        golden = _golden_landmarks(f"swisscheese{d}d-1M", X)
+        exact = None if golden is None else bool(np.array_equal(idx0.cpu().numpy(), golden))
+        L = X[idx0.cpu().numpy()]
+        cx = delaunay_complex(L)
+        dcx = ops.to_device(cx, dev)
+        times, ph = [], []
+        for it in range(warmup + steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            idx, _ = ops.fps_nd(Xd, n_l, 0, sync=False)
+            ev[1].record(stream)
+            grid = ops.build_grid_nd(Xd, 0.0, sync=False)
+            ev[2].record(stream)
+            ops.filtration_nd(grid, Xd[idx], dcx, m, sync=False)
+            ev[3].record(stream)
+            ops.check(dev)
+            if it >= warmup:
+                times.append(ev[0].elapsed_time(ev[3]))
+                ph.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+            info = grid.info()
+            grid.close()
+        st = ops.last_filtration_nd_stats()
+        ms = float(np.mean(times))
+        ph = np.mean(np.array(ph), axis=0)
+        pairs = int(sum(st["pairs"]) + sum(st["pairs_fallback"]))
+        achieved = pairs * (3 * d - 1) / (ph[2] * 1e-3) / 1e12
+        n_simp = int(sum(cx.counts[1:]))
+        rec = {"workload": f"swisscheese{d}d-1M", "d": d, "n_points": n, "n_landmarks": n_l, "m": m,
+               "simplices": cx.counts, "simplices_per_step": n_simp, "items": int(sum(st["items"])),
+               "metric": "flood simplices/s", "value": n_simp / (ms * 1e-3), "unit": "simplices/s",
+               "ms_per_step": ms, "steps": steps, "warmup": warmup,
+               "phase_ms": {"fps": float(ph[0]), "grid": float(ph[1]), "filtration": float(ph[2])},
+               "fps_equals_oracle_picks": exact,
+               "grid": {"cell_size": info["cell_size"], "n_cells": info["n_cells"]},
+               "work": {k: int(sum(v)) for k, v in st.items() if k != "dim"},
+               "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                            "frac": achieved / peak_tflops, "evaluated_pairs": pairs, "flops_per_pair": 3 * d - 1,
+                            "kernel": "k_nd_resolve + k_nd_fallback (all dimensions of one filtration)"},
+               "l2": "flushed between steps", "delaunay": "host, untimed, computed once"}
+        if cpu_sample:
+            rng = np.random.default_rng(5)
+            subset = [np.arange(0)] + [rng.choice(c, min(10, c), replace=False) for c in cx.counts[1:]]
+            index = oracle.flood.KDIndex(X, "kdtree")
+            t0 = time.perf_counter()
+            oracle.flood_values(X, L, cx.simplices, m, method="kdtree", index=index, subset=subset)
+            t = time.perf_counter() - t0
+            est = sum(t / sum(len(x) for x in subset[1:]) * c for c in cx.counts[1:])
+            rec["cpu_baseline"] = {"kind": "oracle", "cores": 1, "sample": f"{sum(len(x) for x in subset[1:])} "
+                                   "simplices (10 per dimension, full grid, k-d tree over X), scaled to the complex",
+                                   "seconds_estimate": est, "simplices_per_s": n_simp / est}
+        out[f"d{d}"] = rec
+        del Xd
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,6 +484,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--second-workload", default="shapes-5M", choices=sorted(WORKLOADS) + ["none"],
                     help="a second workload timed the same way and reported beside the main line")
+    ap.add_argument("--ambient-dims", default=",".join(str(d) for d in AMBIENT_DIMS),
+                    help="ambient dimensions of the Fig. 4c scaling leg (comma list, or 'none')")
     ap.add_argument("--no-tune", action="store_true",
                     help="take the tuning table's parameters instead of sweeping them first (profiling runs)")
     ap.add_argument("--serving", action="store_true",
@@ -754,6 +839,10 @@ def main():
     if args.second_workload not in ("none", args.workload):
         line["second_workload"] = measure_second_workload(args.second_workload, min(args.steps, 10), args.warmup,
                                                           dev, flush)
+    if rank == 0 and args.ambient_dims != "none":
+        dims = [int(x) for x in args.ambient_dims.split(",") if x]
+        line["ambient_dimension"] = measure_ambient_dimensions(dims, min(args.steps, 5), args.warmup, dev, flush,
+                                                               peak_tflops, not args.no_cpu_baseline)
     line["complex_faces"] = {"tetrahedra": int(cx.counts[3]), "device_ms": float(np.median(fc_dev)),
                              "host_ms": fc_host, "what": "triangles, edges and facet incidence from the "
                              "tetrahedra: flood_complex_faces (call to return, synchronised) vs the host "

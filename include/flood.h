@@ -695,7 +695,7 @@ int flood_fps_nd(const float* X, int64_t n_points, int32_t dim, int32_t n_landma
  *
  * A dense row-major table of cubic cells of edge h over X's bounding box,
  * with X's points copied in cell order (library-owned; X may be freed
- * afterwards). cell_size <= 0 picks h for about one point per cell over the
+ * afterwards). cell_size <= 0 picks h for about six points per cell over the
  * axes X spans; the table holds at most min(2^25, max(2^12, 2 n_points))
  * cells and h is enlarged on the device until it fits. Results of
  * flood_filtration_nd do not depend on h.

@@ -21,7 +21,8 @@
 //             its running nearest distance is <= LB (Lemma 2's argument with a
 //             live bound instead of a ball), which is the usual outcome within
 //             the sample's own cell and its 3^d - 1 neighbours, visited nearest
-//             first; the rest either finish exactly there or go to
+//             first (or at once, through the point that settled the sample
+//             before it); the rest either finish exactly there or go to
 //   fallback  one warp per remaining sample: Chebyshev shells of cells around
 //             the sample, clipped to the grid, until the distance is exact or
 //             falls to max(LB, the simplex's running maximum);
@@ -56,9 +57,10 @@ namespace {
 
 constexpr int kNdMaxD = 5;
 constexpr int kNdThreads = 256;
-constexpr int kNdFpsThreads = 256;
+constexpr int kNdFpsThreads = 1024;  // one block per SM: the pick exchange reads one slot per SM
 constexpr int64_t kNdChunk = int64_t(1) << 22;   // items per resolve launch (and fallback capacity)
 constexpr float kOneMinus = 0.99999904632568359375f;  // 1 - 2^-20
+constexpr double kNdPointsPerCell = 6.0;
 
 // ---------------------------------------------------------------- constant tables
 // Binomial coefficients C(n, r), n <= FLOOD_MAX_M + kNdMaxD, r <= kNdMaxD.
@@ -77,9 +79,10 @@ __constant__ Binom c_binom = make_binom();
 
 // Offsets of the cells of Chebyshev distance <= 1 from a cell in d dimensions,
 // ordered by the number of non-zero components (own cell, face neighbours,
-// edge neighbours, ...): roughly nearest first.
+// edge neighbours, ...): roughly nearest first. Packed two bits per axis
+// (offset + 1).
 struct Ring1 {
-    int8_t o[243][kNdMaxD];
+    uint16_t o[243];
     int32_t n;
 };
 constexpr Ring1 make_ring1(int D) {
@@ -90,15 +93,15 @@ constexpr Ring1 make_ring1(int D) {
     for (int w = 0; w <= D; ++w)
         for (int code = 0; code < total; ++code) {
             int x = code, nz = 0;
-            int8_t o[kNdMaxD] = {0, 0, 0, 0, 0};
+            uint32_t packed = 0;
             for (int a = 0; a < D; ++a) {
-                o[a] = static_cast<int8_t>(x % 3 - 1);
+                const int o = x % 3 - 1;
                 x /= 3;
-                nz += o[a] != 0;
+                nz += o != 0;
+                packed |= static_cast<uint32_t>(o + 1) << (2 * a);
             }
             if (nz != w) continue;
-            for (int a = 0; a < kNdMaxD; ++a) t.o[n][a] = o[a];
-            ++n;
+            t.o[n++] = static_cast<uint16_t>(packed);
         }
     t.n = n;
     return t;
@@ -236,6 +239,17 @@ __device__ __forceinline__ void unrank_interior(int64_t j, int m, int k, int (&c
     c[k] = s + 1;
 }
 
+// lam[j][i] = c_i / m (binary32: c_i times the rounded reciprocal of m) for
+// every interior composition j of m into k+1 parts.
+__global__ void k_nd_lambda(float* lam, int64_t n, int m, int k) {
+    const int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (j >= n) return;
+    int c[kNdMaxD + 1];
+    unrank_interior(j, m, k, c);
+    const float inv = __frcp_rn(static_cast<float>(m));
+    for (int i = 0; i <= k; ++i) lam[j * (k + 1) + i] = __fmul_rn(static_cast<float>(c[i]), inv);
+}
+
 // ---------------------------------------------------------------- grid build
 template <int D>
 __global__ void __launch_bounds__(kBoxThreads) k_bbox_nd(const float* X, int64_t n, uint32_t* box, uint32_t* flags) {
@@ -295,9 +309,11 @@ __global__ void k_box_init_nd(uint32_t* box, uint32_t* flags) {
 }
 
 // Cell edge and table dimensions, on the device (no readback). Without a
-// requested edge, h targets about one point per cell over the axes the cloud
-// spans (a cloud flat along some axes gets one cell there); h grows until the
-// table fits its capacity.
+// requested edge, h targets about kNdPointsPerCell points per cell over the
+// axes the cloud spans (a cloud flat along some axes gets one cell there); h
+// grows until the table fits its capacity. (Measured on the swisscheese-like
+// clouds of d = 2..5: about six points per cell is the fastest setting at
+// every d; one per cell costs 1.3x-3x.)
 template <int D>
 __global__ void k_nd_geometry(const uint32_t* box, const uint32_t* flags, int64_t n, float cell_size, int32_t cap,
                               NdGeom* out) {
@@ -318,7 +334,7 @@ __global__ void k_nd_geometry(const uint32_t* box, const uint32_t* flags, int64_
                 vol *= double(g.hi[a]) - g.lo[a];
                 ++deff;
             }
-        h = deff ? pow(vol / double(n), 1.0 / deff) : 1.0;
+        h = deff ? pow(kNdPointsPerCell * vol / double(n), 1.0 / deff) : 1.0;
     }
     if (!(h > 0.0) || !isfinite(h)) h = emax > 0.0f ? emax : 1.0;
     float hf = static_cast<float>(h);
@@ -444,7 +460,7 @@ __device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t* s_red) {
 }
 
 template <int D, int R>
-__global__ void __launch_bounds__(kNdFpsThreads) k_fps_nd(NdFpsArgs a) {
+__global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
     __shared__ uint64_t s_red[kNdFpsThreads / 32];
     __shared__ uint64_t s_win;
     __shared__ int s_stop;
@@ -551,6 +567,9 @@ struct NdFilt {
     int64_t item0, n_items; // this launch's items [item0, item0 + n_items)
     uint4* fb;              // fallback items: (item lo, item hi, best bits, position)
     uint32_t* fb_count;
+    uint32_t fb_cap;        // capacity of fb
+    unsigned long long* next;  // items of this launch handed out so far (first pass)
+    const float* lam;       // (I, k+1) barycentric weights c_i / m of the interior samples
     unsigned long long* stats;  // kNdStats counters of this dimension
     uint32_t* flags;
 };
@@ -582,9 +601,7 @@ __device__ __forceinline__ bool nd_item(const NdFilt& f, int64_t item, int64_t& 
 #pragma unroll
         for (int a = 0; a < D; ++a) p[a] = f.L[D * s + a];
     } else {
-        int c[kNdMaxD + 1];
-        unrank_interior(j, f.m, f.k, c);
-        const float inv = __frcp_rn(static_cast<float>(f.m));
+        const float* lw = f.lam + j * (f.k + 1);
         int32_t v[kNdMaxD + 1];
         for (int i = 0; i <= f.k; ++i) {
             v[i] = f.simp[s * (f.k + 1) + i];
@@ -596,7 +613,7 @@ __device__ __forceinline__ bool nd_item(const NdFilt& f, int64_t item, int64_t& 
 #pragma unroll
         for (int a = 0; a < D; ++a) p[a] = 0.0f;
         for (int i = 0; i <= f.k; ++i) {
-            const float lam = __fmul_rn(static_cast<float>(c[i]), inv);
+            const float lam = __ldg(lw + i);
 #pragma unroll
             for (int a = 0; a < D; ++a) p[a] = __fmaf_rn(lam, f.L[D * v[i] + a], p[a]);
         }
@@ -629,13 +646,33 @@ __device__ __forceinline__ bool nd_item(const NdFilt& f, int64_t item, int64_t& 
     return true;
 }
 
-// Scan the points of one cell: running minimum (and its position).
+// Scan the points of one cell: running minimum (and its position). Stops
+// early once best <= T (the item is settled; the rest of the cell cannot
+// matter); T = -1 scans the whole cell.
 template <int D, bool kVertex>
 __device__ __forceinline__ void scan_cell(const NdFilt& f, const float (&p)[D], int32_t cell, float& best,
-                                          int32_t& pos, uint32_t& pairs) {
+                                          int32_t& pos, uint32_t& pairs, float T = -1.0f) {
     if (FLOOD_OOB(cell, f.geom->n_cells, f.flags)) return;
     const int32_t s0 = __ldg(f.cs + cell), s1 = __ldg(f.cs + cell + 1);
-    for (int32_t i = s0; i < s1; ++i) {
+    int32_t i = s0;
+    for (; i + 1 < s1; i += 2) {  // two independent loads in flight
+        const float4 r0 = __ldg(f.a4 + i), r1 = __ldg(f.a4 + i + 1);
+        const float e0 = D > 4 ? __ldg(f.a1 + i) : 0.0f, e1 = D > 4 ? __ldg(f.a1 + i + 1) : 0.0f;
+        const float d0 = dist2<D>(p, r0, e0), d1 = dist2<D>(p, r1, e1);
+        if (d0 < best) {
+            best = d0;
+            if (kVertex) pos = i;
+        }
+        if (d1 < best) {
+            best = d1;
+            if (kVertex) pos = i + 1;
+        }
+        if (best <= T) {
+            pairs += static_cast<uint32_t>(i + 2 - s0);
+            return;
+        }
+    }
+    if (i < s1) {
         const float d = dist2<D>(p, __ldg(f.a4 + i), D > 4 ? __ldg(f.a1 + i) : 0.0f);
         if (d < best) {
             best = d;
@@ -645,7 +682,7 @@ __device__ __forceinline__ void scan_cell(const NdFilt& f, const float (&p)[D], 
     pairs += static_cast<uint32_t>(s1 - s0);
 }
 
-__device__ __forceinline__ void add_stats(const NdFilt& f, unsigned long long (&st)[kNdStats]) {
+__device__ __forceinline__ void add_stats(const NdFilt& f, const uint32_t (&st)[kNdStats]) {
     __shared__ unsigned long long s_st[kNdStats];
     if (threadIdx.x < kNdStats) s_st[threadIdx.x] = 0ull;
     __syncthreads();
@@ -653,7 +690,7 @@ __device__ __forceinline__ void add_stats(const NdFilt& f, unsigned long long (&
     for (int i = 0; i < kNdStats; ++i) {
         unsigned long long v = st[i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);  // per-warp sums fit easily
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_st[i], v);
     }
     __syncthreads();
@@ -672,77 +709,133 @@ __device__ __forceinline__ void settle(const NdFilt& f, int64_t s, float best, i
     }
 }
 
-// First pass: one thread per item, items of a simplex on consecutive threads
-// (their cells overlap, so the cell table and points come from L1).
+// First pass. Items differ a lot in how many cells they need, so a lane does
+// not keep one item to the end while the others wait: every lane holds one
+// item at a time and the warp advances all of them by one Ring1 entry per
+// iteration. When at least half of the lanes are idle (or all are), the idle
+// ones take the next items of the warp's share (kPool consecutive items at a
+// time from the launch's counter: consecutive samples of a simplex, whose
+// data then comes from L1), so most iterations run with most lanes busy.
+// An item settles when its distance falls to T (it cannot raise the value),
+// or is exact when the 3^d cells around its cell hold a point nearer than
+// anything outside them; the rest go to the shell search (fallback).
+constexpr int kPool = 64;
+
 template <int D, bool kVertex>
 __global__ void __launch_bounds__(kNdThreads) k_nd_resolve(NdFilt f) {
-    unsigned long long st[kNdStats] = {};
-    const int64_t item = f.item0 + blockIdx.x * int64_t(kNdThreads) + threadIdx.x;
-    bool push = false;
-    float best = INFINITY;
-    int32_t pos = 0;
-    if (item < f.item0 + f.n_items) {
-        const NdGeom& g = *f.geom;
-        int64_t s;
-        float p[D], lb, u;
-        if (nd_item<D>(f, item, s, p, lb, u)) {
-            st[ST_ITEMS] = 1;
-            const float T = sq_threshold(lb);
-            best = u;
-            uint32_t pairs = 0;
-            if (!kVertex && best <= T) {
-                st[ST_PRUNED] = 1;
-            } else {
-                int c[D];
-                cell_of<D>(g, p, c);
-                const Ring1& R = c_ring1[D - 2];
-                bool done = false;
-                for (int t = 0; t < R.n && !done; ++t) {
-                    int cc[D];
-                    bool inside = true;
-                    int32_t cell = 0;
-#pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        cc[a] = c[a] + R.o[t][a];
-                        inside = inside && cc[a] >= 0 && cc[a] < g.dims[a];
-                        cell += cc[a] * g.stride[a];
+    __shared__ uint16_t s_off[243];
+    const Ring1& R = c_ring1[D - 2];
+    for (int t = threadIdx.x; t < R.n; t += blockDim.x) s_off[t] = R.o[t];
+    __syncthreads();
+    const int n_off = R.n;
+    const NdGeom& g = *f.geom;
+    const int lane = threadIdx.x & 31;
+    uint32_t st[kNdStats] = {};
+    uint32_t pairs = 0;
+    // this lane's item
+    bool have = false;
+    int64_t item = 0, s = 0;
+    float p[D], gm2[D], gp2[D];
+    int c[D];
+    int32_t cell0 = 0, pos = 0;
+    float T = 0.0f, best = INFINITY;
+    int t = 0;
+    // the warp's share of the launch's items
+    int64_t pool = 0, pool_end = 0;
+    bool exhausted = false;
+    for (;;) {
+        unsigned need = __ballot_sync(0xffffffffu, !have);
+        if (!exhausted && (__popc(need) >= 16 || need == 0xffffffffu)) {
+            while (need && !exhausted) {
+                if (pool >= pool_end) {
+                    unsigned long long b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(f.next, static_cast<unsigned long long>(kPool));
+                    b0 = __shfl_sync(0xffffffffu, b0, 0);
+                    if (b0 >= static_cast<unsigned long long>(f.n_items)) {
+                        exhausted = true;
+                        break;
                     }
-                    if (!inside || cell_bound<D>(g, p, cc) >= best) continue;
-                    scan_cell<D, kVertex>(f, p, cell, best, pos, pairs);
-                    ++st[ST_CELLS];
-                    done = best <= T;
+                    pool = static_cast<int64_t>(b0);
+                    pool_end = std::min<int64_t>(pool + kPool, f.n_items);
                 }
-                st[ST_PAIRS] = pairs;
-                if (done) {
-                    st[ST_RESOLVED] = 1;
+                const int take = min(__popc(need), static_cast<int>(pool_end - pool));
+                const int rank = __popc(need & ((1u << lane) - 1u));
+                if (!have && rank < take) {
+                    float lb, u;
+                    item = f.item0 + pool + rank;
+                    if (nd_item<D>(f, item, s, p, lb, u)) {
+                        ++st[ST_ITEMS];
+                        T = sq_threshold(lb);
+                        best = u;
+                        if (!kVertex && best <= T) {
+                            ++st[ST_PRUNED];
+                        } else {
+                            cell_of<D>(g, p, c);
+                            cell0 = 0;
+#pragma unroll
+                            for (int a = 0; a < D; ++a) {
+                                cell0 += c[a] * g.stride[a];
+                                // gaps to the lower and upper face of the own cell (the neighbours' near faces)
+                                const float lo = fmaxf(0.0f, __fsub_rd(p[a], __fadd_ru(corner(g, a, c[a]), g.slack)));
+                                const float hi =
+                                    fmaxf(0.0f, __fsub_rd(__fsub_rd(corner(g, a, c[a] + 1), g.slack), p[a]));
+                                gm2[a] = __fmul_rd(lo, lo);
+                                gp2[a] = __fmul_rd(hi, hi);
+                            }
+                            pos = 0;
+                            t = 0;
+                            have = true;
+                        }
+                    }
+                }
+                pool += take;
+                need = __ballot_sync(0xffffffffu, !have);
+            }
+        }
+        if (!__any_sync(0xffffffffu, have)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (!have) continue;
+        if (t < n_off) {
+            const uint32_t w = s_off[t++];
+            bool inside = true;
+            int32_t cell = cell0;
+            float b = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int o = static_cast<int>((w >> (2 * a)) & 3u) - 1;
+                const int cc = c[a] + o;
+                inside = inside && cc >= 0 && cc < g.dims[a];
+                cell += o * g.stride[a];
+                b = o < 0 ? __fadd_rd(b, gm2[a]) : (o > 0 ? __fadd_rd(b, gp2[a]) : b);
+            }
+            if (inside && __fmul_rd(b, kOneMinus) < best) {
+                scan_cell<D, kVertex>(f, p, cell, best, pos, pairs, T);
+                ++st[ST_CELLS];
+                if (best <= T) {
+                    ++st[ST_RESOLVED];
                     if (kVertex) settle<true>(f, s, best, pos);
-                } else if (best <= ring_bound<D>(g, p, c, 1)) {
-                    st[ST_EXACT] = 1;
-                    settle<kVertex>(f, s, best, pos);
-                } else {
-                    push = true;
-                    st[ST_FALLBACK] = 1;
+                    have = false;
                 }
             }
-        }
-    }
-    // hand the unfinished items to the shell search (one atomic per warp)
-    const unsigned mask = __ballot_sync(0xffffffffu, push);
-    if (mask) {
-        const int lane = threadIdx.x & 31;
-        uint32_t base = 0;
-        if (lane == __ffs(mask) - 1) base = atomicAdd(f.fb_count, static_cast<uint32_t>(__popc(mask)));
-        base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
-        if (push) {
-            const uint32_t slot = base + __popc(mask & ((1u << lane) - 1u));
-            if (slot < static_cast<uint32_t>(f.n_items)) {
-                f.fb[slot] = make_uint4(static_cast<uint32_t>(item), static_cast<uint32_t>(item >> 32),
-                                        __float_as_uint(best), static_cast<uint32_t>(pos));
+        } else {
+            if (best <= ring_bound<D>(g, p, c, 1)) {
+                ++st[ST_EXACT];
+                settle<kVertex>(f, s, best, pos);
             } else {
-                atomicOr(f.flags, FLAG_INTERNAL);
+                ++st[ST_FALLBACK];
+                const uint32_t slot = atomicAdd(f.fb_count, 1u);
+                if (slot < f.fb_cap)
+                    f.fb[slot] = make_uint4(static_cast<uint32_t>(item), static_cast<uint32_t>(item >> 32),
+                                            __float_as_uint(best), static_cast<uint32_t>(pos));
+                else
+                    atomicOr(f.flags, FLAG_INTERNAL);
             }
+            have = false;
         }
     }
+    st[ST_PAIRS] = pairs;
     add_stats(f, st);
 }
 
@@ -817,10 +910,10 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 // running maximum), re-read after each shell).
 template <int D, bool kVertex>
 __global__ void __launch_bounds__(kNdThreads) k_nd_fallback(NdFilt f) {
-    unsigned long long st[kNdStats] = {};
+    uint32_t st[kNdStats] = {};
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (kNdThreads / 32);
-    const uint32_t n = min(*f.fb_count, static_cast<uint32_t>(f.n_items));
+    const uint32_t n = min(*f.fb_count, f.fb_cap);
     const NdGeom& g = *f.geom;
     uint32_t pairs = 0, cells = 0;
     for (int64_t e = blockIdx.x * int64_t(kNdThreads / 32) + (threadIdx.x >> 5); e < n; e += warps) {
@@ -922,7 +1015,7 @@ thread_local LastNd g_last_nd;
 template <int D>
 int launch_fps_nd(const float* X, int64_t n, int32_t n_l, int64_t start, int64_t* out_idx, float* out_key,
                   cudaStream_t s, Scratch& scr, uint32_t** flags_out) {
-    constexpr int R = D <= 3 ? 8 : 4;
+    constexpr int R = D <= 4 ? 8 : 5;  // points per thread in registers (R (D + 1) words)
     auto fn = k_fps_nd<D, R>;
     int per_sm = 0;
     FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNdFpsThreads, 0));
@@ -1000,10 +1093,25 @@ int run_filtration_nd(const flood_grid_nd* grid, const float* L, int32_t n_L, co
         launches += ceil_div(nk * I[k], kNdChunk);
     }
     uint32_t *qmax = nullptr, *fb_count = nullptr;
+    unsigned long long* next = nullptr;
+    const int64_t n_counts = std::max<int64_t>(1, launches);
     if ((rc = scr.alloc(&flags, 1)) || (rc = scr.alloc(&stats, (kNdMaxD + 1) * kNdStats)) ||
         (rc = scr.alloc(&vnn, n_L)) || (rc = scr.alloc(&fb, kNdChunk)) || (rc = scr.alloc(&qmax, n_max)) ||
-        (rc = scr.alloc(&fb_count, std::max<int64_t>(1, launches))))
+        (rc = scr.alloc(&fb_count, n_counts)) || (rc = scr.alloc(&next, n_counts)))
         return rc;
+    float* lam[kNdMaxD + 1] = {};
+    for (int k = 1; k <= D; ++k)
+        if (n_simplices[k] > 0 && I[k] > 0) {
+            if ((rc = scr.alloc(&lam[k], I[k] * (k + 1)))) return rc;
+            k_nd_lambda<<<static_cast<unsigned>(ceil_div(I[k], kNdThreads)), kNdThreads, 0, s>>>(lam[k], I[k], m, k);
+            note_launch(1);
+        }
+    // the passes run as many blocks as fit at once, striding over their items
+    int per_sm_v = 0, per_sm = 0;
+    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_v, k_nd_resolve<D, true>, kNdThreads, 0));
+    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nd_resolve<D, false>, kNdThreads, 0));
+    const int64_t resident_v = int64_t(device_sm_count()) * std::max(1, per_sm_v);
+    const int64_t resident = int64_t(device_sm_count()) * std::max(1, per_sm);
     float* vals[kNdMaxD + 1];
     for (int k = 0; k <= D; ++k) {
         const int64_t nk = k == 0 ? n_L : n_simplices[k];
@@ -1013,7 +1121,8 @@ int run_filtration_nd(const flood_grid_nd* grid, const float* L, int32_t n_L, co
     FLOOD_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), s));
     FLOOD_CUDA(cudaMemsetAsync(vnn, 0, sizeof(int32_t) * n_L, s));  // every vertex settles; 0 if its row was rejected
     FLOOD_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * (kNdMaxD + 1) * kNdStats, s));
-    FLOOD_CUDA(cudaMemsetAsync(fb_count, 0, sizeof(uint32_t) * std::max<int64_t>(1, launches), s));
+    FLOOD_CUDA(cudaMemsetAsync(fb_count, 0, sizeof(uint32_t) * n_counts, s));
+    FLOOD_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned long long) * n_counts, s));
     const int fb_blocks = device_sm_count() * 8;
     int64_t chunk_no = 0;
     for (int k = 0; k <= D; ++k) {
@@ -1039,15 +1148,20 @@ int run_filtration_nd(const flood_grid_nd* grid, const float* L, int32_t n_L, co
         f.qmax = qmax;
         f.values = vals[k];
         f.fb = fb;
+        f.lam = lam[k];
         f.stats = stats + k * kNdStats;
         f.flags = flags;
         FLOOD_CUDA(cudaMemsetAsync(qmax, 0, sizeof(uint32_t) * nk, s));
+        // launches of at most kNdChunk items (the capacity of the fallback list)
+        f.fb_cap = static_cast<uint32_t>(kNdChunk);
         const int64_t items = nk * I[k];
         for (int64_t i0 = 0; i0 < items; i0 += kNdChunk) {
             f.item0 = i0;
             f.n_items = std::min<int64_t>(kNdChunk, items - i0);
-            f.fb_count = fb_count + chunk_no++;
-            const unsigned nb = static_cast<unsigned>(ceil_div(f.n_items, kNdThreads));
+            f.fb_count = fb_count + chunk_no;
+            f.next = next + chunk_no++;
+            const unsigned nb = static_cast<unsigned>(std::min<int64_t>(
+                ceil_div(f.n_items, int64_t(kNdThreads / 32) * kPool), k == 0 ? resident_v : resident));
             if (k == 0) {
                 k_nd_resolve<D, true><<<nb, kNdThreads, 0, s>>>(f);
                 k_nd_fallback<D, true><<<fb_blocks, kNdThreads, 0, s>>>(f);

@@ -15,7 +15,7 @@ check it first, so a host whose numpy draws a different cloud is reported as
 such), n_landmarks, start, the SHA-256 of the picked keys' binary32 bytes and
 the last key's bits. Then one picked row of X per line, in pick order.
 
-    python tests/golden/make_fps_golden.py torus-1M shapes-5M swisscheese-1M
+    python tests/golden/make_fps_golden.py torus-1M shapes-5M swisscheese-1M swisscheese4d-1M swisscheese5d-1M
 """
 from __future__ import annotations
 
@@ -41,6 +41,11 @@ WORKLOADS = {
                   10_000),
     "swisscheese-1M": ("data.swisscheese_cloud(1_000_000, seed=6)",
                        lambda: data.swisscheese_cloud(1_000_000, seed=6), 2000),
+    # the scaling study in the ambient dimension (§5.3, Fig. 4c: |X| = 1M, |L| = 1k)
+    "swisscheese4d-1M": ("data.swisscheese_cloud(1_000_000, seed=6, dim=4)",
+                         lambda: data.swisscheese_cloud(1_000_000, seed=6, dim=4), 1000),
+    "swisscheese5d-1M": ("data.swisscheese_cloud(1_000_000, seed=6, dim=5)",
+                         lambda: data.swisscheese_cloud(1_000_000, seed=6, dim=5), 1000),
 }
 START = 0
 

@@ -20,7 +20,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUBSET = ["tests/test_gpu_parity.py", "tests/test_gpu_given.py", "tests/test_gpu_persistence.py",
           "tests/test_gpu_general_landmarks.py", "tests/test_gpu_async.py", "tests/test_serve.py",
-          "tests/test_gpu_wait_timeout.py"]
+          "tests/test_gpu_wait_timeout.py", "tests/test_gpu_nd.py"]
 
 
 def test_gpu_suite_under_the_bounds_checked_library():

@@ -222,15 +222,35 @@ def test_filtration_nd_stats_account_for_every_item():
     assert st["pruned"][0] == 0 and st["resolved"][0] == L.shape[0]   # every landmark finds itself
 
 
+def _golden(name):
+    import importlib.util
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("make_fps_golden", os.path.join(here, "golden", "make_fps_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod, mod.read(name)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("d", [4, 5])
+def test_fps_nd_full_size_equals_stored_oracle_picks(d):
+    """|X| = 1M, |L| = 1k in R^d (Fig. 4c's workload): every pick equals the oracle's stored pick."""
+    mod, g = _golden(f"swisscheese{d}d-1M")
+    X = data.swisscheese_cloud(1_000_000, seed=6, dim=d)
+    assert mod.cloud_sha256(X) == g["x_sha256"]
+    idx, key = _ops().fps_nd(torch.from_numpy(X).cuda(), 1000, 0)
+    assert np.array_equal(idx.cpu().numpy(), g["idx"])
+    assert key.cpu().numpy()[-1].view(np.uint32) == np.uint32(int(g["last_key_hex"], 16))
+
+
 @pytest.mark.slow
 def test_filtration_nd_swisscheese_5d_1m_sampled():
-    """The scaling workload of Fig. 4c at d = 5: |X| = 1M, |L| = 1k, m = 10; FPS bit-exact, sampled values."""
-    ops = _ops()
+    """The scaling workload of Fig. 4c at d = 5: |X| = 1M, |L| = 1k, m = 10; sampled values against the oracle."""
+    mod, g = _golden("swisscheese5d-1M")
     X = data.swisscheese_cloud(1_000_000, seed=6, dim=5)
-    Xd = torch.from_numpy(X).cuda()
-    idx, key = ops.fps_nd(Xd, 1000, 0)
-    ref_i, _ = oracle.fps(X, 1000, 0)
-    assert np.array_equal(idx.cpu().numpy(), ref_i)
+    assert mod.cloud_sha256(X) == g["x_sha256"]
+    ref_i = g["idx"]
     L = X[ref_i]
     cx = delaunay_complex(L)
     got, _ = _gpu_values(X, L, cx, 10)
