@@ -400,17 +400,23 @@ __global__ void __launch_bounds__(kNdThreads) k_nd_scatter(const float* X, int64
 }
 
 // ---------------------------------------------------------------- FPS in d dimensions
-// Each thread keeps R points (coordinates and current distance) in registers,
-// points g, g + G, ..., g + (R-1) G of the grid's G threads; points beyond
-// R G keep their distance in `dist` and are read from X at every pick. A
-// pick: every thread folds the previous pick into its distances and proposes
-// its best (key bits << 32 | ~index: the larger key, then the lower index);
-// blocks reduce, publish their maximum in slot bank (j & 1) with a release
-// store of the tag j, and every block reads all slots (acquire loads, bounded
-// polls) and reduces them to the same winner. A bank is rewritten two picks
-// later, after every block has read it (a block publishes pick j + 2 only after
+// One block of 1024 threads per SM. Thread g of the G threads owns points
+// g, g + G, g + 2G, ...: the first R of them live in registers (coordinates
+// and current distance), the next E in the block's shared memory (one
+// coordinate plane and a distance plane per row, at most what the SM holds),
+// and any further ones are read from X at every pick with their distance in
+// `dist`. A pick: every thread folds the previous pick into its distances and
+// proposes its best; the warps' maxima meet in shared memory; warp 0 reduces
+// them, publishes the block's maximum in slot bank (j & 1) with one 64-bit
+// release store, reads every block's slot (acquire loads, all of a lane's
+// slots in flight at once, bounded polls) and reduces them to the winner,
+// which all blocks therefore agree on. Two block barriers per pick.
+// A slot word is key bits << 32 | generation << 31 | (2^31 - 1 - index): the
+// larger key wins, then the lower index; the generation bit ((j >> 1) & 1)
+// tells pick j's word from the word of pick j - 2 in the same bank, the only
+// other word the slot can hold then (a block publishes pick j + 2 only after
 // reading every block's pick j + 1, which each block publishes only after
-// reading pick j).
+// reading pick j). Banks start with the generation their first pick does not use.
 struct NdFpsArgs {
     const float* X;
     int64_t n;
@@ -418,25 +424,38 @@ struct NdFpsArgs {
     int64_t start;
     int64_t* out_idx;
     float* out_key;
-    float* dist;
+    float* dist;      // distances of the points beyond the register and shared tiers
     uint64_t* slots;  // [2][blocks]
-    uint32_t* tags;   // [2][blocks]
     uint32_t* flags;
     uint32_t poll_limit;
+    int32_t shared_rows;  // E
 };
 
+constexpr int kNdFpsMaxBlocks = 160;  // slots per lane of warp 0: at most 5
+
 __device__ __forceinline__ uint64_t fps_pack(float key, int64_t i) {
-    return (static_cast<uint64_t>(__float_as_uint(key)) << 32) | (0xffffffffu - static_cast<uint32_t>(i));
+    return (static_cast<uint64_t>(__float_as_uint(key)) << 32) | (0x7fffffffu - static_cast<uint32_t>(i));
 }
 
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ uint32_t fps_generation(int j) { return static_cast<uint32_t>((j >> 1) & 1); }
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
     uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Bank 1 is first used by pick 1 (generation 0), bank 0 by pick 2 (generation 1).
+__global__ void k_fps_nd_slots(uint64_t* slots, int blocks) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < blocks) {
+        slots[b] = 0;                           // bank 0: generation 0
+        slots[blocks + b] = uint64_t(1) << 31;  // bank 1: generation 1
+    }
 }
 
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
@@ -448,26 +467,17 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
     return v;
 }
 
-__device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t* s_red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_max_u64(v);
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    uint64_t r = lane < int(blockDim.x >> 5) ? s_red[lane] : 0ull;
-    r = warp_max_u64(r);
-    __syncthreads();
-    return r;
-}
-
 template <int D, int R>
 __global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
+    extern __shared__ float s_rows[];  // [E][D + 1][kNdFpsThreads]: coordinates, then distance
     __shared__ uint64_t s_red[kNdFpsThreads / 32];
     __shared__ uint64_t s_win;
     __shared__ int s_stop;
     if (*a.flags) return;  // input rejected (non-finite coordinates): every block leaves at once
     const int64_t G = int64_t(gridDim.x) * kNdFpsThreads;
     const int64_t g = blockIdx.x * int64_t(kNdFpsThreads) + threadIdx.x;
-    const int B = gridDim.x;
+    const int B = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int E = a.shared_rows;
     float px[R][D], pd[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -476,10 +486,18 @@ __global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
 #pragma unroll
         for (int c = 0; c < D; ++c) px[r][c] = i < a.n ? a.X[D * i + c] : 0.0f;
     }
+    for (int e = 0; e < E; ++e) {
+        const int64_t i = g + (R + e) * G;
+        float* row = s_rows + size_t(e) * (D + 1) * kNdFpsThreads + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < D; ++c) row[c * kNdFpsThreads] = i < a.n ? a.X[D * i + c] : 0.0f;
+        row[D * kNdFpsThreads] = INFINITY;
+    }
     if (g == 0) {
         a.out_idx[0] = a.start;
         if (a.out_key) a.out_key[0] = INFINITY;
     }
+    if (threadIdx.x == 0) s_stop = 0;
     int64_t w = a.start;
     for (int j = 1; j < a.n_landmarks; ++j) {
         float l[D];
@@ -495,7 +513,19 @@ __global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
                 best = pk > best ? pk : best;
             }
         }
-        for (int64_t i = g + R * G; i < a.n; i += G) {
+        for (int e = 0; e < E; ++e) {
+            const int64_t i = g + (R + e) * G;
+            if (i >= a.n) break;
+            float* row = s_rows + size_t(e) * (D + 1) * kNdFpsThreads + threadIdx.x;
+            float x[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) x[c] = row[c * kNdFpsThreads];
+            const float d = fminf(row[D * kNdFpsThreads], fps_key_nd<D>(x, l));
+            row[D * kNdFpsThreads] = d;
+            const uint64_t pk = fps_pack(d, i);
+            best = pk > best ? pk : best;
+        }
+        for (int64_t i = g + (R + E) * G; i < a.n; i += G) {
             float x[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) x[c] = a.X[D * i + c];
@@ -505,35 +535,48 @@ __global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
             const uint64_t pk = fps_pack(d, i);
             best = pk > best ? pk : best;
         }
-        best = block_max_u64(best, s_red);
+        best = warp_max_u64(best);
+        if (lane == 0) s_red[warp] = best;
+        __syncthreads();
         const int bank = j & 1;
-        if (threadIdx.x == 0) {
-            a.slots[bank * B + blockIdx.x] = best;
-            st_release_u32(a.tags + bank * B + blockIdx.x, static_cast<uint32_t>(j));
-        }
-        if (threadIdx.x == 0) s_stop = 0;
-        __syncthreads();
-        uint64_t win = 0ull;
-        for (int b = threadIdx.x; b < B; b += kNdFpsThreads) {
-            const uint32_t* tag = a.tags + bank * B + b;
-            uint32_t polls = 0;
-            while (ld_acquire_u32(tag) != static_cast<uint32_t>(j) && ++polls < a.poll_limit) {
+        const uint64_t gen = uint64_t(fps_generation(j)) << 31;
+        if (warp == 0) {
+            uint64_t v = s_red[lane];  // kNdFpsThreads / 32 == 32 warps
+            v = warp_max_u64(v);
+            if (lane == 0) st_release_u64(a.slots + bank * B + blockIdx.x, v | gen);
+            // this lane's slots b = lane, lane + 32, ...: every pending one re-read in each pass
+            uint64_t win = 0ull;
+            uint32_t pending = 0;
+#pragma unroll
+            for (int i = 0; i < kNdFpsMaxBlocks / 32; ++i)
+                if (lane + 32 * i < B) pending |= 1u << i;
+            for (uint32_t polls = 0; pending && polls < a.poll_limit; ++polls) {
+                uint64_t x[kNdFpsMaxBlocks / 32];
+#pragma unroll
+                for (int i = 0; i < kNdFpsMaxBlocks / 32; ++i)
+                    x[i] = (pending >> i) & 1u ? ld_acquire_u64(a.slots + bank * B + lane + 32 * i) : 0ull;
+#pragma unroll
+                for (int i = 0; i < kNdFpsMaxBlocks / 32; ++i)
+                    if (((pending >> i) & 1u) && (x[i] & (uint64_t(1) << 31)) == gen) {
+                        win = x[i] > win ? x[i] : win;
+                        pending &= ~(1u << i);
+                    }
             }
-            if (polls >= a.poll_limit) {
-                atomicOr(a.flags, FLAG_TIMEOUT);
-                s_stop = 1;
-            } else {
-                const uint64_t v = ld_relaxed_u64(a.slots + bank * B + b);
-                win = v > win ? v : win;
+            win = warp_max_u64(win);
+            const bool late = __any_sync(0xffffffffu, pending != 0);
+            if (lane == 0) {
+                s_win = win;
+                if (late) {
+                    atomicOr(a.flags, FLAG_TIMEOUT);
+                    s_stop = 1;
+                }
             }
         }
-        win = block_max_u64(win, s_red);
-        if (threadIdx.x == 0) s_win = win;
         __syncthreads();
-        win = s_win;
         if (s_stop) return;  // a wait gave up: the status reports it; the other blocks give up too
+        const uint64_t win = s_win;
         const float key = __uint_as_float(static_cast<uint32_t>(win >> 32));
-        w = static_cast<int64_t>(0xffffffffu - static_cast<uint32_t>(win));
+        w = static_cast<int64_t>(0x7fffffffu - (static_cast<uint32_t>(win) & 0x7fffffffu));
         if (!(key > 0.0f) || w >= a.n) {  // only copies of picked points are left
             if (g == 0) atomicOr(a.flags, FLAG_DEGENERATE);
             return;
@@ -839,6 +882,15 @@ __global__ void __launch_bounds__(kNdThreads) k_nd_resolve(NdFilt f) {
     add_stats(f, st);
 }
 
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t w = shfl_xor_u64(v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
 // Cells at Chebyshev distance exactly r from c, clipped to the table:
 // enumerated as the cells of the clipped outer box [c - r, c + r] outside the
 // clipped inner box [c - r + 1, c + r - 1], split by the first axis on which a
@@ -893,15 +945,6 @@ struct Shell {
         }
     }
 };
-
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t w = shfl_xor_u64(v, o);
-        v = w < v ? w : v;
-    }
-    return v;
-}
 
 // Second pass: one warp per item left by the first, shells r = 2, 3, ... of
 // cells around the sample's cell, 32 cells at a time, the lanes' minima merged
@@ -1017,31 +1060,47 @@ int launch_fps_nd(const float* X, int64_t n, int32_t n_l, int64_t start, int64_t
                   cudaStream_t s, Scratch& scr, uint32_t** flags_out) {
     constexpr int R = D <= 4 ? 8 : 5;  // points per thread in registers (R (D + 1) words)
     auto fn = k_fps_nd<D, R>;
+    const int sms = device_sm_count();
+    const int64_t want = ceil_div(n, int64_t(kNdFpsThreads) * R);
+    const int blocks_max =
+        static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, std::min(sms, kNdFpsMaxBlocks))));
+    // shared rows for the points past the registers, as many as one block per SM can hold
+    int dev = 0, smem_optin = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    FLOOD_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t row_bytes = size_t(D + 1) * kNdFpsThreads * sizeof(float);
+    const size_t static_bytes = 4096;  // the kernel's own shared variables, with room to spare
+    const int64_t e_max = smem_optin > int(static_bytes) ? (smem_optin - static_bytes) / row_bytes : 0;
+    const int64_t e_want = std::max<int64_t>(0, ceil_div(n, int64_t(blocks_max) * kNdFpsThreads) - R);
+    const int E = static_cast<int>(std::min(e_max, e_want));
+    const size_t smem = size_t(E) * row_bytes;
+    FLOOD_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
     int per_sm = 0;
-    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNdFpsThreads, 0));
+    FLOOD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kNdFpsThreads, smem));
     if (per_sm < 1) {
         set_error("flood_fps_nd: the kernel does not fit on an SM");
         return FLOOD_EINTERNAL;
     }
-    const int64_t want = ceil_div(n, int64_t(kNdFpsThreads) * R);
-    const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(device_sm_count()) * per_sm)));
-    uint32_t *box = nullptr, *tags = nullptr;
+    const int blocks = blocks_max;  // one per SM at most: all resident (cooperative launch)
+    uint32_t* box = nullptr;
     uint64_t* slots = nullptr;
     float* dist = nullptr;
     int rc;
-    const bool overflow = n > int64_t(blocks) * kNdFpsThreads * R;
-    if ((rc = scr.alloc(&box, 2 * kNdMaxD + 1)) || (rc = scr.alloc(&tags, 2 * blocks)) ||
-        (rc = scr.alloc(&slots, 2 * blocks)) || (rc = scr.alloc(&dist, overflow ? n : 1)))
+    const bool overflow = n > int64_t(blocks) * kNdFpsThreads * (R + E);
+    if ((rc = scr.alloc(&box, 2 * kNdMaxD + 1)) || (rc = scr.alloc(&slots, 2 * blocks)) ||
+        (rc = scr.alloc(&dist, overflow ? n : 1)))
         return rc;
     uint32_t* flags = box + 2 * kNdMaxD;
     *flags_out = flags;
-    FLOOD_CUDA(cudaMemsetAsync(tags, 0, sizeof(uint32_t) * 2 * blocks, s));
+    k_fps_nd_slots<<<static_cast<unsigned>(ceil_div(blocks, 128)), 128, 0, s>>>(slots, blocks);
     k_box_init_nd<<<1, 1, 0, s>>>(box, flags);
-    k_bbox_nd<D><<<bbox_blocks(n, device_sm_count()), kBoxThreads, 0, s>>>(X, n, box, flags);
-    NdFpsArgs a{X, n, n_l, start, out_idx, out_key, dist, slots, tags, flags, kWaitPolls};
+    k_bbox_nd<D><<<bbox_blocks(n, sms), kBoxThreads, 0, s>>>(X, n, box, flags);
+    NdFpsArgs a{X, n, n_l, start, out_idx, out_key, dist, slots, flags, kWaitPolls, E};
     void* args[] = {&a};
-    FLOOD_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(blocks), dim3(kNdFpsThreads), args, 0, s));
-    note_launch(3);
+    FLOOD_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(blocks), dim3(kNdFpsThreads), args, smem,
+                                           s));
+    note_launch(4);
     return FLOOD_OK;
 }
 

@@ -61,9 +61,10 @@ def test_fps_nd_bit_exact(d, n, n_l, start, seed):
 
 
 def test_fps_nd_points_beyond_the_register_resident_ones():
-    """2M points in R^5: more than the grid's threads keep in registers, the rest stream from memory."""
+    """3M points in R^5: more than the threads keep in registers and the blocks in shared memory;
+    the rest are read from memory at every pick (all three tiers in use)."""
     rng = np.random.default_rng(81)
-    X = rng.uniform(-1, 1, (2_000_000, 5)).astype(np.float32)
+    X = rng.uniform(-1, 1, (3_000_000, 5)).astype(np.float32)
     idx, key = _ops().fps_nd(torch.from_numpy(X).cuda(), 60, 11)
     ref_i, ref_k = oracle.fps(X, 60, 11)
     assert np.array_equal(idx.cpu().numpy(), ref_i)
