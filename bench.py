@@ -369,7 +369,7 @@ def measure_second_workload(name: str, steps: int, warmup: int, dev, flush) -> d
         ev[1].record(stream)
         grid = ops.build_grid(Xd, cell, sync=False)
         ev[2].record(stream)
-        ops.filtration(grid, Xd[idx], dcx, m, want_src=False, sync=False)
+        ops.filtration(grid, ops.gather_rows(Xd, idx, sync=False), dcx, m, want_src=False, sync=False)
         ev[3].record(stream)
         ops.check(dev)
         grid.close()
@@ -430,7 +430,7 @@ def measure_ambient_dimensions(dims, steps: int, warmup: int, dev, flush, peak_t
             ev[1].record(stream)
             grid = ops.build_grid_nd(Xd, 0.0, sync=False)
             ev[2].record(stream)
-            ops.filtration_nd(grid, Xd[idx], dcx, m, sync=False)
+            ops.filtration_nd(grid, ops.gather_rows(Xd, idx, sync=False), dcx, m, sync=False)
             ev[3].record(stream)
             ops.check(dev)
             if it >= warmup:
@@ -557,7 +557,7 @@ def main():
         grid = ops.build_grid(Xd, cell, sync=False)
         if record:
             ev[2].record(stream)
-        L = Xd[idx]
+        L = ops.gather_rows(Xd, idx, sync=False)
         vals, _ = ops.filtration(grid, L, dcx, m, want_src=False, sync=False)
         if record:
             ev[3].record(stream)
@@ -615,7 +615,7 @@ def main():
         dc = ops.DeviceComplex(cx.n_vertices, [t.to(dev, non_blocking=True) for t in simp_h],
                                [t.to(dev, non_blocking=True) for t in fac_h])
         grid = ops.build_grid(Xg, cell, sync=False)
-        vals, _ = ops.filtration(grid, Xg[idx_h.to(dev)], dc, m, want_src=False, sync=False)
+        vals, _ = ops.filtration(grid, ops.gather_rows(Xg, idx, sync=False), dc, m, want_src=False, sync=False)
         out = [v.cpu() for v in vals]
         ops.check(dev)
         grid.close()
@@ -638,7 +638,7 @@ def main():
         idx, key = ops.fps(Xd, n_l, 0)
         grid = ops.build_grid(Xd, cell)
         e[1].record(stream)
-        vals, _ = ops.filtration_given(grid, Xd[idx], dcx, w_rand, want_src=False)
+        vals, _ = ops.filtration_given(grid, ops.gather_rows(Xd, idx), dcx, w_rand, want_src=False)
         e[2].record(stream)
         e[2].synchronize()
         grid.close()

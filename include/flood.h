@@ -186,6 +186,21 @@ int flood_fps_noalloc(const float* X, int64_t n_points, int32_t n_landmarks, int
                       int64_t* out_idx, float* out_key, void* stream);
 
 /* ------------------------------------------------------------------------
+ * flood_gather_rows — the landmark rows L = X[idx] (§3: the landmarks are the
+ * FPS picks of X; the triangulation and the filtration take L).
+ *
+ *   X      device, (n_points, dim) float32 row-major
+ *   idx    device int64[n_idx], each in [0, n_points) (e.g. flood_fps's out_idx)
+ *   L      device float32 (n_idx, dim) output: L[r] = X[idx[r]] bit for bit
+ *          (idx and L may be NULL when n_idx = 0)
+ * Errors: FLOOD_EINVAL (arguments; 1 <= dim <= 8) on return; through
+ * flood_check: FLOOD_EINVAL (an index out of range; its row is not written).
+ * Asynchronous.
+ * ------------------------------------------------------------------------ */
+int flood_gather_rows(const float* X, int64_t n_points, int32_t dim, const int64_t* idx, int64_t n_idx,
+                      float* L, void* stream);
+
+/* ------------------------------------------------------------------------
  * flood_build_grid — uniform cell grid over X.
  *
  * Replaces the paper's axis-presort and masking matrix (§4.2, App. A.1) as

@@ -165,6 +165,7 @@ _SIGNATURES = {
     "flood_check": (C.c_int, [C.c_void_p]),
     "flood_persistence": (C.c_int, [P4, P4, I64x4, P4, C.c_void_p * 3, C.c_int64 * 3, P4, I64x4,
                                     C.POINTER(C.c_int64), C.c_void_p]),
+    "flood_gather_rows": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "flood_fps_nd": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
     "flood_build_grid_nd": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.POINTER(C.c_void_p),

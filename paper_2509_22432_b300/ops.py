@@ -21,7 +21,7 @@ __all__ = ["check", "fps", "fps_noalloc", "fps_stats", "fps_scratch_bytes", "fps
            "filtration_batch", "filtration_backward", "filtration_given", "filtration_given_backward",
            "complex_faces", "filtration_masked", "persistence", "diagrams_from_pairs",
            "last_filtration_stats", "FloodFunction", "flood_values", "GivenFloodFunction", "flood_values_given",
-           "fps_nd", "GridNd", "build_grid_nd", "filtration_nd", "last_filtration_nd_stats"]
+           "fps_nd", "GridNd", "build_grid_nd", "filtration_nd", "last_filtration_nd_stats", "gather_rows"]
 
 
 def _stream_ptr(device: torch.device) -> C.c_void_p:
@@ -594,3 +594,18 @@ def last_filtration_nd_stats() -> dict:
     for k in ("items", "pruned", "resolved", "exact", "fallback", "pairs", "pairs_fallback", "cells"):
         out[k] = list(getattr(st, k))[:d + 1]
     return out
+
+
+def gather_rows(X: torch.Tensor, idx: torch.Tensor, sync: bool = True) -> torch.Tensor:
+    """L = X[idx] on the device by flood_gather_rows (the landmark rows of FPS's picks)."""
+    if not isinstance(X, torch.Tensor) or not X.is_cuda or X.dtype != torch.float32 or X.dim() != 2:
+        raise ValueError("X must be a float32 CUDA tensor of shape (n, d)")
+    if not isinstance(idx, torch.Tensor) or idx.device != X.device or idx.dtype != torch.int64 or idx.dim() != 1:
+        raise ValueError("idx must be an int64 CUDA tensor of shape (n,) on X's device")
+    X, idx = X.contiguous(), idx.contiguous()
+    L = torch.empty((idx.shape[0], X.shape[1]), dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.get().flood_gather_rows(_ptr(X), X.shape[0], X.shape[1], _ptr(idx), idx.shape[0], _ptr(L),
+                                          _stream_ptr(X.device))
+    _finish(st, "flood_gather_rows", X.device, sync)
+    return L
