@@ -177,8 +177,8 @@ int flood_fps_wait_test(const float* X, int64_t n_points, int32_t n_landmarks, i
  *              flood_fps_scratch_bytes(2^20, 1) bytes, the largest need of
  *              any launch width at that size (points streamed from memory).
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture. All calls share the one array: calls whose work
+ * cudaGetSymbolAddress (with that device current). All calls share the one
+ * array: calls whose work
  * overlaps on the GPU (other streams, other threads) race and corrupt each
  * other's results, so serialise them. Synchronises `stream` before returning.
  * ------------------------------------------------------------------------ */
