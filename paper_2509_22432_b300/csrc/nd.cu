@@ -21,8 +21,9 @@
 //             its running nearest distance is <= LB (Lemma 2's argument with a
 //             live bound instead of a ball), which is the usual outcome within
 //             the sample's own cell and its 3^d - 1 neighbours, visited nearest
-//             first (or at once, through the point that settled the sample
-//             before it); the rest either finish exactly there or go to
+//             first (a lane that finishes takes the next item, so long and
+//             short searches share warps); the rest either finish exactly
+//             there or go to
 //   fallback  one warp per remaining sample: Chebyshev shells of cells around
 //             the sample, clipped to the grid, until the distance is exact or
 //             falls to max(LB, the simplex's running maximum);

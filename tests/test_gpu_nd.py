@@ -181,6 +181,29 @@ def test_filtration_nd_small_m_and_empty_dimensions():
     _assert_close(got, ref, X, "edges and triangles")
 
 
+@pytest.mark.parametrize("d,n", [(5, 7), (5, 12), (4, 9), (4, 40), (2, 4)])
+def test_filtration_nd_tiny_clouds(d, n):
+    """Every point a landmark (L = X): a handful of points, one or a few cells."""
+    rng = np.random.default_rng(100 + n + d)
+    X = rng.uniform(-1, 1, (n, d)).astype(np.float32)
+    cx = delaunay_complex(X)
+    got, _ = _gpu_values(X, X, cx, 6)
+    ref = oracle.flood_values(X, X, cx.simplices, 6).values
+    _assert_close(got, ref, X, f"tiny d={d} n={n}")
+
+
+def test_filtration_nd_large_m_and_duplicates():
+    """m = 19 (20 points per edge, §5.3) in R^4, on a cloud where every point appears three times."""
+    rng = np.random.default_rng(121)
+    base = data.swisscheese_cloud(4000, seed=122, dim=4)
+    X = np.concatenate([base, base, base])
+    L = base[oracle.fps(base, 25, 0)[0]]
+    cx = delaunay_complex(L)
+    got, _ = _gpu_values(X, L, cx, 19)
+    ref = oracle.flood_values(X, L, cx.simplices, 19, method="kdtree").values
+    _assert_close(got, ref, X, "m=19 duplicates")
+
+
 def test_filtration_nd_rejects_bad_input():
     ops = _ops()
     X, L, cx = _case(5, 5000, 20, 61)
