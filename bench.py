@@ -260,12 +260,32 @@ def warm_serving(clouds, m: int = 8):
         run_serving(clouds[:16], 2000.0, batched, m=m, device_faces=True)
 
 
-def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, device_faces: bool = False) -> dict:
+def precompute_tets(clouds, landmark_fraction: float = 0.02) -> dict:
+    """Tetrahedra of every serving cloud's landmarks (the server's own FPS picks, computed here by
+    flood_fps with the server's landmark count), keyed by the landmarks' float32 bytes: with them
+    the server's triangulation callback does no Qhull work, so runs can exclude the host Delaunay."""
+    import torch
+    from paper_2509_22432_b300 import ops
+    from paper_2509_22432_b300.serve import delaunay_tets
+    cache = {}
+    for X in clouds:
+        n = X.shape[0]
+        # the server's count: lround of the binary32 fraction times N
+        n_l = min(max(int(math.floor(float(np.float32(landmark_fraction)) * n + 0.5)), 4), n)
+        idx, _ = ops.fps(torch.from_numpy(X).cuda(), n_l, 0)
+        L = np.ascontiguousarray(X[idx.cpu().numpy()], dtype=np.float32)
+        cache[L.tobytes()] = delaunay_tets(L)
+    return cache
+
+
+def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, device_faces: bool = False,
+                tets_cache: dict | None = None) -> dict:
     """Submit the clouds at Poisson arrival times; return clouds/s and latency percentiles.
 
     batched: the continuous-batching server; otherwise the plain path, one
     cloud at a time through the same kernels (one slot, one worker, batch 1).
-    Latency = arrival -> values on the host, host Delaunay included.
+    Latency = arrival -> values on the host, host Delaunay included unless
+    tets_cache holds every cloud's tetrahedra (precompute_tets).
     device_faces: the host hands over tetrahedra only; faces are built on the device.
     """
     from paper_2509_22432_b300 import data
@@ -273,7 +293,7 @@ def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, d
     arrivals = data.poisson_arrivals(len(clouds), rate, seed=seed)
     kw = (dict(max_inflight=64, max_batch=64, gpu_workers=4, triangulation_workers=8) if batched else
           dict(max_inflight=1, max_batch=1, gpu_workers=1, triangulation_workers=1))
-    with Server(device_budget_bytes=32 << 30, device_faces=device_faces, **kw) as srv:
+    with Server(device_budget_bytes=32 << 30, device_faces=device_faces, tets_cache=tets_cache, **kw) as srv:
         t0 = time.perf_counter()
         tickets = []
         for X, t in zip(clouds, arrivals):
@@ -283,10 +303,13 @@ def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, d
             tickets.append(srv.submit(X, 0, m))
         res = [srv.result(t, timeout_ms=600_000) for t in tickets]
         st = srv.stats()
+        misses = srv.cache_misses
     lat = np.array([r["latency_ms"] for r in res if r["status"] == 0])
     return {"clouds_per_s": st["clouds_per_s"], "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "failed": int(st["failed"]), "batches": int(st["batches"]),
-            "mean_batch": float(st["mean_batch"]), "rate_per_s": rate, "clouds": len(clouds)}
+            "mean_batch": float(st["mean_batch"]), "rate_per_s": rate, "clouds": len(clouds),
+            "host_delaunay": "excluded (precomputed)" if tets_cache is not None else "included",
+            **({"delaunay_cache_misses": int(misses)} if tets_cache is not None else {})}
 
 
 def run_reference(args, wl):
@@ -509,11 +532,13 @@ def main():
         if rank == 0:
             clouds = serving_clouds(512)
             warm_serving(clouds)
+            cache = precompute_tets(clouds)
             for rate in (50, 100, 200, 500, 1000, 2000):
                 for batched in (True, False):
-                    r = run_serving(clouds, rate, batched, device_faces=True)
-                    print(json.dumps({"serving": "batched" if batched else "per-cloud", "faces": "device", **r}),
-                          flush=True)
+                    for tc in (None, cache):
+                        r = run_serving(clouds, rate, batched, device_faces=True, tets_cache=tc)
+                        print(json.dumps({"serving": "batched" if batched else "per-cloud", "faces": "device",
+                                          "device_budget_bytes": 32 << 30, **r}), flush=True)
         return
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -850,13 +875,18 @@ def main():
     if rank == 0 and not args.no_serving:
         clouds = serving_clouds(512)
         warm_serving(clouds)
+        cache = precompute_tets(clouds)
         runs = {}
         for rate in (50.0, 500.0):
             runs[f"{rate:g}"] = {"batched": run_serving(clouds, rate, True, device_faces=True),
-                                 "per_cloud": run_serving(clouds, rate, False, device_faces=True)}
+                                 "per_cloud": run_serving(clouds, rate, False, device_faces=True),
+                                 "batched_no_delaunay": run_serving(clouds, rate, True, device_faces=True,
+                                                                    tets_cache=cache)}
         line["serving"] = {"workload": "512 clouds, 2k-200k points (log-uniform), shape mix, Poisson arrivals, "
-                                       "n_L = 2% of points, m = 8, host Delaunay (Qhull) included, faces built on "
-                                       "the device in both arms",
+                                       "n_L = 2% of points, m = 8, device budget 32 GB, host Delaunay (Qhull, 8 "
+                                       "threads for the batched server) included except in batched_no_delaunay "
+                                       "(tetrahedra precomputed from the same landmarks), faces built on the "
+                                       "device in every arm",
                            "by_rate": runs,
                            "arms": "batched: continuous batching (64 slots, batches of up to 64 clouds); per_cloud: "
                                    "the same kernels one cloud at a time (one slot, batch 1)",

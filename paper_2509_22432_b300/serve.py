@@ -21,10 +21,10 @@ from . import _lib
 from ._lib import RELEASE, ServeConfig, ServeResult, ServeStats, TRIANGULATE
 from .complex import delaunay_complex
 
-__all__ = ["Server"]
+__all__ = ["Server", "delaunay_tets"]
 
 
-def _delaunay_tets(L: np.ndarray) -> np.ndarray:
+def delaunay_tets(L: np.ndarray) -> np.ndarray:
     """Tetrahedra of Del(L) (scipy/Qhull), ascending vertex ids, int32."""
     return np.ascontiguousarray(np.sort(Delaunay(np.asarray(L, np.float64)).simplices, axis=1), dtype=np.int32)
 
@@ -44,11 +44,15 @@ class Server:
     results list the rows of every dimension ("simplices"), whose order is then
     the device's, not lexicographic. device_faces=False builds the whole
     complex on the host (rows in lexicographic order).
+    tets_cache (device_faces only): tetrahedra by the landmarks' float32 bytes,
+    used instead of running Qhull when present (to time the server without
+    the host Delaunay); `cache_misses` counts the landmark sets it lacked.
     """
 
     def __init__(self, device_budget_bytes: int = 16 << 30, max_inflight: int = 64, max_batch: int = 32,
                  gpu_workers: int = 4, triangulation_workers: int = 4, landmark_fraction: float = 0.02,
-                 cell_factor: float = 0.5, triangulate=None, device_faces: bool | None = None):
+                 cell_factor: float = 0.5, triangulate=None, device_faces: bool | None = None,
+                 tets_cache: dict | None = None):
         self._lib = _lib_serve()
         if device_faces is None:
             device_faces = triangulate is None
@@ -56,6 +60,8 @@ class Server:
             raise ValueError("device_faces uses the built-in tetrahedralisation; pass no triangulate")
         self._fn = triangulate or delaunay_complex
         self._device_faces = bool(device_faces)
+        self._tets_cache = tets_cache
+        self.cache_misses = 0
         self._keep = {}
         self._next = 1
         self._lock = threading.Lock()
@@ -75,7 +81,12 @@ class Server:
             arrays = []
             o = out.contents
             if self._device_faces:
-                tets = _delaunay_tets(L)
+                tets = self._tets_cache.get(L.tobytes()) if self._tets_cache is not None else None
+                if tets is None:
+                    if self._tets_cache is not None:
+                        with self._lock:
+                            self.cache_misses += 1
+                    tets = delaunay_tets(L)
                 arrays.append(tets)
                 for k in range(3):
                     o.n_simplices[k] = 0

@@ -80,6 +80,35 @@ def test_device_faces_server_equals_one_cloud_path_per_simplex():
 
 
 @pytest.mark.gpu
+def test_precomputed_tetrahedra_give_the_same_results_without_qhull():
+    """tets_cache (the bench's no-Delaunay arm): the landmarks' tetrahedra looked up by their bytes;
+    every cloud hits the cache and its values are bit for bit those of the Qhull run."""
+    import torch
+    from paper_2509_22432_b300 import ops
+    from paper_2509_22432_b300.serve import Server, delaunay_tets
+    clouds = _clouds(6, seed=11)
+    m = 8
+    cache = {}
+    for X in clouds:
+        n_l = max(4, int(np.floor(float(np.float32(0.02)) * X.shape[0] + 0.5)))  # the server's rounding
+        idx, _ = ops.fps(torch.from_numpy(X).cuda(), n_l, 0)
+        L = np.ascontiguousarray(X[idx.cpu().numpy()], dtype=np.float32)
+        cache[L.tobytes()] = delaunay_tets(L)
+    out = []
+    for tc in (None, cache):
+        with Server(max_inflight=4, max_batch=4, gpu_workers=2, triangulation_workers=2, device_faces=True,
+                    tets_cache=tc) as srv:
+            out.append([srv.result(t, timeout_ms=120_000) for t in [srv.submit(X, 0, m) for X in clouds]])
+            if tc is not None:
+                assert srv.cache_misses == 0
+    for a, b in zip(*out):
+        assert a["status"] == 0 and b["status"] == 0
+        assert np.array_equal(a["landmarks"], b["landmarks"])
+        for k in range(4):
+            assert np.array_equal(a["values"][k].view(np.uint32), b["values"][k].view(np.uint32)), k
+
+
+@pytest.mark.gpu
 def test_failed_triangulation_fails_only_its_request():
     from paper_2509_22432_b300.serve import Server
 
