@@ -219,6 +219,18 @@ def oracle_sample_costs(X, L, cx, m, fps_iters, n_simplices, seed, index=None):
     return t_pick, t_simplex, len(draw)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo), for the CPU-baseline record."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(X, wl, workload):
     """The oracle as it stands, timed on a bounded sample of the workload's own complex.
 
@@ -236,8 +248,9 @@ def cpu_baseline(X, wl, workload):
     t_pick, t_simplex, sampled = oracle_sample_costs(X, L, cx, wl["m"], fps_iters, 1500, seed=0, index=index)
     n_simp = sum(cx.counts[1:])
     step_s = t_pick * (wl["n_l"] - 1) + t_build + t_simplex * n_simp
-    return {"value": n_simp / step_s, "unit": "simplices/s", "cores": os.cpu_count(), "kind": "oracle",
-            "estimate": True, "step_s_estimated": step_s,
+    return {"value": n_simp / step_s, "unit": "simplices/s", "cores": os.cpu_count(), "cpu_model": cpu_model(),
+            "kind": "oracle", "estimate": True, "step_s_estimated": step_s,
+            "threads": "FPS: numpy on one core; k-d tree queries: scipy cKDTree with workers=-1 (all cores)",
             "sample": f"sample of the workload itself, extrapolated to one step: {fps_iters} FPS iterations over all "
                       f"{X.shape[0]} points ({1e3 * t_pick:.1f} ms per pick, x {wl['n_l'] - 1} picks); FP64 k-d tree "
                       f"build ({t_build:.2f} s); flood values of {sampled} simplices drawn uniformly from the "
