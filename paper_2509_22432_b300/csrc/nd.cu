@@ -404,20 +404,29 @@ __global__ void __launch_bounds__(kNdThreads) k_nd_scatter(const float* X, int64
 // One block of 1024 threads per SM. Thread g of the G threads owns points
 // g, g + G, g + 2G, ...: the first R of them live in registers (coordinates
 // and current distance), the next E in the block's shared memory (one
-// coordinate plane and a distance plane per row, at most what the SM holds),
-// and any further ones are read from X at every pick with their distance in
-// `dist`. A pick: every thread folds the previous pick into its distances and
-// proposes its best; the warps' maxima meet in shared memory; warp 0 reduces
-// them, publishes the block's maximum in slot bank (j & 1) with one 64-bit
-// release store, reads every block's slot (acquire loads, all of a lane's
-// slots in flight at once, bounded polls) and reduces them to the winner,
-// which all blocks therefore agree on. Two block barriers per pick.
-// A slot word is key bits << 32 | generation << 31 | (2^31 - 1 - index): the
-// larger key wins, then the lower index; the generation bit ((j >> 1) & 1)
-// tells pick j's word from the word of pick j - 2 in the same bank, the only
-// other word the slot can hold then (a block publishes pick j + 2 only after
-// reading every block's pick j + 1, which each block publishes only after
-// reading pick j). Banks start with the generation their first pick does not use.
+// coordinate plane and a distance plane per row), and any further ones are
+// read from X at every round with their distance in `dist`.
+//
+// Rounds: every thread folds the previous round's picks into its points'
+// distances and keeps its best point (candidate word: key bits << 31 |
+// (2^31 - 1 - index): the larger key, then the lower index) and its second
+// key; each warp reduces to its best candidate and a bound on its other
+// points. Warp 0 publishes the block's two best candidates with their
+// coordinates and a bound U_b on every other point of the block (the larger
+// of its third-best warp candidate and all warps' bounds) in tagged words.
+// Warps 0..7 poll an eighth of the blocks each until every word carries the
+// round's tag and keep its eight best candidates (the ninth joins that
+// eighth's bound). Warp 0 then picks greedily: the best kept candidate
+// (always the next FPS pick: no other point beats it), then, after lowering
+// the other kept candidates' keys by it, the next best while its key stays
+// positive and strictly above the largest bound (every point not kept has a
+// key at most that bound, now and after any pick). Every block makes the
+// same picks, bit for bit those of plain FPS. Points owned by threads spread
+// over the whole cloud make the bounds low: at 1M points in R^5 a round
+// makes about 18 picks.
+// A slot word carries the round's tag r & 3 in its top bits; a block cannot
+// publish round r + 2 (same parity bank) before every block has finished
+// reading round r + 1.
 struct NdFpsArgs {
     const float* X;
     int64_t n;
@@ -426,54 +435,145 @@ struct NdFpsArgs {
     int64_t* out_idx;
     float* out_key;
     float* dist;      // distances of the points beyond the register and shared tiers
-    uint64_t* slots;  // [2][blocks]
+    uint64_t* slots;  // [2][kNdFpsMaxBlocks][kNdSlotWords]
     uint32_t* flags;
     uint32_t poll_limit;
     int32_t shared_rows;  // E
 };
 
-constexpr int kNdFpsMaxBlocks = 160;  // slots per lane of warp 0: at most 5
+constexpr int kNdFpsMaxBlocks = 160;
+constexpr int kNdPollers = 8;                                // warps 0..7 poll
+constexpr int kNdQuarter = kNdFpsMaxBlocks / kNdPollers;     // blocks per poller warp
+constexpr int kNdTop = 2;                                    // candidates a block publishes
+constexpr int kNdKeep = 8;                                   // candidates a poller keeps
+constexpr int kNdEntryWords = 8;                             // cand, up to 5 coordinates, padding
+constexpr int kNdSlotWords = kNdTop * kNdEntryWords;         // 128 bytes per block and bank
+constexpr int kNdMaxPicks = 32;
+constexpr int kNdPairs = (kNdQuarter * kNdTop + 31) / 32;    // (block, entry) pairs per poller lane
+static_assert(kNdPollers * kNdKeep == 64, "warp 0 merges two kept candidates per lane");
+constexpr uint64_t kNdCandMask = (uint64_t(1) << 62) - 1;
 
-__device__ __forceinline__ uint64_t fps_pack(float key, int64_t i) {
-    return (static_cast<uint64_t>(__float_as_uint(key)) << 32) | (0x7fffffffu - static_cast<uint32_t>(i));
+__device__ __forceinline__ uint64_t nd_cand(float key, int64_t i) {
+    return (static_cast<uint64_t>(__float_as_uint(key) & 0x7fffffffu) << 31) |
+           static_cast<uint64_t>(0x7fffffffu - static_cast<uint32_t>(i));
 }
-
-__device__ __forceinline__ uint32_t fps_generation(int j) { return static_cast<uint32_t>((j >> 1) & 1); }
-
-__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ float nd_cand_key(uint64_t c) {
+    return __uint_as_float(static_cast<uint32_t>(c >> 31) & 0x7fffffffu);
 }
-
-__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Bank 1 is first used by pick 1 (generation 0), bank 0 by pick 2 (generation 1).
-__global__ void k_fps_nd_slots(uint64_t* slots, int blocks) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < blocks) {
-        slots[b] = 0;                           // bank 0: generation 0
-        slots[blocks + b] = uint64_t(1) << 31;  // bank 1: generation 1
-    }
+__device__ __forceinline__ int64_t nd_cand_row(uint64_t c) {
+    return static_cast<int64_t>(0x7fffffffu - static_cast<uint32_t>(c & 0x7fffffffu));
 }
 
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+    const uint32_t hi = static_cast<uint32_t>(v >> 32);
+    const uint32_t mh = __reduce_max_sync(0xffffffffu, hi);
+    const uint32_t ml = __reduce_max_sync(0xffffffffu, hi == mh ? static_cast<uint32_t>(v) : 0u);
+    return (static_cast<uint64_t>(mh) << 32) | ml;
+}
+
+__device__ __forceinline__ float warp_max_key(float v) {  // values >= -1: through the order-preserving bits
+    return from_ordered(__reduce_max_sync(0xffffffffu, ordered_bits(v)));
+}
+
+// 30-bit code of a bound, rounded up (decodes to a bound again).
+__device__ __forceinline__ uint32_t nd_up30(float v) {
+    const uint32_t u = ordered_bits(v);
+    return (u > 0xfffffffcu ? 0xffffffffu : (u + 3u) & ~3u) >> 2;
+}
+__device__ __forceinline__ float nd_from30(uint32_t c) { return from_ordered(c << 2); }
+
+__device__ __forceinline__ void bar_sync_n(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Poller warp h: blocks [h kNdQuarter, (h + 1) kNdQuarter) of round r's bank,
+// until every word carries the round's tag. Its kNdKeep best candidates and
+// their coordinates go to qc / qx, its bound on every other point of those
+// blocks to *qb. Returns false if the wait gave up.
+template <int D>
+__device__ __forceinline__ bool nd_poll(const NdFpsArgs& a, int r, int h, int lane, int B, uint64_t* qc,
+                                        float (*qx)[D], float* qb) {
+    const uint64_t tag = static_cast<uint64_t>(r & 3) << 62;
+    const uint64_t* bank = a.slots + static_cast<size_t>(r & 1) * kNdFpsMaxBlocks * kNdSlotWords;
+    uint64_t c[kNdPairs];
+    uint32_t u[kNdPairs];
+    float x[kNdPairs][D];
+    bool ok = false;
+    for (uint32_t polls = 0; polls < a.poll_limit; ++polls) {
+        bool fresh = true;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t w = shfl_xor_u64(v, o);
-        v = w > v ? w : v;
+        for (int q = 0; q < kNdPairs; ++q) {
+            const int pr = lane + 32 * q, b = h * kNdQuarter + pr / kNdTop, e = pr % kNdTop;
+            c[q] = 0ull;
+            u[q] = nd_up30(-1.0f);
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[q][k] = 0.0f;
+            if (pr >= kNdQuarter * kNdTop || b >= B) continue;
+            const uint64_t* ew = bank + static_cast<size_t>(b) * kNdSlotWords + e * kNdEntryWords;
+            uint64_t w[kNdEntryWords];
+            ld_relaxed_v4_u64(ew, w[0], w[1], w[2], w[3]);
+            ld_relaxed_v4_u64(ew + 4, w[4], w[5], w[6], w[7]);
+            uint64_t stale = 0ull;
+#pragma unroll
+            for (int k = 0; k < kNdEntryWords; ++k) stale |= w[k] ^ tag;
+            fresh = fresh && (stale >> 62) == 0ull;
+            c[q] = w[0] & kNdCandMask;
+            if (e == 0) u[q] = static_cast<uint32_t>(w[1] >> 32) & 0x3fffffffu;
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[q][k] = __uint_as_float(static_cast<uint32_t>(w[1 + k]));
+        }
+        if (__all_sync(0xffffffffu, fresh)) {
+            ok = true;
+            break;
+        }
     }
-    return v;
+    uint32_t ub = 0u;
+#pragma unroll
+    for (int q = 0; q < kNdPairs; ++q) ub = max(ub, u[q]);
+    ub = __reduce_max_sync(0xffffffffu, ub);
+#pragma unroll 1
+    for (int k = 0; k <= kNdKeep; ++k) {
+        uint64_t v = 0ull;
+        int vq = 0;
+#pragma unroll
+        for (int q = 0; q < kNdPairs; ++q)
+            if (c[q] > v) {
+                v = c[q];
+                vq = q;
+            }
+        const uint64_t m = warp_max_u64(v);
+        if (k == kNdKeep) {  // the best candidate left out joins the bound
+            if (lane == 0) *qb = fmaxf(nd_from30(ub), m ? nd_cand_key(m) : -1.0f);
+            break;
+        }
+        const int owner = __ffs(__ballot_sync(0xffffffffu, v == m)) - 1;
+        if (lane == owner) {
+            qc[k] = m;
+#pragma unroll
+            for (int q = 0; q < kNdPairs; ++q)
+                if (q == vq) {
+#pragma unroll
+                    for (int kk = 0; kk < D; ++kk) qx[k][kk] = x[q][kk];
+                    c[q] = 0ull;
+                }
+        }
+    }
+    return ok;
 }
 
 template <int D, int R>
 __global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
     extern __shared__ float s_rows[];  // [E][D + 1][kNdFpsThreads]: coordinates, then distance
-    __shared__ uint64_t s_red[kNdFpsThreads / 32];
-    __shared__ uint64_t s_win;
-    __shared__ int s_stop;
+    __shared__ uint64_t s_wc[kNdFpsThreads / 32];     // each warp's best candidate ...
+    __shared__ float s_wx[kNdFpsThreads / 32][D];     // ... its coordinates
+    __shared__ float s_ws[kNdFpsThreads / 32];        // ... and the bound on the warp's other points
+    __shared__ uint64_t s_qc[kNdPollers][kNdKeep];    // kept candidates of each poller
+    __shared__ float s_qx[kNdPollers][kNdKeep][D];
+    __shared__ float s_qb[kNdPollers];
+    __shared__ int s_qok[kNdPollers];
+    __shared__ uint64_t s_pc[kNdMaxPicks];            // the round's picks: candidate words ...
+    __shared__ float s_pick[kNdMaxPicks][D];          // ... and coordinates
+    __shared__ int s_np;                              // picks of the round; <= 0: stop
     if (*a.flags) return;  // input rejected (non-finite coordinates): every block leaves at once
     const int64_t G = int64_t(gridDim.x) * kNdFpsThreads;
     const int64_t g = blockIdx.x * int64_t(kNdFpsThreads) + threadIdx.x;
@@ -498,20 +598,38 @@ __global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
         a.out_idx[0] = a.start;
         if (a.out_key) a.out_key[0] = INFINITY;
     }
-    if (threadIdx.x == 0) s_stop = 0;
-    int64_t w = a.start;
-    for (int j = 1; j < a.n_landmarks; ++j) {
-        float l[D];
+    if (a.n_landmarks <= 1) return;  // the start point is the only pick
+    if (threadIdx.x == 0) {
+        s_np = 1;  // the start point is the pick the first round folds
 #pragma unroll
-        for (int c = 0; c < D; ++c) l[c] = __ldg(a.X + D * w + c);
+        for (int c = 0; c < D; ++c) s_pick[0][c] = a.X[D * a.start + c];
+    }
+    __syncthreads();
+    int j = 1;  // picks recorded
+    for (int r = 1;; ++r) {
+        const int np = s_np;
+        // ---- fold the picks; this thread's best candidate (with coordinates) and second key
         uint64_t best = 0ull;
+        float second = -1.0f, bx[D];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int64_t i = g + r * G;
+        for (int c = 0; c < D; ++c) bx[c] = 0.0f;
+        auto consider = [&](float v, int64_t i, const float(&x)[D]) {
+            const uint64_t pk = nd_cand(v, i);
+            if (pk > best) {
+                second = fmaxf(second, best ? nd_cand_key(best) : -1.0f);
+                best = pk;
+#pragma unroll
+                for (int c = 0; c < D; ++c) bx[c] = x[c];
+            } else {
+                second = fmaxf(second, v);
+            }
+        };
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int64_t i = g + q * G;
             if (i < a.n) {
-                pd[r] = fminf(pd[r], fps_key_nd<D>(px[r], l));
-                const uint64_t pk = fps_pack(pd[r], i);
-                best = pk > best ? pk : best;
+                for (int t = 0; t < np; ++t) pd[q] = fminf(pd[q], fps_key_nd<D>(px[q], s_pick[t]));
+                consider(pd[q], i, px[q]);
             }
         }
         for (int e = 0; e < E; ++e) {
@@ -521,71 +639,136 @@ __global__ void __launch_bounds__(kNdFpsThreads, 1) k_fps_nd(NdFpsArgs a) {
             float x[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) x[c] = row[c * kNdFpsThreads];
-            const float d = fminf(row[D * kNdFpsThreads], fps_key_nd<D>(x, l));
+            float d = row[D * kNdFpsThreads];
+            for (int t = 0; t < np; ++t) d = fminf(d, fps_key_nd<D>(x, s_pick[t]));
             row[D * kNdFpsThreads] = d;
-            const uint64_t pk = fps_pack(d, i);
-            best = pk > best ? pk : best;
+            consider(d, i, x);
         }
         for (int64_t i = g + (R + E) * G; i < a.n; i += G) {
             float x[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) x[c] = a.X[D * i + c];
-            const float k = fps_key_nd<D>(x, l);
-            const float d = j == 1 ? k : fminf(a.dist[i], k);
+            float d = r == 1 ? INFINITY : a.dist[i];
+            for (int t = 0; t < np; ++t) d = fminf(d, fps_key_nd<D>(x, s_pick[t]));
             a.dist[i] = d;
-            const uint64_t pk = fps_pack(d, i);
-            best = pk > best ? pk : best;
+            consider(d, i, x);
         }
-        best = warp_max_u64(best);
-        if (lane == 0) s_red[warp] = best;
+        const uint64_t wb = warp_max_u64(best);
+        const int wo = __ffs(__ballot_sync(0xffffffffu, best == wb)) - 1;
+        const float ws = warp_max_key(lane == wo ? second : (best ? nd_cand_key(best) : -1.0f));
+        if (lane == wo) {
+            s_wc[warp] = wb;
+#pragma unroll
+            for (int c = 0; c < D; ++c) s_wx[warp][c] = bx[c];
+        }
+        if (lane == 0) s_ws[warp] = ws;
         __syncthreads();
-        const int bank = j & 1;
-        const uint64_t gen = uint64_t(fps_generation(j)) << 31;
+        // ---- warp 0: the block's two best candidates and the bound on its other points, published
         if (warp == 0) {
-            uint64_t v = s_red[lane];  // kNdFpsThreads / 32 == 32 warps
-            v = warp_max_u64(v);
-            if (lane == 0) st_release_u64(a.slots + bank * B + blockIdx.x, v | gen);
-            // this lane's slots b = lane, lane + 32, ...: every pending one re-read in each pass
-            uint64_t win = 0ull;
-            uint32_t pending = 0;
+            const uint64_t c = s_wc[lane];
+            const uint64_t m1 = warp_max_u64(c);
+            const int o1 = __ffs(__ballot_sync(0xffffffffu, c == m1)) - 1;
+            const uint64_t c2 = lane == o1 ? 0ull : c;
+            const uint64_t m2 = warp_max_u64(c2);
+            const int o2 = __ffs(__ballot_sync(0xffffffffu, c2 == m2)) - 1;
+            const uint64_t m3 = warp_max_u64(lane == o1 || lane == o2 ? 0ull : c);
+            const float ub = fmaxf(m3 ? nd_cand_key(m3) : -1.0f, warp_max_key(s_ws[lane]));
+            if (lane < kNdTop) {
+                const uint64_t tag = static_cast<uint64_t>(r & 3) << 62;
+                uint64_t* ew = a.slots + static_cast<size_t>(r & 1) * kNdFpsMaxBlocks * kNdSlotWords +
+                               static_cast<size_t>(blockIdx.x) * kNdSlotWords + lane * kNdEntryWords;
+                const int o = lane == 0 ? o1 : o2;
+                uint64_t w[kNdEntryWords];
+                w[0] = tag | (lane == 0 ? m1 : m2);
 #pragma unroll
-            for (int i = 0; i < kNdFpsMaxBlocks / 32; ++i)
-                if (lane + 32 * i < B) pending |= 1u << i;
-            for (uint32_t polls = 0; pending && polls < a.poll_limit; ++polls) {
-                uint64_t x[kNdFpsMaxBlocks / 32];
+                for (int k = 1; k < kNdEntryWords; ++k) w[k] = tag;
 #pragma unroll
-                for (int i = 0; i < kNdFpsMaxBlocks / 32; ++i)
-                    x[i] = (pending >> i) & 1u ? ld_acquire_u64(a.slots + bank * B + lane + 32 * i) : 0ull;
-#pragma unroll
-                for (int i = 0; i < kNdFpsMaxBlocks / 32; ++i)
-                    if (((pending >> i) & 1u) && (x[i] & (uint64_t(1) << 31)) == gen) {
-                        win = x[i] > win ? x[i] : win;
-                        pending &= ~(1u << i);
-                    }
+                for (int k = 0; k < D; ++k) w[1 + k] |= __float_as_uint(s_wx[o][k]);
+                if (lane == 0) w[1] |= static_cast<uint64_t>(nd_up30(ub)) << 32;
+                st_relaxed_v4_u64(ew, w[0], w[1], w[2], w[3]);
+                st_relaxed_v4_u64(ew + 4, w[4], w[5], w[6], w[7]);
             }
-            win = warp_max_u64(win);
-            const bool late = __any_sync(0xffffffffu, pending != 0);
-            if (lane == 0) {
-                s_win = win;
-                if (late) {
-                    atomicOr(a.flags, FLAG_TIMEOUT);
-                    s_stop = 1;
+        }
+        // ---- warps 0..7: poll; warp 0 merges and picks
+        if (warp < kNdPollers) {
+            bar_sync_n(1, kNdPollers * 32);  // warp 0 has published
+            const bool ok = nd_poll<D>(a, r, warp, lane, B, s_qc[warp], s_qx[warp], &s_qb[warp]);
+            if (lane == 0) s_qok[warp] = ok;
+            bar_sync_n(2, kNdPollers * 32);
+        }
+        if (warp == 0) {
+            // lane l holds kept candidates l and l + 32 (candidate e is entry e % kNdKeep of poller e / kNdKeep)
+            const int h0 = lane / kNdKeep, h1 = (lane + 32) / kNdKeep, kk = lane % kNdKeep;
+            const uint64_t me0 = s_qc[h0][kk], me1 = s_qc[h1][kk];
+            float x0[D], x1[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                x0[c] = s_qx[h0][kk][c];
+                x1[c] = s_qx[h1][kk][c];
+            }
+            float U = -1.0f;
+            bool ok = true;
+#pragma unroll
+            for (int h = 0; h < kNdPollers; ++h) {
+                U = fmaxf(U, s_qb[h]);
+                ok = ok && s_qok[h];
+            }
+            const int cap = min(a.n_landmarks - j, kNdMaxPicks);
+            const int64_t row0 = nd_cand_row(me0), row1 = nd_cand_row(me1);
+            float cur0 = nd_cand_key(me0), cur1 = nd_cand_key(me1);
+            bool live0 = me0 != 0ull, live1 = me1 != 0ull;
+            int n = 0;
+            while (n < cap) {
+                const uint64_t wa = live0 ? nd_cand(cur0, row0) : 0ull;  // non-zero for every live candidate
+                const uint64_t wq = live1 ? nd_cand(cur1, row1) : 0ull;
+                const uint64_t w = wa > wq ? wa : wq;
+                const uint64_t mw = warp_max_u64(w);
+                if (mw == 0ull) {  // nothing left: with no pick at all, the points have run out
+                    if (n == 0) {
+                        if (lane == 0) s_pc[0] = 0ull;
+                        n = 1;
+                    }
+                    break;
                 }
+                const float mk = nd_cand_key(mw);
+                if (n > 0 && !(mk > 0.0f && mk > U)) break;
+                const int o = __ffs(__ballot_sync(0xffffffffu, w == mw)) - 1;
+                const bool sec = wq == mw;  // (on lane o)
+                float qv[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) qv[c] = __shfl_sync(0xffffffffu, sec ? x1[c] : x0[c], o);
+                if (lane == o) {
+                    s_pc[n] = mw;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) s_pick[n][c] = qv[c];
+                    if (sec)
+                        live1 = false;
+                    else
+                        live0 = false;
+                }
+                ++n;
+                cur0 = fminf(cur0, fps_key_nd<D>(x0, qv));
+                cur1 = fminf(cur1, fps_key_nd<D>(x1, qv));
+            }
+            __syncwarp();
+            const uint64_t first = s_pc[0];
+            const bool degenerate = first == 0ull || !(nd_cand_key(first) > 0.0f);
+            if (lane == 0) {
+                if (!ok) atomicOr(a.flags, FLAG_TIMEOUT);
+                if (ok && degenerate && blockIdx.x == 0) atomicOr(a.flags, FLAG_DEGENERATE);
+                s_np = ok && !degenerate ? n : -1;
+            }
+            if (ok && !degenerate && blockIdx.x == 0 && lane < n) {
+                const uint64_t pc = s_pc[lane];
+                a.out_idx[j + lane] = nd_cand_row(pc);
+                if (a.out_key) a.out_key[j + lane] = nd_cand_key(pc);
             }
         }
         __syncthreads();
-        if (s_stop) return;  // a wait gave up: the status reports it; the other blocks give up too
-        const uint64_t win = s_win;
-        const float key = __uint_as_float(static_cast<uint32_t>(win >> 32));
-        w = static_cast<int64_t>(0x7fffffffu - (static_cast<uint32_t>(win) & 0x7fffffffu));
-        if (!(key > 0.0f) || w >= a.n) {  // only copies of picked points are left
-            if (g == 0) atomicOr(a.flags, FLAG_DEGENERATE);
-            return;
-        }
-        if (g == 0) {
-            a.out_idx[j] = w;
-            if (a.out_key) a.out_key[j] = key;
-        }
+        const int nn = s_np;
+        if (nn <= 0) return;  // a wait gave up, or the points ran out: the status reports it
+        j += nn;
+        if (j >= a.n_landmarks) return;
     }
 }
 
@@ -1059,7 +1242,7 @@ thread_local LastNd g_last_nd;
 template <int D>
 int launch_fps_nd(const float* X, int64_t n, int32_t n_l, int64_t start, int64_t* out_idx, float* out_key,
                   cudaStream_t s, Scratch& scr, uint32_t** flags_out) {
-    constexpr int R = D <= 4 ? 8 : 5;  // points per thread in registers (R (D + 1) words)
+    constexpr int R = D <= 2 ? 6 : (D == 3 ? 5 : (D == 4 ? 4 : 3));  // points per thread in registers
     auto fn = k_fps_nd<D, R>;
     const int sms = device_sm_count();
     const int64_t want = ceil_div(n, int64_t(kNdFpsThreads) * R);
@@ -1089,19 +1272,19 @@ int launch_fps_nd(const float* X, int64_t n, int32_t n_l, int64_t start, int64_t
     float* dist = nullptr;
     int rc;
     const bool overflow = n > int64_t(blocks) * kNdFpsThreads * (R + E);
-    if ((rc = scr.alloc(&box, 2 * kNdMaxD + 1)) || (rc = scr.alloc(&slots, 2 * blocks)) ||
+    if ((rc = scr.alloc(&box, 2 * kNdMaxD + 1)) || (rc = scr.alloc(&slots, 2 * kNdFpsMaxBlocks * kNdSlotWords)) ||
         (rc = scr.alloc(&dist, overflow ? n : 1)))
         return rc;
     uint32_t* flags = box + 2 * kNdMaxD;
     *flags_out = flags;
-    k_fps_nd_slots<<<static_cast<unsigned>(ceil_div(blocks, 128)), 128, 0, s>>>(slots, blocks);
+    FLOOD_CUDA(cudaMemsetAsync(slots, 0, sizeof(uint64_t) * 2 * kNdFpsMaxBlocks * kNdSlotWords, s));
     k_box_init_nd<<<1, 1, 0, s>>>(box, flags);
     k_bbox_nd<D><<<bbox_blocks(n, sms), kBoxThreads, 0, s>>>(X, n, box, flags);
     NdFpsArgs a{X, n, n_l, start, out_idx, out_key, dist, slots, flags, kWaitPolls, E};
     void* args[] = {&a};
     FLOOD_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(blocks), dim3(kNdFpsThreads), args, smem,
                                            s));
-    note_launch(4);
+    note_launch(3);
     return FLOOD_OK;
 }
 
