@@ -690,7 +690,7 @@ int flood_tuning_clear(void);
  * binary32 squared distance with the d squares summed left to right and
  * every subtraction, product and sum rounded on its own (no fused
  * multiply-add), so picks are bit-exact against any implementation of that
- * arithmetic.
+ * arithmetic. dim = 3 runs flood_fps (the same key and picks).
  *   X          device, (n_points, dim) float32 row-major, finite
  *   dim        2..FLOOD_ND_MAX_DIM
  *   out_idx    device int64[n_landmarks]: the picks, out_idx[0] = start

@@ -1448,6 +1448,8 @@ extern "C" int flood_fps_nd(const float* X, int64_t n_points, int32_t dim, int32
                   "0 <= start < n_points");
         return FLOOD_EINVAL;
     }
+    // three coordinates: the three-dimensional FPS (same key, same picks; its chunk skipping is faster there)
+    if (dim == 3) return flood_fps(X, n_points, n_landmarks, start, out_idx, out_key, stream_);
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
     if (int rc = pending_error(s)) return rc;
     Scratch scr(s);
