@@ -292,7 +292,7 @@ def precompute_tets(clouds, landmark_fraction: float = 0.02) -> dict:
 
 
 def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, device_faces: bool = False,
-                tets_cache: dict | None = None) -> dict:
+                tets_cache: dict | None = None, triangulation_workers: int | None = None) -> dict:
     """Submit the clouds at Poisson arrival times; return clouds/s and latency percentiles.
 
     batched: the continuous-batching server; otherwise the plain path, one
@@ -300,11 +300,16 @@ def run_serving(clouds, rate: float, batched: bool, m: int = 8, seed: int = 4, d
     Latency = arrival -> values on the host, host Delaunay included unless
     tets_cache holds every cloud's tetrahedra (precompute_tets).
     device_faces: the host hands over tetrahedra only; faces are built on the device.
+    triangulation_workers: host threads running Qhull in the batched server
+    (default: one per host core, the measured best; fewer leave the host
+    Delaunay the bottleneck at 500 clouds/s).
     """
     from paper_2509_22432_b300 import data
     from paper_2509_22432_b300.serve import Server
     arrivals = data.poisson_arrivals(len(clouds), rate, seed=seed)
-    kw = (dict(max_inflight=64, max_batch=64, gpu_workers=4, triangulation_workers=8) if batched else
+    if triangulation_workers is None:
+        triangulation_workers = os.cpu_count() or 8
+    kw = (dict(max_inflight=64, max_batch=64, gpu_workers=4, triangulation_workers=triangulation_workers) if batched else
           dict(max_inflight=1, max_batch=1, gpu_workers=1, triangulation_workers=1))
     with Server(device_budget_bytes=32 << 30, device_faces=device_faces, tets_cache=tets_cache, **kw) as srv:
         t0 = time.perf_counter()
@@ -901,7 +906,7 @@ def main():
                                  "batched_no_delaunay": run_serving(clouds, rate, True, device_faces=True,
                                                                     tets_cache=cache)}
         line["serving"] = {"workload": "512 clouds, 2k-200k points (log-uniform), shape mix, Poisson arrivals, "
-                                       "n_L = 2% of points, m = 8, device budget 32 GB, host Delaunay (Qhull, 8 "
+                                       f"n_L = 2% of points, m = 8, device budget 32 GB, host Delaunay (Qhull, {os.cpu_count()} "
                                        "threads for the batched server) included except in batched_no_delaunay "
                                        "(tetrahedra precomputed from the same landmarks), faces built on the "
                                        "device in every arm",

@@ -10,6 +10,7 @@ triangulation callback and marshals results.
 from __future__ import annotations
 
 import ctypes as C
+import os
 import threading
 
 import numpy as np
@@ -38,6 +39,8 @@ class Server:
 
     triangulate(L) -> SimplexLists (default: scipy Delaunay of the landmarks).
     max_batch = 1 gives the plain one-cloud-at-a-time path.
+    triangulation_workers: host threads running the triangulation callback
+    (default: one per host core).
     device_faces (default when no triangulate is given): the callback hands
     over the tetrahedra of the scipy Delaunay triangulation only, and the
     library builds the triangles, edges and facet incidence on the device;
@@ -50,10 +53,12 @@ class Server:
     """
 
     def __init__(self, device_budget_bytes: int = 16 << 30, max_inflight: int = 64, max_batch: int = 32,
-                 gpu_workers: int = 4, triangulation_workers: int = 4, landmark_fraction: float = 0.02,
+                 gpu_workers: int = 4, triangulation_workers: int | None = None, landmark_fraction: float = 0.02,
                  cell_factor: float = 0.5, triangulate=None, device_faces: bool | None = None,
                  tets_cache: dict | None = None):
         self._lib = _lib_serve()
+        if triangulation_workers is None:
+            triangulation_workers = os.cpu_count() or 4
         if device_faces is None:
             device_faces = triangulate is None
         if device_faces and triangulate is not None:
