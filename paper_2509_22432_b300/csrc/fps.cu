@@ -403,6 +403,94 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
     }
 }
 
+// The picks of one round without a dependent chain per pick (X0; lane l
+// holds kept entry l: minimum cur, row, coordinates; bound U >= 0 on every
+// other point). Let S be the live entries with minimum above U, ranked by
+// candidate word. Were no pick to lower another entry, the picks would be S
+// in rank order. In general, going down the ranks, an entry whose minimum no
+// earlier pick lowers is the best entry left (the entries below it have
+// smaller words, the lowered and unranked ones minima <= U), so it is the
+// next pick; an entry that an earlier pick lowers to U or below can no longer
+// be picked this round (a pick needs a minimum above U) and is passed over.
+// The picks are therefore the greedy independent set of the relation "lowers"
+// in rank order (found in a few ballot rounds: a chain is mostly a chunk's
+// best entry lowering its other entries), up to the first entry that a pick
+// lowers but leaves above U, where this rule stops deciding. Lane-indexed
+// masks over S: above (entries ranked higher), lowers (those whose key to
+// this entry is below its minimum), drops (those whose key is <= U).
+// Returns the picks made (written to s.pick / s.pxyz in order, their lanes
+// no longer live); more is set when the greedy loop must continue, with cur
+// already lowered by those picks. With S empty it makes none and leaves the
+// unconditional first pick to the loop.
+__device__ __forceinline__ int rank_picks(FpsShared& s, int lane, uint32_t row, float mx, float my, float mz,
+                                          float bound, int cap, float& cur, bool& live, bool& more) {
+    const float c = cur;
+    const uint64_t w = pack_cand(c, row);
+    const uint32_t S = __ballot_sync(0xffffffffu, live && c > bound);
+    more = true;
+    if (S == 0u) return 0;
+    uint32_t above = 0u, lowers = 0u, drops = 0u;
+    for (uint32_t m = S; m;) {  // four entries per pass, shuffles first, no branch
+        int i[4];
+        i[0] = __ffs(m) - 1;
+        m &= m - 1;
+#pragma unroll
+        for (int t = 1; t < 4; ++t) {
+            i[t] = m ? __ffs(m) - 1 : i[0];
+            m &= m - 1;
+        }
+        uint64_t wi[4];
+        float xi[4], yi[4], zi[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            wi[t] = __shfl_sync(0xffffffffu, w, i[t]);
+            xi[t] = __shfl_sync(0xffffffffu, mx, i[t]);
+            yi[t] = __shfl_sync(0xffffffffu, my, i[t]);
+            zi[t] = __shfl_sync(0xffffffffu, mz, i[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float d = fps_key(mx, my, mz, xi[t], yi[t], zi[t]);
+            const uint32_t bit = wi[t] > w ? 1u << i[t] : 0u;
+            above |= bit;
+            lowers |= d < c ? bit : 0u;
+            drops |= d > bound ? 0u : bit;
+        }
+    }
+    // decided picked (P) / passed over (N): an entry is picked once every
+    // entry that lowers it is passed over, passed over once one of them is
+    // picked; the highest undecided entry is decided in every round
+    uint32_t P = 0u, N = 0u;
+    for (uint32_t und = S; und; und = S & ~(P | N)) {
+        const bool mine = (und >> lane) & 1u;
+        const uint32_t p = __ballot_sync(0xffffffffu, mine && (lowers & ~N) == 0u);
+        const uint32_t q = __ballot_sync(0xffffffffu, mine && (lowers & P) != 0u);
+        P |= p;
+        N |= q;
+    }
+    // lowered by a pick but still above U: the rule stops at the first of them
+    const uint32_t stop = __ballot_sync(0xffffffffu, ((N >> lane) & 1u) && (drops & P) == 0u);
+    const int pos = __popc(P & above);
+    const bool take = ((P >> lane) & 1u) && (stop & above) == 0u && pos < cap;
+    const uint32_t T = __ballot_sync(0xffffffffu, take);
+    const int np = __popc(T);
+    more = stop != 0u && np < cap;
+    if (take) {
+        s.pick[pos] = w;
+        s.pxyz[pos] = make_float4(mx, my, mz, 0.0f);
+        live = false;
+    }
+    if (more) {
+        for (uint32_t t = T; t; t &= t - 1) {
+            const int i = __ffs(t) - 1;
+            const float xi = __shfl_sync(0xffffffffu, mx, i), yi = __shfl_sync(0xffffffffu, my, i),
+                        zi = __shfl_sync(0xffffffffu, mz, i);
+            cur = fminf(cur, fps_key(mx, my, mz, xi, yi, zi));
+        }
+    }
+    return np;
+}
+
 // X0, one round: block reduction, publication, its quarter of the polling,
 // the merge with the other quarters, and the picks.
 __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, int r, int picks_left, int lane) {
@@ -435,12 +523,15 @@ __device__ __forceinline__ void exchange_step(const FpsArgs& a, FpsShared& s, in
     // the bound (the first one unconditionally); each pick lowers the others.
     // The best is the largest candidate word (minimum, then lowest row: rows
     // are distinct), found with one 64-bit warp maximum; its lane by a ballot.
+    // rank_picks makes the picks of the usual case in parallel; the loop
+    // below continues where it cannot decide.
     const int cap = min(picks_left, kMaxPicks);
     const uint32_t row = cand_row(me);
     float cur = cand_key(me);
     bool live = me != 0ull;
-    int np = 0;
-    while (np < cap) {
+    bool more;
+    int np = rank_picks(s, lane, row, mx, my, mz, bound, cap, cur, live, more);
+    while (more && np < cap) {
         const uint64_t w = live ? pack_cand(cur, row) : 0ull;  // non-zero for every live entry
         const uint64_t mw = warp_max_u64(w);
         if (mw == 0ull) {  // no entry left: the round ends (with none at all, an empty pick: degenerate)
