@@ -242,6 +242,8 @@ struct FpsShared {
     float qbound[kPollers];     // each quarter's bound on everything else
     int qstop[kPollers];
     int top[kKeep];             // entry indices of the block's best entries (block_top)
+    uint64_t sc[kPollers][32];  // a quarter's entries above its bound, compacted (poll_quarter)
+    float sx[kPollers][32], sy[kPollers][32], sz[kPollers][32];
 };
 
 __device__ __forceinline__ void shared_init(FpsShared& s) {
@@ -367,6 +369,76 @@ __device__ __forceinline__ void poll_quarter(const FpsArgs& a, FpsShared& s, int
         czb[l] = static_cast<uint32_t>(w3[l]);
     }
     u30 = __reduce_max_sync(0xffffffffu, u30);
+    // Usually few entries lie above the quarter's largest block bound T: keep
+    // the best kKeep of those, ranked in parallel, with the quarter's bound T
+    // (or the best entry left out, if above T). That is what the extraction
+    // below gives: every entry left out is <= that bound, and with at most
+    // kKeep entries above T the kept ones <= T could never be picked but the
+    // first of the round, which is the best one and kept here too.
+    {
+        const float T = bound_from30(u30);
+        int n_above = 0;
+#pragma unroll
+        for (int l = 0; l < kPollLoads; ++l) n_above += __popc(__ballot_sync(0xffffffffu, cand_key(c[l]) > T));
+        if (n_above >= 1 && n_above <= kKeep) {
+            const uint32_t lt = (1u << lane) - 1u;
+            int pos = 0;
+#pragma unroll
+            for (int l = 0; l < kPollLoads; ++l) {
+                const bool above = cand_key(c[l]) > T;
+                const uint32_t bl = __ballot_sync(0xffffffffu, above);
+                if (above) {
+                    const int k = pos + __popc(bl & lt);
+                    s.qc[h][k] = c[l];
+                    s.qx[h][k] = __uint_as_float(cxb[l]);
+                    s.qy[h][k] = __uint_as_float(cyb[l]);
+                    s.qz[h][k] = __uint_as_float(czb[l]);
+                }
+                pos += __popc(bl);
+            }
+            if (lane >= n_above && lane < kKeep) s.qc[h][lane] = 0ull;
+            if (lane == 0) {
+                s.qbound[h] = T;
+                s.qstop[h] = stop;
+            }
+            return;
+        }
+        if (n_above > kKeep && n_above <= 32) {
+            const uint32_t lt = (1u << lane) - 1u;
+            int pos = 0;
+#pragma unroll
+            for (int l = 0; l < kPollLoads; ++l) {
+                const bool above = cand_key(c[l]) > T;
+                const uint32_t bl = __ballot_sync(0xffffffffu, above);
+                if (above) {
+                    const int k = pos + __popc(bl & lt);
+                    s.sc[h][k] = c[l];
+                    s.sx[h][k] = __uint_as_float(cxb[l]);
+                    s.sy[h][k] = __uint_as_float(cyb[l]);
+                    s.sz[h][k] = __uint_as_float(czb[l]);
+                }
+                pos += __popc(bl);
+            }
+            __syncwarp();
+            // lane j < n_above ranks entry j among them (words are distinct)
+            const uint64_t mine = lane < n_above ? s.sc[h][lane] : 0ull;
+            int rank = 0;
+#pragma unroll 4
+            for (int i = 0; i < n_above; ++i) rank += s.sc[h][i] > mine ? 1 : 0;
+            if (lane < n_above) {
+                if (rank < kKeep) {
+                    s.qc[h][rank] = mine;
+                    s.qx[h][rank] = s.sx[h][lane];
+                    s.qy[h][rank] = s.sy[h][lane];
+                    s.qz[h][rank] = s.sz[h][lane];
+                } else if (rank == kKeep) {
+                    s.qbound[h] = fmaxf(T, cand_key(mine));
+                    s.qstop[h] = stop;
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int k = 0; k <= kKeep; ++k) {
         uint64_t v = 0ull;
