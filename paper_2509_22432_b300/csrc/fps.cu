@@ -243,6 +243,7 @@ struct FpsShared {
     int qstop[kPollers];
     int top[kKeep];             // entry indices of the block's best entries (block_top)
     uint64_t sc[kPollers][32];  // a quarter's entries above its bound, compacted (poll_quarter)
+    uint4 ranked[32][2];        // the ranked entries of a round: (word, lane), (x, y, z) (rank_picks)
     float sx[kPollers][32], sy[kPollers][32], sz[kPollers][32];
 };
 
@@ -501,29 +502,29 @@ __device__ __forceinline__ int rank_picks(FpsShared& s, int lane, uint32_t row, 
     const uint32_t S = __ballot_sync(0xffffffffu, live && c > bound);
     more = true;
     if (S == 0u) return 0;
+    // the ranked entries, compacted: four per pass come with two broadcast loads each
+    const int nS = __popc(S);
+    if (live && c > bound) {
+        const int k = __popc(S & ((1u << lane) - 1u));
+        s.ranked[k][0] = make_uint4(static_cast<uint32_t>(w), static_cast<uint32_t>(w >> 32), lane, 0u);
+        s.ranked[k][1] = make_uint4(__float_as_uint(mx), __float_as_uint(my), __float_as_uint(mz), 0u);
+    }
+    __syncwarp();
     uint32_t above = 0u, lowers = 0u, drops = 0u;
-    for (uint32_t m = S; m;) {  // four entries per pass, shuffles first, no branch
-        int i[4];
-        i[0] = __ffs(m) - 1;
-        m &= m - 1;
-#pragma unroll
-        for (int t = 1; t < 4; ++t) {
-            i[t] = m ? __ffs(m) - 1 : i[0];
-            m &= m - 1;
-        }
-        uint64_t wi[4];
-        float xi[4], yi[4], zi[4];
+    for (int k0 = 0; k0 < nS; k0 += 4) {
+        uint4 e[4], q[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            wi[t] = __shfl_sync(0xffffffffu, w, i[t]);
-            xi[t] = __shfl_sync(0xffffffffu, mx, i[t]);
-            yi[t] = __shfl_sync(0xffffffffu, my, i[t]);
-            zi[t] = __shfl_sync(0xffffffffu, mz, i[t]);
+            const int k = min(k0 + t, nS - 1);  // a repeated entry sets the same bits again
+            e[t] = s.ranked[k][0];
+            q[t] = s.ranked[k][1];
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const float d = fps_key(mx, my, mz, xi[t], yi[t], zi[t]);
-            const uint32_t bit = wi[t] > w ? 1u << i[t] : 0u;
+            const uint64_t wi = (static_cast<uint64_t>(e[t].y) << 32) | e[t].x;
+            const float d = fps_key(mx, my, mz, __uint_as_float(q[t].x), __uint_as_float(q[t].y),
+                                    __uint_as_float(q[t].z));
+            const uint32_t bit = wi > w ? 1u << e[t].z : 0u;
             above |= bit;
             lowers |= d < c ? bit : 0u;
             drops |= d > bound ? 0u : bit;
