@@ -238,48 +238,72 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
         members &= vb[j] == 0.0f;
     }
     int n_active = 0;
-    for (int s = lane; s < a.I; s += 32) {
-        float px, py, pz;
-        if (a.w) {
-            const float* lam = a.w + (w * a.I + s) * (k + 1);
-            bool fin = true;
-            for (int j = 1; j <= k; ++j) fin &= isfinite(lam[j]);
-            if (!fin) {
-                if (!SCATTER) atomicOr(&a.ctl->flags, FLAG_NONFINITE);
-                continue;
+    // the whole warp runs every pass (its lanes' samples share buckets, so one
+    // atomic per bucket and pass serves all of them)
+    for (int s0 = 0; s0 < a.I; s0 += 32) {
+        const int s = s0 + lane;
+        bool ok = s < a.I;
+        float x = 0.0f, y = 0.0f, z = 0.0f, u = 0.0f;
+        if (ok) {
+            float px, py, pz;
+            if (a.w) {
+                const float* lam = a.w + (w * a.I + s) * (k + 1);
+                bool fin = true;
+                for (int j = 1; j <= k; ++j) fin &= isfinite(lam[j]);
+                if (!fin) {
+                    if (!SCATTER) atomicOr(&a.ctl->flags, FLAG_NONFINITE);
+                    ok = false;
+                }
+                sample_offset_lambda(S, lam, k, px, py, pz);
+            } else {
+                sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
             }
-            sample_offset_lambda(S, lam, k, px, py, pz);
-        } else {
-            sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
+            if (ok) {
+                if (members) {
+                    const float u2 = vertex_bound_sq(S, k, px, py, pz);
+                    ok = __fsqrt_rn(u2) > lb;  // else it cannot exceed the facet maximum
+                    u = __fsqrt_ru(u2);
+                } else {
+                    u = vertex_bound_general(S, k, px, py, pz, vb);
+                    ok = u > lb;
+                }
+            }
+            if (ok) {
+                ++n_active;
+                x = __fadd_rn(S.v0[0], px);
+                y = __fadd_rn(S.v0[1], py);
+                z = __fadd_rn(S.v0[2], pz);
+            }
         }
-        float u;
-        if (members) {
-            const float u2 = vertex_bound_sq(S, k, px, py, pz);
-            if (!(__fsqrt_rn(u2) > lb)) continue;  // cannot exceed the facet maximum
-            u = __fsqrt_ru(u2);
-        } else {
-            u = vertex_bound_general(S, k, px, py, pz, vb);
-            if (!(u > lb)) continue;
+        int64_t b = 0;
+        if (ok) {
+            b = sample_key(a.geo->lat, x, y, z);
+            if (FLOOD_OOB(b, a.n_buckets, &a.ctl->flags)) ok = false;
         }
-        ++n_active;
-        const float x = __fadd_rn(S.v0[0], px), y = __fadd_rn(S.v0[1], py), z = __fadd_rn(S.v0[2], pz);
-        const int64_t b = sample_key(a.geo->lat, x, y, z);
-        if (FLOOD_OOB(b, a.n_buckets, &a.ctl->flags)) continue;
+        // lanes of one bucket: the first of them takes the atomic for all
+        const uint32_t peers = __match_any_sync(0xffffffffu, ok ? static_cast<uint64_t>(b) : ~static_cast<uint64_t>(lane));
+        const int leader = __ffs(peers) - 1;
         if (!SCATTER) {
-            atomicAdd(&a.bucket_count[b], 1);
+            if (ok && lane == leader) atomicAdd(&a.bucket_count[b], __popc(peers));
         } else {
-            const int32_t pos = a.bucket_start[b] + atomicAdd(&a.bucket_fill[b], 1);
-            if (FLOOD_OOB(pos, a.rec_cap, &a.ctl->flags)) continue;
-            SampleRec r;
-            r.x = x;
-            r.y = y;
-            r.z = z;
-            r.lb = lb;
-            r.sigma = static_cast<int32_t>(w);
-            r.s = s;
-            r.u = u;
-            r.pad = 0;
-            a.recs[pos] = r;
+            int32_t base = 0;
+            if (ok && lane == leader) base = atomicAdd(&a.bucket_fill[b], __popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (ok) {
+                const int32_t pos = a.bucket_start[b] + base + __popc(peers & ((1u << lane) - 1u));
+                if (!FLOOD_OOB(pos, a.rec_cap, &a.ctl->flags)) {
+                    SampleRec r;
+                    r.x = x;
+                    r.y = y;
+                    r.z = z;
+                    r.lb = lb;
+                    r.sigma = static_cast<int32_t>(w);
+                    r.s = s;
+                    r.u = u;
+                    r.pad = 0;
+                    a.recs[pos] = r;
+                }
+            }
         }
     }
     if (!SCATTER) {
@@ -433,20 +457,36 @@ __global__ void __launch_bounds__(kCubeTile) k_cube_scan(const int32_t* count, i
 // start first and the short ones fill in behind them.
 constexpr int kClasses = 64;
 
-__device__ __forceinline__ int group_class(const DimArgs& a, int2 gb) {
-    const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
-    const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
-    float R = 0.0f;
-    for (int32_t i = s_begin; i < s_end; ++i)
-        if (!FLOOD_OOB(i, a.rec_cap, &a.ctl->flags)) R = fmaxf(R, a.recs[i].u);
-    const int c = static_cast<int>(ceilf(R / a.geo->shell_h));
-    return kClasses - 1 - min(max(c, 0), kClasses - 1);  // heavier -> smaller class
-}
-
-__global__ void k_group_class_count(DimArgs a, const int32_t* n_groups, int32_t* class_count) {
-    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= *n_groups) return;
-    atomicAdd(&class_count[group_class(a, a.groups[j])], 1);
+// Class of group j from the largest vertex bound of its samples (one warp
+// per group, grid-stride), stored in gcls; counts per class through a block
+// histogram.
+__global__ void __launch_bounds__(256) k_group_class_count(DimArgs a, const int32_t* n_groups, int32_t* class_count,
+                                                            int32_t* gcls) {
+    __shared__ int32_t s_hist[kClasses];
+    for (int t = threadIdx.x; t < kClasses; t += blockDim.x) s_hist[t] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int32_t ng = *n_groups;
+    const int32_t nw = static_cast<int32_t>(gridDim.x * (blockDim.x >> 5));
+    for (int32_t j = static_cast<int32_t>((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < ng; j += nw) {
+        const int2 gb = a.groups[j];
+        const int32_t s_begin = a.bucket_start[int64_t(gb.x) * kFine] + gb.y * kGroup;
+        const int32_t s_end = min(s_begin + kGroup, a.bucket_start[int64_t(gb.x + 1) * kFine]);
+        float R = 0.0f;
+        for (int32_t i = s_begin + lane; i < s_end; i += 32)
+            if (!FLOOD_OOB(i, a.rec_cap, &a.ctl->flags)) R = fmaxf(R, a.recs[i].u);
+        // non-negative floats order like their bit patterns
+        R = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(R)));
+        const int c = static_cast<int>(ceilf(R / a.geo->shell_h));
+        const int cls = kClasses - 1 - min(max(c, 0), kClasses - 1);  // heavier -> smaller class
+        if (lane == 0) {
+            gcls[j] = cls;
+            atomicAdd(&s_hist[cls], 1);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kClasses; t += blockDim.x)
+        if (s_hist[t]) atomicAdd(&class_count[t], s_hist[t]);
 }
 
 // Every block takes the exclusive scan of the kClasses counts itself (block 0
@@ -454,7 +494,7 @@ __global__ void k_group_class_count(DimArgs a, const int32_t* n_groups, int32_t*
 // places its groups.
 __global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const int32_t* class_count,
                                       int32_t* class_start, int32_t* class_fill, int2* sorted,
-                                      int32_t* groups_out) {
+                                      int32_t* groups_out, const int32_t* gcls) {
     static_assert(kClasses == 64, "two lanes' worth of classes per lane of one warp");
     __shared__ int32_t s_start[kClasses + 1];
     if (blockIdx.x == 0 && threadIdx.x == 32) *groups_out = *n_groups;  // work items of this job (statistics)
@@ -479,11 +519,17 @@ __global__ void k_group_class_scatter(DimArgs a, const int32_t* n_groups, const 
     }
     __syncthreads();
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= *n_groups) return;
-    const int2 gb = a.groups[j];
-    const int c = group_class(a, gb);
-    const int32_t at = s_start[c] + atomicAdd(&class_fill[c], 1);
-    if (!FLOOD_OOB(at, a.groups_cap, &a.ctl->flags)) sorted[at] = gb;
+    const bool ok = j < *n_groups;
+    const int c = ok ? gcls[j] : -1 - static_cast<int>(threadIdx.x & 31);
+    // threads of one class in this warp: the first takes the atomic for all
+    const uint32_t peers = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
+    int32_t base = 0;
+    if (ok && lane == leader) base = atomicAdd(&class_fill[c], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!ok) return;
+    const int32_t at = s_start[c] + base + __popc(peers & ((1u << lane) - 1u));
+    if (!FLOOD_OOB(at, a.groups_cap, &a.ctl->flags)) sorted[at] = a.groups[j];
 }
 
 // ---------------------------------------------------------------- shell streaming
@@ -1580,6 +1626,7 @@ struct JobState {
     int32_t *bstart, *goff;
     int32_t* tile_sums;  // per tile of kCubeTile cubes: samples, then groups
     int2 *groups, *groups_sorted;
+    int32_t* gcls;  // class of each group (cube order)
     SampleRec* recs;
     int heavy_shells;  // groups with at least this many shells go to the CTA kernel
 };
@@ -1704,6 +1751,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
         if ((rc = scr.alloc(&J.bstart, J.n_buckets + 1)) || (rc = scr.alloc(&J.goff, J.n_coarse + 1)) ||
             (rc = scr.alloc(&J.tile_sums, 2 * ceil_div(J.n_coarse, kCubeTile))) ||
             (rc = scr.alloc(&J.groups, J.max_groups)) || (rc = scr.alloc(&J.groups_sorted, J.max_groups)) ||
+            (rc = scr.alloc(&J.gcls, J.max_groups)) ||
             (rc = scr.alloc(&J.recs, J.max_samples)))
             return rc;
         // bucket counts and fills, class table and per-simplex maxima of every
@@ -1799,10 +1847,11 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             const int32_t* n_groups = J.goff + J.n_coarse;
             // cls: counts [0, kClasses), fill [kClasses, 2 kClasses), starts [2 kClasses, 3 kClasses + 1)
             const unsigned gbk = static_cast<unsigned>(ceil_div(J.max_groups, 256));
+            const unsigned gwk = static_cast<unsigned>(std::min<int64_t>(ceil_div(J.max_groups, 8), 148 * 8));
             int32_t* cls = J.cls[k];
-            k_group_class_count<<<gbk, 256, 0, s>>>(a, n_groups, cls);
+            k_group_class_count<<<gwk, 256, 0, s>>>(a, n_groups, cls, J.gcls);
             k_group_class_scatter<<<gbk, 256, 0, s>>>(a, n_groups, cls, cls + 2 * kClasses, cls + kClasses,
-                                                      J.groups_sorted, d_counts + job_of_entry[e] * 4 + k);
+                                                      J.groups_sorted, d_counts + job_of_entry[e] * 4 + k, J.gcls);
             note_launch(6);
             FLOOD_CUDA(cudaGetLastError());
         }
