@@ -111,6 +111,7 @@ struct DimArgs {
     const float* val_lower;  // final values of dimension k-1
     int64_t n_lower;
     const uint8_t* comp;     // grid samples: interior compositions (I, k+1), or
+    const float* lam;        // grid samples: their barycentric coordinates fl(c_j / m) (I, k+1)
     const float* w;          // given samples: barycentric coordinates (n, I, k+1)
     const float* L;
     const float* vbound;     // per landmark: d(v, X) rounded up, 0 for a point of X
@@ -203,6 +204,23 @@ __device__ __forceinline__ int64_t sample_key(const Lattice& L, float x, float y
     return coarse * kFine + fine;
 }
 
+// Largest binary32 q with sqrt_rn(q) <= lb, for a facet maximum lb >= 0:
+// since sqrt_rn is monotone, sqrt_rn(u2) > lb exactly when u2 > q. fl(lb^2)
+// is within a few units in the last place of it; should the search not settle
+// (it always does), 0 keeps every sample, which only costs time.
+__device__ __forceinline__ float sqrt_le_bound(float lb) {
+    if (!(lb > 0.0f) || !(lb < INFINITY)) return 0.0f;
+    float q = __fmul_rn(lb, lb);
+    for (int i = 0; i < 16 && __fsqrt_rn(q) > lb; ++i) q = __uint_as_float(__float_as_uint(q) - 1u);
+    if (__fsqrt_rn(q) > lb) return 0.0f;
+    for (int i = 0; i < 16; ++i) {
+        const float nq = __uint_as_float(__float_as_uint(q) + 1u);
+        if (__fsqrt_rn(nq) > lb) return q;
+        q = nq;
+    }
+    return 0.0f;
+}
+
 // Pass 1 (SCATTER = false) counts active samples per bucket; pass 2 writes
 // them. Both passes evaluate exactly the same arithmetic.
 template <bool SCATTER>
@@ -237,73 +255,51 @@ __global__ void __launch_bounds__(256) k_samples(DimArgs a) {
         vb[j] = a.vbound[ids[j]];
         members &= vb[j] == 0.0f;
     }
+    // sqrt_rn(u2) > lb exactly when u2 > lbq (one comparison per sample)
+    const float lbq = sqrt_le_bound(lb);
     int n_active = 0;
-    // the whole warp runs every pass (its lanes' samples share buckets, so one
-    // atomic per bucket and pass serves all of them)
-    for (int s0 = 0; s0 < a.I; s0 += 32) {
-        const int s = s0 + lane;
-        bool ok = s < a.I;
-        float x = 0.0f, y = 0.0f, z = 0.0f, u = 0.0f;
-        if (ok) {
-            float px, py, pz;
-            if (a.w) {
-                const float* lam = a.w + (w * a.I + s) * (k + 1);
-                bool fin = true;
-                for (int j = 1; j <= k; ++j) fin &= isfinite(lam[j]);
-                if (!fin) {
-                    if (!SCATTER) atomicOr(&a.ctl->flags, FLAG_NONFINITE);
-                    ok = false;
-                }
-                sample_offset_lambda(S, lam, k, px, py, pz);
-            } else {
-                sample_offset(S, a.comp + s * (k + 1), k, a.m, px, py, pz);
+    for (int s = lane; s < a.I; s += 32) {
+        float px, py, pz;
+        if (a.w) {
+            const float* lam = a.w + (w * a.I + s) * (k + 1);
+            bool fin = true;
+            for (int j = 1; j <= k; ++j) fin &= isfinite(lam[j]);
+            if (!fin) {
+                if (!SCATTER) atomicOr(&a.ctl->flags, FLAG_NONFINITE);
+                continue;
             }
-            if (ok) {
-                if (members) {
-                    const float u2 = vertex_bound_sq(S, k, px, py, pz);
-                    ok = __fsqrt_rn(u2) > lb;  // else it cannot exceed the facet maximum
-                    u = __fsqrt_ru(u2);
-                } else {
-                    u = vertex_bound_general(S, k, px, py, pz, vb);
-                    ok = u > lb;
-                }
-            }
-            if (ok) {
-                ++n_active;
-                x = __fadd_rn(S.v0[0], px);
-                y = __fadd_rn(S.v0[1], py);
-                z = __fadd_rn(S.v0[2], pz);
-            }
-        }
-        int64_t b = 0;
-        if (ok) {
-            b = sample_key(a.geo->lat, x, y, z);
-            if (FLOOD_OOB(b, a.n_buckets, &a.ctl->flags)) ok = false;
-        }
-        // lanes of one bucket: the first of them takes the atomic for all
-        const uint32_t peers = __match_any_sync(0xffffffffu, ok ? static_cast<uint64_t>(b) : ~static_cast<uint64_t>(lane));
-        const int leader = __ffs(peers) - 1;
-        if (!SCATTER) {
-            if (ok && lane == leader) atomicAdd(&a.bucket_count[b], __popc(peers));
+            sample_offset_lambda(S, lam, k, px, py, pz);
         } else {
-            int32_t base = 0;
-            if (ok && lane == leader) base = atomicAdd(&a.bucket_fill[b], __popc(peers));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (ok) {
-                const int32_t pos = a.bucket_start[b] + base + __popc(peers & ((1u << lane) - 1u));
-                if (!FLOOD_OOB(pos, a.rec_cap, &a.ctl->flags)) {
-                    SampleRec r;
-                    r.x = x;
-                    r.y = y;
-                    r.z = z;
-                    r.lb = lb;
-                    r.sigma = static_cast<int32_t>(w);
-                    r.s = s;
-                    r.u = u;
-                    r.pad = 0;
-                    a.recs[pos] = r;
-                }
-            }
+            sample_offset_lambda(S, a.lam + s * (k + 1), k, px, py, pz);
+        }
+        float u;
+        if (members) {
+            const float u2 = vertex_bound_sq(S, k, px, py, pz);
+            if (!(u2 > lbq)) continue;  // cannot exceed the facet maximum
+            u = __fsqrt_ru(u2);
+        } else {
+            u = vertex_bound_general(S, k, px, py, pz, vb);
+            if (!(u > lb)) continue;
+        }
+        ++n_active;
+        const float x = __fadd_rn(S.v0[0], px), y = __fadd_rn(S.v0[1], py), z = __fadd_rn(S.v0[2], pz);
+        const int64_t b = sample_key(a.geo->lat, x, y, z);
+        if (FLOOD_OOB(b, a.n_buckets, &a.ctl->flags)) continue;
+        if (!SCATTER) {
+            atomicAdd(&a.bucket_count[b], 1);
+        } else {
+            const int32_t pos = a.bucket_start[b] + atomicAdd(&a.bucket_fill[b], 1);
+            if (FLOOD_OOB(pos, a.rec_cap, &a.ctl->flags)) continue;
+            SampleRec r;
+            r.x = x;
+            r.y = y;
+            r.z = z;
+            r.lb = lb;
+            r.sigma = static_cast<int32_t>(w);
+            r.s = s;
+            r.u = u;
+            r.pad = 0;
+            a.recs[pos] = r;
         }
     }
     if (!SCATTER) {
@@ -1572,6 +1568,32 @@ int device_interior_table(int m, int k, const std::vector<uint8_t>& host, const 
     return FLOOD_OK;
 }
 
+// Barycentric coordinates of the interior grid, fl(c_j / m) in binary32 (the
+// rounding of sample_offset's division), uploaded once per (device, m, k).
+int device_lambda_table(int m, int k, const std::vector<uint8_t>& comp, const float** out) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, float*> cache;
+    int dev = 0;
+    FLOOD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    float*& p = cache[std::make_tuple(dev, m, k)];
+    if (!p) {
+        std::vector<float> lam(comp.size());
+        const volatile float fm = static_cast<float>(m);  // binary32 division, rounded to nearest
+        for (size_t i = 0; i < comp.size(); ++i) lam[i] = static_cast<float>(comp[i]) / fm;
+        float* q = nullptr;
+        FLOOD_CUDA(cudaMalloc(&q, sizeof(float) * std::max<size_t>(lam.size(), 1)));
+        const cudaError_t e = cudaMemcpy(q, lam.data(), sizeof(float) * lam.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(q);
+            return cuda_fail(e, "barycentric table upload");
+        }
+        p = q;
+    }
+    *out = p;
+    return FLOOD_OK;
+}
+
 
 }  // namespace flood
 
@@ -1618,6 +1640,7 @@ struct JobState {
     int64_t n_coarse, n_buckets, max_samples, max_n, max_groups;  // capacities
     std::vector<uint8_t> tables[4];
     const uint8_t* comp[4];
+    const float* lam[4];
     const float* w[4];
     float* vbound;
     // per dimension, carved from one region zeroed by a single memset
@@ -1726,6 +1749,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
         for (int k = 1; k <= 3; ++k) {
             J.I[k] = 0;
             J.comp[k] = nullptr;
+            J.lam[k] = nullptr;
             J.w[k] = nullptr;
             if (J.nk[k] == 0) continue;
             if (given) {
@@ -1738,7 +1762,9 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             J.max_samples = std::max(J.max_samples, J.nk[k] * J.I[k]);
             J.max_n = std::max(J.max_n, J.nk[k]);
             total_samples += J.nk[k] * J.I[k];
-            if (!given && J.I[k] > 0 && (rc = device_interior_table(J.in.m, k, J.tables[k], &J.comp[k]))) return rc;
+            if (!given && J.I[k] > 0 && ((rc = device_interior_table(J.in.m, k, J.tables[k], &J.comp[k])) ||
+                                         (rc = device_lambda_table(J.in.m, k, J.tables[k], &J.lam[k]))))
+                return rc;
         }
         const float div = lattice_divisions(total_samples);
         const int cap_axis = lattice_cap_axis(div);
@@ -1800,6 +1826,7 @@ int filtration_batch(const flood_filtration_job* in, int n_jobs, cudaStream_t s,
             a.val_lower = J.val[k - 1];
             a.n_lower = J.nk[k - 1];
             a.comp = J.comp[k];
+            a.lam = J.lam[k];
             a.w = J.w[k];
             a.L = J.in.L;
             a.vbound = J.vbound;
