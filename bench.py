@@ -41,8 +41,8 @@ FLOPS_PER_PAIR = 6               # one pair = 3 FMAs: |x'|^2 - 2 p'.x'
 # (k_flood_heavy and k_flood, dimensions 1-3: six launches), from one ncu
 # capture; valid only while the filtration source is the one captured, else
 # reported as null.
-FLOOD_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 153_769_728 + 159_744,
-                      "filtration_cu_sha256": "699cfef1827983228fabea1b501bd171d8622a440d836c2fe602ae2f886d4376"}
+FLOOD_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 153_827_584 + 206_592,
+                      "filtration_cu_sha256": "6aa9eb825f15b9a96d5a679d4271b9f911d86ccd16455b02d4408b00b72068dd"}
 
 
 def _source_sha(name: str):
