@@ -547,7 +547,8 @@ int flood_filtration_given_backward(const flood_grid* grid, const float* L, int3
  * (FIFO); it then runs FPS and the grid build on its own stream, is
  * triangulated on the host by the caller's callback, and joins the next
  * batched filtration (flood_filtration_batch) with every other cloud that is
- * ready at that moment. Requests arriving while others run are admitted as
+ * ready at that moment (two batch threads, each on its own stream, so one
+ * batch's host work overlaps another's kernels). Requests arriving while others run are admitted as
  * slots and memory free up, and their work overlaps on the device. Each
  * result equals what the one-cloud path computes on that cloud, bit for bit.
  * ------------------------------------------------------------------------ */

@@ -59,6 +59,8 @@ namespace flood {
 std::vector<uint8_t> interior_table(int m, int k);
 // Device copy of interior_table(m, k) (host: that table), cached per device.
 int device_interior_table(int m, int k, const std::vector<uint8_t>& host, const uint8_t** out);
+// Frees a grid in stream order on s (every use of it must be ordered before s).
+void grid_release_async(flood_grid* g, cudaStream_t s);
 
 // d(v, X) and its rounded-up bound (0 for a point of X) for every landmark;
 // src gets (v, 0). Defined with the filtration kernels.

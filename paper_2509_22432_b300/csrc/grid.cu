@@ -318,6 +318,23 @@ extern "C" int flood_grid_get_info(const flood_grid* g, flood_grid_info* out) {
     return FLOOD_OK;
 }
 
+namespace flood {
+// Release a grid in stream order (cudaFreeAsync on s): for callers that know
+// every use of the grid is ordered before s (the serving loop, whose streams
+// have completed the grid's work when a request finishes). Unlike
+// flood_grid_destroy it does not wait for the whole device.
+void grid_release_async(flood_grid* g, cudaStream_t s) {
+    if (!g) return;
+    if (g->pts) cudaFreeAsync(g->pts, s);
+    if (g->cell_start) cudaFreeAsync(g->cell_start, s);
+    if (g->occupied) cudaFreeAsync(g->occupied, s);
+    if (g->bdist) cudaFreeAsync(g->bdist, s);
+    if (g->geom) cudaFreeAsync(g->geom, s);
+    if (g->ready) cudaEventDestroy(g->ready);
+    free(g);
+}
+}  // namespace flood
+
 extern "C" void flood_grid_destroy(flood_grid* g) {
     if (!g) return;
     if (g->pts) cudaFree(g->pts);

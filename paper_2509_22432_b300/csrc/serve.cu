@@ -35,9 +35,12 @@
 #include "common.cuh"
 
 namespace flood {
+void grid_release_async(flood_grid* g, cudaStream_t s);  // grid.cu: stream-ordered release
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kFloodWorkers = 2;  // threads running batched filtrations
 
 struct Request {
     uint64_t ticket = 0;
@@ -127,9 +130,11 @@ void free_device(Request* r, cudaStream_t st) {
     if (r->L_dev) cudaFreeAsync(r->L_dev, st);
     r->X_dev = r->L_dev = r->key_dev = nullptr;
     r->idx_dev = nullptr;
-    cudaStreamSynchronize(st);
-    if (r->grid) flood_grid_destroy(r->grid);
+    // every use of the grid has completed (the stages wait for their streams);
+    // a stream-ordered release keeps the other workers' streams running
+    if (r->grid) grid_release_async(r->grid, st);
     r->grid = nullptr;
+    cudaStreamSynchronize(st);
 }
 
 // Mark a request finished (successfully or not) and admit queued ones.
@@ -393,7 +398,9 @@ extern "C" int flood_serve_create(const flood_serve_config* cfg, flood_server** 
     cudaGetDevice(&s->device);
     for (int i = 0; i < cfg->gpu_workers; ++i) s->threads.emplace_back(gpu_worker, s);
     for (int i = 0; i < cfg->triangulation_workers; ++i) s->threads.emplace_back(tri_worker, s);
-    s->threads.emplace_back(flood_worker, s);
+    // two batch threads on their own streams: one batch's host work and
+    // copies overlap the other's kernels
+    for (int i = 0; i < kFloodWorkers; ++i) s->threads.emplace_back(flood_worker, s);
     *out = s;
     return FLOOD_OK;
 }
