@@ -834,7 +834,7 @@ __device__ __forceinline__ void process_group(const DimArgs& a, const GridView& 
                 __syncwarp();
                 // two samples per packed FMA chain: the same three rounded
                 // FMAs per pair as the scalar form, in the same order
-#pragma unroll 2
+#pragma unroll 4
                 for (int j = gs; j < n; j += G) {
                     const float4 x = buf[j];
                     const float2 xx = make_float2(x.x, x.x), xy = make_float2(x.y, x.y), xz = make_float2(x.z, x.z),
