@@ -39,10 +39,12 @@ FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
 FLOPS_PER_PAIR = 6               # one pair = 3 FMAs: |x'|^2 - 2 p'.x'
 # DRAM bytes (read + write) of the flood kernels of one filtration on torus-1M
 # (k_flood_heavy and k_flood, dimensions 1-3: six launches), from one ncu
-# capture; valid only while the filtration source is the one captured, else
+# capture at the given launch parameters; valid only while the filtration
+# source is the one captured and the step runs at those parameters, else
 # reported as null.
-FLOOD_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 153_827_584 + 206_592,
-                      "filtration_cu_sha256": "6aa9eb825f15b9a96d5a679d4271b9f911d86ccd16455b02d4408b00b72068dd"}
+FLOOD_DRAM_CAPTURE = {"workload": "torus-1M", "bytes": 153_770_752 + 205_568,
+                      "cell_factor": 0.5, "heavy_shells": 9,
+                      "filtration_cu_sha256": "53db2d106bcc29a3664dc4dec60e438a221c5cda84e13873b12ec62fe1837d2e"}
 
 
 def _source_sha(name: str):
@@ -54,9 +56,11 @@ def _source_sha(name: str):
         return None
 
 
-def _flood_traffic(workload: str):
+def _flood_traffic(workload: str, tuned: dict):
     cap = FLOOD_DRAM_CAPTURE
     if cap["bytes"] is None or workload != cap["workload"]:
+        return None
+    if (tuned["cell_factor"], tuned["heavy_shells"]) != (cap["cell_factor"], cap["heavy_shells"]):
         return None
     if _source_sha("filtration.cu") != cap["filtration_cu_sha256"]:
         return None
@@ -782,8 +786,11 @@ def main():
                      "filtration": float(np.mean([e[2].elapsed_time(e[3]) for e in phase_events])),
                      "flood_kernels": fk},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": _flood_traffic(args.workload),
-                     "traffic_unit": "DRAM bytes of the six flood launches of one filtration (ncu)",
+                     "frac": achieved / peak_tflops, "traffic": _flood_traffic(args.workload, tuned),
+                     "traffic_unit": "DRAM bytes of the six flood launches of one filtration (ncu, at cell factor "
+                                     f"{FLOOD_DRAM_CAPTURE['cell_factor']:g} and heavy threshold "
+                                     f"{FLOOD_DRAM_CAPTURE['heavy_shells']}; null when the step runs at other "
+                                     "parameters or another filtration source)",
                      "kernel": "k_flood_heavy + k_flood (dimensions 1-3), the largest stage of the step",
                      "flops_per_pair": FLOPS_PER_PAIR,
                      "evaluated_pairs": pairs,
