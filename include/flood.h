@@ -691,7 +691,10 @@ int flood_tuning_clear(void);
  * binary32 squared distance with the d squares summed left to right and
  * every subtraction, product and sum rounded on its own (no fused
  * multiply-add), so picks are bit-exact against any implementation of that
- * arithmetic. dim = 3 runs flood_fps (the same key and picks).
+ * arithmetic. dim = 3 runs flood_fps (the same key and picks); dim = 2 runs
+ * flood_fps on the points at z = 0 (the extra key term is an exact 0, so the
+ * keys and picks are the two-dimensional ones bit for bit), with a scratch
+ * copy of 12 * n_points bytes from the stream-ordered pool.
  *   X          device, (n_points, dim) float32 row-major, finite
  *   dim        2..FLOOD_ND_MAX_DIM
  *   out_idx    device int64[n_landmarks]: the picks, out_idx[0] = start

@@ -1440,6 +1440,17 @@ int run_filtration_nd(const flood_grid_nd* grid, const float* L, int32_t n_L, co
 
 using namespace flood;
 
+namespace flood {
+// (n, 2) rows to (n, 3) rows at z = 0.
+__global__ void __launch_bounds__(256) k_plane_to_space(const float* X, int64_t n, float* X3) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    X3[3 * i + 0] = X[2 * i + 0];
+    X3[3 * i + 1] = X[2 * i + 1];
+    X3[3 * i + 2] = 0.0f;
+}
+}  // namespace flood
+
 extern "C" int flood_fps_nd(const float* X, int64_t n_points, int32_t dim, int32_t n_landmarks, int64_t start,
                             int64_t* out_idx, float* out_key, void* stream_) {
     if (!X || !out_idx || dim < 2 || dim > FLOOD_ND_MAX_DIM || n_points < 1 || n_points >= (int64_t(1) << 31) - 1 ||
@@ -1450,6 +1461,24 @@ extern "C" int flood_fps_nd(const float* X, int64_t n_points, int32_t dim, int32
     }
     // three coordinates: the three-dimensional FPS (same key, same picks; its chunk skipping is faster there)
     if (dim == 3) return flood_fps(X, n_points, n_landmarks, start, out_idx, out_key, stream_);
+    // two coordinates: the same, on the points at z = 0. The key gains the term
+    // fl(fl(0 - 0)^2) = 0 and adding 0 is exact, so every key, and every pick,
+    // is the two-dimensional one bit for bit.
+    if (dim == 2) {
+        cudaStream_t s = static_cast<cudaStream_t>(stream_);
+        if (int rc = pending_error(s)) return rc;
+        float* X3 = nullptr;
+        if (cudaMallocAsync(reinterpret_cast<void**>(&X3), sizeof(float) * 3 * size_t(n_points), s) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("flood_fps_nd: device allocation failed");
+            return FLOOD_ENOMEM;
+        }
+        k_plane_to_space<<<static_cast<unsigned>((n_points + 255) / 256), 256, 0, s>>>(X, n_points, X3);
+        note_launch();
+        const int rc = flood_fps(X3, n_points, n_landmarks, start, out_idx, out_key, stream_);
+        cudaFreeAsync(X3, s);  // after the FPS kernels in stream order
+        return rc;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
     if (int rc = pending_error(s)) return rc;
     Scratch scr(s);
