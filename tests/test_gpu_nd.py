@@ -94,6 +94,41 @@ def test_fps_nd_ties_duplicates_and_errors():
     assert np.array_equal(idx.cpu().numpy(), ref_i[:4])
 
 
+def test_fps_nd_two_coordinates_through_the_three_dimensional_kernel():
+    """d = 2 runs the 3-D FPS on the points at z = 0: ties, duplicates, one pick, one point,
+    running out of distinct points, non-finite input and a cloud over many blocks, against the
+    oracle's two-dimensional picks."""
+    ops = _ops()
+    # a 5 x 5 lattice, each point twice: many-way exact ties, lowest index wins
+    g = np.array([[i, j] for i in range(5) for j in range(5)], dtype=np.float32)
+    X = np.concatenate([g, g])
+    idx, key = ops.fps_nd(torch.from_numpy(X).cuda(), 25, 3)
+    ref_i, ref_k = oracle.fps(X, 25, 3)
+    assert np.array_equal(idx.cpu().numpy(), ref_i) and np.array_equal(key.cpu().numpy(), ref_k)
+    idx, key = ops.fps_nd(torch.from_numpy(X).cuda(), 1, 7)     # the start alone
+    assert idx.cpu().numpy().tolist() == [7] and np.isinf(key.cpu().numpy()[0])
+    one = np.array([[0.25, -1.5]], dtype=np.float32)             # a single point
+    idx, _ = ops.fps_nd(torch.from_numpy(one).cuda(), 1, 0)
+    assert idx.cpu().numpy().tolist() == [0]
+    with pytest.raises(FloodError) as e:
+        ops.fps_nd(torch.from_numpy(X).cuda(), 26, 0)           # only 25 distinct points
+    assert e.value.name == "FLOOD_EDEGENERATE"
+    bad = X.copy()
+    bad[11, 1] = np.nan
+    with pytest.raises(FloodError) as e:
+        ops.fps_nd(torch.from_numpy(bad).cuda(), 4, 0)
+    assert e.value.name == "FLOOD_EINVAL"
+    with pytest.raises(FloodError) as e:
+        ops.fps_nd(torch.from_numpy(X).cuda(), 4, 50)          # start out of range
+    assert e.value.name == "FLOOD_EINVAL"
+    # many blocks (points on chip across the grid-wide exchange)
+    Y = data.swisscheese_cloud(200_000, seed=31, dim=2)
+    idx, key = ops.fps_nd(torch.from_numpy(Y).cuda(), 500, 9)
+    ref_i, ref_k = oracle.fps(Y, 500, 9)
+    assert np.array_equal(idx.cpu().numpy(), ref_i)
+    assert np.array_equal(key.cpu().numpy().view(np.uint32), ref_k.astype(np.float32).view(np.uint32))
+
+
 # ---------------------------------------------------------------- flood values
 def _case(d, n, n_l, seed):
     X = data.swisscheese_cloud(n, seed=seed, dim=d)
