@@ -23,7 +23,7 @@ import numpy as np
 from . import _lib
 
 __all__ = ["Entry", "cache_path", "lookup", "set_entry", "entries", "clear", "load", "save", "bucket",
-           "tune_workload", "tune_cloud"]
+           "choose", "tune_workload", "tune_cloud"]
 
 CELL_FACTORS = (0.35, 0.5, 0.7, 1.0)
 HEAVY_SHELLS = (7, 8, 9, 10, 12)
@@ -96,6 +96,17 @@ def save(path: str | None = None) -> str:
     return path
 
 
+def choose(timings: dict):
+    """The tuned pair from {(cell factor, heavy threshold): ms}: the fastest, except that the
+    defaults stay when they were measured and are within KEEP_DEFAULTS_WITHIN of it.
+    Returns ((cell factor, heavy threshold), ms)."""
+    best, ms = min(timings.items(), key=lambda kv: kv[1])
+    d_ms = timings.get(DEFAULTS)
+    if d_ms is not None and d_ms <= ms * (1.0 + KEEP_DEFAULTS_WITHIN):
+        return DEFAULTS, d_ms
+    return best, ms
+
+
 def tune_workload(X, L, cx, m: int, cover: float, cell_factors=CELL_FACTORS, heavy_shells=HEAVY_SHELLS,
                   reps: int = 3) -> dict:
     """Measure grid build + filtration for every (cell factor, heavy threshold) pair on one workload.
@@ -129,10 +140,8 @@ def tune_workload(X, L, cx, m: int, cover: float, cell_factors=CELL_FACTORS, hea
                 grid.close()
                 best = min(best, a.elapsed_time(b))
             timings[(cf, hs)] = best
-    (cf, hs), ms = min(timings.items(), key=lambda kv: kv[1])
+    (cf, hs), ms = choose(timings)
     d_ms = timings.get(DEFAULTS)
-    if d_ms is not None and d_ms <= ms * (1.0 + KEEP_DEFAULTS_WITHIN):
-        (cf, hs), ms = DEFAULTS, d_ms
     set_entry(key, cf, hs)
     return {"bucket": key, "cell_factor": cf, "heavy_shells": hs, "ms": ms,
             "default_ms": d_ms, "timings_ms": {f"{a:g}/{b}": t for (a, b), t in timings.items()}}

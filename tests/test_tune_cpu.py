@@ -68,3 +68,18 @@ def test_bad_entries_and_files_are_rejected(tmp_path):
     assert len(tune.entries()) == 1                      # the line before the bad one stays
     with pytest.raises(FloodError):
         tune.load(str(tmp_path / "missing.txt"))
+
+
+def test_choice_keeps_the_defaults_unless_a_candidate_is_clearly_faster():
+    from paper_2509_22432_b300 import tune
+    d = tune.DEFAULTS
+    # a near-tie (0.16 %): the defaults stay
+    assert tune.choose({(0.7, 7): 1.6367, d: 1.6393, (1.0, 12): 2.0}) == (d, 1.6393)
+    # clearly faster (10 %): the candidate wins
+    assert tune.choose({(0.7, 10): 1.80, d: 2.00}) == ((0.7, 10), 1.80)
+    # just past the margin
+    assert tune.choose({(0.35, 8): 1.0, d: 1.0 * (1.0 + tune.KEEP_DEFAULTS_WITHIN) * 1.001}) == ((0.35, 8), 1.0)
+    # defaults not measured: the fastest
+    assert tune.choose({(0.35, 6): 3.0, (1.0, 12): 2.5}) == ((1.0, 12), 2.5)
+    # defaults fastest
+    assert tune.choose({(0.35, 6): 3.0, d: 2.0}) == (d, 2.0)
