@@ -808,6 +808,10 @@ def main():
                          "per_round_us": round_us, "per_pick_us": pick_us, "late_per_pick_us": late_us,
                          "floor_per_round_us": floor_round_us, "floor_per_pick_us": floor_pick_us,
                          "floor_rounds": floor_st["rounds"],
+                         "picks_per_round": (n_l - 1) / rounds,
+                         "floor_picks_per_round": (n_floor - 1) / max(1, floor_st["rounds"]),
+                         "floor_note": "per pick the floor is a floor; per round it need not be (its rounds "
+                                       "can make more picks, each costing selection time)",
                          "floor_is": f"the same kernel and launch width ({fst['blocks']} blocks) on a cloud of one "
                                     f"256-point chunk per block, {n_floor} picks: the grid exchange and pick "
                                     "selection with almost no chunk work",
