@@ -647,9 +647,12 @@ def main():
 
     # ---- end to end through the public API with host buffers
     Xh = torch.from_numpy(X).pin_memory()
-    simp_h = [t.cpu().pin_memory() for t in dcx.simplices]
-    fac_h = [t.cpu().pin_memory() for t in dcx.facets]
-    h2d = Xh.numel() * 4 + sum(t.numel() * 4 for t in simp_h + fac_h)
+    # the complex's int32 arrays packed in one pinned buffer: one upload per step, device views
+    cx_parts = [t.cpu() for t in dcx.simplices] + [t.cpu() for t in dcx.facets]
+    cx_h = torch.cat([t.reshape(-1) for t in cx_parts]).pin_memory()
+    cx_offs = np.concatenate([[0], np.cumsum([t.numel() for t in cx_parts])]).tolist()
+    n_simp_parts = len(dcx.simplices)
+    h2d = Xh.numel() * 4 + cx_h.numel() * 4
     d2h = n_l * 8 + sum(cx.counts) * 4
     e2e_times = []
     idx_out = torch.empty(n_l, dtype=torch.int64).pin_memory()
@@ -662,8 +665,9 @@ def main():
         idx, key = ops.fps(Xg, n_l, 0, sync=False)
         idx_out.copy_(idx, non_blocking=True)  # the landmarks go to the host (the triangulation's input)
         stream.synchronize()
-        dc = ops.DeviceComplex(cx.n_vertices, [t.to(dev, non_blocking=True) for t in simp_h],
-                               [t.to(dev, non_blocking=True) for t in fac_h])
+        cx_d = cx_h.to(dev, non_blocking=True)
+        views = [cx_d[cx_offs[i]:cx_offs[i + 1]].view(cx_parts[i].shape) for i in range(len(cx_parts))]
+        dc = ops.DeviceComplex(cx.n_vertices, views[:n_simp_parts], views[n_simp_parts:])
         grid = ops.build_grid(Xg, cell, sync=False)
         vals, _ = ops.filtration(grid, ops.gather_rows(Xg, idx, sync=False), dc, m, want_src=False, sync=False)
         off = 0
@@ -675,6 +679,14 @@ def main():
             e2e_times.append(time.perf_counter() - t0)
         grid.close()
     e2e_s = float(np.mean(e2e_times))
+    # the last end-to-end step's results equal the resident-input step's, bit for bit
+    grid_r = ops.build_grid(Xd, cell)
+    vals_r, _ = ops.filtration(grid_r, Xd[idx0], dcx, m, want_src=False)
+    grid_r.close()
+    e2e_exact = bool(torch.equal(idx_out, idx0.cpu()) and
+                     torch.equal(val_out.view(torch.int32), torch.cat([v.cpu() for v in vals_r]).view(torch.int32)))
+    if not e2e_exact:
+        raise RuntimeError("end-to-end step results differ from the resident-input step")
 
     # ---- the same step with uniform random point sets P_sigma (§4.1, Lemma 4)
     # in place of the grid: as many points per simplex as the grid's interior
@@ -817,7 +829,8 @@ def main():
                                     "selection with almost no chunk work",
                          "frac": floor_pick_us / pick_us,
                          "frac_is": "floor per pick / this workload's per pick"},
-        "e2e": {"value": world * n_simp / e2e_s, "unit": "simplices/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": world * n_simp / e2e_s, "unit": "simplices/s", "results_equal_resident_step": e2e_exact,
+                "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
